@@ -1,0 +1,154 @@
+/*
+ * nk.h -- C ABI of libnk: convolutional (Myrtle) and fully-connected NNGP
+ * kernel blocks and the kernel-ridge PCG solve, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Adlam et al., "Kernel Regression with Infinite-Width Neural Networks
+ * on Millions of Examples" (arXiv 2303.05420).  The paper gives its kernels as
+ * Neural Tangents architecture listings (Appendix A) and computes the kernel
+ * matrix as independent blocks of its upper triangle (Figure 1, top); it
+ * solves (K + lambda I) A = Y by preconditioned conjugate gradients with one
+ * CG per target column (Section 2 "Iterative solvers"; Appendix B.3).
+ *
+ * Conventions for every call
+ *   - Pointers named X*, q*, K, Y, A, dK, dX* are DEVICE pointers owned by the
+ *     caller; the library never frees them.  `iters` / `relres` outputs of
+ *     nk_pcg_solve are HOST pointers.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     nk_self_diag, nk_block and nk_block_backward are stream-ordered and
+ *     asynchronous; nk_pcg_solve synchronises the stream before returning.
+ *   - Invalid arguments return NK_ERR_INVALID_ARG synchronously, before any
+ *     work is enqueued.  CUDA errors return NK_ERR_CUDA.  Errors that the
+ *     kernels detect on the device (q <= 0 or NaN feeding a ReLU map, a spin
+ *     limit) are recorded in a device status word of the handle and reported by
+ *     nk_sync_status, which synchronises the stream.
+ *   - nk_last_error gives a one-line description of the last failure.
+ *   - Images are NHWC float32: X[n][H][W][C], contiguous.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef NK_H
+#define NK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NK_OK = 0,
+  NK_ERR_INVALID_ARG = 1,
+  NK_ERR_CUDA = 2,
+  NK_ERR_NUMERICAL = 3,     /* q <= 0 / NaN met by a ReLU map on the device */
+  NK_ERR_NOT_CONVERGED = 4, /* PCG hit maxit; A holds the best iterate */
+  NK_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+  NK_ERR_NO_MEMORY = 6,
+  NK_ERR_UNSUPPORTED = 7    /* valid request that this build does not implement */
+} nk_status;
+
+/* Arithmetic of nk_block:
+ *  NK_PREC_MIXED      fused single-launch path: FP64 self-variances, FP32
+ *                     pixel-pair recursion held on chip, FP64 final combine;
+ *                     K is float*.
+ *  NK_PREC_PLAIN_FP32 layer-wise path, one launch per layer, pixel-pair
+ *                     tensors in HBM, FP32; K is float*.
+ *  NK_PREC_PLAIN_FP64 the same in FP64; K is double*. */
+typedef enum { NK_PREC_PLAIN_FP64 = 0, NK_PREC_PLAIN_FP32 = 1, NK_PREC_MIXED = 2 } nk_prec;
+
+enum { NK_ACT_RELU = 0, NK_ACT_IDENTITY = 1 /* linear network, tests only */ };
+enum { NK_PRECOND_NONE = 0, NK_PRECOND_JACOBI = 1 };
+
+/* Myrtle-family architecture (Appendix A, Myrtle listing): n_stages stages;
+ * stage s holds convs[s] layers of conv(filter x filter, SAME) + activation;
+ * a 2x2 stride-2 average pool sits between consecutive stages; the last
+ * stage ends in a global average pool and a Dense readout.
+ * Myrtle-10 = {3, {3,3,3}}; the Myrtle-5 of the benchmark = {3, {2,1,0}}. */
+typedef struct {
+  int n_stages;   /* 1..4 */
+  int convs[4];   /* convs[0] >= 1 */
+  int filter;     /* 3 (paper) or 1 */
+  int activation; /* NK_ACT_RELU or NK_ACT_IDENTITY */
+} nk_arch;
+
+/* sigma_w^2 = W_std^2 and sigma_b^2 = b_std^2 of every Conv / Dense layer
+ * (Appendix A listings use W_std = sqrt(2), b_std = 0.1). */
+typedef struct {
+  double sigma_w2;
+  double sigma_b2;
+} nk_params;
+
+typedef struct nk_handle nk_handle;
+
+nk_status nk_create(nk_handle** h);
+void nk_destroy(nk_handle* h);
+const char* nk_status_string(nk_status s);
+/* Copies the description of the last failure on this handle into buf. */
+nk_status nk_last_error(nk_handle* h, char* buf, size_t len);
+/* Synchronises `stream`, then reads and clears the handle's device status
+ * word: NK_OK, NK_ERR_NUMERICAL or NK_ERR_TIMEOUT. */
+nk_status nk_sync_status(nk_handle* h, void* stream);
+
+/* Number of per-image self-variance entries: the sum over activation layers
+ * l of H_l * W_l (H_l, W_l the resolution of layer l's stage).  Returns -1 for
+ * an invalid architecture or size. */
+int64_t nk_q_size(const nk_arch* arch, int H, int W);
+
+/* Per-pixel self-variances q_l(p) = K_l(p, p; x, x) for every image and every
+ * activation layer (needed by the ReLU map, stax.Relu in Appendix A).
+ *   X   [n][H][W][C] float32 (device)
+ *   qd  [n][nq] float64 (device, out): q, layer-major then row-major pixels
+ *   qs  [n][nq][2] float32 (device, out, may be NULL): (1/sqrt(q), sqrt(q)),
+ *       (0, 0) where q == 0
+ * with nq = nk_q_size(arch, H, W).  Computed in FP64 from the banded self
+ * covariance K_l(p, p + D; x, x), |D| <= r_s per stage (r = 0 at the last
+ * stage with an activation, r_prev = 2 r + 1 across each pool). */
+nk_status nk_self_diag(nk_handle* h, const nk_arch* arch, const nk_params* prm,
+                       const float* X, int64_t n, int H, int W, int C,
+                       double* qd, float* qs, void* stream);
+
+/* Kernel block K[i - a0][j - b0] = NNGP(Xa[i], Xb[j]) for i in [a0, a1),
+ * j in [b0, b1) (Figure 1, top: blocks of the kernel matrix are computed
+ * independently).
+ *   Xa, Xb      image sets [na][H][W][C], [nb][H][W][C] float32 (device)
+ *   qda, qdb    their nk_self_diag FP64 outputs (used by PLAIN_FP64)
+ *   qsa, qsb    their nk_self_diag FP32 (1/sqrt q, sqrt q) outputs (used by
+ *               MIXED and PLAIN_FP32)
+ *   K, ldk      output, row-major, leading dimension ldk >= b1 - b0;
+ *               float* for MIXED / PLAIN_FP32, double* for PLAIN_FP64
+ *   symmetric   nonzero when Xa == Xb and [a0,a1) == [b0,b1): only i <= j is
+ *               evaluated and mirrored.
+ * The Myrtle readout is K = sigma_w2 * mean_{P,P'} Kt(P, P') + sigma_b2
+ * (GlobalAvgPool then Dense).  MIXED requires filter 3, ReLU, H = W in
+ * {8, 16, 32}, C <= 4 and zero-conv stages only at the end; other valid
+ * requests there return NK_ERR_UNSUPPORTED. */
+nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_prec prec,
+                   const float* Xa, const double* qda, const float* qsa, int64_t a0, int64_t a1,
+                   const float* Xb, const double* qdb, const float* qsb, int64_t b0, int64_t b1,
+                   int H, int W, int C, void* K, int64_t ldk, int symmetric, void* stream);
+
+/* Kernel-ridge solve (K + lambda I) A = Y by Jacobi-preconditioned CG, one CG
+ * per column run in lock-step (Section 2 "Iterative solvers"; Appendix B.3).
+ *   K [N][ldk] float32 (device, symmetric), Y [N][R] float64 (device, row
+ *   major), A [N][R] float64 (device, out).
+ *   prec = NK_PREC_MIXED: FP32 K@P inner solves with FP64 CG scalars, inside
+ *          an FP64 iterative-refinement loop whose true residual
+ *          Y - (K + lambda I) A is accumulated in FP64 (at most refine_max
+ *          outer steps);
+ *   prec = NK_PREC_PLAIN_FP32: FP32 K@P, FP64 scalars, no refinement;
+ *   prec = NK_PREC_PLAIN_FP64: every product in FP64.
+ *   tol     stop when every column has ||r_j|| / ||y_j|| <= tol, r the true
+ *           residual against the float32 K upcast to FP64;
+ *   maxit   bound on the total number of CG iterations;
+ *   iters   (host, out) CG iterations performed (max over columns);
+ *   relres  (host, out, may be NULL) [R] final true relative residuals.
+ * Returns NK_ERR_NOT_CONVERGED (A = best iterate) when maxit is reached.
+ * Synchronises `stream`. */
+nk_status nk_pcg_solve(nk_handle* h, const float* K, int64_t ldk, int64_t N,
+                       const double* Y, int R, double lambda, int precond, nk_prec prec,
+                       double tol, int maxit, int refine_max,
+                       double* A, int* iters, double* relres, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NK_H */

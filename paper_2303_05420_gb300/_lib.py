@@ -1,0 +1,93 @@
+"""ctypes binding of libnk.so (the C ABI declared in include/nk.h).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  Importing this module does not load the library;
+``lib()`` does, and raises if ``libnk.so`` has not been built.  There is no
+CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int, c_int64, c_size_t, c_void_p
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnk.so")
+
+NK_OK, NK_ERR_INVALID_ARG, NK_ERR_CUDA, NK_ERR_NUMERICAL = 0, 1, 2, 3
+NK_ERR_NOT_CONVERGED, NK_ERR_TIMEOUT, NK_ERR_NO_MEMORY, NK_ERR_UNSUPPORTED = 4, 5, 6, 7
+PREC = {"plain_fp64": 0, "plain_fp32": 1, "mixed": 2}
+ACT = {"relu": 0, "identity": 1}
+PRECOND = {"none": 0, "jacobi": 1}
+
+# Every symbol include/nk.h declares (checked by a CPU test).
+EXPORTS = ["nk_create", "nk_destroy", "nk_status_string", "nk_last_error", "nk_sync_status",
+           "nk_q_size", "nk_self_diag", "nk_block", "nk_pcg_solve"]
+
+
+class NkArch(ctypes.Structure):
+    _fields_ = [("n_stages", c_int), ("convs", c_int * 4), ("filter", c_int), ("activation", c_int)]
+
+
+class NkParams(ctypes.Structure):
+    _fields_ = [("sigma_w2", c_double), ("sigma_b2", c_double)]
+
+
+class NkError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libnk status {status}: {msg}")
+        self.status = status
+
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    L.nk_create.argtypes = [POINTER(c_void_p)]
+    L.nk_create.restype = c_int
+    L.nk_destroy.argtypes = [c_void_p]
+    L.nk_destroy.restype = None
+    L.nk_status_string.argtypes = [c_int]
+    L.nk_status_string.restype = c_char_p
+    L.nk_last_error.argtypes = [c_void_p, c_char_p, c_size_t]
+    L.nk_last_error.restype = c_int
+    L.nk_sync_status.argtypes = [c_void_p, c_void_p]
+    L.nk_sync_status.restype = c_int
+    L.nk_q_size.argtypes = [POINTER(NkArch), c_int, c_int]
+    L.nk_q_size.restype = c_int64
+    L.nk_self_diag.argtypes = [c_void_p, POINTER(NkArch), POINTER(NkParams), c_void_p, c_int64, c_int,
+                               c_int, c_int, c_void_p, c_void_p, c_void_p]
+    L.nk_self_diag.restype = c_int
+    L.nk_block.argtypes = [c_void_p, POINTER(NkArch), POINTER(NkParams), c_int,
+                           c_void_p, c_void_p, c_void_p, c_int64, c_int64,
+                           c_void_p, c_void_p, c_void_p, c_int64, c_int64,
+                           c_int, c_int, c_int, c_void_p, c_int64, c_int, c_void_p]
+    L.nk_block.restype = c_int
+    L.nk_pcg_solve.argtypes = [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_int, c_double, c_int,
+                               c_int, c_double, c_int, c_int, c_void_p, POINTER(c_int),
+                               c_void_p, c_void_p]
+    L.nk_pcg_solve.restype = c_int
+    _LIB = L
+    return L
+
+
+def make_arch(convs, filt: int = 3, act: str = "relu") -> NkArch:
+    a = NkArch()
+    a.n_stages = len(convs)
+    for i in range(4):
+        a.convs[i] = convs[i] if i < len(convs) else 0
+    a.filter = filt
+    a.activation = ACT[act]
+    return a
+
+
+def make_params(sw2: float, sb2: float) -> NkParams:
+    return NkParams(float(sw2), float(sb2))

@@ -1,0 +1,132 @@
+"""Python API over libnk: torch tensors in, torch tensors out.
+
+PyTorch supplies device memory and the current CUDA stream; the computation
+is libnk's.  Names follow the C ABI (include/nk.h): ``self_diag``, ``block``,
+``pcg_solve``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+from ctypes import byref, c_int, c_void_p
+from typing import Optional, Sequence, Tuple
+
+import torch
+
+from . import _lib
+from ._lib import NkError, lib, make_arch, make_params
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Handle:
+    """Owns an nk_handle (workspace, device status word)."""
+
+    def __init__(self):
+        self._h = c_void_p()
+        st = lib().nk_create(byref(self._h))
+        if st != 0:
+            raise NkError(st, lib().nk_status_string(st).decode())
+
+    def close(self):
+        if self._h:
+            lib().nk_destroy(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, st: int, what: str):
+        if st != 0:
+            buf = ctypes.create_string_buffer(512)
+            lib().nk_last_error(self._h, buf, 512)
+            raise NkError(st, f"{what}: {buf.value.decode()}")
+
+    def sync_status(self):
+        self.check(lib().nk_sync_status(self._h, c_void_p(_stream())), "nk_sync_status")
+
+    # ------------------------------------------------------------------
+    def q_size(self, convs: Sequence[int], H: int, W: int, filt: int = 3) -> int:
+        a = make_arch(convs, filt)
+        return int(lib().nk_q_size(byref(a), H, W))
+
+    def self_diag(self, X: torch.Tensor, convs: Sequence[int], sw2: float, sb2: float,
+                  filt: int = 3, act: str = "relu") -> Tuple[torch.Tensor, torch.Tensor]:
+        """X [n, H, W, C] float32 CUDA -> (qd [n, nq] float64, qs [n, nq, 2] float32)."""
+        assert X.is_cuda and X.dtype == torch.float32 and X.is_contiguous()
+        n, H, W, C = X.shape
+        a = make_arch(convs, filt, act)
+        p = make_params(sw2, sb2)
+        nq = int(lib().nk_q_size(byref(a), H, W))
+        if nq < 0:
+            raise NkError(_lib.NK_ERR_INVALID_ARG, "invalid architecture / size")
+        qd = torch.empty((n, nq), dtype=torch.float64, device=X.device)
+        qs = torch.empty((n, nq, 2), dtype=torch.float32, device=X.device)
+        st = lib().nk_self_diag(self._h, byref(a), byref(p), c_void_p(_ptr(X)), n, H, W, C,
+                                c_void_p(_ptr(qd)), c_void_p(_ptr(qs)), c_void_p(_stream()))
+        self.check(st, "nk_self_diag")
+        return qd, qs
+
+    def block(self, Xa: torch.Tensor, qa: Tuple[torch.Tensor, torch.Tensor], Xb: torch.Tensor,
+              qb: Tuple[torch.Tensor, torch.Tensor], convs: Sequence[int], sw2: float, sb2: float,
+              prec: str = "mixed", a_range=None, b_range=None, symmetric: bool = False,
+              out: Optional[torch.Tensor] = None, filt: int = 3, act: str = "relu") -> torch.Tensor:
+        """K[i - a0, j - b0] = NNGP(Xa[i], Xb[j]) over the given index ranges."""
+        assert Xa.is_cuda and Xb.is_cuda and Xa.dtype == torch.float32 and Xb.dtype == torch.float32
+        _, H, W, C = Xa.shape
+        a0, a1 = a_range if a_range is not None else (0, Xa.shape[0])
+        b0, b1 = b_range if b_range is not None else (0, Xb.shape[0])
+        dt = torch.float64 if prec == "plain_fp64" else torch.float32
+        if out is None:
+            out = torch.empty((a1 - a0, b1 - b0), dtype=dt, device=Xa.device)
+        assert out.dtype == dt and out.stride(1) == 1
+        a = make_arch(convs, filt, act)
+        p = make_params(sw2, sb2)
+        st = lib().nk_block(self._h, byref(a), byref(p), _lib.PREC[prec],
+                            c_void_p(_ptr(Xa)), c_void_p(_ptr(qa[0])), c_void_p(_ptr(qa[1])), a0, a1,
+                            c_void_p(_ptr(Xb)), c_void_p(_ptr(qb[0])), c_void_p(_ptr(qb[1])), b0, b1,
+                            H, W, C, c_void_p(_ptr(out)), out.stride(0), int(symmetric),
+                            c_void_p(_stream()))
+        self.check(st, "nk_block")
+        return out
+
+    def pcg_solve(self, K: torch.Tensor, Y: torch.Tensor, lam: float, precond: str = "jacobi",
+                  prec: str = "mixed", tol: float = 1e-6, maxit: int = 10000, refine_max: int = 8,
+                  A: Optional[torch.Tensor] = None, allow_not_converged: bool = False):
+        """Solve (K + lam I) A = Y.  K [N, N] float32, Y [N, R] float64 (CUDA).
+        Returns (A, iters, relres[R])."""
+        assert K.dtype == torch.float32 and K.stride(1) == 1
+        assert Y.dtype == torch.float64 and Y.is_contiguous()
+        N, R = Y.shape
+        if A is None:
+            A = torch.empty_like(Y)
+        its = c_int(0)
+        rel = (ctypes.c_double * max(R, 1))()
+        st = lib().nk_pcg_solve(self._h, c_void_p(_ptr(K)), K.stride(0), N, c_void_p(_ptr(Y)), R,
+                                float(lam), _lib.PRECOND[precond], _lib.PREC[prec], float(tol), int(maxit),
+                                int(refine_max), c_void_p(_ptr(A)), byref(its),
+                                ctypes.cast(rel, c_void_p), c_void_p(_stream()))
+        if st == _lib.NK_ERR_NOT_CONVERGED and allow_not_converged:
+            pass
+        else:
+            self.check(st, "nk_pcg_solve")
+        return A, its.value, [rel[i] for i in range(R)]
+
+
+_DEFAULT: Optional[Handle] = None
+
+
+def default_handle() -> Handle:
+    global _DEFAULT
+    if _DEFAULT is None:
+        _DEFAULT = Handle()
+    return _DEFAULT

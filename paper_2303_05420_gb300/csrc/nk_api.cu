@@ -1,0 +1,256 @@
+// libnk C ABI: handle, argument validation and dispatch (declared in nk.h).
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "nk_common.cuh"
+
+nk_status nk_pcg_impl(nk_handle* h, const float* K, int64_t ldk, int64_t N, const double* Y, int R,
+                      double lam, int precond, nk_prec prec, double tol, int maxit, int refine_max,
+                      double* A, int* iters, double* relres, cudaStream_t st);
+
+nk_status nk_fail(nk_handle* h, nk_status s, const char* fmt, ...) {
+  if (h) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(h->err, sizeof(h->err), fmt, ap);
+    va_end(ap);
+  }
+  return s;
+}
+
+nk_status nk_cuda_check(nk_handle* h, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return NK_OK;
+  if (e == cudaErrorMemoryAllocation) {
+    (void)cudaGetLastError();
+    return nk_fail(h, NK_ERR_NO_MEMORY, "%s: %s", what, cudaGetErrorString(e));
+  }
+  return nk_fail(h, NK_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+nk_status nk_workspace(nk_handle* h, size_t bytes, void** out) {
+  if (bytes > h->ws_bytes) {
+    if (h->ws) cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+    cudaError_t e = cudaMalloc(&h->ws, bytes);
+    if (e != cudaSuccess) return nk_cuda_check(h, e, "workspace allocation");
+    h->ws_bytes = bytes;
+  }
+  *out = h->ws;
+  return NK_OK;
+}
+
+bool nk_make_geom(const nk_arch* arch, int H, int W, int C, NkGeom* g, const char** why) {
+  memset(g, 0, sizeof(*g));
+  if (!arch) { *why = "arch is NULL"; return false; }
+  if (arch->n_stages < 1 || arch->n_stages > NK_MAX_STAGES) { *why = "n_stages outside 1..4"; return false; }
+  if (arch->filter != 1 && arch->filter != 3) { *why = "filter must be 1 or 3"; return false; }
+  if (arch->activation != NK_ACT_RELU && arch->activation != NK_ACT_IDENTITY) {
+    *why = "unknown activation";
+    return false;
+  }
+  if (arch->convs[0] < 1) { *why = "the first stage needs at least one conv"; return false; }
+  if (H < 1 || W < 1 || C < 1) { *why = "H, W and C must be positive"; return false; }
+  g->n_stages = arch->n_stages;
+  g->filter = arch->filter;
+  g->act = arch->activation;
+  g->C = C;
+  int h = H, w = W, nl = 0, off = 0;
+  g->last_act_stage = -1;
+  for (int s = 0; s < g->n_stages; ++s) {
+    if (arch->convs[s] < 0) { *why = "negative conv count"; return false; }
+    if (s > 0) {
+      if ((h & 1) || (w & 1)) { *why = "2x2 pooling of an odd-sized image"; return false; }
+      h /= 2;
+      w /= 2;
+    }
+    g->convs[s] = arch->convs[s];
+    g->Hs[s] = h;
+    g->Ws[s] = w;
+    for (int k = 0; k < arch->convs[s]; ++k) {
+      if (nl >= NK_MAX_LAYERS) { *why = "too many layers"; return false; }
+      g->layer_stage[nl] = s;
+      g->layer_qoff[nl] = off;
+      off += h * w;
+      ++nl;
+    }
+    if (arch->convs[s] > 0) g->last_act_stage = s;
+  }
+  g->n_layers = nl;
+  g->nq = off;
+  g->gap_stage = g->n_stages - 1;
+  int r = 0;
+  for (int s = g->last_act_stage; s >= 0; --s) {
+    g->radius[s] = r;
+    r = 2 * r + 1;
+  }
+  return true;
+}
+
+extern "C" {
+
+const char* nk_status_string(nk_status s) {
+  switch (s) {
+    case NK_OK: return "ok";
+    case NK_ERR_INVALID_ARG: return "invalid argument";
+    case NK_ERR_CUDA: return "CUDA error";
+    case NK_ERR_NUMERICAL: return "numerical error (q <= 0 or NaN)";
+    case NK_ERR_NOT_CONVERGED: return "not converged";
+    case NK_ERR_TIMEOUT: return "device wait timed out";
+    case NK_ERR_NO_MEMORY: return "out of device memory";
+    case NK_ERR_UNSUPPORTED: return "unsupported by this build";
+  }
+  return "unknown status";
+}
+
+nk_status nk_create(nk_handle** out) {
+  if (!out) return NK_ERR_INVALID_ARG;
+  *out = nullptr;
+  nk_handle* h = new nk_handle();
+  memset(h, 0, sizeof(*h));
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess) e = cudaMalloc(&h->dstatus, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(h->dstatus, 0, sizeof(unsigned int));
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    if (h->dstatus) cudaFree(h->dstatus);
+    delete h;
+    return e == cudaErrorMemoryAllocation ? NK_ERR_NO_MEMORY : NK_ERR_CUDA;
+  }
+  *out = h;
+  return NK_OK;
+}
+
+void nk_destroy(nk_handle* h) {
+  if (!h) return;
+  if (h->ws) cudaFree(h->ws);
+  if (h->pcg_ws) cudaFree(h->pcg_ws);
+  if (h->dstatus) cudaFree(h->dstatus);
+  delete h;
+}
+
+nk_status nk_last_error(nk_handle* h, char* buf, size_t len) {
+  if (!h || !buf || len == 0) return NK_ERR_INVALID_ARG;
+  snprintf(buf, len, "%s", h->err);
+  return NK_OK;
+}
+
+nk_status nk_sync_status(nk_handle* h, void* stream) {
+  if (!h) return NK_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned int v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, h->dstatus, sizeof(v), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->dstatus, 0, sizeof(unsigned int), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return nk_cuda_check(h, e, "nk_sync_status");
+  if (v & NK_DEV_TIMEOUT) return nk_fail(h, NK_ERR_TIMEOUT, "a device wait gave up");
+  if (v & NK_DEV_NUMERICAL) return nk_fail(h, NK_ERR_NUMERICAL, "q <= 0 or NaN met by a ReLU map");
+  return NK_OK;
+}
+
+int64_t nk_q_size(const nk_arch* arch, int H, int W) {
+  NkGeom g;
+  const char* why = nullptr;
+  if (!nk_make_geom(arch, H, W, 1, &g, &why)) return -1;
+  return g.nq;
+}
+
+nk_status nk_self_diag(nk_handle* h, const nk_arch* arch, const nk_params* prm, const float* X,
+                       int64_t n, int H, int W, int C, double* qd, float* qs, void* stream) {
+  if (!h) return NK_ERR_INVALID_ARG;
+  NkGeom g;
+  const char* why = nullptr;
+  if (!nk_make_geom(arch, H, W, C, &g, &why)) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_self_diag: %s", why);
+  if (!prm) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_self_diag: params is NULL");
+  if (n < 0) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_self_diag: n < 0");
+  if (n == 0) return NK_OK;
+  if (!X || !qd) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_self_diag: X or qd is NULL");
+  if (!(prm->sigma_w2 >= 0.0) || !(prm->sigma_b2 >= 0.0))
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_self_diag: negative variance");
+  const int grid = (int)std::min<int64_t>(n, 2 * (int64_t)h->sm_count);
+  const size_t per = nk_self_diag_ws_per_cta(g);
+  void* ws = nullptr;
+  nk_status s = nk_workspace(h, per * grid, &ws);
+  if (s != NK_OK) return s;
+  cudaError_t e = nk_launch_self_diag(g, prm->sigma_w2, prm->sigma_b2, X, n, qd, qs, (double*)ws, grid,
+                                      h->dstatus, (cudaStream_t)stream);
+  return nk_cuda_check(h, e, "nk_self_diag launch");
+}
+
+nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_prec prec,
+                   const float* Xa, const double* qda, const float* qsa, int64_t a0, int64_t a1,
+                   const float* Xb, const double* qdb, const float* qsb, int64_t b0, int64_t b1,
+                   int H, int W, int C, void* K, int64_t ldk, int symmetric, void* stream) {
+  if (!h) return NK_ERR_INVALID_ARG;
+  NkGeom g;
+  const char* why = nullptr;
+  if (!nk_make_geom(arch, H, W, C, &g, &why)) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block: %s", why);
+  if (!prm) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block: params is NULL");
+  if (!(prm->sigma_w2 >= 0.0) || !(prm->sigma_b2 >= 0.0))
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block: negative variance");
+  if (prec != NK_PREC_PLAIN_FP64 && prec != NK_PREC_PLAIN_FP32 && prec != NK_PREC_MIXED)
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block: unknown precision");
+  if (a0 < 0 || b0 < 0 || a1 < a0 || b1 < b0)
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block: bad index range");
+  if (a1 == a0 || b1 == b0) return NK_OK;
+  if (!Xa || !Xb || !K) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block: NULL image or output pointer");
+  if (ldk < b1 - b0) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block: ldk < b1 - b0");
+  if (symmetric && (Xa != Xb || a0 != b0 || a1 != b1))
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block: symmetric needs Xa == Xb and equal ranges");
+  const bool needq = (g.act == NK_ACT_RELU);
+  if (needq && prec == NK_PREC_PLAIN_FP64 && (!qda || !qdb))
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block: PLAIN_FP64 needs qda and qdb");
+  if (needq && prec != NK_PREC_PLAIN_FP64 && (!qsa || !qsb))
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block: FP32 paths need qsa and qsb");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == NK_PREC_MIXED) {
+    if (!nk_myrtle_fused_supported(g))
+      return nk_fail(h, NK_ERR_UNSUPPORTED,
+                     "nk_block MIXED: needs filter 3, ReLU, H == W in {8,16,32}, C <= 4 and one of "
+                     "the stage patterns (2,1,0) (2,1,1) (3,3,3) (1) (1,1,1)");
+    cudaError_t e = nk_launch_myrtle_fused(g, prm->sigma_w2, prm->sigma_b2, Xa, qsa, a0, a1, Xb, qsb, b0,
+                                           b1, (float*)K, ldk, symmetric, h->sm_count, h->dstatus, st);
+    return nk_cuda_check(h, e, "nk_block fused launch");
+  }
+  const int fp64 = (prec == NK_PREC_PLAIN_FP64);
+  const int64_t na = a1 - a0, nb = b1 - b0;
+  const int64_t npairs = symmetric ? na * (na + 1) / 2 : na * nb;
+  const size_t per_pair = nk_plain_ws_bytes(g, fp64, 1);
+  const size_t budget = (size_t)1 << 30;
+  int64_t chunk = (int64_t)std::max<size_t>(1, budget / per_pair);
+  chunk = std::min<int64_t>(chunk, npairs);
+  void* ws = nullptr;
+  nk_status s = nk_workspace(h, per_pair * chunk, &ws);
+  if (s != NK_OK) return s;
+  cudaError_t e = nk_launch_myrtle_plain(g, fp64, prm->sigma_w2, prm->sigma_b2, Xa, qda, qsa, a0, a1, Xb,
+                                         qdb, qsb, b0, b1, K, ldk, symmetric, ws, chunk, h->dstatus, st);
+  return nk_cuda_check(h, e, "nk_block plain launch");
+}
+
+nk_status nk_pcg_solve(nk_handle* h, const float* K, int64_t ldk, int64_t N, const double* Y, int R,
+                       double lambda, int precond, nk_prec prec, double tol, int maxit, int refine_max,
+                       double* A, int* iters, double* relres, void* stream) {
+  if (!h) return NK_ERR_INVALID_ARG;
+  if (iters) *iters = 0;
+  if (N < 0 || R < 0) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_solve: negative size");
+  if (N == 0 || R == 0) return NK_OK;
+  if (R > 256) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_solve: R > 256");
+  if (!K || !Y || !A) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_solve: NULL pointer");
+  if (ldk < N) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_solve: ldk < N");
+  if (!(lambda >= 0.0)) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_solve: lambda < 0");
+  if (precond != NK_PRECOND_NONE && precond != NK_PRECOND_JACOBI)
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_solve: unknown preconditioner");
+  if (prec != NK_PREC_PLAIN_FP64 && prec != NK_PREC_PLAIN_FP32 && prec != NK_PREC_MIXED)
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_solve: unknown precision");
+  if (!(tol >= 0.0) || maxit < 0 || refine_max < 0)
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_solve: bad tol / maxit / refine_max");
+  return nk_pcg_impl(h, K, ldk, N, Y, R, lambda, precond, prec, tol, maxit, refine_max, A, iters, relres,
+                     (cudaStream_t)stream);
+}
+
+}  // extern "C"

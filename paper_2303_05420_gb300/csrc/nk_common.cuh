@@ -1,0 +1,78 @@
+// Internal definitions shared by the libnk translation units (CUDA side only).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nk.h"
+
+#define NK_MAX_STAGES 4
+#define NK_MAX_LAYERS 32
+
+// Device status word bits (see nk_sync_status).
+#define NK_DEV_NUMERICAL 1u
+#define NK_DEV_TIMEOUT 2u
+
+// Architecture + image size resolved into per-stage / per-layer geometry.
+// Layers are the conv(+activation) layers in network order; their
+// self-variances live at q[layer_qoff[l] + i * W_l + j].
+struct NkGeom {
+  int n_stages;
+  int convs[NK_MAX_STAGES];
+  int filter;
+  int act;
+  int C;
+  int Hs[NK_MAX_STAGES];
+  int Ws[NK_MAX_STAGES];
+  int n_layers;
+  int layer_stage[NK_MAX_LAYERS];
+  int layer_qoff[NK_MAX_LAYERS];
+  int nq;
+  int last_act_stage;  // last stage holding an activation layer (-1: none)
+  int gap_stage;       // the stage whose activations feed the global average pool
+  int radius[NK_MAX_STAGES];  // self-covariance band radius needed per stage
+};
+
+// Returns false (and fills why) when the request is invalid.
+bool nk_make_geom(const nk_arch* arch, int H, int W, int C, NkGeom* g, const char** why);
+
+// Handle internals.
+struct nk_handle {
+  char err[512];
+  unsigned int* dstatus;   // device status word
+  void* ws;                // workspace (device)
+  size_t ws_bytes;
+  int sm_count;
+  int device;
+  // PCG scratch
+  void* pcg_ws;
+  size_t pcg_bytes;
+};
+
+nk_status nk_fail(nk_handle* h, nk_status s, const char* fmt, ...);
+nk_status nk_cuda_check(nk_handle* h, cudaError_t e, const char* what);
+nk_status nk_workspace(nk_handle* h, size_t bytes, void** out);
+
+// Launchers (each returns a CUDA error, arguments already validated).
+cudaError_t nk_launch_self_diag(const NkGeom& g, double sw2, double sb2, const float* X,
+                                int64_t n, double* qd, float* qs, double* ws, int grid,
+                                unsigned int* dstatus, cudaStream_t st);
+size_t nk_self_diag_ws_per_cta(const NkGeom& g);
+
+// Fused (MIXED) Myrtle block.  Returns cudaErrorNotSupported when the
+// architecture / size has no fused instantiation.
+cudaError_t nk_launch_myrtle_fused(const NkGeom& g, double sw2, double sb2, const float* Xa,
+                                   const float* qsa, int64_t a0, int64_t a1, const float* Xb,
+                                   const float* qsb, int64_t b0, int64_t b1, float* K,
+                                   int64_t ldk, int symmetric, int sm_count,
+                                   unsigned int* dstatus, cudaStream_t st);
+bool nk_myrtle_fused_supported(const NkGeom& g);
+
+// Plain layer-wise Myrtle block (FP32 or FP64).
+size_t nk_plain_ws_bytes(const NkGeom& g, int fp64, int64_t pairs_per_chunk);
+cudaError_t nk_launch_myrtle_plain(const NkGeom& g, int fp64, double sw2, double sb2,
+                                   const float* Xa, const double* qda, const float* qsa,
+                                   int64_t a0, int64_t a1, const float* Xb, const double* qdb,
+                                   const float* qsb, int64_t b0, int64_t b1, void* K, int64_t ldk,
+                                   int symmetric, void* ws, int64_t pairs_per_chunk,
+                                   unsigned int* dstatus, cudaStream_t st);

@@ -1,0 +1,80 @@
+// ReLU arc-cosine map (stax.Relu in the Appendix A listings) on the device.
+//
+// For a centred Gaussian pair with variances q, q' and covariance K,
+//   E[relu(u) relu(v)] = sqrt(q q') / (2 pi) * J(c),  c = K / sqrt(q q'),
+//   J(c) = sqrt(1 - c^2) + c (pi - arccos c).
+// Writing J(c) = pi c / 2 + g(c) with the even function
+//   g(c) = sqrt(1 - c^2) + |c| asin|c|
+// and using asin|c| = pi/2 - asin(sqrt(1 - c^2)) when |c| > sqrt(1 - c^2),
+// only asin(m) with m = min(|c|, sqrt(1 - c^2)) in [0, 1/sqrt 2] is needed.
+// asin(m) = m + m^3 P(m^2) with P of degree 6, fitted by
+// csrc/fit_asin.py (near-minimax, Lawson re-weighted least squares;
+// relative error 1.5e-8 in float64, FP32 rounding dominates on the device).
+// J is well conditioned at |c| -> 1 (dJ/dc = pi - arccos c is bounded and
+// dJ/dsqrt(1-c^2) vanishes there), so FP32 suffices for the map itself.
+#pragma once
+
+#include <math.h>
+
+#define NK_PI_F 3.14159265358979323846f
+#define NK_HALF_PI_F 1.57079632679489661923f
+#define NK_PI_D 3.14159265358979323846
+#define NK_INV_2PI_D 0.15915494309189533577
+
+__device__ __forceinline__ float nk_sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// asin(m) for m in [0, 1/sqrt(2)].
+__device__ __forceinline__ float nk_asin_small(float m) {
+  const float z = m * m;
+  float p = 1.112414098e-01f;
+  p = fmaf(p, z, -9.249696326e-02f);
+  p = fmaf(p, z, 7.689475858e-02f);
+  p = fmaf(p, z, 1.641334877e-02f);
+  p = fmaf(p, z, 4.649848860e-02f);
+  p = fmaf(p, z, 7.488511025e-02f);
+  p = fmaf(p, z, 1.666690495e-01f);
+  return fmaf(m * z, p, m);
+}
+
+// J(c) in FP32; c is clamped to [-1, 1].
+__device__ __forceinline__ float nk_J_f32(float c) {
+  c = fminf(fmaxf(c, -1.f), 1.f);
+  const float om = fmaf(-c, c, 1.f);
+  const float sn = nk_sqrt_approx(om);
+  const float a = fabsf(c);
+  const float m = fminf(a, sn);
+  const float as = nk_asin_small(m);
+  const float t = (a > sn) ? (NK_HALF_PI_F - as) : as;
+  const float g = fmaf(a, t, sn);
+  return fmaf(c, NK_HALF_PI_F, g);
+}
+
+// J'(c) = pi - arccos(c) in FP32 (used by the adjoint).
+__device__ __forceinline__ float nk_dJ_f32(float c) {
+  c = fminf(fmaxf(c, -1.f), 1.f);
+  const float om = fmaf(-c, c, 1.f);
+  const float sn = nk_sqrt_approx(om);
+  const float a = fabsf(c);
+  const float m = fminf(a, sn);
+  const float as = nk_asin_small(m);
+  // pi - acos(c) = pi/2 + asin(c)
+  const float asa = (a > sn) ? (NK_HALF_PI_F - as) : as;  // asin|c|
+  return NK_HALF_PI_F + copysignf(asa, c);
+}
+
+// J(c) in FP64 with the CUDA double-precision arccos.
+__device__ __forceinline__ double nk_J_f64(double c) {
+  c = fmin(fmax(c, -1.0), 1.0);
+  return sqrt(fmax(1.0 - c * c, 0.0)) + c * (NK_PI_D - acos(c));
+}
+
+// Full map in FP64: Kt = sqrt(q1 q2)/(2 pi) J(K / sqrt(q1 q2)), 0 if q1 q2 == 0.
+__device__ __forceinline__ double nk_relu_map_f64(double K, double q1, double q2) {
+  const double s = sqrt(q1 * q2);
+  if (!(s > 0.0)) return 0.0;
+  return s * NK_INV_2PI_D * nk_J_f64(K / s);
+}

@@ -1,0 +1,493 @@
+// nk_pcg_solve: Jacobi-preconditioned conjugate gradients for (K + lam I) A = Y
+// with R right-hand sides run in lock-step (Section 2, "Iterative solvers":
+// CG with a preconditioner; Appendix B.3: CG vectorised over tasks).
+//
+// The matvec is the only place K occurs (Section 2), and it is bandwidth
+// bound: K (N x N float32, symmetric) is streamed once per iteration.  Each
+// thread owns 4 consecutive columns i and walks rows j of a row split, using
+// K[j][i] = K[i][j] so that every warp reads 512 contiguous bytes of a row;
+// the R values P[j][:] are a warp-broadcast load.  FP32 products are summed in
+// FP32 over chunks of at most 256 rows and the chunk sums are combined in FP64
+// (row-split partials reduced in FP64 by the next kernel).  CG scalars
+// (alpha, beta, r.z, p.Ap) are FP64.  NK_PREC_MIXED wraps FP32-matvec inner
+// solves in an FP64 iterative-refinement loop whose true residual is formed
+// with FP64 products and sums.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "nk_common.cuh"
+
+namespace {
+
+enum { SC_RZ = 0, SC_RZN, SC_PQ, SC_RR, SC_YY, SC_ACT, SC_ALPHA, SC_BETA, SC_ITER, SC_N };
+
+template <int RB, bool F64, bool VEC>
+__global__ void __launch_bounds__(128)
+k_matvec(const float* __restrict__ K, int64_t ldk, int64_t N, const void* __restrict__ Pin, int R,
+         int rc0, int rcnt, int rows_per_split, double* __restrict__ Qpart) {
+  using T = typename std::conditional<F64, double, float>::type;
+  const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  const int64_t js = (int64_t)blockIdx.y * rows_per_split;
+  const int64_t je = std::min<int64_t>(N, js + rows_per_split);
+  const T* P = reinterpret_cast<const T*>(Pin);
+  T acc[4][RB];
+  double acc64[4][RB];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      acc[c][r] = 0;
+      acc64[c][r] = 0.0;
+    }
+  const bool full = (i0 + 3 < N);
+  int chunk = 0;
+  for (int64_t j = js; j < je; ++j) {
+    float k[4];
+    const float* row = K + j * ldk + i0;
+    if (VEC && full) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(row));
+      k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) k[c] = (i0 + c < N) ? __ldg(row + c) : 0.f;
+    }
+    const T* pr = P + j * R + rc0;
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      if (r < rcnt) {
+        const T p = __ldg(pr + r);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c][r] = fma((T)k[c], p, acc[c][r]);
+      }
+    }
+    if constexpr (!F64) {
+      if (++chunk == 256) {
+        chunk = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int r = 0; r < RB; ++r) {
+            acc64[c][r] += (double)acc[c][r];
+            acc[c][r] = 0;
+          }
+      }
+    }
+  }
+  double* out = Qpart + (int64_t)blockIdx.y * N * R;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    if (i0 + c < N) {
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+        if (r < rcnt) out[(i0 + c) * R + rc0 + r] = acc64[c][r] + (double)acc[c][r];
+    }
+  }
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  return s;  // valid in thread 0
+}
+
+// Q = sum_s Qpart[s] + lam * P ; sc[PQ][r] += P . Q  (one column r per blockIdx.y)
+__global__ void k_reduce_dot(const double* __restrict__ Qpart, int S, int64_t N, int R,
+                             const double* __restrict__ P, double lam, double* __restrict__ Q,
+                             double* __restrict__ sc, int dot_slot) {
+  __shared__ double sh[32];
+  const int r = blockIdx.y;
+  double part = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double q = 0.0;
+    for (int s = 0; s < S; ++s) q += Qpart[(int64_t)s * N * R + i * R + r];
+    const double p = P[i * R + r];
+    q += lam * p;
+    Q[i * R + r] = q;
+    part += p * q;
+  }
+  if (dot_slot >= 0) {
+    const double s = block_sum(part, sh);
+    if (threadIdx.x == 0) atomicAdd(sc + dot_slot * R + r, s);
+  }
+}
+
+// Initialise a CG run on right-hand side B (x = 0): r = B, z = M^{-1} r,
+// p = z, accumulate r.z and B.B.
+__global__ void k_init(const double* __restrict__ B, const double* __restrict__ minv, int64_t N,
+                       int R, double* __restrict__ X, double* __restrict__ Rr,
+                       double* __restrict__ Z, double* __restrict__ P, float* __restrict__ Pf,
+                       double* __restrict__ sc) {
+  __shared__ double sh[32];
+  const int r = blockIdx.y;
+  double rz = 0.0, yy = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i * R + r;
+    const double b = B[e];
+    const double z = minv[i] * b;
+    X[e] = 0.0;
+    Rr[e] = b;
+    Z[e] = z;
+    P[e] = z;
+    Pf[e] = (float)z;
+    rz += b * z;
+    yy += b * b;
+  }
+  double s = block_sum(rz, sh);
+  if (threadIdx.x == 0) atomicAdd(sc + SC_RZ * R + r, s);
+  s = block_sum(yy, sh);
+  if (threadIdx.x == 0) atomicAdd(sc + SC_YY * R + r, s);
+}
+
+__global__ void k_alpha(double* sc, int R) {
+  const int r = threadIdx.x;
+  if (r >= R) return;
+  const double act = sc[SC_ACT * R + r];
+  const double pq = sc[SC_PQ * R + r];
+  sc[SC_ALPHA * R + r] = (act != 0.0 && pq != 0.0) ? sc[SC_RZ * R + r] / pq : 0.0;
+  sc[SC_RZN * R + r] = 0.0;
+  sc[SC_RR * R + r] = 0.0;
+}
+
+__global__ void k_update(const double* __restrict__ minv, int64_t N, int R, double* __restrict__ X,
+                         double* __restrict__ Rr, double* __restrict__ Z,
+                         const double* __restrict__ P, const double* __restrict__ Q,
+                         double* __restrict__ sc) {
+  __shared__ double sh[32];
+  const int r = blockIdx.y;
+  const double alpha = sc[SC_ALPHA * R + r];
+  double rz = 0.0, rr = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i * R + r;
+    X[e] += alpha * P[e];
+    const double rn = Rr[e] - alpha * Q[e];
+    Rr[e] = rn;
+    const double z = minv[i] * rn;
+    Z[e] = z;
+    rz += rn * z;
+    rr += rn * rn;
+  }
+  double s = block_sum(rz, sh);
+  if (threadIdx.x == 0) atomicAdd(sc + SC_RZN * R + r, s);
+  s = block_sum(rr, sh);
+  if (threadIdx.x == 0) atomicAdd(sc + SC_RR * R + r, s);
+}
+
+// beta, activity and iteration counts; *flag = number of active columns.
+__global__ void k_beta(double* sc, int R, double tol2, int* flag) {
+  const int r = threadIdx.x;
+  int act_now = 0;
+  if (r < R) {
+    const double act = sc[SC_ACT * R + r];
+    if (act != 0.0) {
+      const double rzn = sc[SC_RZN * R + r];
+      const double rz = sc[SC_RZ * R + r];
+      sc[SC_BETA * R + r] = (rz != 0.0) ? rzn / rz : 0.0;
+      sc[SC_RZ * R + r] = rzn;
+      sc[SC_ITER * R + r] += 1.0;
+      const bool still = sc[SC_RR * R + r] > tol2 * sc[SC_YY * R + r];
+      sc[SC_ACT * R + r] = still ? 1.0 : 0.0;
+      act_now = still ? 1 : 0;
+    } else {
+      sc[SC_BETA * R + r] = 0.0;
+    }
+    sc[SC_PQ * R + r] = 0.0;
+  }
+  const int n = __syncthreads_count(act_now);
+  if (threadIdx.x == 0) *flag = n;
+}
+
+__global__ void k_direction(int64_t N, int R, const double* __restrict__ Z, double* __restrict__ P,
+                            float* __restrict__ Pf, const double* __restrict__ sc) {
+  const int r = blockIdx.y;
+  if (sc[SC_ACT * R + r] == 0.0) return;
+  const double beta = sc[SC_BETA * R + r];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i * R + r;
+    const double p = Z[e] + beta * P[e];
+    P[e] = p;
+    Pf[e] = (float)p;
+  }
+}
+
+__global__ void k_minv(const float* __restrict__ K, int64_t ldk, int64_t N, double lam, int jacobi,
+                       double* __restrict__ minv) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = jacobi ? (double)K[i * ldk + i] + lam : 1.0;
+    minv[i] = (d != 0.0) ? 1.0 / d : 1.0;
+  }
+}
+
+// out = B - Q, per-column ||out||^2 into sc[SC_RR] (used for true residuals)
+__global__ void k_resid(const double* __restrict__ B, const double* __restrict__ Q, int64_t N, int R,
+                        double* __restrict__ out, double* __restrict__ sc) {
+  __shared__ double sh[32];
+  const int r = blockIdx.y;
+  double rr = 0.0, yy = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i * R + r;
+    const double v = B[e] - Q[e];
+    out[e] = v;
+    rr += v * v;
+    yy += B[e] * B[e];
+  }
+  double s = block_sum(rr, sh);
+  if (threadIdx.x == 0) atomicAdd(sc + SC_RR * R + r, s);
+  s = block_sum(yy, sh);
+  if (threadIdx.x == 0) atomicAdd(sc + SC_YY * R + r, s);
+}
+
+__global__ void k_axpy_cols(int64_t n, double* __restrict__ X, const double* __restrict__ D) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    X[e] += D[e];
+}
+
+__global__ void k_zero(double* p, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    p[e] = 0.0;
+}
+
+__global__ void k_set_active(double* sc, int R) {
+  const int r = threadIdx.x;
+  if (r < R) sc[SC_ACT * R + r] = 1.0;
+}
+
+struct Pcg {
+  int64_t N;
+  int R;
+  const float* K;
+  int64_t ldk;
+  double lam;
+  int S;             // row splits of the matvec
+  int rows_per_split;
+  int sm;
+  cudaStream_t st;
+  double *X, *Rr, *Z, *P, *Q, *Qpart, *minv, *sc, *B2, *D;
+  float* Pf;
+  int* flag;         // device
+  int* hflag;        // pinned host
+};
+
+template <bool F64>
+cudaError_t matvec(const Pcg& c, const void* Pin) {
+  const bool vec = (c.ldk % 4 == 0) && ((reinterpret_cast<uintptr_t>(c.K) & 15) == 0);
+  const int64_t colthreads = (c.N + 3) / 4;
+  dim3 grid((unsigned)((colthreads + 127) / 128), (unsigned)c.S);
+  for (int rc0 = 0; rc0 < c.R; rc0 += 16) {
+    const int rcnt = std::min(16, c.R - rc0);
+#define NK_MV(RB)                                                                                 \
+  if (rcnt <= RB) {                                                                               \
+    if (vec)                                                                                      \
+      k_matvec<RB, F64, true><<<grid, 128, 0, c.st>>>(c.K, c.ldk, c.N, Pin, c.R, rc0, rcnt,       \
+                                                      c.rows_per_split, c.Qpart);                 \
+    else                                                                                          \
+      k_matvec<RB, F64, false><<<grid, 128, 0, c.st>>>(c.K, c.ldk, c.N, Pin, c.R, rc0, rcnt,      \
+                                                       c.rows_per_split, c.Qpart);                \
+    continue;                                                                                     \
+  }
+    NK_MV(1) NK_MV(2) NK_MV(4) NK_MV(8) NK_MV(10) NK_MV(16)
+#undef NK_MV
+  }
+  return cudaGetLastError();
+}
+
+inline dim3 vgrid(const Pcg& c) {
+  int64_t b = (c.N + 255) / 256;
+  if (b > 4 * (int64_t)c.sm) b = 4 * (int64_t)c.sm;
+  return dim3((unsigned)std::max<int64_t>(1, b), (unsigned)c.R);
+}
+
+// True residual out = B - (K + lam I) X in FP64; sc[RR], sc[YY] accumulate.
+cudaError_t true_residual(const Pcg& c, const double* B, const double* Xc, double* out) {
+  k_zero<<<1, 256, 0, c.st>>>(c.sc, (int64_t)SC_N * c.R);
+  cudaError_t e = matvec<true>(c, Xc);
+  if (e != cudaSuccess) return e;
+  k_reduce_dot<<<vgrid(c), 256, 0, c.st>>>(c.Qpart, c.S, c.N, c.R, Xc, c.lam, c.Q, c.sc, -1);
+  k_resid<<<vgrid(c), 256, 0, c.st>>>(B, c.Q, c.N, c.R, out, c.sc);
+  return cudaGetLastError();
+}
+
+// CG on (K + lam I) Xc = B from Xc = 0.  Returns iterations performed (max
+// over columns) through *its, or a negative value on a CUDA error.
+template <bool F64>
+cudaError_t cg_run(const Pcg& c, const double* B, double* Xc, double tol, int maxit, int* its) {
+  k_zero<<<1, 256, 0, c.st>>>(c.sc, (int64_t)SC_N * c.R);
+  k_set_active<<<1, 256, 0, c.st>>>(c.sc, c.R);
+  k_init<<<vgrid(c), 256, 0, c.st>>>(B, c.minv, c.N, c.R, Xc, c.Rr, c.Z, c.P, c.Pf, c.sc);
+  const double tol2 = tol * tol;
+  const int check_every = 8;
+  int it = 0;
+  cudaError_t e = cudaSuccess;
+  while (it < maxit) {
+    const int steps = std::min(check_every, maxit - it);
+    for (int s = 0; s < steps; ++s) {
+      e = F64 ? matvec<true>(c, c.P) : matvec<false>(c, c.Pf);
+      if (e != cudaSuccess) return e;
+      k_reduce_dot<<<vgrid(c), 256, 0, c.st>>>(c.Qpart, c.S, c.N, c.R, c.P, c.lam, c.Q, c.sc,
+                                               SC_PQ);
+      k_alpha<<<1, 256, 0, c.st>>>(c.sc, c.R);
+      k_update<<<vgrid(c), 256, 0, c.st>>>(c.minv, c.N, c.R, Xc, c.Rr, c.Z, c.P, c.Q, c.sc);
+      k_beta<<<1, 256, 0, c.st>>>(c.sc, c.R, tol2, c.flag);
+      k_direction<<<vgrid(c), 256, 0, c.st>>>(c.N, c.R, c.Z, c.P, c.Pf, c.sc);
+    }
+    it += steps;
+    e = cudaMemcpyAsync(c.hflag, c.flag, sizeof(int), cudaMemcpyDeviceToHost, c.st);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(c.st);
+    if (e != cudaSuccess) return e;
+    if (*c.hflag == 0) break;
+  }
+  // exact per-column count
+  double* hsc = (double*)malloc(sizeof(double) * SC_N * c.R);
+  e = cudaMemcpy(hsc, c.sc, sizeof(double) * SC_N * c.R, cudaMemcpyDeviceToHost);
+  int mx = 0;
+  for (int r = 0; r < c.R; ++r) mx = std::max(mx, (int)hsc[SC_ITER * c.R + r]);
+  free(hsc);
+  *its = mx;
+  return e;
+}
+
+}  // namespace
+
+// Host orchestration, called by nk_pcg_solve after argument validation.
+nk_status nk_pcg_impl(nk_handle* h, const float* K, int64_t ldk, int64_t N, const double* Y, int R,
+                      double lam, int precond, nk_prec prec, double tol, int maxit, int refine_max,
+                      double* A, int* iters, double* relres, cudaStream_t st) {
+  Pcg c = {};
+  c.N = N;
+  c.R = R;
+  c.K = K;
+  c.ldk = ldk;
+  c.lam = lam;
+  c.sm = h->sm_count;
+  c.st = st;
+  const int64_t colblocks = ((N + 3) / 4 + 127) / 128;
+  int64_t S = (2 * (int64_t)c.sm + colblocks - 1) / colblocks;
+  S = std::min<int64_t>(S, std::max<int64_t>(1, N / std::max(4 * R, 32)));
+  S = std::max<int64_t>(1, std::min<int64_t>(S, 512));
+  c.S = (int)S;
+  c.rows_per_split = (int)((N + S - 1) / S);
+  const size_t NR = (size_t)N * R;
+  size_t bytes = NR * 8 * 8 + (size_t)S * NR * 8 + (size_t)N * 8 + SC_N * (size_t)R * 8 + NR * 4 + 16 * 256;
+  if (bytes > h->pcg_bytes) {
+    if (h->pcg_ws) cudaFree(h->pcg_ws);
+    h->pcg_ws = nullptr;
+    h->pcg_bytes = 0;
+    if (cudaMalloc(&h->pcg_ws, bytes) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return nk_fail(h, NK_ERR_NO_MEMORY, "pcg workspace of %zu bytes", bytes);
+    }
+    h->pcg_bytes = bytes;
+  }
+  char* w = (char*)h->pcg_ws;
+  auto take = [&](size_t n) { char* p = w; w += (n + 255) / 256 * 256; return p; };
+  c.X = (double*)take(NR * 8);
+  c.Rr = (double*)take(NR * 8);
+  c.Z = (double*)take(NR * 8);
+  c.P = (double*)take(NR * 8);
+  c.Q = (double*)take(NR * 8);
+  c.B2 = (double*)take(NR * 8);
+  c.D = (double*)take(NR * 8);
+  c.Qpart = (double*)take((size_t)S * NR * 8);
+  c.minv = (double*)take((size_t)N * 8);
+  c.sc = (double*)take(SC_N * (size_t)R * 8);
+  c.Pf = (float*)take(NR * 4);
+  c.flag = (int*)take(64);
+  int hflag_storage = 0;
+  int* hflag = nullptr;
+  if (cudaMallocHost(&hflag, sizeof(int)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    hflag = &hflag_storage;
+  }
+  c.hflag = hflag;
+  nk_status ret = NK_OK;
+  cudaError_t e = cudaSuccess;
+  int total_it = 0;
+  double* hsc = (double*)malloc(sizeof(double) * SC_N * R);
+  auto finish = [&](nk_status s) {
+    if (hflag != &hflag_storage) cudaFreeHost(hflag);
+    free(hsc);
+    return s;
+  };
+  k_minv<<<(unsigned)std::min<int64_t>((N + 255) / 256, 4 * c.sm), 256, 0, st>>>(
+      K, ldk, N, lam, precond == NK_PRECOND_JACOBI, c.minv);
+  bool converged = false;
+  if (prec == NK_PREC_MIXED) {
+    // A = 0; loop: Rt = Y - (K + lam I) A (FP64); stop if small; solve the
+    // correction with FP32-matvec CG; A += D.
+    k_zero<<<(unsigned)std::min<int64_t>((NR + 255) / 256, 4 * c.sm), 256, 0, st>>>(A, NR);
+    for (int outer = 0;; ++outer) {
+      e = true_residual(c, Y, A, c.B2);
+      if (e != cudaSuccess) break;
+      e = cudaMemcpyAsync(hsc, c.sc, sizeof(double) * SC_N * R, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) break;
+      double worst = 0.0;
+      for (int r = 0; r < R; ++r) {
+        const double yy = hsc[SC_YY * R + r];
+        const double rel = yy > 0 ? sqrt(hsc[SC_RR * R + r] / yy) : sqrt(hsc[SC_RR * R + r]);
+        if (relres) relres[r] = rel;
+        worst = std::max(worst, rel);
+      }
+      if (worst <= tol) { converged = true; break; }
+      if (outer >= refine_max || total_it >= maxit) break;
+      // inner relative tolerance: enough to reach tol from here, not below
+      // what an FP32 matvec can resolve
+      const double eta = std::max(std::min(0.5 * tol / worst, 1e-2), 1e-6);
+      int its = 0;
+      e = cg_run<false>(c, c.B2, c.D, eta, maxit - total_it, &its);
+      if (e != cudaSuccess) break;
+      total_it += its;
+      k_axpy_cols<<<(unsigned)std::min<int64_t>((NR + 255) / 256, 4 * c.sm), 256, 0, st>>>(NR, A, c.D);
+    }
+  } else {
+    int its = 0;
+    if (prec == NK_PREC_PLAIN_FP64)
+      e = cg_run<true>(c, Y, A, tol, maxit, &its);
+    else
+      e = cg_run<false>(c, Y, A, tol, maxit, &its);
+    total_it = its;
+    if (e == cudaSuccess) e = true_residual(c, Y, A, c.B2);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hsc, c.sc, sizeof(double) * SC_N * R, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) {
+      double worst = 0.0;
+      for (int r = 0; r < R; ++r) {
+        const double yy = hsc[SC_YY * R + r];
+        const double rel = yy > 0 ? sqrt(hsc[SC_RR * R + r] / yy) : sqrt(hsc[SC_RR * R + r]);
+        if (relres) relres[r] = rel;
+        worst = std::max(worst, rel);
+      }
+      converged = worst <= tol;
+    }
+  }
+  if (e != cudaSuccess) return finish(nk_cuda_check(h, e, "pcg"));
+  if (iters) *iters = total_it;
+  if (!converged) {
+    nk_fail(h, NK_ERR_NOT_CONVERGED, "pcg did not reach tol %.3g in %d iterations", tol, total_it);
+    ret = NK_ERR_NOT_CONVERGED;
+  }
+  return finish(ret);
+}

@@ -1,0 +1,173 @@
+"""GPU parity: libnk (through the C ABI) against the float64 CPU oracle.
+
+Tolerances: kernel entries within 1e-5 max-relative for the FP32 / MIXED paths
+and 1e-12 for PLAIN_FP64; self-variances within 1e-12 relative (FP64 on both
+sides); PCG to relative residual 1e-6 and against a Cholesky solve.  Inputs
+are the same seeded float32 images on both sides (the oracle upcasts them).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import nkdata
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def h():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_05420_gb300.api import Handle
+
+    return Handle()
+
+
+def _imgs(n, hw, seed, blur=True):
+    x = nkdata.images(n, hw, 3, seed, blur)
+    x = nkdata.standardise(x)[0]
+    return x.astype(np.float32)
+
+
+def _dev(x):
+    return torch.tensor(x, device="cuda")
+
+
+def _oracle_block(convs, sw2, sb2, xa, xb, symmetric=False, pairs=None):
+    return oracle.myrtle_block(oracle.Arch(convs), sw2, sb2, xa.astype(np.float64),
+                               xb.astype(np.float64), symmetric=symmetric, pairs=pairs).numpy()
+
+
+def _maxrel(got, want):
+    mask = ~np.isnan(want)
+    return float(np.max(np.abs(got[mask] - want[mask]) / np.abs(want[mask])))
+
+
+@pytest.mark.parametrize("hw,convs", [(8, (2, 1, 0)), (8, (3, 3, 3)), (16, (2, 1, 1)), (32, (2, 1, 0))])
+def test_self_diag_matches_oracle(h, hw, convs):
+    x = _imgs(3, hw, 0)
+    qd, qs = h.self_diag(_dev(x), convs, 2.0, 0.01)
+    h.sync_status()
+    qd = qd.cpu().numpy()
+    qs = qs.cpu().numpy()
+    for n in range(3):
+        want = np.concatenate([q.numpy().reshape(-1) for q in
+                               oracle.myrtle_self_q(oracle.Arch(convs), 2.0, 0.01,
+                                                    torch.tensor(x[n].astype(np.float64)))])
+        assert np.allclose(qd[n], want, rtol=1e-12, atol=0)
+        assert np.allclose(qs[n, :, 1], np.sqrt(want), rtol=1e-6)
+        assert np.allclose(qs[n, :, 0], 1 / np.sqrt(want), rtol=1e-6)
+
+
+@pytest.mark.parametrize("hw,convs,sb2", [(8, (2, 1, 0), 0.0), (8, (3, 3, 3), 0.01), (8, (1,), 0.1),
+                                          (16, (2, 1, 0), 0.0), (16, (2, 1, 1), 0.01),
+                                          (8, (1, 1, 1), 0.05)])
+@pytest.mark.parametrize("prec", ["mixed", "plain_fp32", "plain_fp64"])
+def test_block_small_matches_oracle(h, hw, convs, sb2, prec):
+    xa = _imgs(7, hw, 0)
+    xb = _imgs(5, hw, 1)
+    Xa, Xb = _dev(xa), _dev(xb)
+    qa = h.self_diag(Xa, convs, 2.0, sb2)
+    qb = h.self_diag(Xb, convs, 2.0, sb2)
+    K = h.block(Xa, qa, Xb, qb, convs, 2.0, sb2, prec=prec)
+    Ks = h.block(Xa, qa, Xa, qa, convs, 2.0, sb2, prec=prec, symmetric=True)
+    h.sync_status()
+    want = _oracle_block(convs, 2.0, sb2, xa, xb)
+    wants = _oracle_block(convs, 2.0, sb2, xa, xa, symmetric=True)
+    tol = 1e-12 if prec == "plain_fp64" else TOL32
+    assert _maxrel(K.double().cpu().numpy(), want) <= tol
+    assert _maxrel(Ks.double().cpu().numpy(), wants) <= tol
+
+
+def test_block_ragged_ranges_and_ldk(h):
+    convs = (2, 1, 0)
+    x = _imgs(11, 8, 2)
+    X = _dev(x)
+    q = h.self_diag(X, convs, 2.0, 0.0)
+    out = torch.full((5, 9), float("nan"), device="cuda")
+    h.block(X, q, X, q, convs, 2.0, 0.0, prec="mixed", a_range=(3, 8), b_range=(2, 8), out=out[:, :6])
+    sym = torch.full((7, 7), float("nan"), device="cuda")
+    h.block(X, q, X, q, convs, 2.0, 0.0, prec="mixed", a_range=(4, 11), b_range=(4, 11), symmetric=True,
+            out=sym)
+    h.sync_status()
+    want = _oracle_block(convs, 2.0, 0.0, x[3:8], x[2:8])
+    got = out.cpu().numpy()
+    assert _maxrel(got[:, :6], want) <= TOL32
+    assert np.isnan(got[:, 6:]).all()  # beyond the block: untouched
+    wants = _oracle_block(convs, 2.0, 0.0, x[4:11], x[4:11], symmetric=True)
+    assert _maxrel(sym.cpu().numpy(), wants) <= TOL32
+
+
+def test_block_empty_and_invalid(h):
+    from paper_2303_05420_gb300._lib import NkError
+
+    convs = (2, 1, 0)
+    X = _dev(_imgs(4, 8, 0))
+    q = h.self_diag(X, convs, 2.0, 0.0)
+    out = torch.zeros((1, 1), device="cuda")
+    h.block(X, q, X, q, convs, 2.0, 0.0, a_range=(2, 2), b_range=(0, 1), out=out[:0])
+    with pytest.raises(NkError):  # symmetric with different ranges
+        h.block(X, q, X, q, convs, 2.0, 0.0, a_range=(0, 2), b_range=(1, 3), symmetric=True)
+    with pytest.raises(NkError):  # unsupported fused shape (12x12)
+        Y = _dev(_imgs(2, 12, 0))
+        qy = h.self_diag(Y, convs, 2.0, 0.0)
+        h.block(Y, qy, Y, qy, convs, 2.0, 0.0, prec="mixed")
+
+
+@pytest.mark.parametrize("convs", [(2, 1, 0), (3, 3, 3), (2, 1, 1)])
+def test_block_32x32_sampled_pairs(h, convs):
+    sb2 = 0.01 if convs == (3, 3, 3) else 0.0
+    xa = _imgs(6, 32, 0)
+    xb = _imgs(4, 32, 1)
+    Xa, Xb = _dev(xa), _dev(xb)
+    qa = h.self_diag(Xa, convs, 2.0, sb2)
+    qb = h.self_diag(Xb, convs, 2.0, sb2)
+    K = h.block(Xa, qa, Xb, qb, convs, 2.0, sb2, prec="mixed")
+    h.sync_status()
+    pairs = [(0, 0), (1, 3), (5, 2), (3, 1)]
+    want = _oracle_block(convs, 2.0, sb2, xa, xb, pairs=pairs)
+    assert _maxrel(K.cpu().numpy().astype(np.float64), want) <= TOL32
+
+
+def test_pcg_matches_cholesky(h):
+    p = nkdata.image_problem(128, 32, 8, n_classes=10, blur=False)
+    x = p.x_train.astype(np.float32)
+    X = _dev(x)
+    convs = (2, 1, 0)
+    q = h.self_diag(X, convs, 2.0, 0.0)
+    K = h.block(X, q, X, q, convs, 2.0, 0.0, prec="mixed", symmetric=True)
+    Kh = K.double().cpu().numpy()
+    lam = 1e-4 * np.trace(Kh) / Kh.shape[0]
+    Y = torch.tensor(p.y_train, device="cuda")
+    Astar = oracle.cholesky_solve(Kh, p.y_train, lam)
+    for prec in ["mixed", "plain_fp64", "plain_fp32"]:
+        tol = 1e-6 if prec != "plain_fp32" else 1e-4
+        A, its, rel = h.pcg_solve(K, Y, lam, precond="jacobi", prec=prec, tol=tol, maxit=5000)
+        assert max(rel) <= tol, (prec, rel)
+        An = A.cpu().numpy()
+        r = p.y_train - (Kh + lam * np.eye(len(Kh))) @ An
+        assert np.linalg.norm(r, axis=0).max() / np.linalg.norm(p.y_train, axis=0).min() <= 2 * tol
+        kappa = np.linalg.cond(Kh + lam * np.eye(len(Kh)))
+        assert np.linalg.norm(An - Astar) / np.linalg.norm(Astar) <= kappa * tol
+        assert its > 0
+
+
+def test_pcg_not_converged_and_edge(h):
+    from paper_2303_05420_gb300._lib import NK_ERR_NOT_CONVERGED, NkError
+
+    n = 64
+    rng = np.random.default_rng(0)
+    B = rng.standard_normal((n, n))
+    Kh = (B @ B.T / n).astype(np.float32)
+    K = torch.tensor(Kh, device="cuda")
+    Y = torch.tensor(rng.standard_normal((n, 3)), device="cuda")
+    with pytest.raises(NkError) as ei:
+        h.pcg_solve(K, Y, 1e-8, prec="plain_fp64", tol=1e-12, maxit=2)
+    assert ei.value.status == NK_ERR_NOT_CONVERGED
+    A, its, rel = h.pcg_solve(K, Y, 1.0, prec="plain_fp64", tol=1e-10, maxit=500)
+    want = np.linalg.solve(Kh.astype(np.float64) + np.eye(n), Y.cpu().numpy())
+    assert np.allclose(A.cpu().numpy(), want, rtol=1e-8, atol=1e-10)
