@@ -1,0 +1,446 @@
+#!/usr/bin/env python
+"""Benchmark: Myrtle-5 32x32 NNGP kernel entries/s and PCG iterations/s on GB300.
+
+Workload (the headline configuration): Myrtle-5 stage pattern (2, 1, 0),
+sigma_w^2 = 2, sigma_b^2 = 0, 2048 train + 512 test 32x32x3 images (N(0,1)
+noise blurred by a 3x3 box filter, standardised per channel), 10 random
+classes (one-hot minus 0.1).  One step is the whole hot path: per-image
+self-variances, the train-train kernel block (upper triangle, 2,098,176
+unique entries), the test-train block (1,048,576 entries), and the Jacobi
+PCG ridge solve of the train block (10 right-hand sides, lambda = 1e-4 tr(K)/N,
+relative residual 1e-6 with FP64 refinement).  value = unique kernel entries
+per second of the whole step.
+
+Also reported: the fused kernel alone (roofline, plain ALU bound), the plain
+layer-wise FP32 / FP64 forms on sample tiles at equal accuracy, PCG
+iterations/s mixed vs plain FP64, the end-to-end number through host buffers,
+and the CPU oracle on the host cores.
+
+--impl reference times the float64 CPU oracle (the only reference this
+method has) on the same workload and metric, on a bounded sample per step.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Myrtle-5 32x32 kernel entries/s and PCG iters/s: mixed vs plain at rel err<=1e-5"
+CONVS = (2, 1, 0)
+SW2, SB2 = 2.0, 0.0
+REL_LAMBDA = 1e-4
+CONFIGS = {
+    "headline": dict(n_train=2048, n_test=512, hw=32, n_classes=10),
+    "small": dict(n_train=64, n_test=16, hw=32, n_classes=10),
+}
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def algorithmic_ops_per_entry(hw: int, convs=CONVS, C: int = 3) -> float:
+    """FP32 operations per kernel entry by the method's own arithmetic.
+
+    Per pixel pair of a stage and per layer: conv stencil 9 adds + 1 FMA for
+    scale and bias = 10; arc-cosine map 25 (scaling products 2, clamp 2,
+    1 - c^2 1, sqrt 1, range reduction 2, degree-6 arcsine polynomial 8,
+    select 2, assembly 4, output scale 1, stencil-free); seed channel
+    contraction C FMAs; 2x2 pool or global average 1 add."""
+    ops = 0.0
+    n_stages_eff = 1 + (convs[1] > 0 if len(convs) > 1 else 0) + (
+        (convs[1] > 0 and convs[2] > 0) if len(convs) > 2 else 0)
+    for s in range(n_stages_eff):
+        pairs = (hw >> s) ** 4
+        per = 0.0
+        if s == 0:
+            per += C
+        per += convs[s] * (10 + 25)
+        per += 1  # pool scatter or global average
+        ops += pairs * per
+    return ops
+
+
+# --------------------------------------------------------------------------
+# CPU oracle legs (spawned workers; the oracle is test infrastructure, run
+# here only as the cpu_baseline / reference arm)
+# --------------------------------------------------------------------------
+
+def _oracle_worker(args):
+    seed, n_pairs, hw = args
+    import numpy as np
+    import torch
+
+    torch.set_num_threads(1)
+    sys.path.insert(0, ROOT)
+    import oracle
+
+    import nkdata
+
+    x = torch.tensor(nkdata.standardise(nkdata.images(n_pairs + 1, hw, 3, seed, blur=True))[0]
+                     .astype(np.float32).astype(np.float64))
+    arch = oracle.Arch(CONVS)
+    qs = [oracle.myrtle_self_q(arch, SW2, SB2, x[i]) for i in range(n_pairs + 1)]
+    t0 = time.perf_counter()
+    for k in range(n_pairs):
+        oracle.myrtle_layers_pair(arch, SW2, SB2, x[k], x[k + 1], qs[k], qs[k + 1])
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_rate(n_workers: int, pairs_per_worker: int, hw: int, seed0: int = 100):
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(n_workers) as pool:
+        t0 = time.perf_counter()
+        times = pool.map(_oracle_worker, [(seed0 + w, pairs_per_worker, hw) for w in range(n_workers)])
+        wall = time.perf_counter() - t0
+    pairs = n_workers * pairs_per_worker
+    # self-variances are computed outside the timed loop: they are O(N) per
+    # image, negligible against the O(N^2) entries of a full job
+    return pairs / max(times), pairs, max(times), wall
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# --------------------------------------------------------------------------
+# clocks
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+
+def run_ours(args, rank, world, dist):
+    import numpy as np
+    import torch
+
+    import nkdata
+    from paper_2303_05420_gb300.api import Handle
+
+    cfg = CONFIGS[args.config]
+    n_tr, n_te, hw = cfg["n_train"], cfg["n_test"], cfg["hw"]
+
+    # CPU oracle baseline first: its spawn pool starts before any CUDA call
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = host_cores()
+        rate, pairs, tmax, wall = cpu_oracle_rate(cores, args.cpu_pairs, hw)
+        cpu = {"value": rate, "unit": "entries/s", "cores": cores, "kind": "oracle",
+               "sample": f"{pairs} Myrtle-5 32x32 pixel-pair recursions ({args.cpu_pairs} per process, "
+                         f"{cores} spawned processes x 1 thread, float64 torch CPU); self-variances "
+                         f"precomputed outside the timed loop; {tmax:.1f} s"}
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    prob = nkdata.image_problem(n_tr, n_te, hw, n_classes=cfg["n_classes"], blur=True)
+    Xh = torch.tensor(np.concatenate([prob.x_train, prob.x_test]).astype(np.float32)).pin_memory()
+    Yh = torch.tensor(prob.y_train).pin_memory()
+    X = Xh.to(dev)
+    Y = Yh.to(dev)
+    h = Handle()
+    Ktr = torch.empty((n_tr, n_tr), dtype=torch.float32, device=dev)
+    Kte = torch.empty((n_te, n_tr), dtype=torch.float32, device=dev)
+    A = torch.empty((n_tr, Y.shape[1]), dtype=torch.float64, device=dev)
+    entries = n_tr * (n_tr + 1) // 2 + n_te * n_tr
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(Xd, Yd, marks=None):
+        if marks is not None:
+            marks[0].record(stream)
+        q = h.self_diag(Xd, CONVS, SW2, SB2)
+        if marks is not None:
+            marks[1].record(stream)
+        h.block(Xd, q, Xd, q, CONVS, SW2, SB2, prec="mixed", a_range=(0, n_tr), b_range=(0, n_tr),
+                symmetric=True, out=Ktr)
+        h.block(Xd, q, Xd, q, CONVS, SW2, SB2, prec="mixed", a_range=(n_tr, n_tr + n_te),
+                b_range=(0, n_tr), out=Kte)
+        if marks is not None:
+            marks[2].record(stream)
+        _, its, rel = h.pcg_solve(Ktr, Yd, -REL_LAMBDA, precond="jacobi", prec="mixed", tol=1e-6,
+                                  maxit=20000, refine_max=8, A=A)
+        if marks is not None:
+            marks[3].record(stream)
+        return its, rel
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(X, Y)
+    h.sync_status()
+
+    sampler = ClockSampler(dev.index)
+    step_ms, sd_ms, blk_ms, pcg_ms, iters, rels = [], [], [], [], [], []
+    launches0 = h.launch_count()
+    sampler.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        barrier()
+        marks = [ev() for _ in range(4)]
+        its, rel = step(X, Y, marks)
+        torch.cuda.synchronize()
+        step_ms.append(marks[0].elapsed_time(marks[3]))
+        sd_ms.append(marks[0].elapsed_time(marks[1]))
+        blk_ms.append(marks[1].elapsed_time(marks[2]))
+        pcg_ms.append(marks[2].elapsed_time(marks[3]))
+        iters.append(its)
+        rels.append(max(rel))
+    barrier()
+    clocks = sampler.stop()
+    launches = h.launch_count() - launches0
+    h.sync_status()
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * entries * args.steps / (total_ms / 1e3)
+
+    # ---- end to end through host buffers (H2D inputs, D2H solution + test block)
+    Ah = torch.empty_like(A, device="cpu").pin_memory()
+    Kteh = torch.empty_like(Kte, device="cpu").pin_memory()
+    e2e_ms = []
+    for k in range(max(1, args.e2e_steps)):
+        flush.zero_()
+        barrier()
+        a, b = ev(), ev()
+        a.record(stream)
+        Xd = Xh.to(dev, non_blocking=True)
+        Yd = Yh.to(dev, non_blocking=True)
+        step(Xd, Yd)
+        Ah.copy_(A, non_blocking=True)
+        Kteh.copy_(Kte, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_val = world * entries / (statistics.mean(e2e_ms) / 1e3)
+
+    # ---- kernel-only roofline of the fused Myrtle kernel
+    ops_entry = algorithmic_ops_per_entry(hw)
+    blk_s = statistics.mean(blk_ms) / 1e3
+    # the block interval also holds nothing else: two fused launches
+    achieved_tops = ops_entry * entries / blk_s / 1e12
+    peak_clock = clocks.get("sm_max_mhz") or 2070.0
+    peak_tops = SM_COUNT * FP32_LANES_PER_SM * peak_clock * 1e6 / 1e12
+
+    # ---- plain layer-wise forms on sample tiles, at equal accuracy
+    extra = {}
+    if not args.skip_plain:
+        q = h.self_diag(X, CONVS, SW2, SB2)
+        tile = min(64, n_tr)
+        res = {}
+        for prec, t in [("mixed", tile), ("plain_fp32", tile), ("plain_fp64", min(16, n_tr))]:
+            out = torch.empty((t, t), dtype=torch.float64 if prec == "plain_fp64" else torch.float32,
+                              device=dev)
+            h.block(X, q, X, q, CONVS, SW2, SB2, prec=prec, a_range=(0, t), b_range=(t, 2 * t), out=out)
+            torch.cuda.synchronize()
+            a, b = ev(), ev()
+            a.record(stream)
+            h.block(X, q, X, q, CONVS, SW2, SB2, prec=prec, a_range=(0, t), b_range=(t, 2 * t), out=out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            res[prec] = (t * t / (a.elapsed_time(b) / 1e3), out.double().cpu())
+        k16 = res["plain_fp64"][1]
+        extra["plain_fp32_entries_per_s"] = res["plain_fp32"][0]
+        extra["plain_fp64_entries_per_s"] = res["plain_fp64"][0]
+        extra["mixed_tile_entries_per_s"] = res["mixed"][0]
+        extra["mixed_over_plain_fp32"] = res["mixed"][0] / res["plain_fp32"][0]
+        extra["maxrel_mixed_vs_plain_fp64"] = float(((res["mixed"][1][:16, :16] - k16).abs() / k16.abs()).max())
+        extra["maxrel_plain_fp32_vs_plain_fp64"] = float(((res["plain_fp32"][1][:16, :16] - k16).abs()
+                                                          / k16.abs()).max())
+        extra["plain_tiles"] = f"{tile}x{tile} (fp32, mixed), 16x16 (fp64) train pairs"
+        # PCG: mixed vs plain FP64 on the same train block
+        for prec in ["mixed", "plain_fp64"]:
+            a, b = ev(), ev()
+            a.record(stream)
+            _, its, rel = h.pcg_solve(Ktr, Y, -REL_LAMBDA, precond="jacobi", prec=prec, tol=1e-6,
+                                      maxit=20000, refine_max=8, A=A, allow_not_converged=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            extra[f"pcg_{prec}_iters"] = its
+            extra[f"pcg_{prec}_iters_per_s"] = its / (ms / 1e3)
+            extra[f"pcg_{prec}_relres"] = max(rel)
+    lam_used = h.last_lambda()
+
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "entries/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"myrtle5_(2,1,0)_{hw}x{hw}_train{n_tr}_test{n_te}_pcg10rhs",
+                   "entries_per_step": entries, "parallelism": f"replicas{world}",
+                   "precision": "FP64 self-variances, FP32 on-chip recursion, FP64 combine; "
+                                "PCG FP32 matvec + FP64 scalars + FP64 refinement",
+                   "l2": "256 MB buffer written between timed steps"},
+        "pcg_iters_per_s": statistics.mean(iters) / (statistics.mean(pcg_ms) / 1e3),
+        "pcg_iters": iters[-1],
+        "pcg_relres": rels[-1],
+        "lambda": lam_used,
+        "breakdown_ms": {"self_diag": statistics.mean(sd_ms), "blocks": statistics.mean(blk_ms),
+                         "pcg": statistics.mean(pcg_ms)},
+        "kernel_only_entries_per_s": entries / blk_s,
+        "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "TFLOP/s",
+                     "frac": achieved_tops / peak_tops, "traffic": None,
+                     "kernel": "k_myrtle_fused",
+                     "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                    f"{peak_clock:.0f} MHz (FP32 ops/s)",
+                     "ops_per_entry": ops_entry},
+        "e2e": {"value": e2e_val, "unit": "entries/s",
+                "h2d_bytes_per_step": Xh.numel() * 4 + Yh.numel() * 8,
+                "d2h_bytes_per_step": Ah.numel() * 8 + Kteh.numel() * 4},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# --------------------------------------------------------------------------
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cfg = CONFIGS[args.config]
+    cores = host_cores()
+    per_step = []
+    for k in range(args.warmup + args.steps):
+        rate, pairs, tmax, wall = cpu_oracle_rate(cores, args.ref_pairs, cfg["hw"], seed0=1000 + 97 * k)
+        if k >= args.warmup:
+            per_step.append((rate, pairs, tmax))
+    value = statistics.mean(r for r, _, _ in per_step)
+    n_tr, n_te = cfg["n_train"], cfg["n_test"]
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "entries/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(t for _, _, t in per_step),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"myrtle5_(2,1,0)_{cfg['hw']}x{cfg['hw']}_train{n_tr}_test{n_te}_pcg10rhs",
+                   "parallelism": "cpu_processes"},
+        "cpu_baseline": {"value": value, "unit": "entries/s", "cores": cores, "kind": "oracle",
+                         "sample": f"each step {cores * args.ref_pairs} pixel-pair recursions of the "
+                                   f"workload's 32x32 Myrtle-5 kernel, {cores} spawned processes x 1 thread"},
+        "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="nk", choices=["nk", "reference"])
+    ap.add_argument("--config", default="headline", choices=sorted(CONFIGS))
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-pairs", type=int, default=3)
+    ap.add_argument("--ref-pairs", type=int, default=4)
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    run_ours(args, rank, world, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -93,6 +93,13 @@ nk_status nk_sync_status(nk_handle* h, void* stream);
  * an invalid architecture or size. */
 int64_t nk_q_size(const nk_arch* arch, int H, int W);
 
+/* Number of CUDA kernels launched through this handle since nk_create (a
+ * host-side count, for measurement). */
+int64_t nk_launch_count(nk_handle* h);
+
+/* The ridge lambda used by the last nk_pcg_solve on this handle. */
+double nk_last_lambda(nk_handle* h);
+
 /* Per-pixel self-variances q_l(p) = K_l(p, p; x, x) for every image and every
  * activation layer (needed by the ReLU map, stax.Relu in Appendix A).
  *   X   [n][H][W][C] float32 (device)
@@ -136,6 +143,9 @@ nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_p
  *          outer steps);
  *   prec = NK_PREC_PLAIN_FP32: FP32 K@P, FP64 scalars, no refinement;
  *   prec = NK_PREC_PLAIN_FP64: every product in FP64.
+ *   lambda  >= 0: the ridge; < 0: relative ridge, lambda_used =
+ *           -lambda * tr(K) / N with tr(K) summed on the device in FP64
+ *           (nk_last_lambda returns lambda_used);
  *   tol     stop when every column has ||r_j|| / ||y_j|| <= tol, r the true
  *           residual against the float32 K upcast to FP64;
  *   maxit   bound on the total number of CG iterations;

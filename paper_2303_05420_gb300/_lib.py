@@ -23,7 +23,7 @@ PRECOND = {"none": 0, "jacobi": 1}
 
 # Every symbol include/nk.h declares (checked by a CPU test).
 EXPORTS = ["nk_create", "nk_destroy", "nk_status_string", "nk_last_error", "nk_sync_status",
-           "nk_q_size", "nk_self_diag", "nk_block", "nk_pcg_solve"]
+           "nk_q_size", "nk_launch_count", "nk_last_lambda", "nk_self_diag", "nk_block", "nk_pcg_solve"]
 
 
 class NkArch(ctypes.Structure):
@@ -63,6 +63,10 @@ def lib():
     L.nk_sync_status.restype = c_int
     L.nk_q_size.argtypes = [POINTER(NkArch), c_int, c_int]
     L.nk_q_size.restype = c_int64
+    L.nk_launch_count.argtypes = [c_void_p]
+    L.nk_launch_count.restype = c_int64
+    L.nk_last_lambda.argtypes = [c_void_p]
+    L.nk_last_lambda.restype = c_double
     L.nk_self_diag.argtypes = [c_void_p, POINTER(NkArch), POINTER(NkParams), c_void_p, c_int64, c_int,
                                c_int, c_int, c_void_p, c_void_p, c_void_p]
     L.nk_self_diag.restype = c_int

@@ -51,6 +51,12 @@ class Handle:
             lib().nk_last_error(self._h, buf, 512)
             raise NkError(st, f"{what}: {buf.value.decode()}")
 
+    def launch_count(self) -> int:
+        return int(lib().nk_launch_count(self._h))
+
+    def last_lambda(self) -> float:
+        return float(lib().nk_last_lambda(self._h))
+
     def sync_status(self):
         self.check(lib().nk_sync_status(self._h, c_void_p(_stream())), "nk_sync_status")
 

@@ -165,7 +165,8 @@ template <typename T>
 cudaError_t run_plain(const NkGeom& g, double sw2, double sb2, const float* Xa, const double* qda,
                       const float* qsa, int64_t a0, int64_t a1, const float* Xb, const double* qdb,
                       const float* qsb, int64_t b0, int64_t b1, T* K, int64_t ldk, int symmetric,
-                      void* ws, int64_t chunk, unsigned int* dstatus, cudaStream_t st) {
+                      void* ws, int64_t chunk, unsigned int* dstatus, cudaStream_t st,
+                      int64_t* launches) {
   const int64_t na = a1 - a0, nb = b1 - b0;
   const int64_t npairs_total = symmetric ? na * (na + 1) / 2 : na * nb;
   const int64_t HW0 = (int64_t)g.Hs[0] * g.Ws[0];
@@ -176,12 +177,14 @@ cudaError_t run_plain(const NkGeom& g, double sw2, double sb2, const float* Xa, 
     const int64_t np = (npairs_total - pair0 < chunk) ? npairs_total - pair0 : chunk;
     T* cur = buf0;
     T* nxt = buf1;
+    *launches += 2;  // input covariance + global average
     k_input_cov<T><<<grid_for(np * HW0 * HW0), 256, 0, st>>>(Xa, Xb, a0, b0, na, nb, symmetric,
                                                              pair0, np, g.Hs[0], g.Ws[0], g.C, cur);
     int layer = 0;
     int H = g.Hs[0], W = g.Ws[0];
     for (int s = 0; s < g.n_stages; ++s) {
       if (s > 0) {
+        ++*launches;
         k_pool<T><<<grid_for(np * (int64_t)(H / 2) * (W / 2) * (H / 2) * (W / 2)), 256, 0, st>>>(
             cur, nxt, np, H, W);
         T* t = cur; cur = nxt; nxt = t;
@@ -190,6 +193,7 @@ cudaError_t run_plain(const NkGeom& g, double sw2, double sb2, const float* Xa, 
       }
       const int64_t HW = (int64_t)H * W;
       for (int k = 0; k < g.convs[s]; ++k, ++layer) {
+        *launches += (g.act == NK_ACT_RELU) ? 2 : 1;
         k_conv<T><<<grid_for(np * HW * HW), 256, 0, st>>>(cur, nxt, np, H, W, g.filter, a_conv,
                                                           (T)sb2);
         T* t = cur; cur = nxt; nxt = t;
@@ -220,10 +224,10 @@ cudaError_t nk_launch_myrtle_plain(const NkGeom& g, int fp64, double sw2, double
                                    int64_t a0, int64_t a1, const float* Xb, const double* qdb,
                                    const float* qsb, int64_t b0, int64_t b1, void* K, int64_t ldk,
                                    int symmetric, void* ws, int64_t chunk, unsigned int* dstatus,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, int64_t* launches) {
   if (fp64)
     return run_plain<double>(g, sw2, sb2, Xa, qda, qsa, a0, a1, Xb, qdb, qsb, b0, b1,
-                             reinterpret_cast<double*>(K), ldk, symmetric, ws, chunk, dstatus, st);
+                             reinterpret_cast<double*>(K), ldk, symmetric, ws, chunk, dstatus, st, launches);
   return run_plain<float>(g, sw2, sb2, Xa, qda, qsa, a0, a1, Xb, qdb, qsb, b0, b1,
-                          reinterpret_cast<float*>(K), ldk, symmetric, ws, chunk, dstatus, st);
+                          reinterpret_cast<float*>(K), ldk, symmetric, ws, chunk, dstatus, st, launches);
 }

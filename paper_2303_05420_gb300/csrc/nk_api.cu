@@ -153,6 +153,10 @@ nk_status nk_sync_status(nk_handle* h, void* stream) {
   return NK_OK;
 }
 
+int64_t nk_launch_count(nk_handle* h) { return h ? h->launches : 0; }
+
+double nk_last_lambda(nk_handle* h) { return h ? h->last_lambda : 0.0; }
+
 int64_t nk_q_size(const nk_arch* arch, int H, int W) {
   NkGeom g;
   const char* why = nullptr;
@@ -177,6 +181,7 @@ nk_status nk_self_diag(nk_handle* h, const nk_arch* arch, const nk_params* prm, 
   void* ws = nullptr;
   nk_status s = nk_workspace(h, per * grid, &ws);
   if (s != NK_OK) return s;
+  h->launches += 1;
   cudaError_t e = nk_launch_self_diag(g, prm->sigma_w2, prm->sigma_b2, X, n, qd, qs, (double*)ws, grid,
                                       h->dstatus, (cudaStream_t)stream);
   return nk_cuda_check(h, e, "nk_self_diag launch");
@@ -213,6 +218,7 @@ nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_p
       return nk_fail(h, NK_ERR_UNSUPPORTED,
                      "nk_block MIXED: needs filter 3, ReLU, H == W in {8,16,32}, C <= 4 and one of "
                      "the stage patterns (2,1,0) (2,1,1) (3,3,3) (1) (1,1,1)");
+    h->launches += 1;
     cudaError_t e = nk_launch_myrtle_fused(g, prm->sigma_w2, prm->sigma_b2, Xa, qsa, a0, a1, Xb, qsb, b0,
                                            b1, (float*)K, ldk, symmetric, h->sm_count, h->dstatus, st);
     return nk_cuda_check(h, e, "nk_block fused launch");
@@ -228,7 +234,8 @@ nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_p
   nk_status s = nk_workspace(h, per_pair * chunk, &ws);
   if (s != NK_OK) return s;
   cudaError_t e = nk_launch_myrtle_plain(g, fp64, prm->sigma_w2, prm->sigma_b2, Xa, qda, qsa, a0, a1, Xb,
-                                         qdb, qsb, b0, b1, K, ldk, symmetric, ws, chunk, h->dstatus, st);
+                                         qdb, qsb, b0, b1, K, ldk, symmetric, ws, chunk, h->dstatus, st,
+                                         &h->launches);
   return nk_cuda_check(h, e, "nk_block plain launch");
 }
 
@@ -242,7 +249,7 @@ nk_status nk_pcg_solve(nk_handle* h, const float* K, int64_t ldk, int64_t N, con
   if (R > 256) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_solve: R > 256");
   if (!K || !Y || !A) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_solve: NULL pointer");
   if (ldk < N) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_solve: ldk < N");
-  if (!(lambda >= 0.0)) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_solve: lambda < 0");
+  if (lambda != lambda) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_solve: lambda is NaN");
   if (precond != NK_PRECOND_NONE && precond != NK_PRECOND_JACOBI)
     return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_solve: unknown preconditioner");
   if (prec != NK_PREC_PLAIN_FP64 && prec != NK_PREC_PLAIN_FP32 && prec != NK_PREC_MIXED)

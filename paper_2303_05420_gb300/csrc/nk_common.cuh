@@ -44,6 +44,8 @@ struct nk_handle {
   size_t ws_bytes;
   int sm_count;
   int device;
+  int64_t launches;        // kernels launched through this handle
+  double last_lambda;      // ridge used by the last nk_pcg_solve
   // PCG scratch
   void* pcg_ws;
   size_t pcg_bytes;
@@ -75,4 +77,4 @@ cudaError_t nk_launch_myrtle_plain(const NkGeom& g, int fp64, double sw2, double
                                    int64_t a0, int64_t a1, const float* Xb, const double* qdb,
                                    const float* qsb, int64_t b0, int64_t b1, void* K, int64_t ldk,
                                    int symmetric, void* ws, int64_t pairs_per_chunk,
-                                   unsigned int* dstatus, cudaStream_t st);
+                                   unsigned int* dstatus, cudaStream_t st, int64_t* launches);

@@ -256,6 +256,15 @@ __global__ void k_resid(const double* __restrict__ B, const double* __restrict__
   if (threadIdx.x == 0) atomicAdd(sc + SC_YY * R + r, s);
 }
 
+// tr(K) in FP64 (one block)
+__global__ void k_trace(const float* __restrict__ K, int64_t ldk, int64_t N, double* out) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) acc += (double)K[i * ldk + i];
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) *out = s;
+}
+
 __global__ void k_axpy_cols(int64_t n, double* __restrict__ X, const double* __restrict__ D) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x)
@@ -287,6 +296,7 @@ struct Pcg {
   float* Pf;
   int* flag;         // device
   int* hflag;        // pinned host
+  int64_t* nlaunch;  // handle launch counter
 };
 
 template <bool F64>
@@ -298,6 +308,7 @@ cudaError_t matvec(const Pcg& c, const void* Pin) {
     const int rcnt = std::min(16, c.R - rc0);
 #define NK_MV(RB)                                                                                 \
   if (rcnt <= RB) {                                                                               \
+    ++*c.nlaunch;                                                                                 \
     if (vec)                                                                                      \
       k_matvec<RB, F64, true><<<grid, 128, 0, c.st>>>(c.K, c.ldk, c.N, Pin, c.R, rc0, rcnt,       \
                                                       c.rows_per_split, c.Qpart);                 \
@@ -320,10 +331,13 @@ inline dim3 vgrid(const Pcg& c) {
 
 // True residual out = B - (K + lam I) X in FP64; sc[RR], sc[YY] accumulate.
 cudaError_t true_residual(const Pcg& c, const double* B, const double* Xc, double* out) {
+  ++*c.nlaunch;
   k_zero<<<1, 256, 0, c.st>>>(c.sc, (int64_t)SC_N * c.R);
   cudaError_t e = matvec<true>(c, Xc);
   if (e != cudaSuccess) return e;
+  ++*c.nlaunch;
   k_reduce_dot<<<vgrid(c), 256, 0, c.st>>>(c.Qpart, c.S, c.N, c.R, Xc, c.lam, c.Q, c.sc, -1);
+  ++*c.nlaunch;
   k_resid<<<vgrid(c), 256, 0, c.st>>>(B, c.Q, c.N, c.R, out, c.sc);
   return cudaGetLastError();
 }
@@ -332,8 +346,11 @@ cudaError_t true_residual(const Pcg& c, const double* B, const double* Xc, doubl
 // over columns) through *its, or a negative value on a CUDA error.
 template <bool F64>
 cudaError_t cg_run(const Pcg& c, const double* B, double* Xc, double tol, int maxit, int* its) {
+  ++*c.nlaunch;
   k_zero<<<1, 256, 0, c.st>>>(c.sc, (int64_t)SC_N * c.R);
+  ++*c.nlaunch;
   k_set_active<<<1, 256, 0, c.st>>>(c.sc, c.R);
+  ++*c.nlaunch;
   k_init<<<vgrid(c), 256, 0, c.st>>>(B, c.minv, c.N, c.R, Xc, c.Rr, c.Z, c.P, c.Pf, c.sc);
   const double tol2 = tol * tol;
   const int check_every = 8;
@@ -344,11 +361,16 @@ cudaError_t cg_run(const Pcg& c, const double* B, double* Xc, double tol, int ma
     for (int s = 0; s < steps; ++s) {
       e = F64 ? matvec<true>(c, c.P) : matvec<false>(c, c.Pf);
       if (e != cudaSuccess) return e;
+      ++*c.nlaunch;
       k_reduce_dot<<<vgrid(c), 256, 0, c.st>>>(c.Qpart, c.S, c.N, c.R, c.P, c.lam, c.Q, c.sc,
                                                SC_PQ);
+      ++*c.nlaunch;
       k_alpha<<<1, 256, 0, c.st>>>(c.sc, c.R);
+      ++*c.nlaunch;
       k_update<<<vgrid(c), 256, 0, c.st>>>(c.minv, c.N, c.R, Xc, c.Rr, c.Z, c.P, c.Q, c.sc);
+      ++*c.nlaunch;
       k_beta<<<1, 256, 0, c.st>>>(c.sc, c.R, tol2, c.flag);
+      ++*c.nlaunch;
       k_direction<<<vgrid(c), 256, 0, c.st>>>(c.N, c.R, c.Z, c.P, c.Pf, c.sc);
     }
     it += steps;
@@ -382,6 +404,7 @@ nk_status nk_pcg_impl(nk_handle* h, const float* K, int64_t ldk, int64_t N, cons
   c.lam = lam;
   c.sm = h->sm_count;
   c.st = st;
+  c.nlaunch = &h->launches;
   const int64_t colblocks = ((N + 3) / 4 + 127) / 128;
   int64_t S = (2 * (int64_t)c.sm + colblocks - 1) / colblocks;
   S = std::min<int64_t>(S, std::max<int64_t>(1, N / std::max(4 * R, 32)));
@@ -430,12 +453,27 @@ nk_status nk_pcg_impl(nk_handle* h, const float* K, int64_t ldk, int64_t N, cons
     free(hsc);
     return s;
   };
+  ++h->launches;
+  if (lam < 0.0) {
+    // relative ridge: lam = |lam| * tr(K) / N
+    ++h->launches;
+    k_trace<<<1, 256, 0, st>>>(K, ldk, N, c.sc);
+    double tr = 0.0;
+    e = cudaMemcpyAsync(hsc, c.sc, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return finish(nk_cuda_check(h, e, "pcg trace"));
+    tr = hsc[0];
+    lam = -lam * tr / (double)N;
+    c.lam = lam;
+  }
+  h->last_lambda = lam;
   k_minv<<<(unsigned)std::min<int64_t>((N + 255) / 256, 4 * c.sm), 256, 0, st>>>(
       K, ldk, N, lam, precond == NK_PRECOND_JACOBI, c.minv);
   bool converged = false;
   if (prec == NK_PREC_MIXED) {
     // A = 0; loop: Rt = Y - (K + lam I) A (FP64); stop if small; solve the
     // correction with FP32-matvec CG; A += D.
+    ++h->launches;
     k_zero<<<(unsigned)std::min<int64_t>((NR + 255) / 256, 4 * c.sm), 256, 0, st>>>(A, NR);
     for (int outer = 0;; ++outer) {
       e = true_residual(c, Y, A, c.B2);
@@ -459,6 +497,7 @@ nk_status nk_pcg_impl(nk_handle* h, const float* K, int64_t ldk, int64_t N, cons
       e = cg_run<false>(c, c.B2, c.D, eta, maxit - total_it, &its);
       if (e != cudaSuccess) break;
       total_it += its;
+      ++h->launches;
       k_axpy_cols<<<(unsigned)std::min<int64_t>((NR + 255) / 256, 4 * c.sm), 256, 0, st>>>(NR, A, c.D);
     }
   } else {
