@@ -297,11 +297,14 @@ def run_ours(args, rank, world, dist):
         for prec, t in [("mixed", tile), ("plain_fp32", tile), ("plain_fp64", min(16, n_tr))]:
             out = torch.empty((t, t), dtype=torch.float64 if prec == "plain_fp64" else torch.float32,
                               device=dev)
-            h.block(X, q, X, q, CONVS, SW2, SB2, prec=prec, a_range=(0, t), b_range=(t, 2 * t), out=out)
+            # the same pairs for every form: rows [0, t), columns [tile, tile + t)
+            h.block(X, q, X, q, CONVS, SW2, SB2, prec=prec, a_range=(0, t), b_range=(tile, tile + t),
+                    out=out)
             torch.cuda.synchronize()
             a, b = ev(), ev()
             a.record(stream)
-            h.block(X, q, X, q, CONVS, SW2, SB2, prec=prec, a_range=(0, t), b_range=(t, 2 * t), out=out)
+            h.block(X, q, X, q, CONVS, SW2, SB2, prec=prec, a_range=(0, t), b_range=(tile, tile + t),
+                    out=out)
             b.record(stream)
             torch.cuda.synchronize()
             res[prec] = (t * t / (a.elapsed_time(b) / 1e3), out.double().cpu())
@@ -419,7 +422,7 @@ def main():
     ap.add_argument("--impl", default="nk", choices=["nk", "reference"])
     ap.add_argument("--config", default="headline", choices=sorted(CONFIGS))
     ap.add_argument("--e2e-steps", type=int, default=1)
-    ap.add_argument("--cpu-pairs", type=int, default=3)
+    ap.add_argument("--cpu-pairs", type=int, default=20)
     ap.add_argument("--ref-pairs", type=int, default=4)
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

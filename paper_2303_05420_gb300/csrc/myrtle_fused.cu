@@ -43,6 +43,7 @@
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+#define NK_FUSED_THREADS 512
 
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::
@@ -150,14 +151,25 @@ struct Layout {
 };
 
 // ---------------------------------------------------------------------------
-// Horizontal 3-tap sum of one half-row with halo and the column cut.
+// Thread mapping of a stage at resolution R: a row of the super-plane is split
+// into NQ parts of COLS columns; a warp holds TYW = 32 / NQ shifts t_y and the
+// NQ parts of each (lane = q * TYW + t_y - ty0).
 // ---------------------------------------------------------------------------
-template <int COLS>
-__device__ __forceinline__ void hsum(const float (&A)[COLS], float (&Hc)[COLS], int kl, int h) {
-  const float send = h ? A[0] : A[COLS - 1];
-  const float recv = __shfl_xor_sync(FULL, send, 16);
-  const float left = h ? recv : 0.f;
-  const float right = h ? 0.f : recv;
+template <int R>
+struct Split {
+  static constexpr int NQ = R >= 4 ? 4 : R;
+  static constexpr int COLS = R / NQ;
+  static constexpr int TYW = 32 / NQ;
+  static constexpr int WPT = R > TYW ? R / TYW : 1;  // warps per t_x
+};
+
+// Horizontal 3-tap sum of one row part with halos and the column cut.
+template <int COLS, int NQ, int TYW>
+__device__ __forceinline__ void hsum(const float (&A)[COLS], float (&Hc)[COLS], int kl, int q) {
+  const float fromL = __shfl_up_sync(FULL, A[COLS - 1], TYW);
+  const float fromR = __shfl_down_sync(FULL, A[0], TYW);
+  const float left = (q > 0) ? fromL : 0.f;
+  const float right = (q < NQ - 1) ? fromR : 0.f;
   if constexpr (COLS == 1) {
     Hc[0] = left + A[0] + right;
   } else {
@@ -169,7 +181,7 @@ __device__ __forceinline__ void hsum(const float (&A)[COLS], float (&Hc)[COLS], 
       Hc[k + 1] = s + (k + 2 < COLS ? A[k + 2] : right);
     }
   }
-  // column cut between local columns kl and kl + 1 (warp-uniform per half)
+  // column cut between local columns kl and kl + 1 (uniform per part)
 #define NK_SEAM(m)                                                                    \
   case m:                                                                             \
     if constexpr ((m) < COLS) {                                                       \
@@ -184,7 +196,6 @@ __device__ __forceinline__ void hsum(const float (&A)[COLS], float (&Hc)[COLS], 
       Hc[0] = A[0] + (COLS > 1 ? A[COLS > 1 ? 1 : 0] : right);
       break;
       NK_SEAM(0) NK_SEAM(1) NK_SEAM(2) NK_SEAM(3) NK_SEAM(4) NK_SEAM(5) NK_SEAM(6) NK_SEAM(7)
-      NK_SEAM(8) NK_SEAM(9) NK_SEAM(10) NK_SEAM(11) NK_SEAM(12) NK_SEAM(13) NK_SEAM(14) NK_SEAM(15)
     default:
       break;
   }
@@ -236,7 +247,7 @@ __device__ __forceinline__ void scatter_row(const ScatterTo& s, int t_x, int Ty,
 }
 
 // ---------------------------------------------------------------------------
-// One warp task: super-planes (t_y in ty0 .. ty0+15, t_x) of a stage.
+// One warp task: super-planes (t_y in ty0 .. ty0+TYW-1, t_x) of a stage.
 // ---------------------------------------------------------------------------
 template <int R, int N, bool SEED, bool GAP>
 __device__ __forceinline__ void stage_task(int t_x, int ty0, const float4* __restrict__ xs,
@@ -245,13 +256,14 @@ __device__ __forceinline__ void stage_task(int t_x, int ty0, const float4* __res
                                            const float2* __restrict__ ptab,
                                            const float2* __restrict__ qtab, float b,
                                            const ScatterTo& sc, double& gap) {
-  constexpr int COLS = R / 2;
+  using SP = Split<R>;
+  constexpr int COLS = SP::COLS, NQ = SP::NQ, TYW = SP::TYW;
   constexpr int S = 2 * R + 1;
   const int lane = threadIdx.x & 31;
-  const int tyl = lane & 15, h = lane >> 4;
+  const int q = lane / TYW, tyl = lane - q * TYW;
   const bool act = tyl < R;
   const int t_y = (ty0 + tyl) & (R - 1);
-  const int c0 = h * COLS;
+  const int c0 = q * COLS;
   const int kl = (t_x == 0) ? -100 : (R - 1 - t_x) - c0;
   const bool tyodd = (t_y & 1) != 0;
 
@@ -291,7 +303,7 @@ __device__ __forceinline__ void stage_task(int t_x, int ty0, const float4* __res
       if (r > R) continue;
       float Hc[COLS];
       if (r < R) {
-        hsum<COLS>(A, Hc, kl, h);
+        hsum<COLS, NQ, TYW>(A, Hc, kl, q);
       } else {
 #pragma unroll
         for (int k = 0; k < COLS; ++k) Hc[k] = 0.f;
@@ -306,7 +318,10 @@ __device__ __forceinline__ void stage_task(int t_x, int ty0, const float4* __res
         for (int k = 0; k < COLS; ++k) {
           const float K = fmaf(e, Hc[k], Pp[j][k]) + b;
           const float2 pv = pt[k], qv = qt[k];
-          A[k] = (pv.y * qv.y) * nk_J_f32(K * (pv.x * qv.x));
+          const float c = K * (pv.x * qv.x);
+          // the first layer sees any sign; later correlations are >= 0
+          const float J = (SEED && j == 0) ? nk_J_f32(c) : nk_J01_f32(c);
+          A[k] = (pv.y * qv.y) * J;
         }
       }
       if (r < R) {
@@ -366,7 +381,7 @@ __device__ __forceinline__ void stage_q_tables(const FusedParams& P, int layer0,
 }
 
 template <int R0, int N0, int N1, int N2, int CL>
-__global__ void __launch_bounds__(256, 1) k_myrtle_fused(const __grid_constant__ FusedParams P) {
+__global__ void __launch_bounds__(NK_FUSED_THREADS, 1) k_myrtle_fused(const __grid_constant__ FusedParams P) {
   using L = Layout<R0, N0, N1, N2, CL>;
   constexpr int SE = L::SE;
   constexpr int R1 = L::R1, R2 = L::R2;
@@ -420,12 +435,12 @@ __global__ void __launch_bounds__(256, 1) k_myrtle_fused(const __grid_constant__
     double gap = 0.0;
     // ---- stage 0
     {
-      constexpr int NH = (R0 > 16) ? R0 / 16 : 1;  // warps per t_x
-      constexpr int TXC = R0 / CL;                 // t_x per CTA
+      constexpr int NH = Split<R0>::WPT;  // warps per t_x
+      constexpr int TXC = R0 / CL;        // t_x per CTA
       ScatterTo sc{b1, L::B1_sTy, L::B1_sTx, R1, L::TXL1, rank};
       for (int task = warp; task < TXC * NH; task += nwarps) {
         const int t_x = (int)rank * TXC + task / NH;
-        const int ty0 = (task % NH) * 16;
+        const int ty0 = (task % NH) * Split<R0>::TYW;
         stage_task<R0, N0, true, SE == 1>(t_x, ty0, xs, xq, nullptr, 0, p0, q0, P.sb2, sc, gap);
       }
     }
@@ -438,22 +453,26 @@ __global__ void __launch_bounds__(256, 1) k_myrtle_fused(const __grid_constant__
     if constexpr (SE >= 2) {
       if constexpr (CL > 1) cluster_sync_all(); else __syncthreads();
       constexpr int TXC = R1 / CL;
+      constexpr int NH = Split<R1>::WPT;
       ScatterTo sc{b2, L::B2_sTy, L::B2_sTx, R2, L::TXL2, rank};
-      for (int task = warp; task < TXC; task += nwarps) {
-        const int t_x = (int)rank * TXC + task;
-        const float* inb = b1 + task * L::B1_sTx;
-        stage_task<R1, N1, false, SE == 2>(t_x, 0, nullptr, nullptr, inb, L::B1_sTy, p1, q1, P.sb2,
-                                           sc, gap);
+      for (int task = warp; task < TXC * NH; task += nwarps) {
+        const int tl = task / NH;
+        const int t_x = (int)rank * TXC + tl;
+        const float* inb = b1 + tl * L::B1_sTx;
+        stage_task<R1, N1, false, SE == 2>(t_x, (task % NH) * Split<R1>::TYW, nullptr, nullptr, inb,
+                                           L::B1_sTy, p1, q1, P.sb2, sc, gap);
       }
     }
     if constexpr (SE >= 3) {
       if constexpr (CL > 1) cluster_sync_all(); else __syncthreads();
       if (rank == 0) {
         ScatterTo sc{nullptr, 0, 0, 1, 1, rank};
-        for (int task = warp; task < R2; task += nwarps) {
-          const float* inb = b2 + task * L::B2_sTx;
-          stage_task<R2, N2, false, true>(task, 0, nullptr, nullptr, inb, L::B2_sTy, p2, q2, P.sb2,
-                                          sc, gap);
+        constexpr int NH = Split<R2>::WPT;
+        for (int task = warp; task < R2 * NH; task += nwarps) {
+          const int tl = task / NH;
+          const float* inb = b2 + tl * L::B2_sTx;
+          stage_task<R2, N2, false, true>(tl, (task % NH) * Split<R2>::TYW, nullptr, nullptr, inb,
+                                          L::B2_sTy, p2, q2, P.sb2, sc, gap);
         }
       }
     }
@@ -501,7 +520,7 @@ cudaError_t launch(const FusedParams& P, int sm_count, cudaStream_t st) {
   attr[0].val.clusterDim.x = CL;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(256, 1, 1);
+  cfg.blockDim = dim3(NK_FUSED_THREADS, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cfg.attrs = attr;

@@ -1,4 +1,6 @@
 // ReLU arc-cosine map (stax.Relu in the Appendix A listings) on the device.
+// Two FP32 evaluations of J are provided (asin form below, and the
+// (1-c)^{3/2} form the kernels use).
 //
 // For a centred Gaussian pair with variances q, q' and covariance K,
 //   E[relu(u) relu(v)] = sqrt(q q') / (2 pi) * J(c),  c = K / sqrt(q q'),
@@ -40,8 +42,43 @@ __device__ __forceinline__ float nk_asin_small(float m) {
   return fmaf(m * z, p, m);
 }
 
-// J(c) in FP32; c is clamped to [-1, 1].
+// Second form used by the kernels: J(c) = pi c + (1 - c)^{3/2} B(c) on
+// [0, 1], B a degree-6 polynomial fitted by csrc/fit_jpos.py (max absolute
+// error of J 3e-9 in float64; FP32 rounding dominates on the device).  One
+// square root and 9 FMA-pipe operations.  Correlations after a ReLU layer
+// are >= 0 (a sum of non-negative terms), so every layer but the first uses
+// this form; the first uses J(c) = J(|c|) + pi min(c, 0).
+__device__ __forceinline__ float nk_B_poly(float c) {
+  float p = 3.246730975e-04f;
+  p = fmaf(p, c, -1.462184683e-03f);
+  p = fmaf(p, c, 3.599365081e-03f);
+  p = fmaf(p, c, -7.651096654e-03f);
+  p = fmaf(p, c, 1.879499484e-02f);
+  p = fmaf(p, c, -7.079588207e-02f);
+  p = fmaf(p, c, 9.999999970e-01f);
+  return p;
+}
+
+// J(c) for c >= 0 (values above 1 are clamped).
+__device__ __forceinline__ float nk_J01_f32(float c) {
+  c = fminf(c, 1.f);
+  const float u = 1.f - c;
+  const float w3 = u * nk_sqrt_approx(u);
+  return fmaf(w3, nk_B_poly(c), NK_PI_F * c);
+}
+
+// J(c) in FP32 for any c (clamped to [-1, 1]).
 __device__ __forceinline__ float nk_J_f32(float c) {
+  const float a = fminf(fabsf(c), 1.f);
+  const float u = 1.f - a;
+  const float w3 = u * nk_sqrt_approx(u);
+  const float j = fmaf(w3, nk_B_poly(a), NK_PI_F * a);
+  return fmaf(NK_PI_F, fmaxf(fminf(c, 0.f), -1.f), j);
+}
+
+// The asin-based form of J(c) (kept as an independent second evaluation for
+// tests): J(c) = pi c/2 + sqrt(1-c^2) + |c| asin|c| with the range reduction.
+__device__ __forceinline__ float nk_J_asin_f32(float c) {
   c = fminf(fmaxf(c, -1.f), 1.f);
   const float om = fmaf(-c, c, 1.f);
   const float sn = nk_sqrt_approx(om);

@@ -490,9 +490,11 @@ nk_status nk_pcg_impl(nk_handle* h, const float* K, int64_t ldk, int64_t N, cons
       }
       if (worst <= tol) { converged = true; break; }
       if (outer >= refine_max || total_it >= maxit) break;
-      // inner relative tolerance: enough to reach tol from here, not below
-      // what an FP32 matvec can resolve
-      const double eta = std::max(std::min(0.5 * tol / worst, 1e-2), 1e-6);
+      // inner relative tolerance: what is still needed to reach tol, but no
+      // tighter than 1e-4 per sweep (FP32-product CG on ill-conditioned
+      // kernels stalls long before its rounding floor; two or three
+      // refinement sweeps at 1e-4 each are cheaper) and no looser than 1e-1
+      const double eta = std::min(std::max(0.5 * tol / worst, 1e-4), 1e-1);
       int its = 0;
       e = cg_run<false>(c, c.B2, c.D, eta, maxit - total_it, &its);
       if (e != cudaSuccess) break;
