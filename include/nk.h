@@ -126,7 +126,7 @@ nk_status nk_self_diag(nk_handle* h, const nk_arch* arch, const nk_params* prm,
  *               evaluated and mirrored.
  * The Myrtle readout is K = sigma_w2 * mean_{P,P'} Kt(P, P') + sigma_b2
  * (GlobalAvgPool then Dense).  MIXED requires filter 3, ReLU, H = W in
- * {8, 16, 32}, C <= 4 and zero-conv stages only at the end; other valid
+ * {8, 16, 32}, C <= 3 and zero-conv stages only at the end; other valid
  * requests there return NK_ERR_UNSUPPORTED. */
 nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_prec prec,
                    const float* Xa, const double* qda, const float* qsa, int64_t a0, int64_t a1,

@@ -17,33 +17,34 @@
 // stream of R rows of R values, with no halo recomputation, and the R^2
 // super-planes cover the R^4 pixel pairs exactly once.
 //
-// Thread mapping: a warp owns one t_x (warp-uniform, so the column cut is
-// uniform) and 16 consecutive t_y; lane = 16 h + (t_y - ty0) with h the
-// column half.  Each thread streams the rows of its super-plane, holding its
-// R/2 columns in registers; the horizontal 3-tap sum takes one halo value from
-// the partner lane (shfl xor 16), the column cut is fixed by a warp-uniform
-// switch, and the row cut by a 0/1 factor in the vertical FFMAs.  All layers
-// of the stage are pipelined with a one-row delay per layer.  The p-side
-// tables (x, 1/sqrt q, sqrt q at row i) are warp-broadcast loads; the p'-side
-// ones are a conflict-free gather from tables doubled along columns.
+// Thread mapping: a warp owns one t_x and TYW consecutive t_y; each row of a
+// super-plane is split into NQ parts of COLS columns held in registers
+// (lane = q * TYW + t_y - ty0).  Each thread streams the rows of its
+// super-plane; the horizontal 3-tap sum takes its halo from the neighbouring
+// parts (two shuffles), the column cut and the image border enter as 0/1
+// edge factors in the FFMAs, and the row cut as a 0/1 factor in the vertical
+// FFMAs.  All layers of a stage are pipelined with a one-row delay per layer.
+// The p-side tables (x, 1/sqrt q, sqrt q at row i) are warp-broadcast loads;
+// the p'-side ones a conflict-free gather from tables doubled along columns.
 //
 // Pooling: super-plane t of stage s feeds super-plane floor/ceil(t/2) of
 // stage s+1 (odd shifts split by pixel parity); rows are paired in registers
 // and columns paired when t_x is even, the rest goes through shared-memory
 // atomics into the next stage's buffer.  At 32x32 that buffer (64K floats)
 // is distributed over a 4-CTA cluster by T_x and reached through DSMEM.  The
-// last stage is reduced into the global average.
+// last stage is reduced into the global average, combined across the
+// cluster with global FP64 atomics.
 //
 // Scale factors sw2/9, 1/(2 pi), 1/16 and 1/C are folded into the p-side
-// tables, so a conv is 1.5 adds + 2 FFMA + 1 add per pixel pair and the map
-// is ~25 FP32 instructions (nk_map.cuh).
+// tables, so a conv is 2 FFMA (horizontal) + 2 FFMA (vertical) [+ 1 add for
+// sb2] per pixel pair and the map ~15 FP32 instructions plus one square root.
 #include "nk_common.cuh"
 #include "nk_map.cuh"
 
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-#define NK_FUSED_THREADS 512
+constexpr int NTHREADS = 512;
 
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::
@@ -68,10 +69,6 @@ __device__ __forceinline__ unsigned mapa_rank(unsigned a, unsigned rank) {
 
 __device__ __forceinline__ void red_cluster_f32(unsigned a, float v) {
   asm volatile("red.shared::cluster.add.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
-}
-
-__device__ __forceinline__ void st_cluster_f64(unsigned a, double v) {
-  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
 }
 
 // Linear pair index -> (i, j) of the block; the upper triangle row by row
@@ -112,6 +109,21 @@ struct FusedParams {
   float sb2;
   double out_scale;           // sw2 / R_gap^4
   double out_bias;            // sb2
+  double* gacc;               // [2 * nclusters] global-average accumulators
+  int* gcnt;                  // [2 * nclusters] arrival counters
+};
+
+// ---------------------------------------------------------------------------
+// Thread mapping of a stage at resolution R: a row of the super-plane is split
+// into NQ parts of COLS columns; a warp holds TYW = 32 / NQ shifts t_y and the
+// NQ parts of each (lane = q * TYW + t_y - ty0).
+// ---------------------------------------------------------------------------
+template <int R>
+struct Split {
+  static constexpr int NQ = (R == 16) ? 8 : (R >= 4 ? 4 : R);
+  static constexpr int COLS = R / NQ;
+  static constexpr int TYW = 32 / NQ;
+  static constexpr int WPT = R > TYW ? R / TYW : 1;  // warps per t_x
 };
 
 // ---------------------------------------------------------------------------
@@ -145,127 +157,123 @@ struct Layout {
   // the stage-2 buffer reuses the stage-0 x' table, dead once stage 0 is done
   static constexpr size_t b2_off = xq_off;
   static_assert((size_t)B2_size * 4 <= (size_t)R0 * S0 * 16, "stage-2 buffer alias");
-  static constexpr size_t gap_off = (b1_off + (size_t)B1_size * 4 + 15) / 16 * 16;  // double[8]
-  static constexpr size_t red_off = gap_off + 8 * 8;                               // double[32]
-  static constexpr size_t bytes = red_off + 32 * 8;
+  static constexpr size_t red_off = (b1_off + (size_t)B1_size * 4 + 15) / 16 * 16;  // double[32]
+  static constexpr size_t ctr_off = red_off + 32 * 8;                             // int task counter
+  static constexpr size_t bytes = ctr_off + 16;
 };
 
 // ---------------------------------------------------------------------------
-// Thread mapping of a stage at resolution R: a row of the super-plane is split
-// into NQ parts of COLS columns; a warp holds TYW = 32 / NQ shifts t_y and the
-// NQ parts of each (lane = q * TYW + t_y - ty0).
+// Horizontal 3-tap sum of one row part.  e[k] (k = 0..COLS) is the 0/1 factor
+// of the coupling between local columns k-1 and k: 0 across the image border
+// and across the column cut, so e[0] / e[COLS] also gate the halo values.
 // ---------------------------------------------------------------------------
 template <int R>
-struct Split {
-  static constexpr int NQ = R >= 4 ? 4 : R;
-  static constexpr int COLS = R / NQ;
-  static constexpr int TYW = 32 / NQ;
-  static constexpr int WPT = R > TYW ? R / TYW : 1;  // warps per t_x
-};
-
-// Horizontal 3-tap sum of one row part with halos and the column cut.
-template <int COLS, int NQ, int TYW>
-__device__ __forceinline__ void hsum(const float (&A)[COLS], float (&Hc)[COLS], int kl, int q) {
-  const float fromL = __shfl_up_sync(FULL, A[COLS - 1], TYW);
-  const float fromR = __shfl_down_sync(FULL, A[0], TYW);
-  const float left = (q > 0) ? fromL : 0.f;
-  const float right = (q < NQ - 1) ? fromR : 0.f;
-  if constexpr (COLS == 1) {
-    Hc[0] = left + A[0] + right;
-  } else {
+__device__ __forceinline__ void make_edges(float (&e)[Split<R>::COLS + 1], int t_x, int q) {
+  constexpr int COLS = Split<R>::COLS;
+  const int c0 = q * COLS;
+  const int kc = (t_x == 0) ? -100 : R - 1 - t_x;  // cut between global columns kc, kc + 1
 #pragma unroll
-    for (int k = 0; k < COLS; k += 2) {
-      // pairwise sharing: s = A[k] + A[k+1]
-      const float s = A[k] + A[k + 1];
-      Hc[k] = (k == 0 ? left : A[k - 1]) + s;
-      Hc[k + 1] = s + (k + 2 < COLS ? A[k + 2] : right);
-    }
+  for (int k = 0; k <= COLS; ++k) {
+    const int lc = c0 + k - 1;  // edge between global columns lc and lc + 1
+    const bool off = (lc < 0) || (lc + 1 > R - 1) || (lc == kc);
+    e[k] = off ? 0.f : 1.f;
   }
-  // column cut between local columns kl and kl + 1 (uniform per part)
-#define NK_SEAM(m)                                                                    \
-  case m:                                                                             \
-    if constexpr ((m) < COLS) {                                                       \
-      Hc[m] = ((m) > 0 ? A[(m) > 0 ? (m)-1 : 0] : left) + A[m];                       \
-      if constexpr ((m) + 1 < COLS)                                                   \
-        Hc[(m) + 1 < COLS ? (m) + 1 : 0] =                                            \
-            A[(m) + 1 < COLS ? (m) + 1 : 0] + ((m) + 2 < COLS ? A[(m) + 2 < COLS ? (m) + 2 : 0] : right); \
-    }                                                                                 \
-    break;
-  switch (kl) {
-    case -1:
-      Hc[0] = A[0] + (COLS > 1 ? A[COLS > 1 ? 1 : 0] : right);
-      break;
-      NK_SEAM(0) NK_SEAM(1) NK_SEAM(2) NK_SEAM(3) NK_SEAM(4) NK_SEAM(5) NK_SEAM(6) NK_SEAM(7)
-    default:
-      break;
-  }
-#undef NK_SEAM
 }
 
-// Scatter target of the next stage's buffer (which CTA of the cluster owns
-// T_x, and the local float offset).
-struct ScatterTo {
-  float* buf;      // local base of the buffer (same offset in every CTA)
-  int sTy, sTx;    // strides
-  int R2;          // next-stage resolution
-  int txl;         // T_x per owning CTA
-  unsigned rank;   // my rank
+template <int COLS, int TYW>
+__device__ __forceinline__ void hsum(const float (&A)[COLS], float (&Hc)[COLS],
+                                     const float (&e)[COLS + 1]) {
+  const float fromL = __shfl_up_sync(FULL, A[COLS - 1], TYW);
+  const float fromR = __shfl_down_sync(FULL, A[0], TYW);
+#pragma unroll
+  for (int k = 0; k < COLS; ++k) {
+    const float l = (k == 0) ? fromL : A[k > 0 ? k - 1 : 0];
+    const float r = (k == COLS - 1) ? fromR : A[k + 1 < COLS ? k + 1 : 0];
+    Hc[k] = fmaf(e[k + 1], r, fmaf(e[k], l, A[k]));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pooling scatter into the next stage's buffer.  The buffer is laid out
+// [T_y][T_x local][I][Kx] (T_y stride padded to an odd count of floats) and
+// split over the cluster by T_x; a target T_x is resolved once per task to a
+// local pointer or a DSMEM address.
+// ---------------------------------------------------------------------------
+template <int R2_, int TXL_, int sTx_, int sTy_>
+struct OutBuf {
+  static constexpr int R2 = R2_, TXL = TXL_, sTx = sTx_, sTy = sTy_;
 };
 
-__device__ __forceinline__ void scatter_add(const ScatterTo& s, int Ty, int Tx, int I, int Kx,
-                                            float v) {
-  const int owner = Tx / s.txl;
-  const int loc = Tx - owner * s.txl;
-  float* a = s.buf + Ty * s.sTy + loc * s.sTx + I * s.R2 + Kx;
-  if ((unsigned)owner == s.rank) {
-    atomicAdd(a, v);
-  } else {
-    red_cluster_f32(mapa_rank(smem_u32(a), (unsigned)owner), v);
-  }
+struct Tgt {
+  float* ptr;
+  unsigned raddr;
+  int local;
+};
+
+template <class OB>
+__device__ __forceinline__ Tgt make_tgt(float* buf, int Tx, unsigned rank) {
+  const int owner = Tx / OB::TXL;
+  const int loc = Tx - owner * OB::TXL;
+  Tgt t;
+  t.ptr = buf + loc * OB::sTx;
+  t.local = ((unsigned)owner == rank);
+  t.raddr = t.local ? 0u : mapa_rank(smem_u32(t.ptr), (unsigned)owner);
+  return t;
+}
+
+__device__ __forceinline__ void tgt_add(const Tgt& t, int off, float v) {
+  if (t.local)
+    atomicAdd(t.ptr + off, v);
+  else
+    red_cluster_f32(t.raddr + 4u * (unsigned)off, v);
 }
 
 template <int COLS>
-__device__ __forceinline__ void scatter_row(const ScatterTo& s, int t_x, int Ty, int I, int c0,
-                                            const float (&v)[COLS]) {
-  const int R2 = s.R2;
+__device__ __forceinline__ void scatter_row(const Tgt& tE, const Tgt& tO, int t_x, int base,
+                                            int c0, const float (&v)[COLS]) {
   if constexpr (COLS % 2 == 0) {
     if ((t_x & 1) == 0) {
-      const int Tx = t_x >> 1;
 #pragma unroll
-      for (int k = 0; k < COLS; k += 2) scatter_add(s, Ty, Tx, I, (c0 + k) >> 1, v[k] + v[k + 1]);
+      for (int k = 0; k < COLS; k += 2) tgt_add(tE, base + ((c0 + k) >> 1), v[k] + v[k + 1]);
       return;
     }
   }
-  const int TxE = t_x >> 1;                    // even pixel column (odd t_x), or even t_x
-  const int TxO = ((t_x + 1) >> 1) & (R2 - 1); // odd pixel column, odd t_x
 #pragma unroll
   for (int k = 0; k < COLS; ++k) {
     const int c = c0 + k;
-    const int Tx = ((t_x & 1) && (c & 1)) ? TxO : TxE;
-    scatter_add(s, Ty, Tx, I, c >> 1, v[k]);
+    tgt_add(((t_x & 1) && (c & 1)) ? tO : tE, base + (c >> 1), v[k]);
   }
 }
 
 // ---------------------------------------------------------------------------
 // One warp task: super-planes (t_y in ty0 .. ty0+TYW-1, t_x) of a stage.
+// SEED: the input rows are the channel contraction of the two images; else
+// they are read from this stage's pooled buffer.  GAP: the last layer feeds
+// the global average, else the pooling scatter into OB.
 // ---------------------------------------------------------------------------
-template <int R, int N, bool SEED, bool GAP>
+template <int R, int N, bool SEED, bool GAP, bool BIAS, class OB>
 __device__ __forceinline__ void stage_task(int t_x, int ty0, const float4* __restrict__ xs,
                                            const float4* __restrict__ xq,
                                            const float* __restrict__ inb, int in_sTy,
                                            const float2* __restrict__ ptab,
-                                           const float2* __restrict__ qtab, float b,
-                                           const ScatterTo& sc, double& gap) {
+                                           const float2* __restrict__ qtab, float b, float* obuf,
+                                           unsigned rank, double& gap) {
   using SP = Split<R>;
-  constexpr int COLS = SP::COLS, NQ = SP::NQ, TYW = SP::TYW;
+  constexpr int COLS = SP::COLS, TYW = SP::TYW;
   constexpr int S = 2 * R + 1;
   const int lane = threadIdx.x & 31;
   const int q = lane / TYW, tyl = lane - q * TYW;
   const bool act = tyl < R;
   const int t_y = (ty0 + tyl) & (R - 1);
   const int c0 = q * COLS;
-  const int kl = (t_x == 0) ? -100 : (R - 1 - t_x) - c0;
   const bool tyodd = (t_y & 1) != 0;
+  float E[COLS + 1];
+  make_edges<R>(E, t_x, q);
+  Tgt tE{nullptr, 0u, 1}, tO{nullptr, 0u, 1};
+  if constexpr (!GAP) {
+    tE = make_tgt<OB>(obuf, t_x >> 1, rank);
+    tO = (t_x & 1) ? make_tgt<OB>(obuf, ((t_x + 1) >> 1) & (OB::R2 - 1), rank) : tE;
+  }
 
   float Hp[N][COLS], Pp[N][COLS], acc[COLS];
 #pragma unroll
@@ -285,7 +293,7 @@ __device__ __forceinline__ void stage_task(int t_x, int ty0, const float4* __res
 #pragma unroll
         for (int k = 0; k < COLS; ++k) {
           const float4 u = xa[k], w = xb[k];
-          A[k] = fmaf(u.x, w.x, fmaf(u.y, w.y, fmaf(u.z, w.z, u.w * w.w)));
+          A[k] = fmaf(u.x, w.x, fmaf(u.y, w.y, u.z * w.z));
         }
       } else {
         const float* row = inb + t_y * in_sTy + t * R + c0;
@@ -303,7 +311,7 @@ __device__ __forceinline__ void stage_task(int t_x, int ty0, const float4* __res
       if (r > R) continue;
       float Hc[COLS];
       if (r < R) {
-        hsum<COLS, NQ, TYW>(A, Hc, kl, q);
+        hsum<COLS, TYW>(A, Hc, E);
       } else {
 #pragma unroll
         for (int k = 0; k < COLS; ++k) Hc[k] = 0.f;
@@ -316,7 +324,8 @@ __device__ __forceinline__ void stage_task(int t_x, int ty0, const float4* __res
         const float2* qt = qtab + (size_t)j * R * S + pr * S + c0 + t_x;
 #pragma unroll
         for (int k = 0; k < COLS; ++k) {
-          const float K = fmaf(e, Hc[k], Pp[j][k]) + b;
+          float K = fmaf(e, Hc[k], Pp[j][k]);
+          if constexpr (BIAS) K += b;
           const float2 pv = pt[k], qv = qt[k];
           const float c = K * (pv.x * qv.x);
           // the first layer sees any sign; later correlations are >= 0
@@ -349,8 +358,10 @@ __device__ __forceinline__ void stage_task(int t_x, int ty0, const float4* __res
           float v[COLS];
 #pragma unroll
           for (int k = 0; k < COLS; ++k) v[k] = tyodd ? acc[k] : acc[k] + A[k];
-          if (act) scatter_row<COLS>(sc, t_x, t_y >> 1, I, c0, v);
-          if (act && tyodd) scatter_row<COLS>(sc, t_x, ((t_y + 1) >> 1) & (sc.R2 - 1), I, c0, A);
+          if (act) scatter_row<COLS>(tE, tO, t_x, (t_y >> 1) * OB::sTy + I * OB::R2, c0, v);
+          if (act && tyodd)
+            scatter_row<COLS>(tE, tO, t_x, (((t_y + 1) >> 1) & (OB::R2 - 1)) * OB::sTy + I * OB::R2,
+                              c0, A);
         }
       }
     }
@@ -380,11 +391,18 @@ __device__ __forceinline__ void stage_q_tables(const FusedParams& P, int layer0,
   }
 }
 
-template <int R0, int N0, int N1, int N2, int CL>
-__global__ void __launch_bounds__(NK_FUSED_THREADS, 1) k_myrtle_fused(const __grid_constant__ FusedParams P) {
+__device__ __forceinline__ float4 load_x(const float* p, int C, float s) {
+  return make_float4(p[0] * s, C > 1 ? p[1] * s : 0.f, C > 2 ? p[2] * s : 0.f, 0.f);
+}
+
+template <int R0, int N0, int N1, int N2, int CL, bool BIAS>
+__global__ void __launch_bounds__(NTHREADS, 1) k_myrtle_fused(const __grid_constant__ FusedParams P) {
   using L = Layout<R0, N0, N1, N2, CL>;
   constexpr int SE = L::SE;
   constexpr int R1 = L::R1, R2 = L::R2;
+  using OB1 = OutBuf<R1, L::TXL1, L::B1_sTx, L::B1_sTy>;
+  using OB2 = OutBuf<R2, L::TXL2, L::B2_sTx, L::B2_sTy>;
+  using OBG = OutBuf<1, 1, 0, 0>;
   extern __shared__ __align__(16) unsigned char smem[];
   float4* xs = reinterpret_cast<float4*>(smem + L::xs_off);
   float4* xq = reinterpret_cast<float4*>(smem + L::xq_off);
@@ -396,52 +414,53 @@ __global__ void __launch_bounds__(NK_FUSED_THREADS, 1) k_myrtle_fused(const __gr
   float2* q2 = reinterpret_cast<float2*>(smem + L::q2_off);
   float* b1 = reinterpret_cast<float*>(smem + L::b1_off);
   float* b2 = reinterpret_cast<float*>(smem + L::b2_off);
-  double* gap_slots = reinterpret_cast<double*>(smem + L::gap_off);
   double* red = reinterpret_cast<double*>(smem + L::red_off);
+  int* ctr = reinterpret_cast<int*>(smem + L::ctr_off);
 
   const unsigned rank = (CL > 1) ? cluster_rank() : 0u;
   const int64_t cid = blockIdx.x / CL;
   const int64_t ncl = gridDim.x / CL;
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int C = P.C;
+  int iter = 0;
 
-  for (int64_t pidx = cid; pidx < P.npairs; pidx += ncl) {
+  for (int64_t pidx = cid; pidx < P.npairs; pidx += ncl, ++iter) {
     int64_t i, j;
     pair_ij(pidx, P.na, P.nb, P.sym, &i, &j);
     const int64_t ia = P.a0 + i, ib = P.b0 + j;
-    // ---- stage tables
+    // ---- stage tables; zero this CTA's stage-1 buffer and the task counter
     {
       const float* xa = P.Xa + ia * (int64_t)R0 * R0 * C;
       const float* xb = P.Xb + ib * (int64_t)R0 * R0 * C;
-      for (int e = threadIdx.x; e < R0 * R0; e += blockDim.x) {
-        float v[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int c = 0; c < C; ++c) v[c] = xa[e * C + c] * P.xscale;
-        xs[e] = make_float4(v[0], v[1], v[2], v[3]);
-      }
+      for (int e = threadIdx.x; e < R0 * R0; e += blockDim.x) xs[e] = load_x(xa + e * C, C, P.xscale);
       for (int e = threadIdx.x; e < R0 * 2 * R0; e += blockDim.x) {
         const int row = e / (2 * R0), col = e - row * 2 * R0;
-        const float* src = xb + (row * R0 + (col & (R0 - 1))) * C;
-        float v[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int c = 0; c < C; ++c) v[c] = src[c];
-        xq[row * L::S0 + col] = make_float4(v[0], v[1], v[2], v[3]);
+        xq[row * L::S0 + col] = load_x(xb + (row * R0 + (col & (R0 - 1))) * C, C, 1.f);
       }
       stage_q_tables<R0, N0>(P, 0, ia, ib, p0, q0);
       if constexpr (SE >= 2) stage_q_tables<R1, N1>(P, N0, ia, ib, p1, q1);
       if constexpr (SE >= 3) stage_q_tables<R2, N2>(P, N0 + N1, ia, ib, p2, q2);
       for (int e = threadIdx.x; e < L::B1_size; e += blockDim.x) b1[e] = 0.f;
+      if (threadIdx.x == 0) *ctr = 0;
     }
     if constexpr (CL > 1) cluster_sync_all(); else __syncthreads();
 
     double gap = 0.0;
-    // ---- stage 0
+    // ---- stage 0: tasks (t_x, t_y group) taken from a shared counter
     {
       constexpr int NH = Split<R0>::WPT;  // warps per t_x
       constexpr int TXC = R0 / CL;        // t_x per CTA
-      ScatterTo sc{b1, L::B1_sTy, L::B1_sTx, R1, L::TXL1, rank};
-      for (int task = warp; task < TXC * NH; task += nwarps) {
+      constexpr int NT = TXC * NH;
+      for (;;) {
+        int task = 0;
+        if (lane == 0) task = atomicAdd(ctr, 1);
+        task = __shfl_sync(FULL, task, 0);
+        if (task >= NT) break;
         const int t_x = (int)rank * TXC + task / NH;
         const int ty0 = (task % NH) * Split<R0>::TYW;
-        stage_task<R0, N0, true, SE == 1>(t_x, ty0, xs, xq, nullptr, 0, p0, q0, P.sb2, sc, gap);
+        stage_task<R0, N0, true, SE == 1, BIAS, OB1>(t_x, ty0, xs, xq, nullptr, 0, p0, q0, P.sb2, b1,
+                                                     rank, gap);
       }
     }
     if constexpr (SE >= 3) {
@@ -454,73 +473,74 @@ __global__ void __launch_bounds__(NK_FUSED_THREADS, 1) k_myrtle_fused(const __gr
       if constexpr (CL > 1) cluster_sync_all(); else __syncthreads();
       constexpr int TXC = R1 / CL;
       constexpr int NH = Split<R1>::WPT;
-      ScatterTo sc{b2, L::B2_sTy, L::B2_sTx, R2, L::TXL2, rank};
       for (int task = warp; task < TXC * NH; task += nwarps) {
         const int tl = task / NH;
         const int t_x = (int)rank * TXC + tl;
         const float* inb = b1 + tl * L::B1_sTx;
-        stage_task<R1, N1, false, SE == 2>(t_x, (task % NH) * Split<R1>::TYW, nullptr, nullptr, inb,
-                                           L::B1_sTy, p1, q1, P.sb2, sc, gap);
+        stage_task<R1, N1, false, SE == 2, BIAS, OB2>(t_x, (task % NH) * Split<R1>::TYW, nullptr,
+                                                      nullptr, inb, L::B1_sTy, p1, q1, P.sb2, b2,
+                                                      rank, gap);
       }
     }
     if constexpr (SE >= 3) {
       if constexpr (CL > 1) cluster_sync_all(); else __syncthreads();
       if (rank == 0) {
-        ScatterTo sc{nullptr, 0, 0, 1, 1, rank};
         constexpr int NH = Split<R2>::WPT;
         for (int task = warp; task < R2 * NH; task += nwarps) {
           const int tl = task / NH;
           const float* inb = b2 + tl * L::B2_sTx;
-          stage_task<R2, N2, false, true>(tl, (task % NH) * Split<R2>::TYW, nullptr, nullptr, inb,
-                                          L::B2_sTy, p2, q2, P.sb2, sc, gap);
+          stage_task<R2, N2, false, true, BIAS, OBG>(tl, (task % NH) * Split<R2>::TYW, nullptr,
+                                                     nullptr, inb, L::B2_sTy, p2, q2, P.sb2, nullptr,
+                                                     rank, gap);
         }
       }
     }
-    // ---- global average: warp -> CTA -> cluster rank 0
+    // ---- global average: warp -> CTA -> cluster (global FP64 atomics; the
+    // last CTA of the cluster to arrive writes K)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) gap += __shfl_xor_sync(FULL, gap, o);
-    if ((threadIdx.x & 31) == 0) red[warp] = gap;
+    if (lane == 0) red[warp] = gap;
     __syncthreads();
     if (threadIdx.x == 0) {
       double s = 0.0;
       for (int w = 0; w < nwarps; ++w) s += red[w];
-      if constexpr (CL > 1) {
-        st_cluster_f64(mapa_rank(smem_u32(gap_slots + rank), 0u), s);
-      } else {
-        gap_slots[0] = s;
+      const int64_t slot = cid * 2 + (iter & 1);
+      double* acc = P.gacc + slot;
+      int* cnt = P.gcnt + slot;
+      atomicAdd(acc, s);
+      __threadfence();
+      const int old = atomicAdd(cnt, 1);
+      if (old == CL - 1) {
+        __threadfence();
+        const double tot = atomicAdd(acc, 0.0);
+        const float v = (float)(P.out_scale * tot + P.out_bias);
+        P.K[i * P.ldk + j] = v;
+        if (P.sym && i != j) P.K[j * P.ldk + i] = v;
+        atomicExch(reinterpret_cast<unsigned long long*>(acc), 0ull);
+        atomicExch(cnt, 0);
       }
     }
-    if constexpr (CL > 1) cluster_sync_all(); else __syncthreads();
-    if (rank == 0 && threadIdx.x == 0) {
-      double s = 0.0;
-      for (int r = 0; r < CL; ++r) s += gap_slots[r];
-      const float v = (float)(P.out_scale * s + P.out_bias);
-      P.K[i * P.ldk + j] = v;
-      if (P.sym && i != j) P.K[j * P.ldk + i] = v;
-    }
-    // buffers are re-zeroed at the top of the next pair, after every CTA has
-    // passed the barrier above
+    // the next pair's staging only touches this CTA's own tables and b1,
+    // which every warp of this CTA is done with (barrier above); remote CTAs
+    // write into b1 only after the next cluster barrier
   }
 }
 
-template <int R0, int N0, int N1, int N2, int CL>
-cudaError_t launch(const FusedParams& P, int sm_count, cudaStream_t st) {
+template <int R0, int N0, int N1, int N2, int CL, bool BIAS>
+cudaError_t launch(FusedParams P, int sm_count, void* scratch, size_t scratch_bytes,
+                   cudaStream_t st) {
   using L = Layout<R0, N0, N1, N2, CL>;
-  auto kern = k_myrtle_fused<R0, N0, N1, N2, CL>;
+  auto kern = k_myrtle_fused<R0, N0, N1, N2, CL, BIAS>;
   const size_t smem = L::bytes;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (CL > 1) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-  }
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = CL;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(NK_FUSED_THREADS, 1, 1);
+  cfg.blockDim = dim3(NTHREADS, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cfg.attrs = attr;
@@ -536,6 +556,12 @@ cudaError_t launch(const FusedParams& P, int sm_count, cudaStream_t st) {
   }
   if (nclusters > P.npairs) nclusters = (int)P.npairs;
   if (nclusters < 1) nclusters = 1;
+  const size_t need = (size_t)nclusters * 2 * (sizeof(double) + sizeof(int));
+  if (need > scratch_bytes) return cudaErrorInvalidValue;
+  P.gacc = reinterpret_cast<double*>(scratch);
+  P.gcnt = reinterpret_cast<int*>(reinterpret_cast<char*>(scratch) + (size_t)nclusters * 2 * sizeof(double));
+  e = cudaMemsetAsync(scratch, 0, need, st);
+  if (e != cudaSuccess) return e;
   cfg.gridDim = dim3((unsigned)(nclusters * CL), 1, 1);
   e = cudaLaunchKernelEx(&cfg, kern, P);
   if (e != cudaSuccess) return e;
@@ -545,7 +571,7 @@ cudaError_t launch(const FusedParams& P, int sm_count, cudaStream_t st) {
 }  // namespace
 
 bool nk_myrtle_fused_supported(const NkGeom& g) {
-  if (g.filter != 3 || g.act != NK_ACT_RELU || g.C < 1 || g.C > 4) return false;
+  if (g.filter != 3 || g.act != NK_ACT_RELU || g.C < 1 || g.C > 3) return false;
   if (g.Hs[0] != g.Ws[0]) return false;
   const int R0 = g.Hs[0];
   if (R0 != 8 && R0 != 16 && R0 != 32) return false;
@@ -557,23 +583,17 @@ bool nk_myrtle_fused_supported(const NkGeom& g) {
     }
     c[s] = g.convs[s];
   }
-  // zero-conv stages only at the end
-  if (c[1] == 0 && c[2] != 0) return false;
   const bool ok = (c[0] == 2 && c[1] == 1 && c[2] == 0) || (c[0] == 2 && c[1] == 1 && c[2] == 1) ||
                   (c[0] == 3 && c[1] == 3 && c[2] == 3) || (c[0] == 1 && c[1] == 0 && c[2] == 0) ||
                   (c[0] == 1 && c[1] == 1 && c[2] == 1);
-  if (!ok) return false;
-  if (g.n_stages < 3 && c[2] != 0) return false;
-  if (R0 == 8 && c[1] > 0 && c[2] > 0 && g.n_stages >= 3) return true;
-  return true;
+  return ok;
 }
 
 cudaError_t nk_launch_myrtle_fused(const NkGeom& g, double sw2, double sb2, const float* Xa,
                                    const float* qsa, int64_t a0, int64_t a1, const float* Xb,
                                    const float* qsb, int64_t b0, int64_t b1, float* K,
-                                   int64_t ldk, int symmetric, int sm_count,
-                                   unsigned int* dstatus, cudaStream_t st) {
-  (void)dstatus;
+                                   int64_t ldk, int symmetric, int sm_count, void* scratch,
+                                   size_t scratch_bytes, cudaStream_t st) {
   if (!nk_myrtle_fused_supported(g)) return cudaErrorNotSupported;
   FusedParams P = {};
   P.Xa = Xa;
@@ -612,8 +632,11 @@ cudaError_t nk_launch_myrtle_fused(const NkGeom& g, double sw2, double sb2, cons
   P.out_scale = sw2 / ((double)Rg * Rg * Rg * Rg);
   P.out_bias = sb2;
   const int R0 = g.Hs[0];
-#define NK_DISPATCH(RR, A0, A1, A2, CLL) \
-  if (R0 == RR && c[0] == A0 && c[1] == A1 && c[2] == A2) return launch<RR, A0, A1, A2, CLL>(P, sm_count, st);
+  const bool bias = (sb2 != 0.0);
+#define NK_DISPATCH(RR, A0, A1, A2, CLL)                                                     \
+  if (R0 == RR && c[0] == A0 && c[1] == A1 && c[2] == A2)                                    \
+    return bias ? launch<RR, A0, A1, A2, CLL, true>(P, sm_count, scratch, scratch_bytes, st) \
+                : launch<RR, A0, A1, A2, CLL, false>(P, sm_count, scratch, scratch_bytes, st);
   NK_DISPATCH(32, 2, 1, 0, 4)
   NK_DISPATCH(32, 2, 1, 1, 4)
   NK_DISPATCH(32, 3, 3, 3, 4)

@@ -115,9 +115,11 @@ nk_status nk_create(nk_handle** out) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
   if (e == cudaSuccess) e = cudaMalloc(&h->dstatus, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(h->dstatus, 0, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&h->small_ws, 65536);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     if (h->dstatus) cudaFree(h->dstatus);
+    if (h->small_ws) cudaFree(h->small_ws);
     delete h;
     return e == cudaErrorMemoryAllocation ? NK_ERR_NO_MEMORY : NK_ERR_CUDA;
   }
@@ -130,6 +132,7 @@ void nk_destroy(nk_handle* h) {
   if (h->ws) cudaFree(h->ws);
   if (h->pcg_ws) cudaFree(h->pcg_ws);
   if (h->dstatus) cudaFree(h->dstatus);
+  if (h->small_ws) cudaFree(h->small_ws);
   delete h;
 }
 
@@ -216,11 +219,11 @@ nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_p
   if (prec == NK_PREC_MIXED) {
     if (!nk_myrtle_fused_supported(g))
       return nk_fail(h, NK_ERR_UNSUPPORTED,
-                     "nk_block MIXED: needs filter 3, ReLU, H == W in {8,16,32}, C <= 4 and one of "
+                     "nk_block MIXED: needs filter 3, ReLU, H == W in {8,16,32}, C <= 3 and one of "
                      "the stage patterns (2,1,0) (2,1,1) (3,3,3) (1) (1,1,1)");
     h->launches += 1;
     cudaError_t e = nk_launch_myrtle_fused(g, prm->sigma_w2, prm->sigma_b2, Xa, qsa, a0, a1, Xb, qsb, b0,
-                                           b1, (float*)K, ldk, symmetric, h->sm_count, h->dstatus, st);
+                                           b1, (float*)K, ldk, symmetric, h->sm_count, h->small_ws, 65536, st);
     return nk_cuda_check(h, e, "nk_block fused launch");
   }
   const int fp64 = (prec == NK_PREC_PLAIN_FP64);

@@ -46,6 +46,7 @@ struct nk_handle {
   int device;
   int64_t launches;        // kernels launched through this handle
   double last_lambda;      // ridge used by the last nk_pcg_solve
+  void* small_ws;          // 64 KB for per-launch counters / accumulators
   // PCG scratch
   void* pcg_ws;
   size_t pcg_bytes;
@@ -66,8 +67,8 @@ size_t nk_self_diag_ws_per_cta(const NkGeom& g);
 cudaError_t nk_launch_myrtle_fused(const NkGeom& g, double sw2, double sb2, const float* Xa,
                                    const float* qsa, int64_t a0, int64_t a1, const float* Xb,
                                    const float* qsb, int64_t b0, int64_t b1, float* K,
-                                   int64_t ldk, int symmetric, int sm_count,
-                                   unsigned int* dstatus, cudaStream_t st);
+                                   int64_t ldk, int symmetric, int sm_count, void* scratch,
+                                   size_t scratch_bytes, cudaStream_t st);
 bool nk_myrtle_fused_supported(const NkGeom& g);
 
 // Plain layer-wise Myrtle block (FP32 or FP64).
