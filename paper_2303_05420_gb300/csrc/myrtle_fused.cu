@@ -44,7 +44,7 @@
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int NTHREADS = 512;
+constexpr int NTHREADS = 768;
 
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::
@@ -120,7 +120,7 @@ struct FusedParams {
 // ---------------------------------------------------------------------------
 template <int R>
 struct Split {
-  static constexpr int NQ = (R == 16) ? 8 : (R >= 4 ? 4 : R);
+  static constexpr int NQ = (R >= 16) ? 8 : (R >= 4 ? 4 : R);
   static constexpr int COLS = R / NQ;
   static constexpr int TYW = 32 / NQ;
   static constexpr int WPT = R > TYW ? R / TYW : 1;  // warps per t_x
