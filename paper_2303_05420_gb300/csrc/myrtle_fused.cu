@@ -205,43 +205,64 @@ struct OutBuf {
 };
 
 struct Tgt {
-  float* ptr;
-  unsigned raddr;
+  unsigned addr;  // 32-bit shared address (own window) or shared::cluster address
   int local;
 };
+
+__device__ __forceinline__ void red_shared_f32(unsigned a, float v) {
+  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
 
 template <class OB>
 __device__ __forceinline__ Tgt make_tgt(float* buf, int Tx, unsigned rank) {
   const int owner = Tx / OB::TXL;
   const int loc = Tx - owner * OB::TXL;
   Tgt t;
-  t.ptr = buf + loc * OB::sTx;
+  const unsigned a = smem_u32(buf + loc * OB::sTx);
   t.local = ((unsigned)owner == rank);
-  t.raddr = t.local ? 0u : mapa_rank(smem_u32(t.ptr), (unsigned)owner);
+  t.addr = t.local ? a : mapa_rank(a, (unsigned)owner);
   return t;
 }
 
-__device__ __forceinline__ void tgt_add(const Tgt& t, int off, float v) {
-  if (t.local)
-    atomicAdd(t.ptr + off, v);
-  else
-    red_cluster_f32(t.raddr + 4u * (unsigned)off, v);
-}
-
+// Adds one pooled row part.  Whether the targets are in this CTA is uniform
+// over the warp (t_x is), so the branch is taken once per row.
 template <int COLS>
 __device__ __forceinline__ void scatter_row(const Tgt& tE, const Tgt& tO, int t_x, int base,
                                             int c0, const float (&v)[COLS]) {
+  const bool even = (t_x & 1) == 0;
   if constexpr (COLS % 2 == 0) {
-    if ((t_x & 1) == 0) {
+    if (even) {
+      const unsigned a = tE.addr + 4u * (unsigned)(base + (c0 >> 1));
+      if (tE.local) {
 #pragma unroll
-      for (int k = 0; k < COLS; k += 2) tgt_add(tE, base + ((c0 + k) >> 1), v[k] + v[k + 1]);
+        for (int k = 0; k < COLS; k += 2) red_shared_f32(a + 2u * k, v[k] + v[k + 1]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < COLS; k += 2) red_cluster_f32(a + 2u * k, v[k] + v[k + 1]);
+      }
       return;
     }
   }
+  // odd t_x (or a single column): even pixel columns go to tE, odd to tO
+  const unsigned aE = tE.addr + 4u * (unsigned)base;
+  const unsigned aO = tO.addr + 4u * (unsigned)base;
+  if (tE.local && tO.local) {
 #pragma unroll
-  for (int k = 0; k < COLS; ++k) {
-    const int c = c0 + k;
-    tgt_add(((t_x & 1) && (c & 1)) ? tO : tE, base + (c >> 1), v[k]);
+    for (int k = 0; k < COLS; ++k) {
+      const int c = c0 + k;
+      red_shared_f32(((!even && (c & 1)) ? aO : aE) + 4u * (unsigned)(c >> 1), v[k]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < COLS; ++k) {
+      const int c = c0 + k;
+      const bool o = !even && (c & 1);
+      const unsigned a = (o ? aO : aE) + 4u * (unsigned)(c >> 1);
+      if (o ? tO.local : tE.local)
+        red_shared_f32(a, v[k]);
+      else
+        red_cluster_f32(a, v[k]);
+    }
   }
 }
 
@@ -250,7 +271,169 @@ __device__ __forceinline__ void scatter_row(const Tgt& tE, const Tgt& tO, int t_
 // SEED: the input rows are the channel contraction of the two images; else
 // they are read from this stage's pooled buffer.  GAP: the last layer feeds
 // the global average, else the pooling scatter into OB.
+//
+// Row stream: at step t the input row t enters layer 0 and layer j finishes
+// row t - j - 1.  Steps [0, N) fill the pipeline and [R, R + N) drain it;
+// in the steady steps [N, R) every layer is active, so they run without
+// per-layer conditions, two at a time (the pooling pairs rows).
 // ---------------------------------------------------------------------------
+template <int R, int N, bool SEED, bool GAP, bool BIAS, class OB>
+struct Task {
+  using SP = Split<R>;
+  static constexpr int COLS = SP::COLS, TYW = SP::TYW;
+  static constexpr int S = 2 * R + 1;
+  int t_x, t_y, c0;
+  bool act, tyodd;
+  float E[COLS + 1];
+  float Hp[N][COLS], Pp[N][COLS], acc[COLS];
+  Tgt tE, tO;
+  const float4* xs;
+  const float4* xq;
+  const float* inrow;  // this thread's super-plane in the pooled input buffer
+  const float2* ptab;
+  const float2* qtab;
+  float b;
+
+  __device__ __forceinline__ void input_row(int t, float (&A)[COLS]) const {
+    if constexpr (SEED) {
+      const int pr = (t + t_y) & (R - 1);
+      const float4* xa = xs + t * R + c0;
+      const float4* xb = xq + pr * S + c0 + t_x;
+#pragma unroll
+      for (int k = 0; k < COLS; ++k) {
+        const float4 u = xa[k], w = xb[k];
+        A[k] = fmaf(u.x, w.x, fmaf(u.y, w.y, u.z * w.z));
+      }
+    } else {
+      const float* row = inrow + t * R;
+#pragma unroll
+      for (int k = 0; k < COLS; ++k) A[k] = row[k];
+    }
+  }
+
+  // layer j receives row r (r in [0, R)) and finishes row r - 1 (r >= 1)
+  template <int j, bool FIN>
+  __device__ __forceinline__ void layer(int r, float (&A)[COLS]) {
+    float Hc[COLS];
+    hsum<COLS, TYW>(A, Hc, E);
+    const float e = (r != R - t_y) ? 1.f : 0.f;  // edge (r-1, r) not cut
+    if (FIN) finish<j>(r - 1, e, Hc, A);
+#pragma unroll
+    for (int k = 0; k < COLS; ++k) {
+      Pp[j][k] = fmaf(e, Hp[j][k], Hc[k]);
+      Hp[j][k] = Hc[k];
+    }
+  }
+
+  // finish row ro of layer j: vertical sum, bias, ReLU map -> A
+  template <int j>
+  __device__ __forceinline__ void finish(int ro, float e, const float (&Hc)[COLS], float (&A)[COLS]) {
+    const int pr = (ro + t_y) & (R - 1);
+    const float2* pt = ptab + j * R * R + ro * R + c0;
+    const float2* qt = qtab + j * R * S + pr * S + c0 + t_x;
+#pragma unroll
+    for (int k = 0; k < COLS; ++k) {
+      float K = fmaf(e, Hc[k], Pp[j][k]);
+      if constexpr (BIAS) K += b;
+      const float2 pv = pt[k], qv = qt[k];
+      const float c = K * (pv.x * qv.x);
+      // the first layer sees any sign; later correlations are >= 0
+      const float J = (SEED && j == 0) ? nk_J_f32(c) : nk_J01_f32(c);
+      A[k] = (pv.y * qv.y) * J;
+    }
+  }
+
+  // the drain: layer j finishes row R - 1 with no row below
+  template <int j>
+  __device__ __forceinline__ void finish_last(float (&A)[COLS]) {
+    float Hz[COLS];
+#pragma unroll
+    for (int k = 0; k < COLS; ++k) Hz[k] = 0.f;
+    finish<j>(R - 1, 0.f, Hz, A);
+  }
+
+  template <int PAR>
+  __device__ __forceinline__ void output(int ro, const float (&A)[COLS], double& gap) {
+    if constexpr (GAP) {
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < COLS; ++k) s += A[k];
+      if (act) gap += (double)s;
+    } else if constexpr (PAR == 0) {
+#pragma unroll
+      for (int k = 0; k < COLS; ++k) acc[k] = A[k];
+    } else {
+      const int I = ro >> 1;
+      float v[COLS];
+#pragma unroll
+      for (int k = 0; k < COLS; ++k) v[k] = tyodd ? acc[k] : acc[k] + A[k];
+      if (act) scatter_row<COLS>(tE, tO, t_x, (t_y >> 1) * OB::sTy + I * OB::R2, c0, v);
+      if (act && tyodd)
+        scatter_row<COLS>(tE, tO, t_x, (((t_y + 1) >> 1) & (OB::R2 - 1)) * OB::sTy + I * OB::R2, c0, A);
+    }
+  }
+
+  // layers j0 .. j1-1 receive their rows (t - j) and finish the previous ones
+  template <int j0, int j1>
+  __device__ __forceinline__ void layers_fin(int t, float (&A)[COLS]) {
+    if constexpr (j0 < j1) {
+      layer<j0, true>(t - j0, A);
+      layers_fin<j0 + 1, j1>(t, A);
+    }
+  }
+
+  // pipeline fill, step T < N: layers 0..T-1 finish rows, layer T gets row 0
+  template <int T>
+  __device__ __forceinline__ void fill() {
+    if constexpr (T < N) {
+      float A[COLS];
+      input_row(T, A);
+      layers_fin<0, T>(T, A);
+      layer<T, false>(0, A);
+      fill<T + 1>();
+    }
+  }
+
+  // steady step t in [N, R): every layer active; output row t - N
+  template <int PAR>
+  __device__ __forceinline__ void steady(int t, double& gap) {
+    float A[COLS];
+    input_row(t, A);
+    layers_fin<0, N>(t, A);
+    output<PAR>(t - N, A, gap);
+  }
+
+  // pipeline drain, step t = R + D: layer D finishes row R - 1, later layers
+  // get their remaining rows; output row R + D - N
+  template <int D>
+  __device__ __forceinline__ void drain(double& gap) {
+    if constexpr (D < N) {
+      float A[COLS];
+#pragma unroll
+      for (int k = 0; k < COLS; ++k) A[k] = 0.f;
+      finish_last<D>(A);
+      layers_fin<D + 1, N>(R + D, A);
+      output<((R + D - N) & 1)>(R + D - N, A, gap);
+      drain<D + 1>(gap);
+    }
+  }
+
+  __device__ __forceinline__ void run(double& gap) {
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+#pragma unroll
+      for (int k = 0; k < COLS; ++k) Hp[j][k] = Pp[j][k] = 0.f;
+    fill<0>();
+    int t = N;
+    for (; t + 1 < R; t += 2) {
+      steady<0>(t, gap);
+      steady<1>(t + 1, gap);
+    }
+    if (t < R) steady<0>(t, gap);
+    drain<0>(gap);
+  }
+};
+
 template <int R, int N, bool SEED, bool GAP, bool BIAS, class OB>
 __device__ __forceinline__ void stage_task(int t_x, int ty0, const float4* __restrict__ xs,
                                            const float4* __restrict__ xq,
@@ -258,114 +441,30 @@ __device__ __forceinline__ void stage_task(int t_x, int ty0, const float4* __res
                                            const float2* __restrict__ ptab,
                                            const float2* __restrict__ qtab, float b, float* obuf,
                                            unsigned rank, double& gap) {
-  using SP = Split<R>;
-  constexpr int COLS = SP::COLS, TYW = SP::TYW;
-  constexpr int S = 2 * R + 1;
+  using TK = Task<R, N, SEED, GAP, BIAS, OB>;
+  constexpr int TYW = TK::TYW;
+  TK T;
   const int lane = threadIdx.x & 31;
   const int q = lane / TYW, tyl = lane - q * TYW;
-  const bool act = tyl < R;
-  const int t_y = (ty0 + tyl) & (R - 1);
-  const int c0 = q * COLS;
-  const bool tyodd = (t_y & 1) != 0;
-  float E[COLS + 1];
-  make_edges<R>(E, t_x, q);
-  Tgt tE{nullptr, 0u, 1}, tO{nullptr, 0u, 1};
+  T.t_x = t_x;
+  T.act = tyl < R;
+  T.t_y = (ty0 + tyl) & (R - 1);
+  T.c0 = q * TK::COLS;
+  T.tyodd = (T.t_y & 1) != 0;
+  make_edges<R>(T.E, t_x, q);
+  T.tE = Tgt{0u, 1};
+  T.tO = Tgt{0u, 1};
   if constexpr (!GAP) {
-    tE = make_tgt<OB>(obuf, t_x >> 1, rank);
-    tO = (t_x & 1) ? make_tgt<OB>(obuf, ((t_x + 1) >> 1) & (OB::R2 - 1), rank) : tE;
+    T.tE = make_tgt<OB>(obuf, t_x >> 1, rank);
+    T.tO = (t_x & 1) ? make_tgt<OB>(obuf, ((t_x + 1) >> 1) & (OB::R2 - 1), rank) : T.tE;
   }
-
-  float Hp[N][COLS], Pp[N][COLS], acc[COLS];
-#pragma unroll
-  for (int j = 0; j < N; ++j)
-#pragma unroll
-    for (int k = 0; k < COLS; ++k) Hp[j][k] = Pp[j][k] = 0.f;
-#pragma unroll
-  for (int k = 0; k < COLS; ++k) acc[k] = 0.f;
-
-  for (int t = 0; t < R + N; ++t) {
-    float A[COLS];
-    if (t < R) {
-      if constexpr (SEED) {
-        const int pr = (t + t_y) & (R - 1);
-        const float4* xa = xs + t * R + c0;
-        const float4* xb = xq + pr * S + c0 + t_x;
-#pragma unroll
-        for (int k = 0; k < COLS; ++k) {
-          const float4 u = xa[k], w = xb[k];
-          A[k] = fmaf(u.x, w.x, fmaf(u.y, w.y, u.z * w.z));
-        }
-      } else {
-        const float* row = inb + t_y * in_sTy + t * R + c0;
-#pragma unroll
-        for (int k = 0; k < COLS; ++k) A[k] = row[k];
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < COLS; ++k) A[k] = 0.f;
-    }
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      const int r = t - j;  // row entering layer j at this step
-      if (r < 0) break;
-      if (r > R) continue;
-      float Hc[COLS];
-      if (r < R) {
-        hsum<COLS, TYW>(A, Hc, E);
-      } else {
-#pragma unroll
-        for (int k = 0; k < COLS; ++k) Hc[k] = 0.f;
-      }
-      const float e = (r != R - t_y) ? 1.f : 0.f;  // edge (r-1, r) not cut
-      if (r >= 1) {
-        const int ro = r - 1;
-        const int pr = (ro + t_y) & (R - 1);
-        const float2* pt = ptab + (size_t)j * R * R + ro * R + c0;
-        const float2* qt = qtab + (size_t)j * R * S + pr * S + c0 + t_x;
-#pragma unroll
-        for (int k = 0; k < COLS; ++k) {
-          float K = fmaf(e, Hc[k], Pp[j][k]);
-          if constexpr (BIAS) K += b;
-          const float2 pv = pt[k], qv = qt[k];
-          const float c = K * (pv.x * qv.x);
-          // the first layer sees any sign; later correlations are >= 0
-          const float J = (SEED && j == 0) ? nk_J_f32(c) : nk_J01_f32(c);
-          A[k] = (pv.y * qv.y) * J;
-        }
-      }
-      if (r < R) {
-#pragma unroll
-        for (int k = 0; k < COLS; ++k) {
-          Pp[j][k] = fmaf(e, Hp[j][k], Hc[k]);
-          Hp[j][k] = Hc[k];
-        }
-      }
-      if (r == 0) break;
-    }
-    const int ro = t - N;  // output row of the last layer at this step
-    if (ro >= 0 && ro < R) {
-      if constexpr (GAP) {
-        float s = 0.f;
-#pragma unroll
-        for (int k = 0; k < COLS; ++k) s += A[k];
-        if (act) gap += (double)s;
-      } else {
-        if ((ro & 1) == 0) {
-#pragma unroll
-          for (int k = 0; k < COLS; ++k) acc[k] = A[k];
-        } else {
-          const int I = ro >> 1;
-          float v[COLS];
-#pragma unroll
-          for (int k = 0; k < COLS; ++k) v[k] = tyodd ? acc[k] : acc[k] + A[k];
-          if (act) scatter_row<COLS>(tE, tO, t_x, (t_y >> 1) * OB::sTy + I * OB::R2, c0, v);
-          if (act && tyodd)
-            scatter_row<COLS>(tE, tO, t_x, (((t_y + 1) >> 1) & (OB::R2 - 1)) * OB::sTy + I * OB::R2,
-                              c0, A);
-        }
-      }
-    }
-  }
+  T.xs = xs;
+  T.xq = xq;
+  T.inrow = SEED ? nullptr : inb + T.t_y * in_sTy + T.c0;
+  T.ptab = ptab;
+  T.qtab = qtab;
+  T.b = b;
+  T.run(gap);
 }
 
 // ---------------------------------------------------------------------------
