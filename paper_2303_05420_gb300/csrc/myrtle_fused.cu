@@ -418,11 +418,55 @@ struct Task {
     }
   }
 
+  // Generic step t (any R, N): layer j handles r = t - j when 0 <= r <= R.
+  template <int j>
+  __device__ __forceinline__ void gen_layers(int t, float (&A)[COLS]) {
+    if constexpr (j < N) {
+      const int r = t - j;
+      if (r < 0) return;
+      if (r <= R) {
+        if (r == R)
+          finish_last<j>(A);
+        else if (r >= 1)
+          layer<j, true>(r, A);
+        else
+          layer<j, false>(r, A);
+        if (r == 0) return;
+      }
+      gen_layers<j + 1>(t, A);
+    }
+  }
+
+  __device__ __forceinline__ void generic_run(double& gap) {
+    for (int t = 0; t < R + N; ++t) {
+      float A[COLS];
+      if (t < R) {
+        input_row(t, A);
+      } else {
+#pragma unroll
+        for (int k = 0; k < COLS; ++k) A[k] = 0.f;
+      }
+      gen_layers<0>(t, A);
+      const int ro = t - N;
+      if (ro >= 0 && ro < R) {
+        if (ro & 1)
+          output<1>(ro, A, gap);
+        else
+          output<0>(ro, A, gap);
+      }
+    }
+  }
+
   __device__ __forceinline__ void run(double& gap) {
 #pragma unroll
     for (int j = 0; j < N; ++j)
 #pragma unroll
       for (int k = 0; k < COLS; ++k) Hp[j][k] = Pp[j][k] = 0.f;
+    if constexpr (N > R) {
+      // tiny last stages (R = 2 with three layers): no steady state
+      generic_run(gap);
+      return;
+    }
     fill<0>();
     int t = N;
     for (; t + 1 < R; t += 2) {
