@@ -133,6 +133,24 @@ nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_p
                    const float* Xb, const double* qdb, const float* qsb, int64_t b0, int64_t b1,
                    int H, int W, int C, void* K, int64_t ldk, int symmetric, void* stream);
 
+/* Autotuner for the fused (NK_PREC_MIXED) kernel, the block-tile queue's
+ * launch shape (Figure 1, top: blocks are "batched further" to fit the
+ * device).  Times each launch variant of the fused kernel for this
+ * architecture, image size, channel count and sigma_b2 == 0 or not, on a
+ * synthetic 12 x 12 block of hashed images (allocated and freed here), and
+ * caches the fastest in the handle; later nk_block calls with the same key
+ * use it (without a tuned entry, variant 0).  Variants at 32x32: 0 = 768
+ * threads x 8 row parts, 1 = 512 x 8, 2 = 512 x 4; other sizes have one.
+ * *variant (may be NULL) receives the choice.  Synchronises `stream`. */
+nk_status nk_autotune(nk_handle* h, const nk_arch* arch, const nk_params* prm, int H, int W, int C,
+                      int* variant, void* stream);
+
+/* Pins the fused-kernel launch variant for a key without timing (e.g. a
+ * choice saved from an earlier nk_autotune).  NK_ERR_INVALID_ARG for a
+ * variant this size does not have. */
+nk_status nk_autotune_set(nk_handle* h, const nk_arch* arch, const nk_params* prm, int H, int W, int C,
+                          int variant);
+
 /* Kernel-ridge solve (K + lambda I) A = Y by Jacobi-preconditioned CG, one CG
  * per column run in lock-step (Section 2 "Iterative solvers"; Appendix B.3).
  *   K [N][ldk] float32 (device, symmetric), Y [N][R] float64 (device, row

@@ -82,6 +82,24 @@ class Handle:
         self.check(st, "nk_self_diag")
         return qd, qs
 
+    def autotune(self, convs: Sequence[int], sw2: float, sb2: float, H: int, W: int, C: int = 3,
+                 filt: int = 3) -> int:
+        """Times the fused-kernel launch variants for this shape; caches and
+        returns the chosen variant."""
+        a = make_arch(convs, filt)
+        p = make_params(sw2, sb2)
+        v = c_int(0)
+        st = lib().nk_autotune(self._h, byref(a), byref(p), H, W, C, byref(v), c_void_p(_stream()))
+        self.check(st, "nk_autotune")
+        return v.value
+
+    def autotune_set(self, convs: Sequence[int], sw2: float, sb2: float, H: int, W: int, variant: int,
+                     C: int = 3, filt: int = 3):
+        a = make_arch(convs, filt)
+        p = make_params(sw2, sb2)
+        self.check(lib().nk_autotune_set(self._h, byref(a), byref(p), H, W, C, int(variant)),
+                   "nk_autotune_set")
+
     def block(self, Xa: torch.Tensor, qa: Tuple[torch.Tensor, torch.Tensor], Xb: torch.Tensor,
               qb: Tuple[torch.Tensor, torch.Tensor], convs: Sequence[int], sw2: float, sb2: float,
               prec: str = "mixed", a_range=None, b_range=None, symmetric: bool = False,

@@ -90,6 +90,52 @@ bool nk_make_geom(const nk_arch* arch, int H, int W, int C, NkGeom* g, const cha
   return true;
 }
 
+namespace {
+
+void tune_key(const NkGeom& g, bool bias, int* key) {
+  key[0] = g.n_stages > 0 ? g.convs[0] : 0;
+  key[1] = g.n_stages > 1 ? g.convs[1] : 0;
+  key[2] = g.n_stages > 2 ? g.convs[2] : 0;
+  key[3] = g.n_stages;
+  key[4] = g.Hs[0];
+  key[5] = g.Ws[0];
+  key[6] = g.C;
+  key[7] = bias ? 1 : 0;
+}
+
+int tune_lookup(const nk_handle* h, const int* key) {
+  for (int i = 0; i < h->tune_n; ++i)
+    if (memcmp(h->tune_key[i], key, sizeof(int) * 8) == 0) return h->tune_variant[i];
+  return 0;
+}
+
+void tune_store(nk_handle* h, const int* key, int v) {
+  for (int i = 0; i < h->tune_n; ++i)
+    if (memcmp(h->tune_key[i], key, sizeof(int) * 8) == 0) {
+      h->tune_variant[i] = v;
+      return;
+    }
+  const int i = (h->tune_n < 16) ? h->tune_n++ : 15;
+  memcpy(h->tune_key[i], key, sizeof(int) * 8);
+  h->tune_variant[i] = v;
+}
+
+// Synthetic images for timing: a counter hash mapped to [-1.7, 1.7].
+__global__ void k_synth_images(float* x, int64_t n, uint32_t seed) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t v = (uint32_t)i * 0x9E3779B1u ^ seed;
+    v ^= v >> 16;
+    v *= 0x85EBCA6Bu;
+    v ^= v >> 13;
+    v *= 0xC2B2AE35u;
+    v ^= v >> 16;
+    x[i] = ((float)(v >> 8) * (1.0f / 16777216.0f) - 0.5f) * 3.4f;
+  }
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* nk_status_string(nk_status s) {
@@ -221,9 +267,12 @@ nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_p
       return nk_fail(h, NK_ERR_UNSUPPORTED,
                      "nk_block MIXED: needs filter 3, ReLU, H == W in {8,16,32}, C <= 3 and one of "
                      "the stage patterns (2,1,0) (2,1,1) (3,3,3) (1) (1,1,1)");
+    int key[8];
+    tune_key(g, prm->sigma_b2 != 0.0, key);
     h->launches += 1;
     cudaError_t e = nk_launch_myrtle_fused(g, prm->sigma_w2, prm->sigma_b2, Xa, qsa, a0, a1, Xb, qsb, b0,
-                                           b1, (float*)K, ldk, symmetric, h->sm_count, h->small_ws, 65536, st);
+                                           b1, (float*)K, ldk, symmetric, h->sm_count, h->small_ws, 65536,
+                                           tune_lookup(h, key), st);
     return nk_cuda_check(h, e, "nk_block fused launch");
   }
   const int fp64 = (prec == NK_PREC_PLAIN_FP64);
@@ -240,6 +289,100 @@ nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_p
                                          qdb, qsb, b0, b1, K, ldk, symmetric, ws, chunk, h->dstatus, st,
                                          &h->launches);
   return nk_cuda_check(h, e, "nk_block plain launch");
+}
+
+nk_status nk_autotune(nk_handle* h, const nk_arch* arch, const nk_params* prm, int H, int W, int C,
+                      int* variant, void* stream) {
+  if (!h) return NK_ERR_INVALID_ARG;
+  NkGeom g;
+  const char* why = nullptr;
+  if (!nk_make_geom(arch, H, W, C, &g, &why)) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_autotune: %s", why);
+  if (!prm || !(prm->sigma_w2 >= 0.0) || !(prm->sigma_b2 >= 0.0))
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_autotune: bad params");
+  if (!nk_myrtle_fused_supported(g))
+    return nk_fail(h, NK_ERR_UNSUPPORTED, "nk_autotune: no fused kernel for this architecture / size");
+  int key[8];
+  tune_key(g, prm->sigma_b2 != 0.0, key);
+  const int nvar = (g.Hs[0] == 32) ? NK_FUSED_VARIANTS : 1;
+  if (nvar == 1) {
+    tune_store(h, key, 0);
+    if (variant) *variant = 0;
+    return NK_OK;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // synthetic block: na x nb pairs, about four pairs per 4-CTA cluster
+  const int na = 12, nb = 12, n = na + nb;
+  const size_t nimg = (size_t)n * H * W * C;
+  float* X = nullptr;
+  double* qd = nullptr;
+  float* qs = nullptr;
+  float* K = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  nk_status ret = NK_OK;
+  cudaError_t e = cudaMalloc(&X, nimg * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&qd, (size_t)n * g.nq * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&qs, (size_t)n * g.nq * 2 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&K, (size_t)na * nb * sizeof(float));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  int best = 0;
+  if (e == cudaSuccess) {
+    ++h->launches;
+    k_synth_images<<<64, 256, 0, st>>>(X, (int64_t)nimg, 0x1234567u);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    nk_status s = nk_self_diag(h, arch, prm, X, n, H, W, C, qd, qs, stream);
+    if (s != NK_OK) ret = s;
+  }
+  float best_ms = 1e30f;
+  for (int v = 0; v < nvar && e == cudaSuccess && ret == NK_OK; ++v) {
+    float ms_min = 1e30f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+      e = cudaEventRecord(e0, st);
+      ++h->launches;
+      if (e == cudaSuccess)
+        e = nk_launch_myrtle_fused(g, prm->sigma_w2, prm->sigma_b2, X, qs, 0, na, X, qs, na, n, K, nb, 0,
+                                   h->sm_count, h->small_ws, 65536, v, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0 && ms < ms_min) ms_min = ms;  // first run warms up
+    }
+    if (e == cudaSuccess && ms_min < best_ms) {
+      best_ms = ms_min;
+      best = v;
+    }
+  }
+  if (e != cudaSuccess && ret == NK_OK) ret = nk_cuda_check(h, e, "nk_autotune");
+  if (ret == NK_OK) {
+    tune_store(h, key, best);
+    if (variant) *variant = best;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(X);
+  cudaFree(qd);
+  cudaFree(qs);
+  cudaFree(K);
+  return ret;
+}
+
+nk_status nk_autotune_set(nk_handle* h, const nk_arch* arch, const nk_params* prm, int H, int W, int C,
+                          int variant) {
+  if (!h) return NK_ERR_INVALID_ARG;
+  NkGeom g;
+  const char* why = nullptr;
+  if (!nk_make_geom(arch, H, W, C, &g, &why)) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_autotune_set: %s", why);
+  if (!prm) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_autotune_set: params is NULL");
+  const int nvar = (g.Hs[0] == 32) ? NK_FUSED_VARIANTS : 1;
+  if (variant < 0 || variant >= nvar)
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_autotune_set: variant outside 0..%d", nvar - 1);
+  int key[8];
+  tune_key(g, prm->sigma_b2 != 0.0, key);
+  tune_store(h, key, variant);
+  return NK_OK;
 }
 
 nk_status nk_pcg_solve(nk_handle* h, const float* K, int64_t ldk, int64_t N, const double* Y, int R,

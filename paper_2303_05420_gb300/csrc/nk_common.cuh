@@ -47,6 +47,10 @@ struct nk_handle {
   int64_t launches;        // kernels launched through this handle
   double last_lambda;      // ridge used by the last nk_pcg_solve
   void* small_ws;          // 64 KB for per-launch counters / accumulators
+  // autotune cache: fused-kernel launch variant per (stage pattern, size, C, bias)
+  int tune_n;
+  int tune_key[16][8];
+  int tune_variant[16];
   // PCG scratch
   void* pcg_ws;
   size_t pcg_bytes;
@@ -68,7 +72,9 @@ cudaError_t nk_launch_myrtle_fused(const NkGeom& g, double sw2, double sb2, cons
                                    const float* qsa, int64_t a0, int64_t a1, const float* Xb,
                                    const float* qsb, int64_t b0, int64_t b1, float* K,
                                    int64_t ldk, int symmetric, int sm_count, void* scratch,
-                                   size_t scratch_bytes, cudaStream_t st);
+                                   size_t scratch_bytes, int variant, cudaStream_t st);
+// Number of launch variants of the fused kernel at 32x32 (nk_autotune).
+#define NK_FUSED_VARIANTS 3
 bool nk_myrtle_fused_supported(const NkGeom& g);
 
 // Plain layer-wise Myrtle block (FP32 or FP64).

@@ -181,3 +181,24 @@ def test_pcg_not_converged_and_edge(h):
     A, its, rel = h.pcg_solve(K, Y, 1.0, prec="plain_fp64", tol=1e-10, maxit=500)
     want = np.linalg.solve(Kh.astype(np.float64) + np.eye(n), Y.cpu().numpy())
     assert np.allclose(A.cpu().numpy(), want, rtol=1e-8, atol=1e-10)
+
+
+def test_autotune_variants_agree(h):
+    """Every launch variant the autotuner may pick computes the same block."""
+    from paper_2303_05420_gb300._lib import NkError
+
+    x = _imgs(6, 32, 4)
+    X = _dev(x)
+    for convs, sb2 in [((2, 1, 0), 0.0), ((3, 3, 3), 0.01)]:
+        q = h.self_diag(X, convs, 2.0, sb2)
+        chosen = h.autotune(convs, 2.0, sb2, 32, 32, 3)
+        assert 0 <= chosen < 3
+        ref = _oracle_block(convs, 2.0, sb2, x[:3], x[3:])
+        for v in range(3):
+            h.autotune_set(convs, 2.0, sb2, 32, 32, v)
+            K = h.block(X, q, X, q, convs, 2.0, sb2, prec="mixed", a_range=(0, 3), b_range=(3, 6))
+            h.sync_status()
+            assert _maxrel(K.double().cpu().numpy(), ref) <= TOL32, v
+        h.autotune_set(convs, 2.0, sb2, 32, 32, chosen)
+    with pytest.raises(NkError):
+        h.autotune_set((2, 1, 0), 2.0, 0.0, 32, 32, 3)
