@@ -151,6 +151,30 @@ nk_status nk_autotune(nk_handle* h, const nk_arch* arch, const nk_params* prm, i
 nk_status nk_autotune_set(nk_handle* h, const nk_arch* arch, const nk_params* prm, int H, int W, int C,
                           int variant);
 
+/* Fused (NK_PREC_MIXED) kernel block that allocates no device memory and
+ * needs no handle.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc when they need a block -- code being
+ * recorded into a CUDA graph, a process whose device memory is reserved up
+ * front by its own allocator, a plugin whose host framework owns all device
+ * memory -- since nk_create allocates.  Arguments and results are those of
+ * nk_block with prec = NK_PREC_MIXED (qsa / qsb from nk_self_diag, computed
+ * beforehand); the launch variant is 0.  The kernel's scratch (two
+ * accumulator slots of 12 bytes per 4-CTA or 1-CTA cluster) is a fixed
+ * 16 KB device array inside the library, shared by all calls on a device:
+ *   - the first call on a device looks up that array's device address with
+ *     the device current; make that first call before any stream capture;
+ *   - each call clears the slots it uses (stream-ordered) before its kernel;
+ *   - calls whose kernels overlap on the GPU (unordered streams) race on the
+ *     array; order them on one stream;
+ *   - a GPU whose SM count needs more than 16 KB (over 682 SMs) is rejected
+ *     with NK_ERR_INVALID_ARG.
+ * err_buf (may be NULL) receives a one-line description of any failure. */
+nk_status nk_block_fused_noalloc(const nk_arch* arch, const nk_params* prm,
+                                 const float* Xa, const float* qsa, int64_t a0, int64_t a1,
+                                 const float* Xb, const float* qsb, int64_t b0, int64_t b1,
+                                 int H, int W, int C, float* K, int64_t ldk, int symmetric,
+                                 void* stream, char* err_buf, size_t err_len);
+
 /* Kernel-ridge solve (K + lambda I) A = Y by Jacobi-preconditioned CG, one CG
  * per column run in lock-step (Section 2 "Iterative solvers"; Appendix B.3).
  *   K [N][ldk] float32 (device, symmetric), Y [N][R] float64 (device, row

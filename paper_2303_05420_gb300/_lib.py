@@ -24,7 +24,7 @@ PRECOND = {"none": 0, "jacobi": 1}
 # Every symbol include/nk.h declares (checked by a CPU test).
 EXPORTS = ["nk_create", "nk_destroy", "nk_status_string", "nk_last_error", "nk_sync_status",
            "nk_q_size", "nk_launch_count", "nk_last_lambda", "nk_self_diag", "nk_block", "nk_autotune",
-           "nk_autotune_set", "nk_pcg_solve"]
+           "nk_autotune_set", "nk_block_fused_noalloc", "nk_pcg_solve"]
 
 
 class NkArch(ctypes.Structure):
@@ -81,6 +81,10 @@ def lib():
     L.nk_autotune.restype = c_int
     L.nk_autotune_set.argtypes = [c_void_p, POINTER(NkArch), POINTER(NkParams), c_int, c_int, c_int, c_int]
     L.nk_autotune_set.restype = c_int
+    L.nk_block_fused_noalloc.argtypes = [POINTER(NkArch), POINTER(NkParams), c_void_p, c_void_p, c_int64,
+                                         c_int64, c_void_p, c_void_p, c_int64, c_int64, c_int, c_int,
+                                         c_int, c_void_p, c_int64, c_int, c_void_p, c_char_p, c_size_t]
+    L.nk_block_fused_noalloc.restype = c_int
     L.nk_pcg_solve.argtypes = [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_int, c_double, c_int,
                                c_int, c_double, c_int, c_int, c_void_p, POINTER(c_int),
                                c_void_p, c_void_p]
