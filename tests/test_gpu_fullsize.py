@@ -1,0 +1,83 @@
+"""Parity at the headline size, in the launch configuration bench.py times.
+
+2048 train + 512 test 32x32x3 images (the benchmark's generator), Myrtle-5
+(2,1,0), sigma_w^2 = 2, sigma_b^2 = 0, after nk_autotune: the full train block
+(symmetric) and test block on the GPU; sampled entries against the float64
+oracle one by one (train diagonal, train off-diagonal, test); properties at
+full size: finite, positive, symmetric, positive semi-definite in float64;
+the MIXED PCG solve reaches relative residual 1e-6 against the float32 K
+upcast to float64.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import nkdata
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def headline():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_05420_gb300.api import Handle
+
+    p = nkdata.image_problem(2048, 512, 32, n_classes=10, blur=True)
+    x = np.concatenate([p.x_train, p.x_test]).astype(np.float32)
+    h = Handle()
+    X = torch.tensor(x, device="cuda")
+    convs = (2, 1, 0)
+    h.autotune(convs, 2.0, 0.0, 32, 32, 3)
+    q = h.self_diag(X, convs, 2.0, 0.0)
+    Ktr = h.block(X, q, X, q, convs, 2.0, 0.0, prec="mixed", a_range=(0, 2048), b_range=(0, 2048),
+                  symmetric=True)
+    Kte = h.block(X, q, X, q, convs, 2.0, 0.0, prec="mixed", a_range=(2048, 2560), b_range=(0, 2048))
+    h.sync_status()
+    return h, x, p, Ktr, Kte
+
+
+def test_sampled_entries_match_oracle(headline):
+    h, x, p, Ktr, Kte = headline
+    arch = oracle.Arch((2, 1, 0))
+    xs = torch.tensor(x.astype(np.float64))
+    samples = [("tr", 0, 0), ("tr", 7, 7), ("tr", 3, 2047), ("tr", 1500, 611), ("tr", 1024, 1025),
+               ("te", 0, 0), ("te", 511, 2047), ("te", 100, 1234)]
+    Kt, Ke = Ktr.cpu().numpy(), Kte.cpu().numpy()
+    qcache = {}
+
+    def q_of(i):
+        if i not in qcache:
+            qcache[i] = oracle.myrtle_self_q(arch, 2.0, 0.0, xs[i])
+        return qcache[i]
+
+    for which, i, j in samples:
+        ia = i if which == "tr" else 2048 + i
+        want, _, _ = oracle.kernels.myrtle_layers_pair(arch, 2.0, 0.0, xs[ia], xs[j], q_of(ia), q_of(j))
+        got = Kt[i, j] if which == "tr" else Ke[i, j]
+        assert abs(float(got) - float(want)) <= 1e-5 * abs(float(want)), (which, i, j, got, float(want))
+
+
+def test_fullsize_properties(headline):
+    h, x, p, Ktr, Kte = headline
+    Kt = Ktr.double().cpu().numpy()
+    assert np.isfinite(Kt).all() and np.isfinite(Kte.cpu().numpy()).all()
+    assert (Kt > 0).all()
+    assert np.array_equal(Kt, Kt.T)
+    ev = np.linalg.eigvalsh(Kt)
+    assert ev.min() >= -1e-6 * ev.max()  # float32 entries: PSD up to their rounding
+
+
+def test_fullsize_pcg(headline):
+    h, x, p, Ktr, Kte = headline
+    Y = torch.tensor(p.y_train, device="cuda")
+    A, its, rel = h.pcg_solve(Ktr, Y, -1e-4, precond="jacobi", prec="mixed", tol=1e-6, maxit=20000)
+    Kt = Ktr.double().cpu().numpy()
+    lam = h.last_lambda()
+    assert abs(lam - 1e-4 * np.trace(Kt) / 2048) <= 1e-12 * lam
+    r = p.y_train - (Kt + lam * np.eye(2048)) @ A.cpu().numpy()
+    rel_true = np.linalg.norm(r, axis=0) / np.linalg.norm(p.y_train, axis=0)
+    assert rel_true.max() <= 1e-6
+    assert np.allclose(rel_true, rel, rtol=1e-3, atol=1e-9)
