@@ -133,6 +133,29 @@ nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_p
                    const float* Xb, const double* qdb, const float* qsb, int64_t b0, int64_t b1,
                    int H, int W, int C, void* K, int64_t ldk, int symmetric, void* stream);
 
+/* Adjoint of nk_block (no counterpart printed in the paper; it differentiates
+ * the Appendix A Myrtle kernel for a kernel-ridge loss).  Given the upstream
+ * gradient dK of the block [a0,a1) x [b0,b1), ACCUMULATES (+=)
+ *   dXa[i][H][W][C] for i in [a0, a1)   (absolute image index; may be NULL)
+ *   dXb[j][H][W][C] for j in [b0, b1)   (may be NULL)
+ *   *dsw2, *dsb2                        (device doubles)
+ * through the whole recursion, including the dependence of the self-variances
+ * q on the images and on sigma_w2, sigma_b2.
+ *   prec   NK_PREC_PLAIN_FP32 or NK_PREC_MIXED: float dK, dXa, dXb; FP32
+ *          pixel-pair tensors; NK_PREC_PLAIN_FP64: double dK, dXa, dXb.
+ *          The self-variance adjoint is FP64 in all cases.
+ *   qda, qdb   nk_self_diag FP64 outputs (required); qsa, qsb its FP32 scale
+ *              tables (required unless PLAIN_FP64).
+ *   symmetric  the block is the upper triangle of Xa x Xa: dK[i][j] and
+ *              dK[j][i] both count for that entry; dXa must equal dXb.
+ * Needs sigma_w2 > 0 and C <= 4.  The forward tensors of each layer are
+ * recomputed per chunk of pairs and kept in the handle's workspace. */
+nk_status nk_block_backward(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_prec prec,
+                            const float* Xa, const double* qda, const float* qsa, int64_t a0, int64_t a1,
+                            const float* Xb, const double* qdb, const float* qsb, int64_t b0, int64_t b1,
+                            int H, int W, int C, const void* dK, int64_t lddk, int symmetric, void* dXa,
+                            void* dXb, double* dsw2, double* dsb2, void* stream);
+
 /* Autotuner for the fused (NK_PREC_MIXED) kernel, the block-tile queue's
  * launch shape (Figure 1, top: blocks are "batched further" to fit the
  * device).  Times each launch variant of the fused kernel for this

@@ -123,6 +123,26 @@ class Handle:
         self.check(st, "nk_block")
         return out
 
+    def block_backward(self, Xa, qa, Xb, qb, convs, sw2, sb2, dK, dXa, dXb, dsw2, dsb2,
+                       prec: str = "plain_fp32", a_range=None, b_range=None, symmetric: bool = False,
+                       filt: int = 3, act: str = "relu"):
+        """Accumulates (+=) the adjoint of block(...) for upstream gradient dK
+        into dXa, dXb (image-shaped, may be None), dsw2, dsb2 (1-element
+        float64 CUDA tensors)."""
+        _, H, W, C = Xa.shape
+        a0, a1 = a_range if a_range is not None else (0, Xa.shape[0])
+        b0, b1 = b_range if b_range is not None else (0, Xb.shape[0])
+        a = make_arch(convs, filt, act)
+        p = make_params(sw2, sb2)
+        assert dK.stride(1) == 1
+        st = lib().nk_block_backward(self._h, byref(a), byref(p), _lib.PREC[prec],
+                                     c_void_p(_ptr(Xa)), c_void_p(_ptr(qa[0])), c_void_p(_ptr(qa[1])), a0, a1,
+                                     c_void_p(_ptr(Xb)), c_void_p(_ptr(qb[0])), c_void_p(_ptr(qb[1])), b0, b1,
+                                     H, W, C, c_void_p(_ptr(dK)), dK.stride(0), int(symmetric),
+                                     c_void_p(_ptr(dXa)), c_void_p(_ptr(dXb)), c_void_p(_ptr(dsw2)),
+                                     c_void_p(_ptr(dsb2)), c_void_p(_stream()))
+        self.check(st, "nk_block_backward")
+
     def pcg_solve(self, K: torch.Tensor, Y: torch.Tensor, lam: float, precond: str = "jacobi",
                   prec: str = "mixed", tol: float = 1e-6, maxit: int = 10000, refine_max: int = 8,
                   A: Optional[torch.Tensor] = None, allow_not_converged: bool = False):
@@ -154,3 +174,51 @@ def default_handle() -> Handle:
     if _DEFAULT is None:
         _DEFAULT = Handle()
     return _DEFAULT
+
+
+class NNGPBlock(torch.autograd.Function):
+    """K = NNGP(Xa, Xb) for the Myrtle-family architecture ``convs`` as a
+    differentiable op: forward by nk_self_diag + nk_block, backward by
+    nk_block_backward (gradients for Xa, Xb, sigma_w^2, sigma_b^2).
+
+    apply(Xa, Xb, sw2, sb2, handle, convs, symmetric, prec, bprec): Xa, Xb
+    float32 CUDA images [n, H, W, C]; sw2, sb2 0-dim float64 tensors.
+    symmetric: Xb is Xa and only the upper triangle is computed.  prec is the
+    forward precision ("mixed", "plain_fp32", "plain_fp64"), bprec the
+    adjoint's ("plain_fp32" or "plain_fp64").
+    """
+
+    @staticmethod
+    def forward(ctx, Xa, Xb, sw2, sb2, handle, convs, symmetric, prec, bprec):
+        h = handle
+        s, b = float(sw2), float(sb2)
+        qa = h.self_diag(Xa, convs, s, b)
+        qb = qa if symmetric else h.self_diag(Xb, convs, s, b)
+        K = h.block(Xa, qa, Xb, qb, convs, s, b, prec=prec, symmetric=symmetric)
+        ctx.h, ctx.convs, ctx.sym, ctx.bprec = h, convs, symmetric, bprec
+        ctx.sw2, ctx.sb2 = s, b
+        ctx.save_for_backward(Xa, Xb, qa[0], qa[1], qb[0], qb[1])
+        return K
+
+    @staticmethod
+    def backward(ctx, dK):
+        Xa, Xb, qda, qsa, qdb, qsb = ctx.saved_tensors
+        fp64 = ctx.bprec == "plain_fp64"
+        dt = torch.float64 if fp64 else torch.float32
+        dK = dK.to(dt).contiguous()
+        dXa = torch.zeros(Xa.shape, dtype=dt, device=Xa.device)
+        dXb = dXa if ctx.sym else torch.zeros(Xb.shape, dtype=dt, device=Xb.device)
+        dsw2 = torch.zeros(1, dtype=torch.float64, device=Xa.device)
+        dsb2 = torch.zeros(1, dtype=torch.float64, device=Xa.device)
+        ctx.h.block_backward(Xa, (qda, qsa), Xb, (qdb, qsb), ctx.convs, ctx.sw2, ctx.sb2, dK, dXa, dXb,
+                             dsw2, dsb2, prec=ctx.bprec, symmetric=ctx.sym)
+        gXa = dXa.to(Xa.dtype)
+        gXb = None if ctx.sym else dXb.to(Xb.dtype)
+        return gXa, gXb, dsw2.reshape(()), dsb2.reshape(()), None, None, None, None, None
+
+
+def nngp_block(Xa, Xb, sw2, sb2, convs, handle: Optional[Handle] = None, symmetric: bool = False,
+               prec: str = "mixed", bprec: str = "plain_fp32"):
+    """Differentiable Myrtle NNGP block (see NNGPBlock)."""
+    h = handle or default_handle()
+    return NNGPBlock.apply(Xa, Xb, sw2, sb2, h, tuple(convs), symmetric, prec, bprec)

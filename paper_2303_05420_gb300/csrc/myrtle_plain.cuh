@@ -1,0 +1,159 @@
+// Plain layer-wise Myrtle kernels shared by the forward (myrtle_plain.cu) and
+// the adjoint (myrtle_backward.cu): one thread per pixel-pair element.
+#pragma once
+
+#include "nk_common.cuh"
+#include "nk_map.cuh"
+
+namespace nkp {
+
+// Maps a linear pair index of the block to (i, j).  Symmetric blocks
+// enumerate the upper triangle (j >= i) row by row.
+__device__ __forceinline__ void pair_of(int64_t idx, int64_t na, int64_t nb, int symmetric,
+                                        int64_t* i, int64_t* j) {
+  if (!symmetric) {
+    *i = idx / nb;
+    *j = idx - (*i) * nb;
+    return;
+  }
+  const double m = (double)na;
+  double t = (2.0 * m + 1.0) * (2.0 * m + 1.0) - 8.0 * (double)idx;
+  int64_t r = (int64_t)floor(((2.0 * m + 1.0) - sqrt(t > 0 ? t : 0)) / 2.0);
+  if (r < 0) r = 0;
+  if (r > na - 1) r = na - 1;
+  // S(r) = r*m - r(r-1)/2 is the first index of row r
+  for (int it = 0; it < 4 && r > 0 && r * na - r * (r - 1) / 2 > idx; ++it) --r;
+  for (int it = 0; it < 4 && r + 1 < na && (r + 1) * na - (r + 1) * r / 2 <= idx; ++it) ++r;
+  *i = r;
+  *j = r + (idx - (r * na - r * (r - 1) / 2));
+}
+
+template <typename T>
+__global__ void k_input_cov(const float* __restrict__ Xa, const float* __restrict__ Xb,
+                            int64_t a0, int64_t b0, int64_t na, int64_t nb, int symmetric,
+                            int64_t pair0, int64_t npairs, int H, int W, int C, T* __restrict__ out) {
+  const int64_t HW = (int64_t)H * W, HW2 = HW * HW;
+  const int64_t total = npairs * HW2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pr = e / HW2, rem = e - pr * HW2;
+    const int64_t p = rem / HW, pp = rem - p * HW;
+    int64_t i, j;
+    pair_of(pair0 + pr, na, nb, symmetric, &i, &j);
+    const float* x = Xa + (a0 + i) * HW * C + p * C;
+    const float* y = Xb + (b0 + j) * HW * C + pp * C;
+    T acc = 0;
+    for (int c = 0; c < C; ++c) acc += (T)x[c] * (T)y[c];
+    out[e] = acc / (T)C;
+  }
+}
+
+template <typename T>
+__global__ void k_conv(const T* __restrict__ in, T* __restrict__ out, int64_t npairs, int H, int W,
+                       int filt, T a, T b) {
+  const int64_t HW = (int64_t)H * W, HW2 = HW * HW;
+  const int64_t total = npairs * HW2;
+  const int r = filt / 2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pr = e / HW2, rem = e - pr * HW2;
+    const int p = (int)(rem / HW), pp = (int)(rem - (int64_t)p * HW);
+    const int i = p / W, j = p % W, k = pp / W, l = pp % W;
+    T acc = 0;
+    for (int dy = -r; dy <= r; ++dy)
+      for (int dx = -r; dx <= r; ++dx) {
+        const int i2 = i + dy, j2 = j + dx, k2 = k + dy, l2 = l + dx;
+        if (i2 >= 0 && i2 < H && j2 >= 0 && j2 < W && k2 >= 0 && k2 < H && l2 >= 0 && l2 < W)
+          acc += in[pr * HW2 + (int64_t)(i2 * W + j2) * HW + k2 * W + l2];
+      }
+    out[e] = a * acc + b;
+  }
+}
+
+// ReLU map with self-variances of the pair's two images at this layer.
+template <typename T>
+__global__ void k_relu(T* __restrict__ K, int64_t npairs, int HW, int64_t na, int64_t nb,
+                       int symmetric, int64_t pair0, int64_t a0, int64_t b0,
+                       const double* __restrict__ qda, const double* __restrict__ qdb,
+                       const float* __restrict__ qsa, const float* __restrict__ qsb, int64_t nq,
+                       int qoff, unsigned int* dstatus) {
+  const int64_t HW2 = (int64_t)HW * HW, total = npairs * HW2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pr = e / HW2, rem = e - pr * HW2;
+    const int p = (int)(rem / HW), pp = (int)(rem - (int64_t)p * HW);
+    int64_t i, j;
+    pair_of(pair0 + pr, na, nb, symmetric, &i, &j);
+    if constexpr (sizeof(T) == 8) {
+      const double q1 = qda[(a0 + i) * nq + qoff + p];
+      const double q2 = qdb[(b0 + j) * nq + qoff + pp];
+      if (!(q1 >= 0.0) || !(q2 >= 0.0)) atomicOr(dstatus, NK_DEV_NUMERICAL);
+      K[e] = nk_relu_map_f64(K[e], q1, q2);
+    } else {
+      const float2 s1 = reinterpret_cast<const float2*>(qsa)[(a0 + i) * nq + qoff + p];
+      const float2 s2 = reinterpret_cast<const float2*>(qsb)[(b0 + j) * nq + qoff + pp];
+      const float s = s1.y * s2.y;
+      float v = 0.f;
+      if (s > 0.f) {
+        float c = K[e] * (s1.x * s2.x);
+        c = fminf(fmaxf(c, -1.f), 1.f);
+        v = s * (0.15915494309189533577f) *
+            (sqrtf(fmaxf(1.f - c * c, 0.f)) + c * (NK_PI_F - acosf(c)));
+      }
+      K[e] = v;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_pool(const T* __restrict__ in, T* __restrict__ out, int64_t npairs, int H, int W) {
+  const int Ho = H / 2, Wo = W / 2;
+  const int64_t HW = (int64_t)H * W, HWo = (int64_t)Ho * Wo;
+  const int64_t total = npairs * HWo * HWo;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pr = e / (HWo * HWo), rem = e - pr * HWo * HWo;
+    const int P = (int)(rem / HWo), PP = (int)(rem - (int64_t)P * HWo);
+    const int I = P / Wo, J = P % Wo, K2 = PP / Wo, L = PP % Wo;
+    T acc = 0;
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        for (int c = 0; c < 2; ++c)
+          for (int d = 0; d < 2; ++d)
+            acc += in[pr * HW * HW + (int64_t)((2 * I + a) * W + 2 * J + b) * HW +
+                      (2 * K2 + c) * W + 2 * L + d];
+    out[e] = acc / (T)16;
+  }
+}
+
+template <typename T>
+__global__ void k_gap(const T* __restrict__ in, int64_t HW2, int64_t na, int64_t nb, int symmetric,
+                      int64_t pair0, T sw2, T sb2, T* __restrict__ K, int64_t ldk) {
+  __shared__ double red[32];
+  const int64_t pr = blockIdx.x;
+  double acc = 0.0;
+  for (int64_t e = threadIdx.x; e < HW2; e += blockDim.x) acc += (double)in[pr * HW2 + e];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) {
+      int64_t i, j;
+      pair_of(pair0 + pr, na, nb, symmetric, &i, &j);
+      const T v = (T)((double)sw2 * (acc / (double)HW2) + (double)sb2);
+      K[i * ldk + j] = v;
+      if (symmetric && i != j) K[j * ldk + i] = v;
+    }
+  }
+}
+
+inline int grid_for(int64_t total) {
+  int64_t g = (total + 255) / 256;
+  if (g > 152 * 64) g = 152 * 64;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace nkp

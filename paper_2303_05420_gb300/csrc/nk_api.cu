@@ -291,6 +291,44 @@ nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_p
   return nk_cuda_check(h, e, "nk_block plain launch");
 }
 
+nk_status nk_block_backward(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_prec prec,
+                            const float* Xa, const double* qda, const float* qsa, int64_t a0, int64_t a1,
+                            const float* Xb, const double* qdb, const float* qsb, int64_t b0, int64_t b1,
+                            int H, int W, int C, const void* dK, int64_t lddk, int symmetric, void* dXa,
+                            void* dXb, double* dsw2, double* dsb2, void* stream) {
+  if (!h) return NK_ERR_INVALID_ARG;
+  NkGeom g;
+  const char* why = nullptr;
+  if (!nk_make_geom(arch, H, W, C, &g, &why))
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_backward: %s", why);
+  if (!prm || !(prm->sigma_w2 > 0.0) || !(prm->sigma_b2 >= 0.0))
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_backward: needs sigma_w2 > 0 and sigma_b2 >= 0");
+  if (prec != NK_PREC_PLAIN_FP64 && prec != NK_PREC_PLAIN_FP32 && prec != NK_PREC_MIXED)
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_backward: unknown precision");
+  if (C > 4) return nk_fail(h, NK_ERR_UNSUPPORTED, "nk_block_backward: C > 4");
+  if (a0 < 0 || b0 < 0 || a1 < a0 || b1 < b0)
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_backward: bad index range");
+  if (a1 == a0 || b1 == b0) return NK_OK;
+  if (!Xa || !Xb || !dK || !dsw2 || !dsb2)
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_backward: NULL image, dK or dsigma pointer");
+  if (lddk < b1 - b0) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_backward: lddk < b1 - b0");
+  if (symmetric && (Xa != Xb || a0 != b0 || a1 != b1 || dXa != dXb))
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_backward: symmetric needs Xa == Xb, equal ranges, dXa == dXb");
+  const bool relu = (g.act == NK_ACT_RELU);
+  const int fp64 = (prec == NK_PREC_PLAIN_FP64);
+  if (relu && (!qda || !qdb || (!fp64 && (!qsa || !qsb))))
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_backward: needs qda, qdb (and qsa, qsb for FP32)");
+  const int64_t na = a1 - a0, nb = b1 - b0;
+  const int64_t npairs = symmetric ? na * (na + 1) / 2 : na * nb;
+  void* ws = nullptr;
+  nk_status s = nk_workspace(h, nk_backward_ws_bytes(g, fp64, npairs, na, nb, symmetric, h->sm_count), &ws);
+  if (s != NK_OK) return s;
+  cudaError_t e = nk_launch_backward(g, fp64, prm->sigma_w2, prm->sigma_b2, Xa, qda, qsa, a0, a1, Xb, qdb, qsb,
+                                     b0, b1, dK, lddk, symmetric, dXa, dXb, dsw2, dsb2, ws, h->sm_count,
+                                     (cudaStream_t)stream, &h->launches, h->dstatus);
+  return nk_cuda_check(h, e, "nk_block_backward");
+}
+
 nk_status nk_autotune(nk_handle* h, const nk_arch* arch, const nk_params* prm, int H, int W, int C,
                       int* variant, void* stream) {
   if (!h) return NK_ERR_INVALID_ARG;

@@ -77,6 +77,16 @@ cudaError_t nk_launch_myrtle_fused(const NkGeom& g, double sw2, double sb2, cons
 #define NK_FUSED_VARIANTS 3
 bool nk_myrtle_fused_supported(const NkGeom& g);
 
+// Adjoint of the Myrtle block (layer-wise, FP32 or FP64 pixel-pair tensors).
+size_t nk_backward_ws_bytes(const NkGeom& g, int fp64, int64_t npairs, int64_t na, int64_t nb, int sym,
+                            int sm);
+cudaError_t nk_launch_backward(const NkGeom& g, int fp64, double sw2, double sb2, const float* Xa,
+                               const double* qda, const float* qsa, int64_t a0, int64_t a1, const float* Xb,
+                               const double* qdb, const float* qsb, int64_t b0, int64_t b1, const void* dK,
+                               int64_t lddk, int sym, void* dXa, void* dXb, double* dsw2, double* dsb2,
+                               void* ws, int sm, cudaStream_t st, int64_t* launches,
+                               unsigned int* dstatus);
+
 // Plain layer-wise Myrtle block (FP32 or FP64).
 size_t nk_plain_ws_bytes(const NkGeom& g, int fp64, int64_t pairs_per_chunk);
 cudaError_t nk_launch_myrtle_plain(const NkGeom& g, int fp64, double sw2, double sb2,
