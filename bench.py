@@ -332,6 +332,8 @@ def run_ours(args, rank, world, dist):
             extra[f"pcg_{prec}_iters_per_s"] = its / (ms / 1e3)
             extra[f"pcg_{prec}_relres"] = max(rel)
     lam_used = h.last_lambda()
+    if args.grad:
+        extra.update(grad_leg(h, dev))
 
     line = {
         "metric": METRIC,
@@ -375,6 +377,49 @@ def run_ours(args, rank, world, dist):
     line.update(extra)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def grad_leg(h, dev):
+    """Myrtle-10 kernel-ridge support-set loss, 100 support x 2048 target
+    32x32 images (same generator), sigma_w^2 = 2, sigma_b^2 = 0.01: forward
+    blocks K_ss (upper triangle) and K_ts by the fused kernel, loss in torch,
+    gradients w.r.t. the support pixels, sigma_w^2 and sigma_b^2 by the FP32
+    layer-wise adjoint.  One untimed warm-up, one timed pass."""
+    import numpy as np
+    import torch
+
+    import nkdata
+    from paper_2303_05420_gb300.api import nngp_block
+
+    convs = (3, 3, 3)
+    sup = nkdata.standardise(nkdata.images(100, 32, 3, nkdata.SEED_SUPPORT, blur=True))[0]
+    tgt = nkdata.standardise(nkdata.images(2048, 32, 3, nkdata.SEED_TEST, blur=True))[0]
+    ys = torch.tensor(nkdata.labels(100, 10), device=dev)
+    yt = torch.tensor(nkdata.labels(2048, 10, seed=9), device=dev)
+    Xt = torch.tensor(tgt.astype(np.float32), device=dev)
+    h.autotune(convs, 2.0, 0.01, 32, 32, 3)
+
+    def once():
+        Xs = torch.tensor(sup.astype(np.float32), device=dev, requires_grad=True)
+        s = torch.tensor(2.0, dtype=torch.float64, device=dev, requires_grad=True)
+        b = torch.tensor(0.01, dtype=torch.float64, device=dev, requires_grad=True)
+        Kss = nngp_block(Xs, Xs, s, b, convs, h, symmetric=True, prec="mixed", bprec="plain_fp32").double()
+        Kts = nngp_block(Xt, Xs, s, b, convs, h, prec="mixed", bprec="plain_fp32").double()
+        lam = 1e-6 * float(torch.trace(Kss)) / 100
+        A = torch.linalg.solve(Kss + lam * torch.eye(100, dtype=torch.float64, device=dev), ys)
+        L = 0.5 * ((Kts @ A - yt) ** 2).mean()
+        L.backward()
+        return float(L), float(s.grad), float(b.grad)
+
+    once()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L, gs, gb = once()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    entries = 100 * 101 // 2 + 2048 * 100
+    return {"grad_myrtle10_100x2048_s": dt, "grad_entries_per_s": entries / dt,
+            "grad_loss": L, "grad_dsw2": gs, "grad_dsb2": gb}
 
 
 # --------------------------------------------------------------------------
@@ -429,6 +474,8 @@ def main():
     ap.add_argument("--ref-pairs", type=int, default=4)
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grad", action="store_true",
+                    help="also time the Myrtle-10 kernel-ridge gradient (100 support x 2048 targets)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
