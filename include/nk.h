@@ -133,6 +133,23 @@ nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_p
                    const float* Xb, const double* qdb, const float* qsb, int64_t b0, int64_t b1,
                    int H, int W, int C, void* K, int64_t ldk, int symmetric, void* stream);
 
+/* Fully-connected ReLU NNGP block (Appendix A, FC3 listing: Dense + Relu
+ * `depth` times, Dense readout):
+ *   K_0 = x . x' / d;  K = sigma_w2 K_0 + sigma_b2;
+ *   depth times: K <- sigma_w2 * relu_map(K) + sigma_b2
+ * for rows i in [a0, a1) of Xa and j in [b0, b1) of Xb (row-major [n][d]
+ * float32, device), into K[i - a0][j - b0] (float32, leading dimension
+ * ldk).  The Gram is a split-BF16 tcgen05 GEMM (x = hi + lo, three BF16
+ * products per pair of elements, FP32 accumulation in TMEM) with the
+ * recursion fused into its epilogue; the per-row self-variances are FP64.
+ * symmetric: Xa == Xb, equal ranges; tiles below the diagonal are skipped and
+ * each entry is stored at (i, j) and (j, i).  depth 0..8.  Uses a handle
+ * workspace of (na + nb) * 6 d bytes for the split operands.  A device wait
+ * that runs out is reported by nk_sync_status as NK_ERR_TIMEOUT. */
+nk_status nk_fc_block(nk_handle* h, int depth, const nk_params* prm, const float* Xa, int64_t a0, int64_t a1,
+                      const float* Xb, int64_t b0, int64_t b1, int d, float* K, int64_t ldk, int symmetric,
+                      void* stream);
+
 /* Adjoint of nk_block (no counterpart printed in the paper; it differentiates
  * the Appendix A Myrtle kernel for a kernel-ridge loss).  Given the upstream
  * gradient dK of the block [a0,a1) x [b0,b1), ACCUMULATES (+=)

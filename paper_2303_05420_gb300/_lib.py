@@ -23,7 +23,7 @@ PRECOND = {"none": 0, "jacobi": 1}
 
 # Every symbol include/nk.h declares (checked by a CPU test).
 EXPORTS = ["nk_create", "nk_destroy", "nk_status_string", "nk_last_error", "nk_sync_status",
-           "nk_q_size", "nk_launch_count", "nk_last_lambda", "nk_self_diag", "nk_block", "nk_block_backward",
+           "nk_q_size", "nk_launch_count", "nk_last_lambda", "nk_self_diag", "nk_block", "nk_block_backward", "nk_fc_block",
            "nk_autotune",
            "nk_autotune_set", "nk_block_fused_noalloc", "nk_pcg_solve"]
 
@@ -83,6 +83,9 @@ def lib():
                                     c_int, c_int, c_int, c_void_p, c_int64, c_int,
                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     L.nk_block_backward.restype = c_int
+    L.nk_fc_block.argtypes = [c_void_p, c_int, POINTER(NkParams), c_void_p, c_int64, c_int64, c_void_p, c_int64,
+                              c_int64, c_int, c_void_p, c_int64, c_int, c_void_p]
+    L.nk_fc_block.restype = c_int
     L.nk_autotune.argtypes = [c_void_p, POINTER(NkArch), POINTER(NkParams), c_int, c_int, c_int,
                               POINTER(c_int), c_void_p]
     L.nk_autotune.restype = c_int

@@ -123,6 +123,23 @@ class Handle:
         self.check(st, "nk_block")
         return out
 
+    def fc_block(self, Xa: torch.Tensor, Xb: torch.Tensor, sw2: float, sb2: float, depth: int = 3,
+                 a_range=None, b_range=None, symmetric: bool = False,
+                 out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """FC NNGP block (tensor-core Gram + fused arc-cosine recursion)."""
+        assert Xa.dtype == torch.float32 and Xa.is_contiguous() and Xb.is_contiguous()
+        d = Xa.shape[1]
+        a0, a1 = a_range if a_range is not None else (0, Xa.shape[0])
+        b0, b1 = b_range if b_range is not None else (0, Xb.shape[0])
+        if out is None:
+            out = torch.empty((a1 - a0, b1 - b0), dtype=torch.float32, device=Xa.device)
+        p = make_params(sw2, sb2)
+        st = lib().nk_fc_block(self._h, int(depth), byref(p), c_void_p(_ptr(Xa)), a0, a1, c_void_p(_ptr(Xb)),
+                               b0, b1, d, c_void_p(_ptr(out)), out.stride(0), int(symmetric),
+                               c_void_p(_stream()))
+        self.check(st, "nk_fc_block")
+        return out
+
     def block_backward(self, Xa, qa, Xb, qb, convs, sw2, sb2, dK, dXa, dXb, dsw2, dsb2,
                        prec: str = "plain_fp32", a_range=None, b_range=None, symmetric: bool = False,
                        filt: int = 3, act: str = "relu"):

@@ -1,0 +1,284 @@
+// nk_fc_block: fully-connected ReLU NNGP kernel block (Appendix A, FC3
+// listing) on the tensor cores.
+//
+//   K_0 = x . x' / d;  K = sw2 K_0 + sb2;  depth times: K <- sw2 relu_map(K) + sb2
+//
+// The Gram X_a X_b^T is the one dense contraction of the method (d = 3072
+// for the CIFAR-shaped inputs).  It runs as a BF16 tcgen05 GEMM with FP32
+// accumulation in TMEM on split operands: x = x_hi + x_lo (BF16 each), and
+// x . x' ~ hi.hi' + hi.lo' + lo.hi' is one GEMM over a tripled K with
+// A' = [hi | hi | lo] and B' = [hi' | lo' | hi'] (zero-padded to a multiple
+// of 64).  Operand tiles (128 x 64 and 256 x 64 BF16) arrive by TMA with
+// 128-byte swizzle through a 4-stage mbarrier pipeline; one thread issues the
+// MMAs; four epilogue warps read the 128 x 256 FP32 accumulator from TMEM and
+// apply the whole arc-cosine recursion per entry before storing K.  The
+// self-variances q_l of each row follow the closed diagonal recursion
+// q_1 = sw2 |x|^2/d + sb2, q_{l+1} = sw2 q_l / 2 + sb2 (FP64).
+// Symmetric blocks run only tiles touching the upper triangle and store each
+// entry at (i, j) and (j, i).  Every mbarrier wait is bounded; on a timeout
+// the kernel records NK_DEV_TIMEOUT and skips its stores.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "nk_common.cuh"
+#include "nk_map.cuh"
+#include "tc_gemm.cuh"
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr uint32_t WAIT_LIMIT = 1u << 26;
+constexpr int MAX_DEPTH = 8;
+
+struct GemmSmem {
+  alignas(1024) __nv_bfloat16 A[STAGES][BM * BK];
+  alignas(1024) __nv_bfloat16 B[STAGES][BN * BK];
+  uint64_t full[STAGES], empty[STAGES], done;
+  uint32_t tslot;
+};
+
+struct FcParams {
+  int64_t M, N;          // rows of A', B'
+  int kpad;              // padded K' (multiple of 64)
+  int depth;
+  float kscale;          // sw2 / d
+  float sb2;
+  const float2* qa;      // [M][depth] (1/sqrt q_l, sqrt q_l * sw2/(2 pi))
+  const float2* qb;      // [N][depth] (1/sqrt q_l, sqrt q_l)
+  float* K;
+  int64_t ldk;
+  int sym;
+  int ntn;               // tiles along N
+  unsigned int* dstatus;
+};
+
+__global__ void __launch_bounds__(192, 1)
+k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+          const __grid_constant__ FcParams P) {
+  const int64_t tile = blockIdx.x;
+  const int tm = (int)(tile / P.ntn), tn = (int)(tile % P.ntn);
+  const int64_t m0 = (int64_t)tm * BM, n0 = (int64_t)tn * BN;
+  // symmetric: skip tiles entirely below the diagonal (no entry with i <= j)
+  if (P.sym && n0 + BN - 1 < m0) return;
+  extern __shared__ __align__(1024) unsigned char raw[];
+  GemmSmem& S = *reinterpret_cast<GemmSmem*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk = P.kpad / BK;
+  if (warp == 0 && lane == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(&S.full[s], 1);
+      tc::mbar_init(&S.empty[s], 1);
+    }
+    tc::mbar_init(&S.done, 1);
+    tc::mbar_fence_init();
+    tc::prefetch_tmap(&ta);
+    tc::prefetch_tmap(&tb);
+  }
+  if (warp == 1) tc::tmem_alloc(&S.tslot, 256);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tbase = S.tslot;
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES && !tc::mbar_wait(&S.empty[s], ((kb / STAGES) & 1) ^ 1, WAIT_LIMIT)) {
+        atomicOr(P.dstatus, NK_DEV_TIMEOUT);
+        break;
+      }
+      tc::mbar_arrive_expect_tx(&S.full[s], (BM + BN) * BK * 2);
+      tc::tma_load_2d(S.A[s], &ta, &S.full[s], kb * BK, (int)m0);
+      tc::tma_load_2d(S.B[s], &tb, &S.full[s], kb * BK, (int)n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (!tc::mbar_wait(&S.full[s], (kb / STAGES) & 1, WAIT_LIMIT)) {
+        atomicOr(P.dstatus, NK_DEV_TIMEOUT);
+        break;
+      }
+      tc::tc_fence_after();
+      const uint32_t a0 = tc::smem_addr(S.A[s]), b0 = tc::smem_addr(S.B[s]);
+#pragma unroll
+      for (int k = 0; k < BK / 16; ++k)
+        tc::mma_bf16(tbase, tc::sdesc_k128(a0 + 32 * k), tc::sdesc_k128(b0 + 32 * k), idesc, (kb | k) != 0);
+      tc::mma_commit(&S.empty[s]);
+    }
+    tc::mma_commit(&S.done);
+  } else if (warp >= 2) {
+    // epilogue: TMEM lane quarter q holds tile rows 32q .. 32q+31
+    const int q = warp & 3;
+    const bool ok = tc::mbar_wait(&S.done, 0, WAIT_LIMIT);
+    if (!ok) atomicOr(P.dstatus, NK_DEV_TIMEOUT);
+    tc::tc_fence_after();
+    const int64_t i = m0 + 32 * q + lane;
+    const bool rowok = ok && i < P.M;
+    float2 ra[MAX_DEPTH];
+#pragma unroll
+    for (int l = 0; l < MAX_DEPTH; ++l) ra[l] = (rowok && l < P.depth) ? P.qa[i * P.depth + l] : make_float2(0.f, 0.f);
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      float v[32];
+      tc::tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+      if (!rowok) continue;
+#pragma unroll 4
+      for (int e = 0; e < 32; ++e) {
+        const int64_t j = n0 + c0 + e;
+        float K = fmaf(P.kscale, v[e], P.sb2);
+        for (int l = 0; l < P.depth; ++l) {
+          const float2 rb = P.qb[j < P.N ? j * P.depth + l : 0];
+          const float c = K * (ra[l].x * rb.x);
+          const float J = (l == 0) ? nk_J_f32(c) : nk_J01_f32(c);
+          K = fmaf(ra[l].y * rb.y, J, P.sb2);
+        }
+        v[e] = K;
+      }
+      // row-major stores of row i; mirror column stores for symmetric blocks
+#pragma unroll 4
+      for (int e = 0; e < 32; ++e) {
+        const int64_t j = n0 + c0 + e;
+        if (j >= P.N) break;
+        if (P.sym && j < i) continue;
+        P.K[i * P.ldk + j] = v[e];
+        if (P.sym && j != i) P.K[j * P.ldk + i] = v[e];
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tbase, 256);
+}
+
+// A' = [hi | hi | lo] (role a) or B' = [hi | lo | hi] (role b), zero-padded to kpad.
+__global__ void k_split_bf16(const float* __restrict__ X, int64_t rows, int d, int kpad, int role_b,
+                             __nv_bfloat16* __restrict__ out) {
+  const int64_t total = rows * (int64_t)kpad;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / kpad;
+    const int k = (int)(e - r * kpad);
+    float v = 0.f;
+    if (k < 3 * d) {
+      const int seg = k / d, c = k - seg * d;
+      const float x = X[r * d + c];
+      const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+      const bool want_lo = role_b ? (seg == 1) : (seg == 2);
+      v = want_lo ? __bfloat162float(__float2bfloat16_rn(x - __bfloat162float(hi))) : __bfloat162float(hi);
+    }
+    out[e] = __float2bfloat16_rn(v);
+  }
+}
+
+// Per-row self-variances of every layer in FP64 -> (1/sqrt q, sqrt q * f)
+__global__ void k_fc_q(const float* __restrict__ X, int64_t rows, int d, int depth, double sw2, double sb2,
+                       float fold, float2* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += nw) {
+    double s = 0.0;
+    for (int k = lane; k < d; k += 32) {
+      const double x = X[r * d + k];
+      s += x * x;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      double q = sw2 * s / d + sb2;
+      for (int l = 0; l < depth; ++l) {
+        const float2 o = q > 0.0 ? make_float2((float)(1.0 / sqrt(q)), (float)(sqrt(q) * fold))
+                                 : make_float2(0.f, 0.f);
+        out[r * depth + l] = o;
+        q = sw2 * q / 2.0 + sb2;
+      }
+    }
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, void* ptr, int64_t rows, int kpad, int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
+  cuuint32_t box[2] = {BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+size_t nk_fc_ws_bytes(int64_t na, int64_t nb, int d, int depth) {
+  // A' and B' have different layouts even for a symmetric block
+  const int64_t kpad = (3 * (int64_t)d + BK - 1) / BK * BK;
+  return ((size_t)na + nb) * kpad * 2 + ((size_t)na + nb) * depth * sizeof(float2) + 4 * 1024;
+}
+
+cudaError_t nk_launch_fc_block(int depth, double sw2, double sb2, const float* Xa, int64_t a0, int64_t a1,
+                               const float* Xb, int64_t b0, int64_t b1, int d, float* K, int64_t ldk, int sym,
+                               void* ws, int sm, unsigned int* dstatus, cudaStream_t st, int64_t* launches) {
+  (void)sm;
+  const int64_t na = a1 - a0, nb = b1 - b0;
+  const int kpad = (int)((3 * (int64_t)d + BK - 1) / BK * BK);
+  char* w = reinterpret_cast<char*>(ws);
+  auto take = [&](size_t bytes) {
+    char* p = w;
+    w += (bytes + 1023) / 1024 * 1024;
+    return p;
+  };
+  __nv_bfloat16* Ap = reinterpret_cast<__nv_bfloat16*>(take((size_t)na * kpad * 2));
+  __nv_bfloat16* Bp = reinterpret_cast<__nv_bfloat16*>(take((size_t)nb * kpad * 2));
+  float2* qa = reinterpret_cast<float2*>(take((size_t)na * depth * sizeof(float2)));
+  float2* qb = reinterpret_cast<float2*>(take((size_t)nb * depth * sizeof(float2)));
+  const float* xa = Xa + a0 * (int64_t)d;
+  const float* xb = Xb + b0 * (int64_t)d;
+  auto grid = [](int64_t total) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 32)); };
+  *launches += 4;
+  k_split_bf16<<<grid(na * kpad), 256, 0, st>>>(xa, na, d, kpad, 0, Ap);
+  k_split_bf16<<<grid(nb * kpad), 256, 0, st>>>(xb, nb, d, kpad, 1, Bp);
+  const double inv2pi = 0.15915494309189533577;
+  k_fc_q<<<grid(na * 32), 256, 0, st>>>(xa, na, d, depth, sw2, sb2, (float)(sw2 * inv2pi), qa);
+  k_fc_q<<<grid(nb * 32), 256, 0, st>>>(xb, nb, d, depth, sw2, sb2, 1.f, qb);
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, Ap, na, kpad, BM) || !make_map(&tb, Bp, nb, kpad, BN)) return cudaErrorInvalidValue;
+  FcParams P = {};
+  P.M = na;
+  P.N = nb;
+  P.kpad = kpad;
+  P.depth = depth;
+  P.kscale = (float)(sw2 / d);
+  P.sb2 = (float)sb2;
+  P.qa = qa;
+  P.qb = qb;
+  P.K = K;
+  P.ldk = ldk;
+  P.sym = sym;
+  P.ntn = (int)((nb + BN - 1) / BN);
+  const int64_t ntm = (na + BM - 1) / BM;
+  const size_t smem = sizeof(GemmSmem) + 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_fc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  P.dstatus = dstatus;
+  ++*launches;
+  k_fc_gram<<<(unsigned)(ntm * P.ntn), 192, smem, st>>>(ta, tb, P);
+  return cudaGetLastError();
+}

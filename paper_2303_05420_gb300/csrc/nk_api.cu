@@ -329,6 +329,32 @@ nk_status nk_block_backward(nk_handle* h, const nk_arch* arch, const nk_params* 
   return nk_cuda_check(h, e, "nk_block_backward");
 }
 
+nk_status nk_fc_block(nk_handle* h, int depth, const nk_params* prm, const float* Xa, int64_t a0, int64_t a1,
+                      const float* Xb, int64_t b0, int64_t b1, int d, float* K, int64_t ldk, int symmetric,
+                      void* stream) {
+  if (!h) return NK_ERR_INVALID_ARG;
+  if (depth < 0 || depth > 8) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_fc_block: depth outside 0..8");
+  if (!prm || !(prm->sigma_w2 >= 0.0) || !(prm->sigma_b2 >= 0.0))
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_fc_block: bad params");
+  if (d < 1) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_fc_block: d < 1");
+  if (a0 < 0 || b0 < 0 || a1 < a0 || b1 < b0)
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_fc_block: bad index range");
+  if (a1 == a0 || b1 == b0) return NK_OK;
+  if (!Xa || !Xb || !K) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_fc_block: NULL pointer");
+  if (ldk < b1 - b0) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_fc_block: ldk < b1 - b0");
+  if (symmetric && (Xa != Xb || a0 != b0 || a1 != b1))
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_fc_block: symmetric needs Xa == Xb and equal ranges");
+  if (a1 - a0 > (1 << 30) || b1 - b0 > (1 << 30))
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_fc_block: more than 2^30 rows");
+  void* ws = nullptr;
+  nk_status s = nk_workspace(h, nk_fc_ws_bytes(a1 - a0, b1 - b0, d, depth), &ws);
+  if (s != NK_OK) return s;
+  cudaError_t e = nk_launch_fc_block(depth, prm->sigma_w2, prm->sigma_b2, Xa, a0, a1, Xb, b0, b1, d, K, ldk,
+                                     symmetric, ws, h->sm_count, h->dstatus, (cudaStream_t)stream, &h->launches);
+  if (e == cudaErrorInvalidValue) return nk_fail(h, NK_ERR_CUDA, "nk_fc_block: tensor map encoding failed");
+  return nk_cuda_check(h, e, "nk_fc_block");
+}
+
 nk_status nk_autotune(nk_handle* h, const nk_arch* arch, const nk_params* prm, int H, int W, int C,
                       int* variant, void* stream) {
   if (!h) return NK_ERR_INVALID_ARG;

@@ -77,6 +77,12 @@ cudaError_t nk_launch_myrtle_fused(const NkGeom& g, double sw2, double sb2, cons
 #define NK_FUSED_VARIANTS 3
 bool nk_myrtle_fused_supported(const NkGeom& g);
 
+// FC NNGP block on the tensor cores (fc_gram.cu).
+size_t nk_fc_ws_bytes(int64_t na, int64_t nb, int d, int depth);
+cudaError_t nk_launch_fc_block(int depth, double sw2, double sb2, const float* Xa, int64_t a0, int64_t a1,
+                               const float* Xb, int64_t b0, int64_t b1, int d, float* K, int64_t ldk, int sym,
+                               void* ws, int sm, unsigned int* dstatus, cudaStream_t st, int64_t* launches);
+
 // Adjoint of the Myrtle block (layer-wise, FP32 or FP64 pixel-pair tensors).
 size_t nk_backward_ws_bytes(const NkGeom& g, int fp64, int64_t npairs, int64_t na, int64_t nb, int sym,
                             int sm);
