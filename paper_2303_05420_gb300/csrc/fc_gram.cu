@@ -15,7 +15,11 @@
 // self-variances q_l of each row follow the closed diagonal recursion
 // q_1 = sw2 |x|^2/d + sb2, q_{l+1} = sw2 q_l / 2 + sb2 (FP64).
 // Symmetric blocks run only tiles touching the upper triangle and store each
-// entry at (i, j) and (j, i).  Every mbarrier wait is bounded; on a timeout
+// entry at (i, j) and (j, i).  The tensor core's FP32 accumulator rounds
+// once per 16-element MMA step; for a sum of 3d positive products (a row
+// with itself) those roundings drift one way, about 2e-5 relative at
+// d = 3072, so self pairs take their K_1 from the FP64 norm; rows that are
+// near copies of each other keep a bias of that order.  Every mbarrier wait is bounded; on a timeout
 // the kernel records NK_DEV_TIMEOUT and skips its stores.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -52,6 +56,11 @@ struct FcParams {
   int sym;
   int ntn;               // tiles along N
   unsigned int* dstatus;
+  // self pairs (same image on both sides: Xa == Xb and a0 + i == b0 + j)
+  // take K_1 = sw2 |x|^2/d + sb2 from the FP64 norm instead of the Gram
+  int same;
+  int64_t selfoff;       // a0 - b0
+  const float* q1a;      // [M]
 };
 
 __global__ void __launch_bounds__(192, 1)
@@ -129,6 +138,7 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       for (int e = 0; e < 32; ++e) {
         const int64_t j = n0 + c0 + e;
         float K = fmaf(P.kscale, v[e], P.sb2);
+        if (P.same && j == i + P.selfoff) K = P.q1a[i];
         for (int l = 0; l < P.depth; ++l) {
           const float2 rb = P.qb[j < P.N ? j * P.depth + l : 0];
           const float c = K * (ra[l].x * rb.x);
@@ -173,9 +183,10 @@ __global__ void k_split_bf16(const float* __restrict__ X, int64_t rows, int d, i
   }
 }
 
-// Per-row self-variances of every layer in FP64 -> (1/sqrt q, sqrt q * f)
+// Per-row self-variances of every layer in FP64 -> (1/sqrt q, sqrt q * f);
+// q1 (optional) receives q_1 = sw2 |x|^2/d + sb2.
 __global__ void k_fc_q(const float* __restrict__ X, int64_t rows, int d, int depth, double sw2, double sb2,
-                       float fold, float2* __restrict__ out) {
+                       float fold, float2* __restrict__ out, float* __restrict__ q1) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += nw) {
@@ -187,6 +198,7 @@ __global__ void k_fc_q(const float* __restrict__ X, int64_t rows, int d, int dep
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
       double q = sw2 * s / d + sb2;
+      if (q1) q1[r] = (float)q;
       for (int l = 0; l < depth; ++l) {
         const float2 o = q > 0.0 ? make_float2((float)(1.0 / sqrt(q)), (float)(sqrt(q) * fold))
                                  : make_float2(0.f, 0.f);
@@ -230,7 +242,7 @@ bool make_map(CUtensorMap* m, void* ptr, int64_t rows, int kpad, int box_rows) {
 size_t nk_fc_ws_bytes(int64_t na, int64_t nb, int d, int depth) {
   // A' and B' have different layouts even for a symmetric block
   const int64_t kpad = (3 * (int64_t)d + BK - 1) / BK * BK;
-  return ((size_t)na + nb) * kpad * 2 + ((size_t)na + nb) * depth * sizeof(float2) + 4 * 1024;
+  return ((size_t)na + nb) * kpad * 2 + ((size_t)na + nb) * depth * sizeof(float2) + (size_t)na * 4 + 5 * 1024;
 }
 
 cudaError_t nk_launch_fc_block(int depth, double sw2, double sb2, const float* Xa, int64_t a0, int64_t a1,
@@ -249,6 +261,7 @@ cudaError_t nk_launch_fc_block(int depth, double sw2, double sb2, const float* X
   __nv_bfloat16* Bp = reinterpret_cast<__nv_bfloat16*>(take((size_t)nb * kpad * 2));
   float2* qa = reinterpret_cast<float2*>(take((size_t)na * depth * sizeof(float2)));
   float2* qb = reinterpret_cast<float2*>(take((size_t)nb * depth * sizeof(float2)));
+  float* q1a = reinterpret_cast<float*>(take((size_t)na * sizeof(float)));
   const float* xa = Xa + a0 * (int64_t)d;
   const float* xb = Xb + b0 * (int64_t)d;
   auto grid = [](int64_t total) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 32)); };
@@ -256,8 +269,8 @@ cudaError_t nk_launch_fc_block(int depth, double sw2, double sb2, const float* X
   k_split_bf16<<<grid(na * kpad), 256, 0, st>>>(xa, na, d, kpad, 0, Ap);
   k_split_bf16<<<grid(nb * kpad), 256, 0, st>>>(xb, nb, d, kpad, 1, Bp);
   const double inv2pi = 0.15915494309189533577;
-  k_fc_q<<<grid(na * 32), 256, 0, st>>>(xa, na, d, depth, sw2, sb2, (float)(sw2 * inv2pi), qa);
-  k_fc_q<<<grid(nb * 32), 256, 0, st>>>(xb, nb, d, depth, sw2, sb2, 1.f, qb);
+  k_fc_q<<<grid(na * 32), 256, 0, st>>>(xa, na, d, depth, sw2, sb2, (float)(sw2 * inv2pi), qa, q1a);
+  k_fc_q<<<grid(nb * 32), 256, 0, st>>>(xb, nb, d, depth, sw2, sb2, 1.f, qb, nullptr);
   CUtensorMap ta, tb;
   if (!make_map(&ta, Ap, na, kpad, BM) || !make_map(&tb, Bp, nb, kpad, BN)) return cudaErrorInvalidValue;
   FcParams P = {};
@@ -273,6 +286,9 @@ cudaError_t nk_launch_fc_block(int depth, double sw2, double sb2, const float* X
   P.ldk = ldk;
   P.sym = sym;
   P.ntn = (int)((nb + BN - 1) / BN);
+  P.same = (Xa == Xb);
+  P.selfoff = a0 - b0;
+  P.q1a = q1a;
   const int64_t ntm = (na + BM - 1) / BM;
   const size_t smem = sizeof(GemmSmem) + 1024;
   cudaError_t e = cudaFuncSetAttribute(k_fc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
