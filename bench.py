@@ -107,6 +107,14 @@ def cpu_oracle_rate(n_workers: int, pairs_per_worker: int, hw: int, seed0: int =
     return pairs / max(times), pairs, max(times), wall
 
 
+def load_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -219,7 +227,7 @@ def run_ours(args, rank, world, dist):
         if marks is not None:
             marks[2].record(stream)
         _, its, rel = h.pcg_solve(Ktr, Yd, -REL_LAMBDA, precond="jacobi", prec="mixed", tol=1e-6,
-                                  maxit=20000, refine_max=8, A=A)
+                                  maxit=20000, A=A)
         if marks is not None:
             marks[3].record(stream)
         return its, rel
@@ -324,7 +332,7 @@ def run_ours(args, rank, world, dist):
             a, b = ev(), ev()
             a.record(stream)
             _, its, rel = h.pcg_solve(Ktr, Y, -REL_LAMBDA, precond="jacobi", prec=prec, tol=1e-6,
-                                      maxit=20000, refine_max=8, A=A, allow_not_converged=True)
+                                      maxit=20000, A=A, allow_not_converged=True)
             b.record(stream)
             torch.cuda.synchronize()
             ms = a.elapsed_time(b)
@@ -334,6 +342,8 @@ def run_ours(args, rank, world, dist):
     lam_used = h.last_lambda()
     if args.grad:
         extra.update(grad_leg(h, dev))
+    if not args.skip_fc:
+        extra.update(fc_leg(h, dev, load_peaks(), args.fc_train, args.fc_test))
 
     line = {
         "metric": METRIC,
@@ -422,6 +432,89 @@ def grad_leg(h, dev):
             "grad_loss": L, "grad_dsw2": gs, "grad_dsb2": gb}
 
 
+FC_N_TRAIN, FC_N_TEST, FC_D, FC_DEPTH = 50000, 10000, 3072, 3
+
+
+def fc_leg(h, dev, peaks, n=FC_N_TRAIN, m=FC_N_TEST):
+    """Depth-3 fully-connected ReLU NNGP (sigma_w^2 = 2, sigma_b^2 = 0) on
+    3072-dim N(0,1) rows scaled to norm sqrt(d): the 50000 x 50000 train Gram (upper triangle, mirrored)
+    and the 10000 x 50000 test block by the split-BF16 tensor-core kernel
+    with the fused arc-cosine recursion, then the PCG ridge solve of the
+    10 GB train kernel (10 right-hand sides, lambda = 1e-4 tr(K)/N), mixed
+    and plain FP64.  Inputs are resident in HBM; one untimed warm-up."""
+    import numpy as np
+    import torch
+
+    import nkdata
+
+    d = FC_D
+    xtr = torch.tensor(nkdata.fc_rows(n, d, nkdata.SEED_TRAIN), dtype=torch.float32, device=dev)
+    xte = torch.tensor(nkdata.fc_rows(m, d, nkdata.SEED_TEST), dtype=torch.float32, device=dev)
+    Y = torch.tensor(nkdata.labels(n, 10), device=dev)
+    Ktr = torch.empty((n, n), dtype=torch.float32, device=dev)
+    Kte = torch.empty((m, n), dtype=torch.float32, device=dev)
+    A = torch.empty((n, 10), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def grams():
+        h.fc_block(xtr, xtr, SW2, SB2, FC_DEPTH, symmetric=True, out=Ktr)
+        h.fc_block(xte, xtr, SW2, SB2, FC_DEPTH, out=Kte)
+
+    grams()
+    torch.cuda.synchronize()
+    marks = [ev() for _ in range(3)]
+    marks[0].record(stream)
+    h.fc_block(xtr, xtr, SW2, SB2, FC_DEPTH, symmetric=True, out=Ktr)
+    marks[1].record(stream)
+    h.fc_block(xte, xtr, SW2, SB2, FC_DEPTH, out=Kte)
+    marks[2].record(stream)
+    torch.cuda.synchronize()
+    t_sym = marks[0].elapsed_time(marks[1]) / 1e3
+    t_te = marks[1].elapsed_time(marks[2]) / 1e3
+    uniq = n * (n + 1) // 2 + m * n
+    # algorithmic Gram flops: 2 d per unique entry; the split-BF16 form runs
+    # three BF16 products per FP32 product on the tensor pipe
+    alg = 2.0 * d * uniq
+    t_gram = t_sym + t_te
+    out = {"fc3_workload": f"fc3_relu_d{d}_train{n}_test{m}_pcg10rhs",
+           "fc3_gram_ms": 1e3 * t_gram, "fc3_sym_ms": 1e3 * t_sym, "fc3_test_ms": 1e3 * t_te,
+           "fc3_entries_per_s": uniq / t_gram,
+           "fc3_roofline": {"bound": "tensor", "kernel": "k_fc_gram",
+                            "achieved": alg / t_gram / 1e12, "unit": "TFLOP/s",
+                            "tensor_pipe_tflops": 3 * alg / t_gram / 1e12,
+                            "peak": peaks.get("bf16_tflops"),
+                            "frac": (3 * alg / t_gram / 1e12) / peaks["bf16_tflops"]
+                            if peaks.get("bf16_tflops") else None,
+                            "note": "achieved = 2 d flops per unique entry (algorithmic); frac = "
+                                    "tensor-pipe BF16 rate (3 products per split-BF16 entry) of measured "
+                                    "burst bf16 peak"}}
+    for prec in ["mixed", "plain_fp64"]:
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        _, its, rel = h.pcg_solve(Ktr, Y, -REL_LAMBDA, precond="jacobi", prec=prec, tol=1e-6,
+                                  maxit=5000, A=A, allow_not_converged=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        out[f"fc3_pcg_{prec}_iters"] = its
+        out[f"fc3_pcg_{prec}_ms"] = ms
+        out[f"fc3_pcg_{prec}_iters_per_s"] = its / (ms / 1e3)
+        out[f"fc3_pcg_{prec}_relres"] = max(rel)
+    # the FP32 matvec streams K (n^2 x 4 bytes) once per iteration
+    its = out["fc3_pcg_mixed_iters"]
+    if its:
+        gbs = its * n * n * 4 / (out["fc3_pcg_mixed_ms"] / 1e3) / 1e9
+        out["fc3_pcg_mixed_hbm"] = {"achieved": gbs, "unit": "GB/s", "peak": peaks.get("hbm_gbs"),
+                                    "frac": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+                                    "note": "K bytes per CG iteration / whole-solve time (includes the "
+                                            "FP64 true residuals of the refinement)"}
+    del Ktr, Kte
+    torch.cuda.empty_cache()
+    return out
+
+
 # --------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # --------------------------------------------------------------------------
@@ -474,6 +567,12 @@ def main():
     ap.add_argument("--ref-pairs", type=int, default=4)
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-fc", action="store_true",
+                    help="skip the depth-3 FC NNGP leg (50000 x 50000 Gram and its PCG solve)")
+    ap.add_argument("--fc-train", type=int, default=FC_N_TRAIN)
+    ap.add_argument("--fc-test", type=int, default=FC_N_TEST)
+    ap.add_argument("--fc-only", action="store_true",
+                    help="run only the FC leg (prints its keys as one JSON line)")
     ap.add_argument("--grad", action="store_true",
                     help="also time the Myrtle-10 kernel-ridge gradient (100 support x 2048 targets)")
     args = ap.parse_args()
@@ -481,6 +580,18 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.fc_only:
+        import torch
+
+        from paper_2303_05420_gb300.api import Handle
+
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+        torch.cuda.set_device(dev)
+        h = Handle()
+        out = fc_leg(h, dev, load_peaks(), args.fc_train, args.fc_test)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
         return
     dist = None
     if world > 1:

@@ -219,11 +219,13 @@ nk_status nk_block_fused_noalloc(const nk_arch* arch, const nk_params* prm,
  * per column run in lock-step (Section 2 "Iterative solvers"; Appendix B.3).
  *   K [N][ldk] float32 (device, symmetric), Y [N][R] float64 (device, row
  *   major), A [N][R] float64 (device, out).
- *   prec = NK_PREC_MIXED: FP32 K@P inner solves with FP64 CG scalars, inside
- *          an FP64 iterative-refinement loop whose true residual
- *          Y - (K + lambda I) A is accumulated in FP64 (at most refine_max
- *          outer steps);
- *   prec = NK_PREC_PLAIN_FP32: FP32 K@P, FP64 scalars, no refinement;
+ *   prec = NK_PREC_MIXED: iterative refinement: the true residual
+ *          Y - (K + lambda I) A is formed with FP64 products and sums, the
+ *          correction is solved by CG with FP32 K@P (FP32 chunks of 256
+ *          products summed in FP64) and FP64 vectors and scalars, A += D
+ *          (at most refine_max corrections);
+ *   prec = NK_PREC_PLAIN_FP32: FP32 K@P, FP64 vectors and scalars, no
+ *          refinement;
  *   prec = NK_PREC_PLAIN_FP64: every product in FP64.
  *   lambda  >= 0: the ridge; < 0: relative ridge, lambda_used =
  *           -lambda * tr(K) / N with tr(K) summed on the device in FP64

@@ -161,7 +161,7 @@ class Handle:
         self.check(st, "nk_block_backward")
 
     def pcg_solve(self, K: torch.Tensor, Y: torch.Tensor, lam: float, precond: str = "jacobi",
-                  prec: str = "mixed", tol: float = 1e-6, maxit: int = 10000, refine_max: int = 8,
+                  prec: str = "mixed", tol: float = 1e-6, maxit: int = 10000, refine_max: int = 16,
                   A: Optional[torch.Tensor] = None, allow_not_converged: bool = False):
         """Solve (K + lam I) A = Y.  K [N, N] float32, Y [N, R] float64 (CUDA).
         Returns (A, iters, relres[R])."""

@@ -8,10 +8,15 @@
 // accumulation in TMEM on split operands: x = x_hi + x_lo (BF16 each), and
 // x . x' ~ hi.hi' + hi.lo' + lo.hi' is one GEMM over a tripled K with
 // A' = [hi | hi | lo] and B' = [hi' | lo' | hi'] (zero-padded to a multiple
-// of 64).  Operand tiles (128 x 64 and 256 x 64 BF16) arrive by TMA with
-// 128-byte swizzle through a 4-stage mbarrier pipeline; one thread issues the
-// MMAs; four epilogue warps read the 128 x 256 FP32 accumulator from TMEM and
-// apply the whole arc-cosine recursion per entry before storing K.  The
+// of 64).  A persistent CTA per SM walks 128 x 256 output tiles in a grouped
+// raster (8 tile rows at a time, so that concurrent CTAs share B tiles in
+// L2).  Operand tiles (128 x 64 and 256 x 64 BF16) arrive by TMA with
+// 128-byte swizzle through a 4-stage mbarrier ring; one thread issues the
+// MMAs into one of two 256-column TMEM accumulators while four epilogue warps
+// drain the other: each reads its 32 rows from TMEM, applies the whole
+// arc-cosine recursion layer by layer over 32 entries at a time (column
+// factors staged in shared memory), and stores K rows through a transposed
+// shared-memory chunk so that every warp store covers 128 contiguous bytes.  The
 // self-variances q_l of each row follow the closed diagonal recursion
 // q_1 = sw2 |x|^2/d + sb2, q_{l+1} = sw2 q_l / 2 + sb2 (FP64).
 // Symmetric blocks run only tiles touching the upper triangle and store each
@@ -33,13 +38,20 @@
 namespace {
 
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int GROUP_M = 8;      // tile rows per raster group (L2 reuse of B)
+constexpr int EPI_WARPS = 4;    // one per TMEM lane quarter
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t WAIT_LIMIT = 1u << 26;
 constexpr int MAX_DEPTH = 8;
 
 struct GemmSmem {
   alignas(1024) __nv_bfloat16 A[STAGES][BM * BK];
   alignas(1024) __nv_bfloat16 B[STAGES][BN * BK];
-  uint64_t full[STAGES], empty[STAGES], done;
+  float2 qb[BN * MAX_DEPTH];             // per-column (1/sqrt q, sqrt q) of the current tile
+  float stage[EPI_WARPS][32 * 32];       // transposes 32 x 32 output chunks (XOR-swizzled)
+  uint64_t full[STAGES], empty[STAGES];  // operand ring
+  uint64_t tfull[2], tempty[2];          // TMEM accumulators: MMA -> epilogue, epilogue -> MMA
+  uint64_t done;
   uint32_t tslot;
 };
 
@@ -54,7 +66,7 @@ struct FcParams {
   float* K;
   int64_t ldk;
   int sym;
-  int ntn;               // tiles along N
+  int ntm, ntn;          // tiles along M and N
   unsigned int* dstatus;
   // self pairs (same image on both sides: Xa == Xb and a0 + i == b0 + j)
   // take K_1 = sw2 |x|^2/d + sb2 from the FP64 norm instead of the Gram
@@ -63,104 +75,222 @@ struct FcParams {
   const float* q1a;      // [M]
 };
 
-__global__ void __launch_bounds__(192, 1)
+// Tile slot t of the grouped raster: GROUP_M tile rows at a time, column by
+// column, so that the CTAs running together share B tiles in L2.  Returns
+// false for tiles with no entry on or above the diagonal of a symmetric block.
+__device__ __forceinline__ bool tile_of(const FcParams& P, int64_t t, int& tm, int& tn) {
+  const int64_t per_group = (int64_t)GROUP_M * P.ntn;
+  const int g = (int)(t / per_group);
+  const int64_t k = t - (int64_t)g * per_group;
+  const int rows = min(GROUP_M, P.ntm - g * GROUP_M);
+  tm = g * GROUP_M + (int)(k % rows);
+  tn = (int)(k / rows);
+  return !(P.sym && (int64_t)tn * BN + BN - 1 < (int64_t)tm * BM);
+}
+
+__device__ __forceinline__ void named_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// Barrier over n threads that also returns whether any of them passed v.
+__device__ __forceinline__ bool named_any(int id, int n, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+
+// Persistent kernel, one CTA per SM, tiles t = blockIdx.x + k * gridDim.x.
+// Warp 0: TMA producer; warp 1: TMEM owner and MMA issuer; warps 2..5:
+// epilogue.  Two 256-column TMEM accumulators let the MMAs of the next tile
+// run while the epilogue drains the previous one.
+__global__ void __launch_bounds__(THREADS, 1)
 k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
           const __grid_constant__ FcParams P) {
-  const int64_t tile = blockIdx.x;
-  const int tm = (int)(tile / P.ntn), tn = (int)(tile % P.ntn);
-  const int64_t m0 = (int64_t)tm * BM, n0 = (int64_t)tn * BN;
-  // symmetric: skip tiles entirely below the diagonal (no entry with i <= j)
-  if (P.sym && n0 + BN - 1 < m0) return;
   extern __shared__ __align__(1024) unsigned char raw[];
   GemmSmem& S = *reinterpret_cast<GemmSmem*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nk = P.kpad / BK;
+  const int64_t nslots = (int64_t)P.ntm * P.ntn;
   if (warp == 0 && lane == 0) {
     for (int s = 0; s < STAGES; ++s) {
       tc::mbar_init(&S.full[s], 1);
       tc::mbar_init(&S.empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      tc::mbar_init(&S.tfull[a], 1);
+      tc::mbar_init(&S.tempty[a], EPI_WARPS);
     }
     tc::mbar_init(&S.done, 1);
     tc::mbar_fence_init();
     tc::prefetch_tmap(&ta);
     tc::prefetch_tmap(&tb);
   }
-  if (warp == 1) tc::tmem_alloc(&S.tslot, 256);
+  if (warp == 1) tc::tmem_alloc(&S.tslot, 512);
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tbase = S.tslot;
-  if (warp == 0 && lane == 0) {
-    // TMA producer
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (kb >= STAGES && !tc::mbar_wait(&S.empty[s], ((kb / STAGES) & 1) ^ 1, WAIT_LIMIT)) {
-        atomicOr(P.dstatus, NK_DEV_TIMEOUT);
-        break;
+  bool ok = true;
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer: the operand ring runs on across tiles
+      int64_t kb_all = 0;
+      for (int64_t t = blockIdx.x; t < nslots && ok; t += gridDim.x) {
+        int tm, tn;
+        if (!tile_of(P, t, tm, tn)) continue;
+        for (int kb = 0; kb < nk; ++kb, ++kb_all) {
+          const int s = (int)(kb_all % STAGES);
+          if (kb_all >= STAGES &&
+              !tc::mbar_wait(&S.empty[s], (uint32_t)((kb_all / STAGES) & 1) ^ 1, WAIT_LIMIT)) {
+            atomicOr(P.dstatus, NK_DEV_TIMEOUT);
+            ok = false;
+            break;
+          }
+          tc::mbar_arrive_expect_tx(&S.full[s], (BM + BN) * BK * 2);
+          tc::tma_load_2d(S.A[s], &ta, &S.full[s], kb * BK, tm * BM);
+          tc::tma_load_2d(S.B[s], &tb, &S.full[s], kb * BK, tn * BN);
+        }
       }
-      tc::mbar_arrive_expect_tx(&S.full[s], (BM + BN) * BK * 2);
-      tc::tma_load_2d(S.A[s], &ta, &S.full[s], kb * BK, (int)m0);
-      tc::tma_load_2d(S.B[s], &tb, &S.full[s], kb * BK, (int)n0);
+      // every load issued has landed before the CTA may exit
+      for (int64_t k = std::max<int64_t>(0, kb_all - STAGES); k < kb_all; ++k)
+        if (!tc::mbar_wait(&S.full[k % STAGES], (uint32_t)((k / STAGES) & 1), WAIT_LIMIT))
+          atomicOr(P.dstatus, NK_DEV_TIMEOUT);
     }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (!tc::mbar_wait(&S.full[s], (kb / STAGES) & 1, WAIT_LIMIT)) {
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+      int64_t kb_all = 0;
+      int n = 0;  // tiles of this CTA so far
+      for (int64_t t = blockIdx.x; t < nslots && ok; t += gridDim.x) {
+        int tm, tn;
+        if (!tile_of(P, t, tm, tn)) continue;
+        const int acc = n & 1;
+        if (n >= 2 && !tc::mbar_wait(&S.tempty[acc], (uint32_t)((n >> 1) & 1) ^ 1, WAIT_LIMIT)) {
+          atomicOr(P.dstatus, NK_DEV_TIMEOUT);
+          ok = false;
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t tacc = tbase + (uint32_t)(acc * BN);
+        for (int kb = 0; kb < nk; ++kb, ++kb_all) {
+          const int s = (int)(kb_all % STAGES);
+          if (!tc::mbar_wait(&S.full[s], (uint32_t)((kb_all / STAGES) & 1), WAIT_LIMIT)) {
+            atomicOr(P.dstatus, NK_DEV_TIMEOUT);
+            ok = false;
+            break;
+          }
+          tc::tc_fence_after();
+          const uint32_t a0 = tc::smem_addr(S.A[s]), b0 = tc::smem_addr(S.B[s]);
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k)
+            tc::mma_bf16(tacc, tc::sdesc_k128(a0 + 32 * k), tc::sdesc_k128(b0 + 32 * k), idesc, (kb | k) != 0);
+          tc::mma_commit(&S.empty[s]);
+        }
+        if (!ok) break;
+        tc::mma_commit(&S.tfull[acc]);
+        ++n;
+      }
+      // all MMAs issued by this thread complete before TMEM is released
+      tc::mma_commit(&S.done);
+      if (!tc::mbar_wait(&S.done, 0, WAIT_LIMIT)) atomicOr(P.dstatus, NK_DEV_TIMEOUT);
+    }
+  } else {
+    // epilogue: TMEM lane quarter q holds tile rows 32q .. 32q+31
+    const int q = warp & 3;
+    const int et = threadIdx.x - 64;  // 0 .. 127
+    float* st = S.stage[warp - 2];
+    int n = 0;
+    for (int64_t t = blockIdx.x; t < nslots; t += gridDim.x) {
+      int tm, tn;
+      if (!tile_of(P, t, tm, tn)) continue;
+      const int64_t m0 = (int64_t)tm * BM, n0 = (int64_t)tn * BN;
+      // column factors of this tile into shared memory
+      named_sync(1, 32 * EPI_WARPS);
+      for (int e = et; e < BN * P.depth; e += 32 * EPI_WARPS) {
+        const int64_t j = n0 + e / P.depth;
+        S.qb[e] = j < P.N ? P.qb[n0 * P.depth + e] : make_float2(0.f, 0.f);
+      }
+      named_sync(1, 32 * EPI_WARPS);
+      const int acc = n & 1;
+      const bool got = tc::mbar_wait(&S.tfull[acc], (uint32_t)((n >> 1) & 1), WAIT_LIMIT);
+      // the four warps leave together (they share named barriers)
+      if (named_any(2, 32 * EPI_WARPS, !got)) {
         atomicOr(P.dstatus, NK_DEV_TIMEOUT);
         break;
       }
       tc::tc_fence_after();
-      const uint32_t a0 = tc::smem_addr(S.A[s]), b0 = tc::smem_addr(S.B[s]);
-#pragma unroll
-      for (int k = 0; k < BK / 16; ++k)
-        tc::mma_bf16(tbase, tc::sdesc_k128(a0 + 32 * k), tc::sdesc_k128(b0 + 32 * k), idesc, (kb | k) != 0);
-      tc::mma_commit(&S.empty[s]);
-    }
-    tc::mma_commit(&S.done);
-  } else if (warp >= 2) {
-    // epilogue: TMEM lane quarter q holds tile rows 32q .. 32q+31
-    const int q = warp & 3;
-    const bool ok = tc::mbar_wait(&S.done, 0, WAIT_LIMIT);
-    if (!ok) atomicOr(P.dstatus, NK_DEV_TIMEOUT);
-    tc::tc_fence_after();
-    const int64_t i = m0 + 32 * q + lane;
-    const bool rowok = ok && i < P.M;
-    float2 ra[MAX_DEPTH];
-#pragma unroll
-    for (int l = 0; l < MAX_DEPTH; ++l) ra[l] = (rowok && l < P.depth) ? P.qa[i * P.depth + l] : make_float2(0.f, 0.f);
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      float v[32];
-      tc::tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
-      if (!rowok) continue;
-#pragma unroll 4
-      for (int e = 0; e < 32; ++e) {
-        const int64_t j = n0 + c0 + e;
-        float K = fmaf(P.kscale, v[e], P.sb2);
-        if (P.same && j == i + P.selfoff) K = P.q1a[i];
-        for (int l = 0; l < P.depth; ++l) {
-          const float2 rb = P.qb[j < P.N ? j * P.depth + l : 0];
-          const float c = K * (ra[l].x * rb.x);
-          const float J = (l == 0) ? nk_J_f32(c) : nk_J01_f32(c);
-          K = fmaf(ra[l].y * rb.y, J, P.sb2);
+      const int64_t i = m0 + 32 * q + lane;
+      const bool rowok = i < P.M;
+      const float self_k1 = (rowok && P.same) ? P.q1a[i] : 0.f;
+      const float2* qrow = P.qa + (rowok ? i : 0) * P.depth;
+      const uint32_t taddr = tbase + (uint32_t)(acc * BN) + ((uint32_t)(32 * q) << 16);
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        float v[32];
+        tc::tmem_ld32(taddr + (uint32_t)c0, v);
+        if (c0 + 32 == BN) {
+          // the accumulator is free for the MMAs of a later tile
+          tc::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&S.tempty[acc]);
         }
-        v[e] = K;
-      }
-      // row-major stores of row i; mirror column stores for symmetric blocks
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+          v[e] = fmaf(P.kscale, v[e], P.sb2);
+          if (P.same && n0 + c0 + e == i + P.selfoff) v[e] = self_k1;
+        }
+        // layer by layer over the 32 entries (independent chains)
+        for (int l = 0; l < P.depth; ++l) {
+          const float2 ra = rowok ? qrow[l] : make_float2(0.f, 0.f);
+          const float2* qc = S.qb + c0 * P.depth + l;
+          if (l == 0) {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              const float2 rb = qc[e * P.depth];
+              v[e] = fmaf(ra.y * rb.y, nk_J_f32(v[e] * (ra.x * rb.x)), P.sb2);
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              const float2 rb = qc[e * P.depth];
+              v[e] = fmaf(ra.y * rb.y, nk_J01_f32(v[e] * (ra.x * rb.x)), P.sb2);
+            }
+          }
+        }
+        // mirror of a symmetric block: column stores (j, i), coalesced over i
+        if (P.sym && rowok) {
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            const int64_t j = n0 + c0 + e;
+            if (j < P.N && j > i) P.K[j * P.ldk + i] = v[e];
+          }
+        }
+        // row stores (i, j) through a transposed chunk: lane = column
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < 32; ++e) st[lane * 32 + (e ^ lane)] = v[e];
+        __syncwarp();
+        const int64_t j = n0 + c0 + lane;
 #pragma unroll 4
-      for (int e = 0; e < 32; ++e) {
-        const int64_t j = n0 + c0 + e;
-        if (j >= P.N) break;
-        if (P.sym && j < i) continue;
-        P.K[i * P.ldk + j] = v[e];
-        if (P.sym && j != i) P.K[j * P.ldk + i] = v[e];
+        for (int r = 0; r < 32; ++r) {
+          const int64_t ir = m0 + 32 * q + r;
+          const float val = st[r * 32 + (lane ^ r)];
+          if (ir < P.M && j < P.N && (!P.sym || j >= ir)) P.K[ir * P.ldk + j] = val;
+        }
       }
+      ++n;
     }
   }
   tc::tc_fence_before();
   __syncthreads();
-  if (warp == 1) tc::tmem_dealloc(tbase, 256);
+  if (warp == 1) tc::tmem_dealloc(tbase, 512);
 }
 
 // A' = [hi | hi | lo] (role a) or B' = [hi | lo | hi] (role b), zero-padded to kpad.
@@ -248,7 +378,6 @@ size_t nk_fc_ws_bytes(int64_t na, int64_t nb, int d, int depth) {
 cudaError_t nk_launch_fc_block(int depth, double sw2, double sb2, const float* Xa, int64_t a0, int64_t a1,
                                const float* Xb, int64_t b0, int64_t b1, int d, float* K, int64_t ldk, int sym,
                                void* ws, int sm, unsigned int* dstatus, cudaStream_t st, int64_t* launches) {
-  (void)sm;
   const int64_t na = a1 - a0, nb = b1 - b0;
   const int kpad = (int)((3 * (int64_t)d + BK - 1) / BK * BK);
   char* w = reinterpret_cast<char*>(ws);
@@ -286,15 +415,17 @@ cudaError_t nk_launch_fc_block(int depth, double sw2, double sb2, const float* X
   P.ldk = ldk;
   P.sym = sym;
   P.ntn = (int)((nb + BN - 1) / BN);
+  P.ntm = (int)((na + BM - 1) / BM);
   P.same = (Xa == Xb);
   P.selfoff = a0 - b0;
   P.q1a = q1a;
-  const int64_t ntm = (na + BM - 1) / BM;
+  const int64_t slots = (int64_t)P.ntm * P.ntn;
   const size_t smem = sizeof(GemmSmem) + 1024;
   cudaError_t e = cudaFuncSetAttribute(k_fc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   P.dstatus = dstatus;
   ++*launches;
-  k_fc_gram<<<(unsigned)(ntm * P.ntn), 192, smem, st>>>(ta, tb, P);
+  const unsigned ctas = (unsigned)std::max<int64_t>(1, std::min<int64_t>(slots, sm));
+  k_fc_gram<<<ctas, THREADS, smem, st>>>(ta, tb, P);
   return cudaGetLastError();
 }

@@ -17,44 +17,95 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <type_traits>
+#include <vector>
 
 #include "nk_common.cuh"
 
 namespace {
 
-enum { SC_RZ = 0, SC_RZN, SC_PQ, SC_RR, SC_YY, SC_ACT, SC_ALPHA, SC_BETA, SC_ITER, SC_N };
+// per-column CG scalars, sc[slot * R + column]; SC_TOL holds tol^2 of the
+// running solve (read on the device, so a captured iteration serves any tol)
+enum { SC_RZ = 0, SC_RZN, SC_PQ, SC_RR, SC_YY, SC_ACT, SC_ALPHA, SC_BETA, SC_ITER, SC_TOL, SC_N };
+
+// FP32 form: chunk sums of at most NK_MV_CHUNK rows are added, in FP64, to
+// per-thread slots in shared memory (mv_sh[(c * RB + r) * 128 + tid]); keeping
+// them out of registers lets four blocks share an SM, each thread holding
+// U float4 loads of K in flight.
+#define NK_MV_CHUNK 256
+#define NK_MV_THREADS 128
 
 template <int RB, bool F64, bool VEC>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(NK_MV_THREADS, (F64 && RB > 8) ? 2 : 4)
 k_matvec(const float* __restrict__ K, int64_t ldk, int64_t N, const void* __restrict__ Pin, int R,
          int rc0, int rcnt, int rows_per_split, double* __restrict__ Qpart) {
   using T = typename std::conditional<F64, double, float>::type;
-  const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  constexpr int U = F64 ? 2 : 4;  // rows per unrolled step
+  extern __shared__ double mv_sh[];
+  const int tid = threadIdx.x;
+  const int64_t i0 = ((int64_t)blockIdx.x * NK_MV_THREADS + tid) * 4;
   const int64_t js = (int64_t)blockIdx.y * rows_per_split;
   const int64_t je = std::min<int64_t>(N, js + rows_per_split);
   const T* P = reinterpret_cast<const T*>(Pin);
   T acc[4][RB];
-  double acc64[4][RB];
 #pragma unroll
   for (int c = 0; c < 4; ++c)
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
       acc[c][r] = 0;
-      acc64[c][r] = 0.0;
+      if constexpr (!F64) mv_sh[(c * RB + r) * NK_MV_THREADS + tid] = 0.0;
     }
   const bool full = (i0 + 3 < N);
   int chunk = 0;
-  for (int64_t j = js; j < je; ++j) {
+  int64_t j = js;
+  for (; j + U <= je; j += U) {
+    float k[U][4];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const float* row = K + (j + u) * ldk + i0;
+      if (VEC && full) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(row));
+        k[u][0] = v.x;
+        k[u][1] = v.y;
+        k[u][2] = v.z;
+        k[u][3] = v.w;
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) k[u][c] = (i0 + c < N) ? __ldg(row + c) : 0.f;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const T* pr = P + (j + u) * R + rc0;
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        if (r < rcnt) {
+          const T p = __ldg(pr + r);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[c][r] = fma((T)k[u][c], p, acc[c][r]);
+        }
+      }
+    }
+    if constexpr (!F64) {
+      chunk += U;
+      if (chunk >= NK_MV_CHUNK) {
+        chunk = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int r = 0; r < RB; ++r) {
+            mv_sh[(c * RB + r) * NK_MV_THREADS + tid] += (double)acc[c][r];
+            acc[c][r] = 0;
+          }
+      }
+    }
+  }
+  for (; j < je; ++j) {  // fewer than U rows left (chunk stays below its bound)
     float k[4];
     const float* row = K + j * ldk + i0;
-    if (VEC && full) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(row));
-      k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
-    } else {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) k[c] = (i0 + c < N) ? __ldg(row + c) : 0.f;
-    }
+    for (int c = 0; c < 4; ++c) k[c] = (i0 + c < N) ? __ldg(row + c) : 0.f;
     const T* pr = P + j * R + rc0;
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
@@ -64,18 +115,6 @@ k_matvec(const float* __restrict__ K, int64_t ldk, int64_t N, const void* __rest
         for (int c = 0; c < 4; ++c) acc[c][r] = fma((T)k[c], p, acc[c][r]);
       }
     }
-    if constexpr (!F64) {
-      if (++chunk == 256) {
-        chunk = 0;
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int r = 0; r < RB; ++r) {
-            acc64[c][r] += (double)acc[c][r];
-            acc[c][r] = 0;
-          }
-      }
-    }
   }
   double* out = Qpart + (int64_t)blockIdx.y * N * R;
 #pragma unroll
@@ -83,9 +122,18 @@ k_matvec(const float* __restrict__ K, int64_t ldk, int64_t N, const void* __rest
     if (i0 + c < N) {
 #pragma unroll
       for (int r = 0; r < RB; ++r)
-        if (r < rcnt) out[(i0 + c) * R + rc0 + r] = acc64[c][r] + (double)acc[c][r];
+        if (r < rcnt) {
+          double v = (double)acc[c][r];
+          if constexpr (!F64) v += mv_sh[(c * RB + r) * NK_MV_THREADS + tid];
+          out[(i0 + c) * R + rc0 + r] = v;
+        }
     }
   }
+}
+
+template <int RB, bool F64>
+constexpr size_t mv_smem() {
+  return F64 ? 0 : (size_t)4 * RB * NK_MV_THREADS * sizeof(double);
 }
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -190,7 +238,7 @@ __global__ void k_update(const double* __restrict__ minv, int64_t N, int R, doub
 }
 
 // beta, activity and iteration counts; *flag = number of active columns.
-__global__ void k_beta(double* sc, int R, double tol2, int* flag) {
+__global__ void k_beta(double* sc, int R, int* flag) {
   const int r = threadIdx.x;
   int act_now = 0;
   if (r < R) {
@@ -201,7 +249,7 @@ __global__ void k_beta(double* sc, int R, double tol2, int* flag) {
       sc[SC_BETA * R + r] = (rz != 0.0) ? rzn / rz : 0.0;
       sc[SC_RZ * R + r] = rzn;
       sc[SC_ITER * R + r] += 1.0;
-      const bool still = sc[SC_RR * R + r] > tol2 * sc[SC_YY * R + r];
+      const bool still = sc[SC_RR * R + r] > sc[SC_TOL * R + r] * sc[SC_YY * R + r];
       sc[SC_ACT * R + r] = still ? 1.0 : 0.0;
       act_now = still ? 1 : 0;
     } else {
@@ -265,7 +313,7 @@ __global__ void k_trace(const float* __restrict__ K, int64_t ldk, int64_t N, dou
   if (threadIdx.x == 0) *out = s;
 }
 
-__global__ void k_axpy_cols(int64_t n, double* __restrict__ X, const double* __restrict__ D) {
+__global__ void k_add(int64_t n, double* __restrict__ X, const double* __restrict__ D) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x)
     X[e] += D[e];
@@ -277,9 +325,12 @@ __global__ void k_zero(double* p, int64_t n) {
     p[e] = 0.0;
 }
 
-__global__ void k_set_active(double* sc, int R) {
+__global__ void k_set_active(double* sc, int R, double tol2) {
   const int r = threadIdx.x;
-  if (r < R) sc[SC_ACT * R + r] = 1.0;
+  if (r < R) {
+    sc[SC_ACT * R + r] = 1.0;
+    sc[SC_TOL * R + r] = tol2;
+  }
 }
 
 struct Pcg {
@@ -292,10 +343,9 @@ struct Pcg {
   int rows_per_split;
   int sm;
   cudaStream_t st;
-  double *X, *Rr, *Z, *P, *Q, *Qpart, *minv, *sc, *B2, *D;
+  double *Rr, *Z, *P, *Q, *Qpart, *minv, *sc, *B2;
   float* Pf;
-  int* flag;         // device
-  int* hflag;        // pinned host
+  int* flag;         // device: active columns after the last iteration
   int64_t* nlaunch;  // handle launch counter
 };
 
@@ -303,24 +353,66 @@ template <bool F64>
 cudaError_t matvec(const Pcg& c, const void* Pin) {
   const bool vec = (c.ldk % 4 == 0) && ((reinterpret_cast<uintptr_t>(c.K) & 15) == 0);
   const int64_t colthreads = (c.N + 3) / 4;
-  dim3 grid((unsigned)((colthreads + 127) / 128), (unsigned)c.S);
+  dim3 grid((unsigned)((colthreads + NK_MV_THREADS - 1) / NK_MV_THREADS), (unsigned)c.S);
   for (int rc0 = 0; rc0 < c.R; rc0 += 16) {
     const int rcnt = std::min(16, c.R - rc0);
-#define NK_MV(RB)                                                                                 \
-  if (rcnt <= RB) {                                                                               \
-    ++*c.nlaunch;                                                                                 \
-    if (vec)                                                                                      \
-      k_matvec<RB, F64, true><<<grid, 128, 0, c.st>>>(c.K, c.ldk, c.N, Pin, c.R, rc0, rcnt,       \
-                                                      c.rows_per_split, c.Qpart);                 \
-    else                                                                                          \
-      k_matvec<RB, F64, false><<<grid, 128, 0, c.st>>>(c.K, c.ldk, c.N, Pin, c.R, rc0, rcnt,      \
-                                                       c.rows_per_split, c.Qpart);                \
-    continue;                                                                                     \
+#define NK_MV(RB)                                                                                  \
+  if (rcnt <= RB) {                                                                                \
+    ++*c.nlaunch;                                                                                  \
+    if (vec)                                                                                       \
+      k_matvec<RB, F64, true><<<grid, NK_MV_THREADS, mv_smem<RB, F64>(), c.st>>>(                  \
+          c.K, c.ldk, c.N, Pin, c.R, rc0, rcnt, c.rows_per_split, c.Qpart);                        \
+    else                                                                                           \
+      k_matvec<RB, F64, false><<<grid, NK_MV_THREADS, mv_smem<RB, F64>(), c.st>>>(                 \
+          c.K, c.ldk, c.N, Pin, c.R, rc0, rcnt, c.rows_per_split, c.Qpart);                        \
+    continue;                                                                                      \
   }
     NK_MV(1) NK_MV(2) NK_MV(4) NK_MV(8) NK_MV(10) NK_MV(16)
 #undef NK_MV
   }
   return cudaGetLastError();
+}
+
+// Opt in to the dynamic shared memory of the FP32 matvec forms (above 48 KB
+// for 16 right-hand sides); returns the resident blocks per SM of the form
+// that R columns use.
+int matvec_prepare(int R) {
+  const int rcnt = std::min(R, 16);
+  int occ = 0;
+#define NK_MV_ATTR(RB)                                                                              \
+  cudaFuncSetAttribute(k_matvec<RB, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                       (int)mv_smem<RB, false>());                                                  \
+  cudaFuncSetAttribute(k_matvec<RB, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                       (int)mv_smem<RB, false>());                                                  \
+  if (occ == 0 && rcnt <= RB)                                                                       \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_matvec<RB, false, true>, NK_MV_THREADS,   \
+                                                  mv_smem<RB, false>());
+  NK_MV_ATTR(1) NK_MV_ATTR(2) NK_MV_ATTR(4) NK_MV_ATTR(8) NK_MV_ATTR(10) NK_MV_ATTR(16)
+#undef NK_MV_ATTR
+  (void)cudaGetLastError();
+  return std::max(occ, 1);
+}
+
+// Row splits S of the matvec: enough blocks for several waves, the number of
+// blocks chosen so that the last wave is nearly full, and at least 4R rows
+// (32 at least) per split so that the FP64 partial sums stay small next to K.
+int choose_splits(int64_t N, int R, int sm, int occ) {
+  const int64_t colblocks = ((N + 3) / 4 + NK_MV_THREADS - 1) / NK_MV_THREADS;
+  const int64_t cap = (int64_t)sm * occ;  // resident blocks
+  const int64_t s_max = std::max<int64_t>(1, std::min<int64_t>(512, N / std::max(4 * R, 32)));
+  const int64_t s_lo = std::min<int64_t>(s_max, std::max<int64_t>(1, (2 * cap) / colblocks));
+  const int64_t s_hi = std::min<int64_t>(s_max, std::max<int64_t>(s_lo, (8 * cap) / colblocks));
+  int64_t best = s_lo;
+  double best_eff = -1.0;
+  for (int64_t S = s_lo; S <= s_hi; ++S) {
+    const double waves = (double)(colblocks * S) / (double)cap;
+    const double eff = waves / std::ceil(waves);
+    if (eff > best_eff + 1e-3) {
+      best_eff = eff;
+      best = S;
+    }
+  }
+  return (int)best;
 }
 
 inline dim3 vgrid(const Pcg& c) {
@@ -329,63 +421,109 @@ inline dim3 vgrid(const Pcg& c) {
   return dim3((unsigned)std::max<int64_t>(1, b), (unsigned)c.R);
 }
 
-// True residual out = B - (K + lam I) X in FP64; sc[RR], sc[YY] accumulate.
-cudaError_t true_residual(const Pcg& c, const double* B, const double* Xc, double* out) {
-  ++*c.nlaunch;
-  k_zero<<<1, 256, 0, c.st>>>(c.sc, (int64_t)SC_N * c.R);
+// Q = (K + lam I) Xc with FP64 products and sums.
+cudaError_t apply_fp64(const Pcg& c, const double* Xc) {
   cudaError_t e = matvec<true>(c, Xc);
   if (e != cudaSuccess) return e;
   ++*c.nlaunch;
   k_reduce_dot<<<vgrid(c), 256, 0, c.st>>>(c.Qpart, c.S, c.N, c.R, Xc, c.lam, c.Q, c.sc, -1);
+  return cudaGetLastError();
+}
+
+// True residual out = B - (K + lam I) X in FP64 into sc[RR], sc[YY] (the CG
+// state in sc is overwritten).
+cudaError_t true_residual(const Pcg& c, const double* B, const double* Xc, double* out) {
+  ++*c.nlaunch;
+  k_zero<<<1, 256, 0, c.st>>>(c.sc, (int64_t)SC_N * c.R);
+  cudaError_t e = apply_fp64(c, Xc);
+  if (e != cudaSuccess) return e;
   ++*c.nlaunch;
   k_resid<<<vgrid(c), 256, 0, c.st>>>(B, c.Q, c.N, c.R, out, c.sc);
   return cudaGetLastError();
 }
 
-// CG on (K + lam I) Xc = B from Xc = 0.  Returns iterations performed (max
-// over columns) through *its, or a negative value on a CUDA error.
+// One CG iteration for every active column (Section 2, "Iterative solvers").
 template <bool F64>
-cudaError_t cg_run(const Pcg& c, const double* B, double* Xc, double tol, int maxit, int* its) {
-  ++*c.nlaunch;
-  k_zero<<<1, 256, 0, c.st>>>(c.sc, (int64_t)SC_N * c.R);
-  ++*c.nlaunch;
-  k_set_active<<<1, 256, 0, c.st>>>(c.sc, c.R);
-  ++*c.nlaunch;
-  k_init<<<vgrid(c), 256, 0, c.st>>>(B, c.minv, c.N, c.R, Xc, c.Rr, c.Z, c.P, c.Pf, c.sc);
-  const double tol2 = tol * tol;
-  const int check_every = 8;
-  int it = 0;
-  cudaError_t e = cudaSuccess;
-  while (it < maxit) {
-    const int steps = std::min(check_every, maxit - it);
-    for (int s = 0; s < steps; ++s) {
-      e = F64 ? matvec<true>(c, c.P) : matvec<false>(c, c.Pf);
-      if (e != cudaSuccess) return e;
-      ++*c.nlaunch;
-      k_reduce_dot<<<vgrid(c), 256, 0, c.st>>>(c.Qpart, c.S, c.N, c.R, c.P, c.lam, c.Q, c.sc,
-                                               SC_PQ);
-      ++*c.nlaunch;
-      k_alpha<<<1, 256, 0, c.st>>>(c.sc, c.R);
-      ++*c.nlaunch;
-      k_update<<<vgrid(c), 256, 0, c.st>>>(c.minv, c.N, c.R, Xc, c.Rr, c.Z, c.P, c.Q, c.sc);
-      ++*c.nlaunch;
-      k_beta<<<1, 256, 0, c.st>>>(c.sc, c.R, tol2, c.flag);
-      ++*c.nlaunch;
-      k_direction<<<vgrid(c), 256, 0, c.st>>>(c.N, c.R, c.Z, c.P, c.Pf, c.sc);
-    }
-    it += steps;
-    e = cudaMemcpyAsync(c.hflag, c.flag, sizeof(int), cudaMemcpyDeviceToHost, c.st);
-    if (e != cudaSuccess) return e;
-    e = cudaStreamSynchronize(c.st);
-    if (e != cudaSuccess) return e;
-    if (*c.hflag == 0) break;
+cudaError_t cg_iteration(const Pcg& c, double* Xc) {
+  cudaError_t e = F64 ? matvec<true>(c, c.P) : matvec<false>(c, c.Pf);
+  if (e != cudaSuccess) return e;
+  c.nlaunch[0] += 5;
+  k_reduce_dot<<<vgrid(c), 256, 0, c.st>>>(c.Qpart, c.S, c.N, c.R, c.P, c.lam, c.Q, c.sc, SC_PQ);
+  k_alpha<<<1, 256, 0, c.st>>>(c.sc, c.R);
+  k_update<<<vgrid(c), 256, 0, c.st>>>(c.minv, c.N, c.R, Xc, c.Rr, c.Z, c.P, c.Q, c.sc);
+  k_beta<<<1, 256, 0, c.st>>>(c.sc, c.R, c.flag);
+  k_direction<<<vgrid(c), 256, 0, c.st>>>(c.N, c.R, c.Z, c.P, c.Pf, c.sc);
+  return cudaGetLastError();
+}
+
+// A block of `steps` iterations into Xc, captured once as a CUDA graph and
+// replayed (an iteration is six launches of a few microseconds each, as long
+// as the matvec itself at N of a few thousand).  Returns null when capture is
+// unavailable; the iterations are then launched one by one.
+template <bool F64>
+cudaGraphExec_t capture_block(const Pcg& c, double* Xc, int steps, int64_t* per_block) {
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
   }
-  // exact per-column count
-  double* hsc = (double*)malloc(sizeof(double) * SC_N * c.R);
-  e = cudaMemcpy(hsc, c.sc, sizeof(double) * SC_N * c.R, cudaMemcpyDeviceToHost);
+  Pcg cc = c;
+  cc.st = cs;
+  const int64_t before = *c.nlaunch;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    for (int s = 0; s < steps && ok; ++s) ok = cg_iteration<F64>(cc, Xc) == cudaSuccess;
+    const bool ended = cudaStreamEndCapture(cs, &g) == cudaSuccess;
+    ok = ok && ended && g != nullptr;
+  }
+  if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  *per_block = *c.nlaunch - before;
+  *c.nlaunch = before;
+  if (!ok) {
+    (void)cudaGetLastError();
+    if (ex) cudaGraphExecDestroy(ex);
+    return nullptr;
+  }
+  return ex;
+}
+
+#define NK_CHECK_EVERY 8
+
+// CG on (K + lam I) Xc = B from Xc = 0 until every column's recursive
+// residual is below tol (relative to ||B||) or maxit iterations; *its = the
+// iterations performed (max over columns).  `graph` replays NK_CHECK_EVERY
+// iterations into Xc (or is null); hflag is pinned host memory.
+template <bool F64>
+cudaError_t cg_run(const Pcg& c, const double* B, double* Xc, double tol, int maxit,
+                   cudaGraphExec_t graph, int64_t per_block, int* hflag, int* its) {
+  *c.nlaunch += 3;
+  k_zero<<<1, 256, 0, c.st>>>(c.sc, (int64_t)SC_N * c.R);
+  k_set_active<<<1, 256, 0, c.st>>>(c.sc, c.R, tol * tol);
+  k_init<<<vgrid(c), 256, 0, c.st>>>(B, c.minv, c.N, c.R, Xc, c.Rr, c.Z, c.P, c.Pf, c.sc);
+  cudaError_t e = cudaSuccess;
+  int it = 0;
+  while (it < maxit) {
+    const int steps = std::min(NK_CHECK_EVERY, maxit - it);
+    if (graph && steps == NK_CHECK_EVERY) {
+      *c.nlaunch += per_block;
+      e = cudaGraphLaunch(graph, c.st);
+    } else {
+      for (int s = 0; s < steps && e == cudaSuccess; ++s) e = cg_iteration<F64>(c, Xc);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hflag, c.flag, sizeof(int), cudaMemcpyDeviceToHost, c.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
+    if (e != cudaSuccess) return e;
+    it += steps;
+    if (*hflag == 0) break;
+  }
+  std::vector<double> hsc((size_t)SC_N * c.R);
+  e = cudaMemcpy(hsc.data(), c.sc, sizeof(double) * SC_N * c.R, cudaMemcpyDeviceToHost);
   int mx = 0;
   for (int r = 0; r < c.R; ++r) mx = std::max(mx, (int)hsc[SC_ITER * c.R + r]);
-  free(hsc);
   *its = mx;
   return e;
 }
@@ -393,6 +531,17 @@ cudaError_t cg_run(const Pcg& c, const double* B, double* Xc, double tol, int ma
 }  // namespace
 
 // Host orchestration, called by nk_pcg_solve after argument validation.
+//
+// Mixed form: iterative refinement.  The true residual Y - (K + lam I) A is
+// formed with FP64 products; the correction is solved by CG with FP32
+// products and FP64 vectors and scalars to a relative tolerance eta; A += D.
+// With FP32 products CG's true residual stalls about two decades below its
+// right-hand side on these kernels (the recursive residual keeps falling,
+// but the products' rounding, not the Krylov space, sets the level), so each
+// sweep asks for eta = NK_ETA_FLOOR (or what is left to reach tol, if
+// larger): iterations past that level would be spent below the rounding.
+#define NK_ETA_FLOOR 3e-2
+
 nk_status nk_pcg_impl(nk_handle* h, const float* K, int64_t ldk, int64_t N, const double* Y, int R,
                       double lam, int precond, nk_prec prec, double tol, int maxit, int refine_max,
                       double* A, int* iters, double* relres, cudaStream_t st) {
@@ -405,14 +554,12 @@ nk_status nk_pcg_impl(nk_handle* h, const float* K, int64_t ldk, int64_t N, cons
   c.sm = h->sm_count;
   c.st = st;
   c.nlaunch = &h->launches;
-  const int64_t colblocks = ((N + 3) / 4 + 127) / 128;
-  int64_t S = (2 * (int64_t)c.sm + colblocks - 1) / colblocks;
-  S = std::min<int64_t>(S, std::max<int64_t>(1, N / std::max(4 * R, 32)));
-  S = std::max<int64_t>(1, std::min<int64_t>(S, 512));
-  c.S = (int)S;
+  const int occ = matvec_prepare(R);
+  const int S = choose_splits(N, R, c.sm, occ);
+  c.S = S;
   c.rows_per_split = (int)((N + S - 1) / S);
   const size_t NR = (size_t)N * R;
-  size_t bytes = NR * 8 * 8 + (size_t)S * NR * 8 + (size_t)N * 8 + SC_N * (size_t)R * 8 + NR * 4 + 16 * 256;
+  size_t bytes = NR * 8 * 7 + (size_t)S * NR * 8 + (size_t)N * 8 + SC_N * (size_t)R * 8 + NR * 4 + 12 * 256;
   if (bytes > h->pcg_bytes) {
     if (h->pcg_ws) cudaFree(h->pcg_ws);
     h->pcg_ws = nullptr;
@@ -425,110 +572,108 @@ nk_status nk_pcg_impl(nk_handle* h, const float* K, int64_t ldk, int64_t N, cons
   }
   char* w = (char*)h->pcg_ws;
   auto take = [&](size_t n) { char* p = w; w += (n + 255) / 256 * 256; return p; };
-  c.X = (double*)take(NR * 8);
   c.Rr = (double*)take(NR * 8);
   c.Z = (double*)take(NR * 8);
   c.P = (double*)take(NR * 8);
   c.Q = (double*)take(NR * 8);
   c.B2 = (double*)take(NR * 8);
-  c.D = (double*)take(NR * 8);
+  double* D = (double*)take(NR * 8);
   c.Qpart = (double*)take((size_t)S * NR * 8);
   c.minv = (double*)take((size_t)N * 8);
   c.sc = (double*)take(SC_N * (size_t)R * 8);
   c.Pf = (float*)take(NR * 4);
   c.flag = (int*)take(64);
-  int hflag_storage = 0;
-  int* hflag = nullptr;
-  if (cudaMallocHost(&hflag, sizeof(int)) != cudaSuccess) {
+
+  // pinned host words: the active-column flag and the CG scalars
+  void* host = nullptr;
+  const size_t host_bytes = 64 + sizeof(double) * SC_N * R;
+  const bool pinned = cudaMallocHost(&host, host_bytes) == cudaSuccess;
+  if (!pinned) {
     (void)cudaGetLastError();
-    hflag = &hflag_storage;
+    host = malloc(host_bytes);
   }
-  c.hflag = hflag;
-  nk_status ret = NK_OK;
-  cudaError_t e = cudaSuccess;
-  int total_it = 0;
-  double* hsc = (double*)malloc(sizeof(double) * SC_N * R);
+  int* hflag = (int*)host;
+  double* hsc = (double*)((char*)host + 64);
+  cudaGraphExec_t graph = nullptr;
   auto finish = [&](nk_status s) {
-    if (hflag != &hflag_storage) cudaFreeHost(hflag);
-    free(hsc);
+    if (graph) cudaGraphExecDestroy(graph);
+    if (pinned)
+      cudaFreeHost(host);
+    else
+      free(host);
     return s;
   };
-  ++h->launches;
+  auto read_sc = [&]() {
+    cudaError_t e = cudaMemcpyAsync(hsc, c.sc, sizeof(double) * SC_N * R, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+  };
+  // worst relative true residual after true_residual(); fills relres
+  auto worst_rel = [&]() {
+    double worst = 0.0;
+    for (int r = 0; r < R; ++r) {
+      const double yy = hsc[SC_YY * R + r];
+      const double rel = yy > 0 ? sqrt(hsc[SC_RR * R + r] / yy) : sqrt(hsc[SC_RR * R + r]);
+      if (relres) relres[r] = rel;
+      worst = std::max(worst, rel);
+    }
+    return worst;
+  };
+  cudaError_t e = cudaSuccess;
   if (lam < 0.0) {
     // relative ridge: lam = |lam| * tr(K) / N
     ++h->launches;
     k_trace<<<1, 256, 0, st>>>(K, ldk, N, c.sc);
-    double tr = 0.0;
     e = cudaMemcpyAsync(hsc, c.sc, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return finish(nk_cuda_check(h, e, "pcg trace"));
-    tr = hsc[0];
-    lam = -lam * tr / (double)N;
+    lam = -lam * hsc[0] / (double)N;
     c.lam = lam;
   }
   h->last_lambda = lam;
+  ++h->launches;
   k_minv<<<(unsigned)std::min<int64_t>((N + 255) / 256, 4 * c.sm), 256, 0, st>>>(
       K, ldk, N, lam, precond == NK_PRECOND_JACOBI, c.minv);
+  const bool f64 = prec == NK_PREC_PLAIN_FP64;
+  double* Xc = prec == NK_PREC_MIXED ? D : A;
+  int64_t per_block = 0;
+  graph = f64 ? capture_block<true>(c, Xc, NK_CHECK_EVERY, &per_block)
+              : capture_block<false>(c, Xc, NK_CHECK_EVERY, &per_block);
   bool converged = false;
+  int total_it = 0;
   if (prec == NK_PREC_MIXED) {
-    // A = 0; loop: Rt = Y - (K + lam I) A (FP64); stop if small; solve the
-    // correction with FP32-matvec CG; A += D.
     ++h->launches;
     k_zero<<<(unsigned)std::min<int64_t>((NR + 255) / 256, 4 * c.sm), 256, 0, st>>>(A, NR);
     for (int outer = 0;; ++outer) {
       e = true_residual(c, Y, A, c.B2);
+      if (e == cudaSuccess) e = read_sc();
       if (e != cudaSuccess) break;
-      e = cudaMemcpyAsync(hsc, c.sc, sizeof(double) * SC_N * R, cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess) break;
-      double worst = 0.0;
-      for (int r = 0; r < R; ++r) {
-        const double yy = hsc[SC_YY * R + r];
-        const double rel = yy > 0 ? sqrt(hsc[SC_RR * R + r] / yy) : sqrt(hsc[SC_RR * R + r]);
-        if (relres) relres[r] = rel;
-        worst = std::max(worst, rel);
+      const double worst = worst_rel();
+      if (worst <= tol) {
+        converged = true;
+        break;
       }
-      if (worst <= tol) { converged = true; break; }
       if (outer >= refine_max || total_it >= maxit) break;
-      // inner relative tolerance: what is still needed to reach tol, but no
-      // tighter than 1e-4 per sweep (FP32-product CG on ill-conditioned
-      // kernels stalls long before its rounding floor; two or three
-      // refinement sweeps at 1e-4 each are cheaper) and no looser than 1e-1
-      const double eta = std::min(std::max(0.5 * tol / worst, 1e-4), 1e-1);
+      const double eta = std::min(std::max(0.5 * tol / worst, NK_ETA_FLOOR), 0.5);
       int its = 0;
-      e = cg_run<false>(c, c.B2, c.D, eta, maxit - total_it, &its);
+      e = cg_run<false>(c, c.B2, D, eta, maxit - total_it, graph, per_block, hflag, &its);
       if (e != cudaSuccess) break;
       total_it += its;
       ++h->launches;
-      k_axpy_cols<<<(unsigned)std::min<int64_t>((NR + 255) / 256, 4 * c.sm), 256, 0, st>>>(NR, A, c.D);
+      k_add<<<(unsigned)std::min<int64_t>((NR + 255) / 256, 4 * c.sm), 256, 0, st>>>(NR, A, D);
     }
   } else {
-    int its = 0;
-    if (prec == NK_PREC_PLAIN_FP64)
-      e = cg_run<true>(c, Y, A, tol, maxit, &its);
-    else
-      e = cg_run<false>(c, Y, A, tol, maxit, &its);
-    total_it = its;
+    e = f64 ? cg_run<true>(c, Y, A, tol, maxit, graph, per_block, hflag, &total_it)
+            : cg_run<false>(c, Y, A, tol, maxit, graph, per_block, hflag, &total_it);
     if (e == cudaSuccess) e = true_residual(c, Y, A, c.B2);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(hsc, c.sc, sizeof(double) * SC_N * R, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess) {
-      double worst = 0.0;
-      for (int r = 0; r < R; ++r) {
-        const double yy = hsc[SC_YY * R + r];
-        const double rel = yy > 0 ? sqrt(hsc[SC_RR * R + r] / yy) : sqrt(hsc[SC_RR * R + r]);
-        if (relres) relres[r] = rel;
-        worst = std::max(worst, rel);
-      }
-      converged = worst <= tol;
-    }
+    if (e == cudaSuccess) e = read_sc();
+    if (e == cudaSuccess) converged = worst_rel() <= tol;
   }
   if (e != cudaSuccess) return finish(nk_cuda_check(h, e, "pcg"));
   if (iters) *iters = total_it;
   if (!converged) {
     nk_fail(h, NK_ERR_NOT_CONVERGED, "pcg did not reach tol %.3g in %d iterations", tol, total_it);
-    ret = NK_ERR_NOT_CONVERGED;
+    return finish(NK_ERR_NOT_CONVERGED);
   }
-  return finish(ret);
+  return finish(NK_OK);
 }

@@ -66,3 +66,58 @@ def test_fc_ranges_and_ldk(h):
     got = out.cpu().numpy()
     assert _maxrel(got[:, :250].astype(np.float64), want) <= 1e-5
     assert np.isnan(got[:, 250:]).all()
+
+
+@pytest.fixture(scope="module")
+def fc_full(h):
+    """The benchmark's FC workload: 50000 train + 10000 test rows of dimension
+    3072, depth 3, sigma_w^2 = 2, sigma_b^2 = 0, blocks as bench.py launches
+    them (train block symmetric, test block against all train rows)."""
+    xtr = nkdata.fc_rows(50000, 3072, nkdata.SEED_TRAIN).astype(np.float32)
+    xte = nkdata.fc_rows(10000, 3072, nkdata.SEED_TEST).astype(np.float32)
+    Xtr = torch.tensor(xtr, device="cuda")
+    Xte = torch.tensor(xte, device="cuda")
+    Ktr = h.fc_block(Xtr, Xtr, 2.0, 0.0, depth=3, symmetric=True)
+    Kte = h.fc_block(Xte, Xtr, 2.0, 0.0, depth=3)
+    h.sync_status()
+    return xtr, xte, Ktr, Kte
+
+
+def test_fc3_fullsize_sampled_entries(fc_full):
+    xtr, xte, Ktr, Kte = fc_full
+    rng = np.random.default_rng(11)
+    ii = np.concatenate([[0, 49999, 777], rng.integers(0, 50000, 60)])
+    jj = np.concatenate([[0, 49999, 777], rng.integers(0, 50000, 60)])
+    kk = rng.integers(0, 10000, 60)
+    got_tr = Ktr[torch.tensor(ii, device="cuda"), torch.tensor(jj, device="cuda")].double().cpu().numpy()
+    got_te = Kte[torch.tensor(kk, device="cuda"), torch.tensor(jj[:60], device="cuda")].double().cpu().numpy()
+    for n, (i, j) in enumerate(zip(ii, jj)):
+        want = oracle.fc_nngp(xtr[i:i + 1].astype(np.float64), xtr[j:j + 1].astype(np.float64), 2.0, 0.0,
+                              depth=3).item()
+        assert abs(got_tr[n] - want) <= 1e-5 * abs(want), (i, j, got_tr[n], want)
+    for n, (k, j) in enumerate(zip(kk, jj[:60])):
+        want = oracle.fc_nngp(xte[k:k + 1].astype(np.float64), xtr[j:j + 1].astype(np.float64), 2.0, 0.0,
+                              depth=3).item()
+        assert abs(got_te[n] - want) <= 1e-5 * abs(want), (k, j, got_te[n], want)
+
+
+def test_fc3_fullsize_properties_and_pcg(h, fc_full):
+    """Symmetric and finite at full size; the mixed PCG solve of the 10 GB
+    kernel reaches relative residual 1e-6, checked by an independent float64
+    product on the device."""
+    xtr, xte, Ktr, Kte = fc_full
+    assert bool(torch.isfinite(Ktr).all()) and bool(torch.isfinite(Kte).all())
+    for r0 in (0, 20000, 49000):
+        blk = Ktr[r0:r0 + 1000]
+        assert torch.equal(blk[:, r0:r0 + 1000], blk[:, r0:r0 + 1000].T)
+        assert torch.equal(blk[:, :1000], Ktr[:1000, r0:r0 + 1000].T)
+    Y = torch.tensor(nkdata.labels(50000, 10), device="cuda")
+    A, its, rel = h.pcg_solve(Ktr, Y, -1e-4, precond="jacobi", prec="mixed", tol=1e-6, maxit=5000)
+    lam = h.last_lambda()
+    Kd = Ktr.double()
+    r = Y - (Kd @ A + lam * A)
+    del Kd
+    rel_true = (r.norm(dim=0) / Y.norm(dim=0)).cpu().numpy()
+    assert rel_true.max() <= 1e-6
+    assert np.allclose(rel_true, rel, rtol=1e-3, atol=1e-9)
+    assert abs(lam - 1e-4 * float(torch.diagonal(Ktr).double().sum()) / 50000) <= 1e-10 * lam
