@@ -433,10 +433,11 @@ def grad_leg(h, dev):
 
 
 FC_N_TRAIN, FC_N_TEST, FC_D, FC_DEPTH = 50000, 10000, 3072, 3
+FC_SW2, FC_SB2 = 2.0, 0.01  # the FC3 listing's W_std = sqrt 2, b_std = 0.1
 
 
 def fc_leg(h, dev, peaks, n=FC_N_TRAIN, m=FC_N_TEST):
-    """Depth-3 fully-connected ReLU NNGP (sigma_w^2 = 2, sigma_b^2 = 0) on
+    """Depth-3 fully-connected ReLU NNGP (sigma_w^2 = 2, sigma_b^2 = 0.01) on
     3072-dim N(0,1) rows scaled to norm sqrt(d): the 50000 x 50000 train Gram (upper triangle, mirrored)
     and the 10000 x 50000 test block by the split-BF16 tensor-core kernel
     with the fused arc-cosine recursion, then the PCG ridge solve of the
@@ -458,16 +459,16 @@ def fc_leg(h, dev, peaks, n=FC_N_TRAIN, m=FC_N_TEST):
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
     def grams():
-        h.fc_block(xtr, xtr, SW2, SB2, FC_DEPTH, symmetric=True, out=Ktr)
-        h.fc_block(xte, xtr, SW2, SB2, FC_DEPTH, out=Kte)
+        h.fc_block(xtr, xtr, FC_SW2, FC_SB2, FC_DEPTH, symmetric=True, out=Ktr)
+        h.fc_block(xte, xtr, FC_SW2, FC_SB2, FC_DEPTH, out=Kte)
 
     grams()
     torch.cuda.synchronize()
     marks = [ev() for _ in range(3)]
     marks[0].record(stream)
-    h.fc_block(xtr, xtr, SW2, SB2, FC_DEPTH, symmetric=True, out=Ktr)
+    h.fc_block(xtr, xtr, FC_SW2, FC_SB2, FC_DEPTH, symmetric=True, out=Ktr)
     marks[1].record(stream)
-    h.fc_block(xte, xtr, SW2, SB2, FC_DEPTH, out=Kte)
+    h.fc_block(xte, xtr, FC_SW2, FC_SB2, FC_DEPTH, out=Kte)
     marks[2].record(stream)
     torch.cuda.synchronize()
     t_sym = marks[0].elapsed_time(marks[1]) / 1e3

@@ -12,11 +12,10 @@
 // raster (8 tile rows at a time, so that concurrent CTAs share B tiles in
 // L2).  Operand tiles (128 x 64 and 256 x 64 BF16) arrive by TMA with
 // 128-byte swizzle through a 4-stage mbarrier ring; one thread issues the
-// MMAs into one of two 256-column TMEM accumulators while four epilogue warps
-// drain the other: each reads its 32 rows from TMEM, applies the whole
+// MMAs into one of two 256-column TMEM accumulators while eight epilogue warps
+// drain the other: each reads 32 rows x 128 columns from TMEM, applies the whole
 // arc-cosine recursion layer by layer over 32 entries at a time (column
-// factors staged in shared memory), and stores K rows through a transposed
-// shared-memory chunk so that every warp store covers 128 contiguous bytes.  The
+// factors staged in shared memory) and stores 16 bytes of a K row per lane.  The
 // self-variances q_l of each row follow the closed diagonal recursion
 // q_1 = sw2 |x|^2/d + sb2, q_{l+1} = sw2 q_l / 2 + sb2 (FP64).
 // Symmetric blocks run only tiles touching the upper triangle and store each
@@ -38,8 +37,8 @@
 namespace {
 
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
-constexpr int GROUP_M = 8;      // tile rows per raster group (L2 reuse of B)
-constexpr int EPI_WARPS = 4;    // one per TMEM lane quarter
+constexpr int GROUP_M = 16;     // tile rows per raster group (L2 reuse of B)
+constexpr int EPI_WARPS = 8;    // two per TMEM lane quarter, 128 columns each
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t WAIT_LIMIT = 1u << 26;
 constexpr int MAX_DEPTH = 8;
@@ -48,7 +47,7 @@ struct GemmSmem {
   alignas(1024) __nv_bfloat16 A[STAGES][BM * BK];
   alignas(1024) __nv_bfloat16 B[STAGES][BN * BK];
   float2 qb[BN * MAX_DEPTH];             // per-column (1/sqrt q, sqrt q) of the current tile
-  float stage[EPI_WARPS][32 * 32];       // transposes 32 x 32 output chunks (XOR-swizzled)
+  float2 qa[BM * MAX_DEPTH];             // per-row (1/sqrt q, sqrt q * sw2/(2 pi))
   uint64_t full[STAGES], empty[STAGES];  // operand ring
   uint64_t tfull[2], tempty[2];          // TMEM accumulators: MMA -> epilogue, epilogue -> MMA
   uint64_t done;
@@ -107,7 +106,7 @@ __device__ __forceinline__ bool named_any(int id, int n, bool v) {
 }
 
 // Persistent kernel, one CTA per SM, tiles t = blockIdx.x + k * gridDim.x.
-// Warp 0: TMA producer; warp 1: TMEM owner and MMA issuer; warps 2..5:
+// Warp 0: TMA producer; warp 1: TMEM owner and MMA issuer; warps 2..9:
 // epilogue.  Two 256-column TMEM accumulators let the MMAs of the next tile
 // run while the epilogue drains the previous one.
 __global__ void __launch_bounds__(THREADS, 1)
@@ -203,52 +202,62 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       if (!tc::mbar_wait(&S.done, 0, WAIT_LIMIT)) atomicOr(P.dstatus, NK_DEV_TIMEOUT);
     }
   } else {
-    // epilogue: TMEM lane quarter q holds tile rows 32q .. 32q+31
+    // epilogue: TMEM lane quarter q holds tile rows 32q .. 32q+31; the two
+    // warps of a quarter take columns [0, 128) and [128, 256)
     const int q = warp & 3;
-    const int et = threadIdx.x - 64;  // 0 .. 127
-    float* st = S.stage[warp - 2];
+    const int cbeg = ((warp - 2) >> 2) * (BN / 2);
+    const int et = threadIdx.x - 64;  // 0 .. 32 * EPI_WARPS - 1
+    const bool vec_ok = (P.ldk % 4 == 0) && ((reinterpret_cast<uintptr_t>(P.K) & 15) == 0);
     int n = 0;
     for (int64_t t = blockIdx.x; t < nslots; t += gridDim.x) {
       int tm, tn;
       if (!tile_of(P, t, tm, tn)) continue;
       const int64_t m0 = (int64_t)tm * BM, n0 = (int64_t)tn * BN;
-      // column factors of this tile into shared memory
+      // row and column factors of this tile into shared memory
       named_sync(1, 32 * EPI_WARPS);
       for (int e = et; e < BN * P.depth; e += 32 * EPI_WARPS) {
         const int64_t j = n0 + e / P.depth;
         S.qb[e] = j < P.N ? P.qb[n0 * P.depth + e] : make_float2(0.f, 0.f);
       }
+      for (int e = et; e < BM * P.depth; e += 32 * EPI_WARPS) {
+        const int64_t i = m0 + e / P.depth;
+        S.qa[e] = i < P.M ? P.qa[m0 * P.depth + e] : make_float2(0.f, 0.f);
+      }
       named_sync(1, 32 * EPI_WARPS);
       const int acc = n & 1;
       const bool got = tc::mbar_wait(&S.tfull[acc], (uint32_t)((n >> 1) & 1), WAIT_LIMIT);
-      // the four warps leave together (they share named barriers)
+      // the epilogue warps leave together (they share named barriers)
       if (named_any(2, 32 * EPI_WARPS, !got)) {
         atomicOr(P.dstatus, NK_DEV_TIMEOUT);
         break;
       }
       tc::tc_fence_after();
-      const int64_t i = m0 + 32 * q + lane;
+      const int row = 32 * q + lane;
+      const int64_t i = m0 + row;
       const bool rowok = i < P.M;
       const float self_k1 = (rowok && P.same) ? P.q1a[i] : 0.f;
-      const float2* qrow = P.qa + (rowok ? i : 0) * P.depth;
+      const float2* qr = S.qa + row * P.depth;
       const uint32_t taddr = tbase + (uint32_t)(acc * BN) + ((uint32_t)(32 * q) << 16);
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int c0 = cbeg; c0 < cbeg + BN / 2; c0 += 32) {
         float v[32];
         tc::tmem_ld32(taddr + (uint32_t)c0, v);
-        if (c0 + 32 == BN) {
-          // the accumulator is free for the MMAs of a later tile
+        if (c0 + 32 == cbeg + BN / 2) {
+          // this warp's part of the accumulator is free for a later tile
           tc::tc_fence_before();
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(&S.tempty[acc]);
         }
+        if (P.same) {
+          const int64_t d = i + P.selfoff - (n0 + c0);  // column of the self pair, if in this chunk
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
-          v[e] = fmaf(P.kscale, v[e], P.sb2);
-          if (P.same && n0 + c0 + e == i + P.selfoff) v[e] = self_k1;
+          for (int e = 0; e < 32; ++e) v[e] = (d == e) ? self_k1 : fmaf(P.kscale, v[e], P.sb2);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 32; ++e) v[e] = fmaf(P.kscale, v[e], P.sb2);
         }
         // layer by layer over the 32 entries (independent chains)
         for (int l = 0; l < P.depth; ++l) {
-          const float2 ra = rowok ? qrow[l] : make_float2(0.f, 0.f);
+          const float2 ra = qr[l];
           const float2* qc = S.qb + c0 * P.depth + l;
           if (l == 0) {
 #pragma unroll
@@ -264,25 +273,29 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
             }
           }
         }
+        if (!rowok) continue;
+        const int64_t jb = n0 + c0;
         // mirror of a symmetric block: column stores (j, i), coalesced over i
-        if (P.sym && rowok) {
+        if (P.sym) {
 #pragma unroll
           for (int e = 0; e < 32; ++e) {
-            const int64_t j = n0 + c0 + e;
+            const int64_t j = jb + e;
             if (j < P.N && j > i) P.K[j * P.ldk + i] = v[e];
           }
         }
-        // row stores (i, j) through a transposed chunk: lane = column
-        __syncwarp();
+        // row stores (i, j): 16 bytes per lane; the two halves of a 32-byte
+        // sector come from the same lane in consecutive stores
+        float* krow = P.K + i * P.ldk + jb;
 #pragma unroll
-        for (int e = 0; e < 32; ++e) st[lane * 32 + (e ^ lane)] = v[e];
-        __syncwarp();
-        const int64_t j = n0 + c0 + lane;
-#pragma unroll 4
-        for (int r = 0; r < 32; ++r) {
-          const int64_t ir = m0 + 32 * q + r;
-          const float val = st[r * 32 + (lane ^ r)];
-          if (ir < P.M && j < P.N && (!P.sym || j >= ir)) P.K[ir * P.ldk + j] = val;
+        for (int e4 = 0; e4 < 32; e4 += 4) {
+          const int64_t j = jb + e4;
+          if (vec_ok && j + 3 < P.N && (!P.sym || j >= i)) {
+            *reinterpret_cast<float4*>(krow + e4) = make_float4(v[e4], v[e4 + 1], v[e4 + 2], v[e4 + 3]);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (j + u < P.N && (!P.sym || j + u >= i)) krow[e4 + u] = v[e4 + u];
+          }
         }
       }
       ++n;

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(NK_MV_THREADS, (F64 && RB > 8) ? 2 : 4)
 k_matvec(const float* __restrict__ K, int64_t ldk, int64_t N, const void* __restrict__ Pin, int R,
          int rc0, int rcnt, int rows_per_split, double* __restrict__ Qpart) {
   using T = typename std::conditional<F64, double, float>::type;
-  constexpr int U = F64 ? 2 : 4;  // rows per unrolled step
+  constexpr int U = F64 ? 2 : 8;  // rows per unrolled step
   extern __shared__ double mv_sh[];
   const int tid = threadIdx.x;
   const int64_t i0 = ((int64_t)blockIdx.x * NK_MV_THREADS + tid) * 4;
@@ -134,6 +134,84 @@ k_matvec(const float* __restrict__ K, int64_t ldk, int64_t N, const void* __rest
 template <int RB, bool F64>
 constexpr size_t mv_smem() {
   return F64 ? 0 : (size_t)4 * RB * NK_MV_THREADS * sizeof(double);
+}
+
+// K @ X for the true residual, with X = Xh + Xl split into two FP32 arrays
+// (Xh = fl32(X), Xl = fl32(X - Xh)).  Each product k * xh is taken exactly
+// as a pair (p, e) (p = fl32(k xh), e = fma(k, xh, -p)); p enters a
+// double-FP32 sum (s, c) through Knuth's TwoSum, and e + k * xl go to the low
+// part.  Every step rounds at about 2^-48 relative to the running sum, close
+// to FP64, on the FP32 units (64 times the FP64 rate on this part).
+template <int RB>
+__global__ void __launch_bounds__(NK_MV_THREADS, RB > 8 ? 3 : 4)
+k_matvec_df(const float* __restrict__ K, int64_t ldk, int64_t N, const float* __restrict__ Xh,
+            const float* __restrict__ Xl, int R, int rc0, int rcnt, int rows_per_split,
+            double* __restrict__ Qpart) {
+  constexpr int CPT = 2;  // columns per thread
+  const int tid = threadIdx.x;
+  const int64_t i0 = ((int64_t)blockIdx.x * NK_MV_THREADS + tid) * CPT;
+  const int64_t js = (int64_t)blockIdx.y * rows_per_split;
+  const int64_t je = std::min<int64_t>(N, js + rows_per_split);
+  float sh[CPT][RB], sl[CPT][RB];
+#pragma unroll
+  for (int c = 0; c < CPT; ++c)
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      sh[c][r] = 0.f;
+      sl[c][r] = 0.f;
+    }
+  const bool vec = (i0 + CPT - 1 < N) && (ldk % 2 == 0) && ((reinterpret_cast<uintptr_t>(K) & 7) == 0);
+  for (int64_t j = js; j < je; ++j) {
+    float k[CPT];
+    const float* row = K + j * ldk + i0;
+    if (vec) {
+      const float2 v = __ldg(reinterpret_cast<const float2*>(row));
+      k[0] = v.x;
+      k[1] = v.y;
+    } else {
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) k[c] = (i0 + c < N) ? __ldg(row + c) : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      if (r < rcnt) {
+        const float xh = __ldg(Xh + j * R + rc0 + r);
+        const float xl = __ldg(Xl + j * R + rc0 + r);
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          // explicit roundings: no contraction of p into the sum
+          const float p = __fmul_rn(k[c], xh);
+          const float e = fmaf(k[c], xh, -p);
+          const float t = __fadd_rn(sh[c][r], p);  // TwoSum(sh, p)
+          const float bp = __fsub_rn(t, sh[c][r]);
+          const float err = __fadd_rn(__fsub_rn(sh[c][r], __fsub_rn(t, bp)), __fsub_rn(p, bp));
+          sh[c][r] = t;
+          sl[c][r] = __fadd_rn(sl[c][r], __fadd_rn(err, fmaf(k[c], xl, e)));
+        }
+      }
+    }
+  }
+  double* out = Qpart + (int64_t)blockIdx.y * N * R;
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) {
+    if (i0 + c < N) {
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+        if (r < rcnt) out[(i0 + c) * R + rc0 + r] = (double)sh[c][r] + (double)sl[c][r];
+    }
+  }
+}
+
+// Xh = fl32(X), Xl = fl32(X - Xh)
+__global__ void k_split_f32(int64_t n, const double* __restrict__ X, float* __restrict__ Xh,
+                            float* __restrict__ Xl) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double x = X[e];
+    const float h = (float)x;
+    Xh[e] = h;
+    Xl[e] = (float)(x - (double)h);
+  }
 }
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -345,6 +423,7 @@ struct Pcg {
   cudaStream_t st;
   double *Rr, *Z, *P, *Q, *Qpart, *minv, *sc, *B2;
   float* Pf;
+  float *Xh, *Xl;    // double-FP32 split of the iterate (true residuals)
   int* flag;         // device: active columns after the last iteration
   int64_t* nlaunch;  // handle launch counter
 };
@@ -421,21 +500,46 @@ inline dim3 vgrid(const Pcg& c) {
   return dim3((unsigned)std::max<int64_t>(1, b), (unsigned)c.R);
 }
 
-// Q = (K + lam I) Xc with FP64 products and sums.
-cudaError_t apply_fp64(const Pcg& c, const double* Xc) {
-  cudaError_t e = matvec<true>(c, Xc);
-  if (e != cudaSuccess) return e;
+// Q = (K + lam I) Xc with FP64 products and sums (exact_fp64) or with the
+// double-FP32 products and sums of k_matvec_df.
+cudaError_t apply_accurate(const Pcg& c, const double* Xc, bool exact_fp64) {
+  if (exact_fp64) {
+    cudaError_t e = matvec<true>(c, Xc);
+    if (e != cudaSuccess) return e;
+  } else {
+    const int64_t NR = c.N * (int64_t)c.R;
+    ++*c.nlaunch;
+    k_split_f32<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((NR + 255) / 256, 4 * (int64_t)c.sm)), 256,
+                  0, c.st>>>(NR, Xc, c.Xh, c.Xl);
+    const int64_t colthreads = (c.N + 1) / 2;  // two columns per thread
+    dim3 grid((unsigned)((colthreads + NK_MV_THREADS - 1) / NK_MV_THREADS), (unsigned)c.S);
+    for (int rc0 = 0; rc0 < c.R; rc0 += 16) {
+      const int rcnt = std::min(16, c.R - rc0);
+      ++*c.nlaunch;
+      if (rcnt <= 4)
+        k_matvec_df<4><<<grid, NK_MV_THREADS, 0, c.st>>>(c.K, c.ldk, c.N, c.Xh, c.Xl, c.R, rc0, rcnt,
+                                                         c.rows_per_split, c.Qpart);
+      else if (rcnt <= 10)
+        k_matvec_df<10><<<grid, NK_MV_THREADS, 0, c.st>>>(c.K, c.ldk, c.N, c.Xh, c.Xl, c.R, rc0, rcnt,
+                                                          c.rows_per_split, c.Qpart);
+      else
+        k_matvec_df<16><<<grid, NK_MV_THREADS, 0, c.st>>>(c.K, c.ldk, c.N, c.Xh, c.Xl, c.R, rc0, rcnt,
+                                                          c.rows_per_split, c.Qpart);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   ++*c.nlaunch;
   k_reduce_dot<<<vgrid(c), 256, 0, c.st>>>(c.Qpart, c.S, c.N, c.R, Xc, c.lam, c.Q, c.sc, -1);
   return cudaGetLastError();
 }
 
-// True residual out = B - (K + lam I) X in FP64 into sc[RR], sc[YY] (the CG
-// state in sc is overwritten).
-cudaError_t true_residual(const Pcg& c, const double* B, const double* Xc, double* out) {
+// True residual out = B - (K + lam I) X into sc[RR], sc[YY] (the CG state
+// in sc is overwritten).
+cudaError_t true_residual(const Pcg& c, const double* B, const double* Xc, double* out, bool exact_fp64) {
   ++*c.nlaunch;
   k_zero<<<1, 256, 0, c.st>>>(c.sc, (int64_t)SC_N * c.R);
-  cudaError_t e = apply_fp64(c, Xc);
+  cudaError_t e = apply_accurate(c, Xc, exact_fp64);
   if (e != cudaSuccess) return e;
   ++*c.nlaunch;
   k_resid<<<vgrid(c), 256, 0, c.st>>>(B, c.Q, c.N, c.R, out, c.sc);
@@ -559,7 +663,7 @@ nk_status nk_pcg_impl(nk_handle* h, const float* K, int64_t ldk, int64_t N, cons
   c.S = S;
   c.rows_per_split = (int)((N + S - 1) / S);
   const size_t NR = (size_t)N * R;
-  size_t bytes = NR * 8 * 7 + (size_t)S * NR * 8 + (size_t)N * 8 + SC_N * (size_t)R * 8 + NR * 4 + 12 * 256;
+  size_t bytes = NR * 8 * 7 + (size_t)S * NR * 8 + (size_t)N * 8 + SC_N * (size_t)R * 8 + NR * 4 * 3 + 14 * 256;
   if (bytes > h->pcg_bytes) {
     if (h->pcg_ws) cudaFree(h->pcg_ws);
     h->pcg_ws = nullptr;
@@ -582,6 +686,8 @@ nk_status nk_pcg_impl(nk_handle* h, const float* K, int64_t ldk, int64_t N, cons
   c.minv = (double*)take((size_t)N * 8);
   c.sc = (double*)take(SC_N * (size_t)R * 8);
   c.Pf = (float*)take(NR * 4);
+  c.Xh = (float*)take(NR * 4);
+  c.Xl = (float*)take(NR * 4);
   c.flag = (int*)take(64);
 
   // pinned host words: the active-column flag and the CG scalars
@@ -645,7 +751,16 @@ nk_status nk_pcg_impl(nk_handle* h, const float* K, int64_t ldk, int64_t N, cons
     ++h->launches;
     k_zero<<<(unsigned)std::min<int64_t>((NR + 255) / 256, 4 * c.sm), 256, 0, st>>>(A, NR);
     for (int outer = 0;; ++outer) {
-      e = true_residual(c, Y, A, c.B2);
+      if (outer == 0) {
+        // A = 0: the residual is Y itself
+        h->launches += 3;
+        k_zero<<<1, 256, 0, st>>>(c.sc, (int64_t)SC_N * R);
+        k_zero<<<(unsigned)std::min<int64_t>((NR + 255) / 256, 4 * c.sm), 256, 0, st>>>(c.Q, NR);
+        k_resid<<<vgrid(c), 256, 0, st>>>(Y, c.Q, N, R, c.B2, c.sc);
+        e = cudaGetLastError();
+      } else {
+        e = true_residual(c, Y, A, c.B2, false);
+      }
       if (e == cudaSuccess) e = read_sc();
       if (e != cudaSuccess) break;
       const double worst = worst_rel();
@@ -665,7 +780,7 @@ nk_status nk_pcg_impl(nk_handle* h, const float* K, int64_t ldk, int64_t N, cons
   } else {
     e = f64 ? cg_run<true>(c, Y, A, tol, maxit, graph, per_block, hflag, &total_it)
             : cg_run<false>(c, Y, A, tol, maxit, graph, per_block, hflag, &total_it);
-    if (e == cudaSuccess) e = true_residual(c, Y, A, c.B2);
+    if (e == cudaSuccess) e = true_residual(c, Y, A, c.B2, f64);
     if (e == cudaSuccess) e = read_sc();
     if (e == cudaSuccess) converged = worst_rel() <= tol;
   }

@@ -71,14 +71,14 @@ def test_fc_ranges_and_ldk(h):
 @pytest.fixture(scope="module")
 def fc_full(h):
     """The benchmark's FC workload: 50000 train + 10000 test rows of dimension
-    3072, depth 3, sigma_w^2 = 2, sigma_b^2 = 0, blocks as bench.py launches
+    3072, depth 3, sigma_w^2 = 2, sigma_b^2 = 0.01, blocks as bench.py launches
     them (train block symmetric, test block against all train rows)."""
     xtr = nkdata.fc_rows(50000, 3072, nkdata.SEED_TRAIN).astype(np.float32)
     xte = nkdata.fc_rows(10000, 3072, nkdata.SEED_TEST).astype(np.float32)
     Xtr = torch.tensor(xtr, device="cuda")
     Xte = torch.tensor(xte, device="cuda")
-    Ktr = h.fc_block(Xtr, Xtr, 2.0, 0.0, depth=3, symmetric=True)
-    Kte = h.fc_block(Xte, Xtr, 2.0, 0.0, depth=3)
+    Ktr = h.fc_block(Xtr, Xtr, 2.0, 0.01, depth=3, symmetric=True)
+    Kte = h.fc_block(Xte, Xtr, 2.0, 0.01, depth=3)
     h.sync_status()
     return xtr, xte, Ktr, Kte
 
@@ -92,11 +92,11 @@ def test_fc3_fullsize_sampled_entries(fc_full):
     got_tr = Ktr[torch.tensor(ii, device="cuda"), torch.tensor(jj, device="cuda")].double().cpu().numpy()
     got_te = Kte[torch.tensor(kk, device="cuda"), torch.tensor(jj[:60], device="cuda")].double().cpu().numpy()
     for n, (i, j) in enumerate(zip(ii, jj)):
-        want = oracle.fc_nngp(xtr[i:i + 1].astype(np.float64), xtr[j:j + 1].astype(np.float64), 2.0, 0.0,
+        want = oracle.fc_nngp(xtr[i:i + 1].astype(np.float64), xtr[j:j + 1].astype(np.float64), 2.0, 0.01,
                               depth=3).item()
         assert abs(got_tr[n] - want) <= 1e-5 * abs(want), (i, j, got_tr[n], want)
     for n, (k, j) in enumerate(zip(kk, jj[:60])):
-        want = oracle.fc_nngp(xte[k:k + 1].astype(np.float64), xtr[j:j + 1].astype(np.float64), 2.0, 0.0,
+        want = oracle.fc_nngp(xte[k:k + 1].astype(np.float64), xtr[j:j + 1].astype(np.float64), 2.0, 0.01,
                               depth=3).item()
         assert abs(got_te[n] - want) <= 1e-5 * abs(want), (k, j, got_te[n], want)
 
