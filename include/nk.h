@@ -215,6 +215,37 @@ nk_status nk_block_fused_noalloc(const nk_arch* arch, const nk_params* prm,
                                  int H, int W, int C, float* K, int64_t ldk, int symmetric,
                                  void* stream, char* err_buf, size_t err_len);
 
+/* One block of a kernel-block queue (nk_block_queue).  Images NHWC float32
+ * of side H == W, self-variance pairs qs from nk_self_diag for that size,
+ * output K[(i - a0) * ldk + (j - b0)] as in nk_block. */
+typedef struct {
+  const float* Xa;
+  const float* qsa;
+  int64_t a0, a1;
+  const float* Xb;
+  const float* qsb;
+  int64_t b0, b1;
+  int H, W;
+  float* K;
+  int64_t ldk;
+  int symmetric;
+} nk_block_task;
+
+#define NK_QUEUE_MAX 8
+
+/* Several kernel blocks (Figure 1: blocks of the kernel matrix are computed
+ * independently and batched to fill the device), possibly of different image
+ * sizes, in ONE persistent launch of the fused MIXED kernel.  Every block uses
+ * the same architecture, parameters and channel count C; image sides 8, 16
+ * or 32 (other sizes: NK_ERR_UNSUPPORTED).  A 32x32 pair is computed by a
+ * 4-CTA cluster, a 16x16 or 8x8 pair by one CTA; larger images are queued
+ * first.  Stream-ordered and asynchronous; allocates nothing, so it may be
+ * captured in a CUDA graph (the handle's 64 KB scratch holds the
+ * global-average slots: calls on one handle must be stream-ordered).
+ * n_tasks in 0..NK_QUEUE_MAX; tasks is a host array. */
+nk_status nk_block_queue(nk_handle* h, const nk_arch* arch, const nk_params* prm, int C,
+                         const nk_block_task* tasks, int n_tasks, void* stream);
+
 /* Kernel-ridge solve (K + lambda I) A = Y by Jacobi-preconditioned CG, one CG
  * per column run in lock-step (Section 2 "Iterative solvers"; Appendix B.3).
  *   K [N][ldk] float32 (device, symmetric), Y [N][R] float64 (device, row

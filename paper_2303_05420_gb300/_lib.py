@@ -25,7 +25,7 @@ PRECOND = {"none": 0, "jacobi": 1}
 EXPORTS = ["nk_create", "nk_destroy", "nk_status_string", "nk_last_error", "nk_sync_status",
            "nk_q_size", "nk_launch_count", "nk_last_lambda", "nk_self_diag", "nk_block", "nk_block_backward", "nk_fc_block",
            "nk_autotune",
-           "nk_autotune_set", "nk_block_fused_noalloc", "nk_pcg_solve"]
+           "nk_autotune_set", "nk_block_fused_noalloc", "nk_block_queue", "nk_pcg_solve"]
 
 
 class NkArch(ctypes.Structure):
@@ -34,6 +34,15 @@ class NkArch(ctypes.Structure):
 
 class NkParams(ctypes.Structure):
     _fields_ = [("sigma_w2", c_double), ("sigma_b2", c_double)]
+
+
+class NkBlockTask(ctypes.Structure):
+    _fields_ = [("Xa", c_void_p), ("qsa", c_void_p), ("a0", c_int64), ("a1", c_int64),
+                ("Xb", c_void_p), ("qsb", c_void_p), ("b0", c_int64), ("b1", c_int64),
+                ("H", c_int), ("W", c_int), ("K", c_void_p), ("ldk", c_int64), ("symmetric", c_int)]
+
+
+NK_QUEUE_MAX = 8
 
 
 class NkError(RuntimeError):
@@ -95,6 +104,9 @@ def lib():
                                          c_int64, c_void_p, c_void_p, c_int64, c_int64, c_int, c_int,
                                          c_int, c_void_p, c_int64, c_int, c_void_p, c_char_p, c_size_t]
     L.nk_block_fused_noalloc.restype = c_int
+    L.nk_block_queue.argtypes = [c_void_p, POINTER(NkArch), POINTER(NkParams), c_int, POINTER(NkBlockTask),
+                                 c_int, c_void_p]
+    L.nk_block_queue.restype = c_int
     L.nk_pcg_solve.argtypes = [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_int, c_double, c_int,
                                c_int, c_double, c_int, c_int, c_void_p, POINTER(c_int),
                                c_void_p, c_void_p]

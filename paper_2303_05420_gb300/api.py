@@ -123,6 +123,38 @@ class Handle:
         self.check(st, "nk_block")
         return out
 
+    def block_queue(self, tasks: Sequence[dict], convs: Sequence[int], sw2: float, sb2: float,
+                    filt: int = 3) -> list:
+        """Several MIXED kernel blocks, of image sides 8, 16 or 32, in one
+        persistent launch (nk_block_queue).  Each task is a dict with keys
+        Xa, qa, Xb, qb (self_diag outputs), optional a_range, b_range,
+        symmetric, out.  Returns the output tensors in task order."""
+        if len(tasks) > _lib.NK_QUEUE_MAX:
+            raise NkError(_lib.NK_ERR_INVALID_ARG, f"at most {_lib.NK_QUEUE_MAX} tasks")
+        arr = (_lib.NkBlockTask * max(1, len(tasks)))()
+        outs = []
+        C = None
+        for k, t in enumerate(tasks):
+            Xa, Xb = t["Xa"], t["Xb"]
+            assert Xa.is_cuda and Xa.dtype == torch.float32 and Xb.dtype == torch.float32
+            _, H, W, Ck = Xa.shape
+            C = Ck if C is None else C
+            a0, a1 = t.get("a_range") or (0, Xa.shape[0])
+            b0, b1 = t.get("b_range") or (0, Xb.shape[0])
+            out = t.get("out")
+            if out is None:
+                out = torch.empty((a1 - a0, b1 - b0), dtype=torch.float32, device=Xa.device)
+            assert out.dtype == torch.float32 and out.stride(1) == 1
+            outs.append(out)
+            arr[k] = _lib.NkBlockTask(_ptr(Xa), _ptr(t["qa"][1]), a0, a1, _ptr(Xb), _ptr(t["qb"][1]), b0, b1,
+                                      H, W, _ptr(out), out.stride(0), int(bool(t.get("symmetric", False))))
+        a = make_arch(convs, filt)
+        p = make_params(sw2, sb2)
+        st = lib().nk_block_queue(self._h, byref(a), byref(p), int(C or 3), arr, len(tasks),
+                                  c_void_p(_stream()))
+        self.check(st, "nk_block_queue")
+        return outs
+
     def fc_block(self, Xa: torch.Tensor, Xb: torch.Tensor, sw2: float, sb2: float, depth: int = 3,
                  a_range=None, b_range=None, symmetric: bool = False,
                  out: Optional[torch.Tensor] = None) -> torch.Tensor:

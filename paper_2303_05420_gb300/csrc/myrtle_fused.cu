@@ -21,12 +21,10 @@ bool nk_myrtle_fused_supported(const NkGeom& g) {
   return ok;
 }
 
-cudaError_t nk_launch_myrtle_fused(const NkGeom& g, double sw2, double sb2, const float* Xa,
-                                   const float* qsa, int64_t a0, int64_t a1, const float* Xb,
-                                   const float* qsb, int64_t b0, int64_t b1, float* K,
-                                   int64_t ldk, int symmetric, int sm_count, void* scratch,
-                                   size_t scratch_bytes, int variant, cudaStream_t st) {
-  if (!nk_myrtle_fused_supported(g)) return cudaErrorNotSupported;
+// Kernel parameters of one block (everything but the scratch slots).
+nkf::FusedParams nk_fused_params(const NkGeom& g, double sw2, double sb2, const float* Xa, const float* qsa,
+                                 int64_t a0, int64_t a1, const float* Xb, const float* qsb, int64_t b0,
+                                 int64_t b1, float* K, int64_t ldk, int symmetric) {
   nkf::FusedParams P = {};
   P.Xa = Xa;
   P.Xb = Xb;
@@ -38,7 +36,6 @@ cudaError_t nk_launch_myrtle_fused(const NkGeom& g, double sw2, double sb2, cons
   P.nb = b1 - b0;
   P.sym = symmetric;
   P.npairs = symmetric ? P.na * (P.na + 1) / 2 : P.na * P.nb;
-  if (P.npairs <= 0) return cudaSuccess;
   P.K = K;
   P.ldk = ldk;
   P.C = g.C;
@@ -63,6 +60,18 @@ cudaError_t nk_launch_myrtle_fused(const NkGeom& g, double sw2, double sb2, cons
   const int Rg = g.Hs[0] >> (SE - 1);
   P.out_scale = sw2 / ((double)Rg * Rg * Rg * Rg);
   P.out_bias = sb2;
+  return P;
+}
+
+cudaError_t nk_launch_myrtle_fused(const NkGeom& g, double sw2, double sb2, const float* Xa,
+                                   const float* qsa, int64_t a0, int64_t a1, const float* Xb,
+                                   const float* qsb, int64_t b0, int64_t b1, float* K,
+                                   int64_t ldk, int symmetric, int sm_count, void* scratch,
+                                   size_t scratch_bytes, int variant, cudaStream_t st) {
+  if (!nk_myrtle_fused_supported(g)) return cudaErrorNotSupported;
+  nkf::FusedParams P = nk_fused_params(g, sw2, sb2, Xa, qsa, a0, a1, Xb, qsb, b0, b1, K, ldk, symmetric);
+  if (P.npairs <= 0) return cudaSuccess;
+  int c[3] = {g.convs[0], g.n_stages > 1 ? g.convs[1] : 0, g.n_stages > 2 ? g.convs[2] : 0};
   const int R0 = g.Hs[0];
   const bool bias = (sb2 != 0.0);
   const int v = (R0 == 32) ? variant : 0;

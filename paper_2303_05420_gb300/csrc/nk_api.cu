@@ -5,6 +5,7 @@
 
 #include <algorithm>
 
+#include "myrtle_fused.cuh"
 #include "nk_common.cuh"
 
 nk_status nk_pcg_impl(nk_handle* h, const float* K, int64_t ldk, int64_t N, const double* Y, int R,
@@ -289,6 +290,68 @@ nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_p
                                          qdb, qsb, b0, b1, K, ldk, symmetric, ws, chunk, h->dstatus, st,
                                          &h->launches);
   return nk_cuda_check(h, e, "nk_block plain launch");
+}
+
+nk_status nk_block_queue(nk_handle* h, const nk_arch* arch, const nk_params* prm, int C,
+                         const nk_block_task* tasks, int n_tasks, void* stream) {
+  if (!h) return NK_ERR_INVALID_ARG;
+  if (!prm) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_queue: params is NULL");
+  if (!(prm->sigma_w2 >= 0.0) || !(prm->sigma_b2 >= 0.0))
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_queue: negative variance");
+  if (n_tasks < 0 || n_tasks > NK_QUEUE_MAX)
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_queue: n_tasks outside 0..%d", NK_QUEUE_MAX);
+  if (n_tasks > 0 && !tasks) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_queue: tasks is NULL");
+  // validate every block before anything is enqueued
+  struct Item {
+    int R;
+    nkf::FusedParams P;
+  } items[NK_QUEUE_MAX];
+  int n = 0;
+  int c[3] = {0, 0, 0};
+  for (int t = 0; t < n_tasks; ++t) {
+    const nk_block_task& T = tasks[t];
+    NkGeom g;
+    const char* why = nullptr;
+    if (!nk_make_geom(arch, T.H, T.W, C, &g, &why))
+      return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_queue task %d: %s", t, why);
+    if (T.a0 < 0 || T.b0 < 0 || T.a1 < T.a0 || T.b1 < T.b0)
+      return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_queue task %d: bad index range", t);
+    if (T.a1 == T.a0 || T.b1 == T.b0) continue;
+    if (!T.Xa || !T.Xb || !T.K || !T.qsa || !T.qsb)
+      return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_queue task %d: NULL pointer", t);
+    if (T.ldk < T.b1 - T.b0) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_queue task %d: ldk < b1 - b0", t);
+    if (T.symmetric && (T.Xa != T.Xb || T.a0 != T.b0 || T.a1 != T.b1))
+      return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_queue task %d: symmetric needs Xa == Xb and equal ranges",
+                     t);
+    if (!nk_myrtle_fused_supported(g))
+      return nk_fail(h, NK_ERR_UNSUPPORTED,
+                     "nk_block_queue task %d: needs filter 3, ReLU, H == W in {8,16,32}, C <= 3 and one of "
+                     "the stage patterns (2,1,0) (2,1,1) (3,3,3) (1) (1,1,1)", t);
+    c[0] = g.convs[0];
+    c[1] = g.n_stages > 1 ? g.convs[1] : 0;
+    c[2] = g.n_stages > 2 ? g.convs[2] : 0;
+    items[n].R = T.H;
+    items[n].P = nk_fused_params(g, prm->sigma_w2, prm->sigma_b2, T.Xa, T.qsa, T.a0, T.a1, T.Xb, T.qsb, T.b0,
+                                 T.b1, T.K, T.ldk, T.symmetric);
+    ++n;
+  }
+  if (n == 0) return NK_OK;
+  // largest images first (their items are the longest)
+  std::stable_sort(items, items + n, [](const Item& x, const Item& y) { return x.R > y.R; });
+  nkf::QueueParams Q = {};
+  Q.n = n;
+  Q.item0[0] = 0;
+  for (int b = 0; b < n; ++b) {
+    Q.R[b] = items[b].R;
+    Q.B[b] = items[b].P;
+    const int64_t np = items[b].P.npairs;
+    const int64_t nit = (items[b].R == 32) ? np : (np + nkf::QUEUE_CL - 1) / nkf::QUEUE_CL;
+    Q.item0[b + 1] = Q.item0[b] + nit;
+  }
+  h->launches += 1;
+  cudaError_t e = nkf::launch_queue(c, prm->sigma_b2 != 0.0, Q, h->sm_count, h->small_ws, 65536,
+                                    (cudaStream_t)stream);
+  return nk_cuda_check(h, e, "nk_block_queue launch");
 }
 
 nk_status nk_block_backward(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_prec prec,
