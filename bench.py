@@ -206,7 +206,11 @@ def run_ours(args, rank, world, dist):
     Y = Yh.to(dev)
     h = Handle()
     # autotune the fused kernel's launch shape for this workload (setup, untimed)
-    variant = h.autotune(CONVS, SW2, SB2, hw, hw, 3)
+    if args.fused_variant is None:
+        variant = h.autotune(CONVS, SW2, SB2, hw, hw, 3)
+    else:
+        variant = args.fused_variant
+        h.autotune_set(CONVS, SW2, SB2, hw, hw, variant)
     Ktr = torch.empty((n_tr, n_tr), dtype=torch.float32, device=dev)
     Kte = torch.empty((n_te, n_tr), dtype=torch.float32, device=dev)
     A = torch.empty((n_tr, Y.shape[1]), dtype=torch.float64, device=dev)
@@ -342,6 +346,8 @@ def run_ours(args, rank, world, dist):
     lam_used = h.last_lambda()
     if args.grad:
         extra.update(grad_leg(h, dev))
+    if not args.skip_queue:
+        extra.update(queue_leg(h, dev))
     if not args.skip_fc:
         extra.update(fc_leg(h, dev, load_peaks(), args.fc_train, args.fc_test))
 
@@ -430,6 +436,73 @@ def grad_leg(h, dev):
     entries = 100 * 101 // 2 + 2048 * 100
     return {"grad_myrtle10_100x2048_s": dt, "grad_entries_per_s": entries / dt,
             "grad_loss": L, "grad_dsw2": gs, "grad_dsb2": gb}
+
+
+def queue_leg(h, dev):
+    """Mixed-resolution block queue (the 64x64 + 32x32 workload's structure
+    one octave down, the sizes the fused kernel covers): 512 train + 128 test
+    32x32 images (blur generator) and their 2x2-average 16x16 companions,
+    Myrtle-5 (2,1,0), sigma_w^2 = 2, sigma_b^2 = 0, 200 classes.  The four
+    blocks (train upper triangle and test block at each resolution) run as
+    one persistent launch captured in a CUDA graph; timed by replaying the
+    graph, beside the same blocks as four separate nk_block launches.  Then
+    the 200-right-hand-side MIXED PCG solve of the 32x32 train block."""
+    import numpy as np
+    import torch
+
+    import nkdata
+
+    n_tr, n_te = 512, 128
+    prob = nkdata.image_problem(n_tr, n_te, 32, n_classes=200, blur=True)
+    x32 = np.concatenate([prob.x_train, prob.x_test]).astype(np.float32)
+    x16 = nkdata.downsample2(np.concatenate([prob.x_train, prob.x_test])).astype(np.float32)
+    X32 = torch.tensor(x32, device=dev)
+    X16 = torch.tensor(x16, device=dev)
+    q32 = h.self_diag(X32, CONVS, SW2, SB2)
+    q16 = h.self_diag(X16, CONVS, SW2, SB2)
+    tasks = []
+    for X, q in ((X32, q32), (X16, q16)):
+        tasks.append(dict(Xa=X, qa=q, Xb=X, qb=q, a_range=(0, n_tr), b_range=(0, n_tr), symmetric=True,
+                          out=torch.empty((n_tr, n_tr), dtype=torch.float32, device=dev)))
+        tasks.append(dict(Xa=X, qa=q, Xb=X, qb=q, a_range=(n_tr, n_tr + n_te), b_range=(0, n_tr),
+                          out=torch.empty((n_te, n_tr), dtype=torch.float32, device=dev)))
+    entries = 2 * (n_tr * (n_tr + 1) // 2 + n_te * n_tr)
+    h.block_queue(tasks, CONVS, SW2, SB2)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="relaxed"):
+        h.block_queue(tasks, CONVS, SW2, SB2)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    g.replay()
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    a.record(stream)
+    g.replay()
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_queue = a.elapsed_time(b) / 1e3
+    a, b = ev(), ev()
+    a.record(stream)
+    for t in tasks:
+        h.block(t["Xa"], t["qa"], t["Xb"], t["qb"], CONVS, SW2, SB2, prec="mixed", a_range=t["a_range"],
+                b_range=t["b_range"], symmetric=t.get("symmetric", False), out=t["out"])
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_sep = a.elapsed_time(b) / 1e3
+    h.sync_status()
+    Y = torch.tensor(prob.y_train, device=dev)
+    a, b = ev(), ev()
+    a.record(stream)
+    _, its, rel = h.pcg_solve(tasks[0]["out"], Y, -REL_LAMBDA, precond="jacobi", prec="mixed", tol=1e-6,
+                              maxit=20000, allow_not_converged=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return {"queue_workload": "myrtle5_(2,1,0)_32x32+16x16_train512_test128_200cls_one_launch_graph",
+            "queue_entries": entries, "queue_graph_ms": 1e3 * t_queue,
+            "queue_entries_per_s": entries / t_queue, "queue_separate_launches_ms": 1e3 * t_sep,
+            "queue_pcg200_iters": its, "queue_pcg200_ms": a.elapsed_time(b),
+            "queue_pcg200_relres": max(rel)}
 
 
 FC_N_TRAIN, FC_N_TEST, FC_D, FC_DEPTH = 50000, 10000, 3072, 3
@@ -568,6 +641,10 @@ def main():
     ap.add_argument("--ref-pairs", type=int, default=4)
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fused-variant", type=int, default=None,
+                    help="pin the fused kernel's launch variant instead of autotuning it")
+    ap.add_argument("--skip-queue", action="store_true",
+                    help="skip the mixed-resolution block-queue leg")
     ap.add_argument("--skip-fc", action="store_true",
                     help="skip the depth-3 FC NNGP leg (50000 x 50000 Gram and its PCG solve)")
     ap.add_argument("--fc-train", type=int, default=FC_N_TRAIN)

@@ -880,6 +880,8 @@ cudaError_t launch_queue(const int c[3], bool bias, QueueParams& Q, int sm_count
 // the stage pattern c[0..2], bias flag and launch variant.
 cudaError_t dispatch_r32(const int c[3], bool bias, int variant, FusedParams& P, int sm_count,
                          void* scratch, size_t scratch_bytes, cudaStream_t st);
+cudaError_t dispatch_r32_v2(const int c[3], bool bias, int variant, FusedParams& P, int sm_count,
+                             void* scratch, size_t scratch_bytes, cudaStream_t st);
 cudaError_t dispatch_r16(const int c[3], bool bias, int variant, FusedParams& P, int sm_count,
                          void* scratch, size_t scratch_bytes, cudaStream_t st);
 cudaError_t dispatch_r8(const int c[3], bool bias, int variant, FusedParams& P, int sm_count,

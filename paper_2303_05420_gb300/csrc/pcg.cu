@@ -230,17 +230,59 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return s;  // valid in thread 0
 }
 
-// Q = sum_s Qpart[s] + lam * P ; sc[PQ][r] += P . Q  (one column r per blockIdx.y)
+// True in every thread of the block that arrives last in this launch
+// (after all other blocks' global writes and atomics are visible); that block
+// resets the counter for the next launch.
+__device__ __forceinline__ bool last_block(int* done) {
+  __shared__ int is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int total = (int)(gridDim.x * gridDim.y);
+    const int old = atomicAdd(done, 1);
+    is_last = (old == total - 1);
+    if (is_last) atomicExch(done, 0);
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last != 0;
+}
+
+// alpha = r.z / p.Ap per running column; clears the sums of the update
+__device__ __forceinline__ void finish_alpha(double* sc, int R) {
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    const double act = __ldcg(sc + SC_ACT * R + r);
+    const double pq = __ldcg(sc + SC_PQ * R + r);
+    sc[SC_ALPHA * R + r] = (act != 0.0 && pq != 0.0) ? __ldcg(sc + SC_RZ * R + r) / pq : 0.0;
+    sc[SC_RZN * R + r] = 0.0;
+    sc[SC_RR * R + r] = 0.0;
+  }
+}
+
+// Q = sum_s Qpart[s] + lam * P ; sc[PQ][r] += P . Q  (one column r per
+// blockIdx.y); with `done`, the last block also forms alpha.
 __global__ void k_reduce_dot(const double* __restrict__ Qpart, int S, int64_t N, int R,
                              const double* __restrict__ P, double lam, double* __restrict__ Q,
-                             double* __restrict__ sc, int dot_slot) {
+                             double* __restrict__ sc, int dot_slot, int* done) {
   __shared__ double sh[32];
   const int r = blockIdx.y;
   double part = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double q = 0.0;
-    for (int s = 0; s < S; ++s) q += Qpart[(int64_t)s * N * R + i * R + r];
+    // the S partial loads are independent: keep eight in flight
+    const double* src = Qpart + i * R + r;
+    const int64_t stride = N * (int64_t)R;
+    double q0 = 0.0, q1 = 0.0;
+    int s = 0;
+    for (; s + 8 <= S; s += 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = src[(int64_t)(s + u) * stride];
+      q0 += (v[0] + v[1]) + (v[2] + v[3]);
+      q1 += (v[4] + v[5]) + (v[6] + v[7]);
+    }
+    for (; s < S; ++s) q0 += src[(int64_t)s * stride];
+    double q = q0 + q1;
     const double p = P[i * R + r];
     q += lam * p;
     Q[i * R + r] = q;
@@ -250,6 +292,7 @@ __global__ void k_reduce_dot(const double* __restrict__ Qpart, int S, int64_t N,
     const double s = block_sum(part, sh);
     if (threadIdx.x == 0) atomicAdd(sc + dot_slot * R + r, s);
   }
+  if (done && last_block(done)) finish_alpha(sc, R);
 }
 
 // Initialise a CG run on right-hand side B (x = 0): r = B, z = M^{-1} r,
@@ -280,20 +323,40 @@ __global__ void k_init(const double* __restrict__ B, const double* __restrict__ 
   if (threadIdx.x == 0) atomicAdd(sc + SC_YY * R + r, s);
 }
 
-__global__ void k_alpha(double* sc, int R) {
-  const int r = threadIdx.x;
-  if (r >= R) return;
-  const double act = sc[SC_ACT * R + r];
-  const double pq = sc[SC_PQ * R + r];
-  sc[SC_ALPHA * R + r] = (act != 0.0 && pq != 0.0) ? sc[SC_RZ * R + r] / pq : 0.0;
-  sc[SC_RZN * R + r] = 0.0;
-  sc[SC_RR * R + r] = 0.0;
+// beta, activity and iteration counts for every column; *flag = number of
+// columns still running; clears p.Ap for the next iteration.
+__device__ __forceinline__ void finish_beta(double* sc, int R, int* flag) {
+  int running = 0;
+  for (int r0 = 0; r0 < R; r0 += blockDim.x) {
+    const int r = r0 + threadIdx.x;
+    int act_now = 0;
+    if (r < R) {
+      const double act = __ldcg(sc + SC_ACT * R + r);
+      if (act != 0.0) {
+        const double rzn = __ldcg(sc + SC_RZN * R + r);
+        const double rz = __ldcg(sc + SC_RZ * R + r);
+        sc[SC_BETA * R + r] = (rz != 0.0) ? rzn / rz : 0.0;
+        sc[SC_RZ * R + r] = rzn;
+        sc[SC_ITER * R + r] += 1.0;
+        const bool still = __ldcg(sc + SC_RR * R + r) > sc[SC_TOL * R + r] * sc[SC_YY * R + r];
+        sc[SC_ACT * R + r] = still ? 1.0 : 0.0;
+        act_now = still ? 1 : 0;
+      } else {
+        sc[SC_BETA * R + r] = 0.0;
+      }
+      sc[SC_PQ * R + r] = 0.0;
+    }
+    running += __syncthreads_count(act_now);
+  }
+  if (threadIdx.x == 0) *flag = running;
 }
 
+// x += alpha p, r -= alpha q, z = M^{-1} r, r.z and r.r; the last block forms
+// beta and the activity flags.
 __global__ void k_update(const double* __restrict__ minv, int64_t N, int R, double* __restrict__ X,
                          double* __restrict__ Rr, double* __restrict__ Z,
                          const double* __restrict__ P, const double* __restrict__ Q,
-                         double* __restrict__ sc) {
+                         double* __restrict__ sc, int* done, int* flag) {
   __shared__ double sh[32];
   const int r = blockIdx.y;
   const double alpha = sc[SC_ALPHA * R + r];
@@ -313,30 +376,7 @@ __global__ void k_update(const double* __restrict__ minv, int64_t N, int R, doub
   if (threadIdx.x == 0) atomicAdd(sc + SC_RZN * R + r, s);
   s = block_sum(rr, sh);
   if (threadIdx.x == 0) atomicAdd(sc + SC_RR * R + r, s);
-}
-
-// beta, activity and iteration counts; *flag = number of active columns.
-__global__ void k_beta(double* sc, int R, int* flag) {
-  const int r = threadIdx.x;
-  int act_now = 0;
-  if (r < R) {
-    const double act = sc[SC_ACT * R + r];
-    if (act != 0.0) {
-      const double rzn = sc[SC_RZN * R + r];
-      const double rz = sc[SC_RZ * R + r];
-      sc[SC_BETA * R + r] = (rz != 0.0) ? rzn / rz : 0.0;
-      sc[SC_RZ * R + r] = rzn;
-      sc[SC_ITER * R + r] += 1.0;
-      const bool still = sc[SC_RR * R + r] > sc[SC_TOL * R + r] * sc[SC_YY * R + r];
-      sc[SC_ACT * R + r] = still ? 1.0 : 0.0;
-      act_now = still ? 1 : 0;
-    } else {
-      sc[SC_BETA * R + r] = 0.0;
-    }
-    sc[SC_PQ * R + r] = 0.0;
-  }
-  const int n = __syncthreads_count(act_now);
-  if (threadIdx.x == 0) *flag = n;
+  if (last_block(done)) finish_beta(sc, R, flag);
 }
 
 __global__ void k_direction(int64_t N, int R, const double* __restrict__ Z, double* __restrict__ P,
@@ -425,6 +465,7 @@ struct Pcg {
   float* Pf;
   float *Xh, *Xl;    // double-FP32 split of the iterate (true residuals)
   int* flag;         // device: active columns after the last iteration
+  int* done;         // device: block arrival counters [2] (reset by the last block)
   int64_t* nlaunch;  // handle launch counter
 };
 
@@ -530,7 +571,7 @@ cudaError_t apply_accurate(const Pcg& c, const double* Xc, bool exact_fp64) {
     if (e != cudaSuccess) return e;
   }
   ++*c.nlaunch;
-  k_reduce_dot<<<vgrid(c), 256, 0, c.st>>>(c.Qpart, c.S, c.N, c.R, Xc, c.lam, c.Q, c.sc, -1);
+  k_reduce_dot<<<vgrid(c), 256, 0, c.st>>>(c.Qpart, c.S, c.N, c.R, Xc, c.lam, c.Q, c.sc, -1, nullptr);
   return cudaGetLastError();
 }
 
@@ -551,11 +592,9 @@ template <bool F64>
 cudaError_t cg_iteration(const Pcg& c, double* Xc) {
   cudaError_t e = F64 ? matvec<true>(c, c.P) : matvec<false>(c, c.Pf);
   if (e != cudaSuccess) return e;
-  c.nlaunch[0] += 5;
-  k_reduce_dot<<<vgrid(c), 256, 0, c.st>>>(c.Qpart, c.S, c.N, c.R, c.P, c.lam, c.Q, c.sc, SC_PQ);
-  k_alpha<<<1, 256, 0, c.st>>>(c.sc, c.R);
-  k_update<<<vgrid(c), 256, 0, c.st>>>(c.minv, c.N, c.R, Xc, c.Rr, c.Z, c.P, c.Q, c.sc);
-  k_beta<<<1, 256, 0, c.st>>>(c.sc, c.R, c.flag);
+  c.nlaunch[0] += 3;
+  k_reduce_dot<<<vgrid(c), 256, 0, c.st>>>(c.Qpart, c.S, c.N, c.R, c.P, c.lam, c.Q, c.sc, SC_PQ, c.done);
+  k_update<<<vgrid(c), 256, 0, c.st>>>(c.minv, c.N, c.R, Xc, c.Rr, c.Z, c.P, c.Q, c.sc, c.done + 1, c.flag);
   k_direction<<<vgrid(c), 256, 0, c.st>>>(c.N, c.R, c.Z, c.P, c.Pf, c.sc);
   return cudaGetLastError();
 }
@@ -689,6 +728,11 @@ nk_status nk_pcg_impl(nk_handle* h, const float* K, int64_t ldk, int64_t N, cons
   c.Xh = (float*)take(NR * 4);
   c.Xl = (float*)take(NR * 4);
   c.flag = (int*)take(64);
+  c.done = c.flag + 4;  // same 64-byte slot: flag, pad, done[2]
+  {
+    const cudaError_t z = cudaMemsetAsync(c.flag, 0, 64, st);
+    if (z != cudaSuccess) return nk_cuda_check(h, z, "pcg counters");
+  }
 
   // pinned host words: the active-column flag and the CG scalars
   void* host = nullptr;
