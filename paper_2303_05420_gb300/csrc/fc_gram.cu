@@ -8,9 +8,11 @@
 // accumulation in TMEM on split operands: x = x_hi + x_lo (BF16 each), and
 // x . x' ~ hi.hi' + hi.lo' + lo.hi' is one GEMM over a tripled K with
 // A' = [hi | hi | lo] and B' = [hi' | lo' | hi'] (zero-padded to a multiple
-// of 64).  A persistent CTA per SM walks 128 x 256 output tiles in a grouped
-// raster (8 tile rows at a time, so that concurrent CTAs share B tiles in
-// L2).  Operand tiles (128 x 64 and 256 x 64 BF16) arrive by TMA with
+// of 64).  Persistent clusters of two CTAs (one per SM) walk pairs of
+// vertically adjacent 128 x 256 output tiles in a grouped raster (16 tile rows
+// at a time, so that concurrent clusters share B tiles in L2); the two CTAs
+// of a cluster share the B tile, each loading half of it by TMA multicast
+// into both, which halves B's L2-to-SM traffic.  Operand tiles (128 x 64 and 256 x 64 BF16) arrive by TMA with
 // 128-byte swizzle through a 4-stage mbarrier ring; one thread issues the
 // MMAs into one of two 256-column TMEM accumulators while eight epilogue warps
 // drain the other: each reads 32 rows x 128 columns from TMEM, applies the whole
@@ -38,6 +40,7 @@ namespace {
 
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 constexpr int GROUP_M = 16;     // tile rows per raster group (L2 reuse of B)
+constexpr int CLUSTER = 2;      // CTAs sharing each B tile (TMA multicast)
 constexpr int EPI_WARPS = 8;    // two per TMEM lane quarter, 128 columns each
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t WAIT_LIMIT = 1u << 26;
@@ -74,17 +77,24 @@ struct FcParams {
   const float* q1a;      // [M]
 };
 
-// Tile slot t of the grouped raster: GROUP_M tile rows at a time, column by
-// column, so that the CTAs running together share B tiles in L2.  Returns
-// false for tiles with no entry on or above the diagonal of a symmetric block.
-__device__ __forceinline__ bool tile_of(const FcParams& P, int64_t t, int& tm, int& tn) {
-  const int64_t per_group = (int64_t)GROUP_M * P.ntn;
+// Tile slot t of the grouped raster over pair rows: a pair row is CLUSTER
+// consecutive tile rows that share every B tile (one per CTA of a cluster);
+// GROUP_M tile rows at a time, column by column, so that the clusters running
+// together share B tiles in L2.  Returns this CTA's tile, and false when the
+// cluster's first tile has no entry on or above the diagonal of a symmetric
+// block (both CTAs then skip the slot).
+__device__ __forceinline__ bool tile_of(const FcParams& P, int64_t t, int rank, int& tm, int& tn) {
+  constexpr int GP = GROUP_M / CLUSTER;  // pair rows per group
+  const int ntp = (P.ntm + CLUSTER - 1) / CLUSTER;
+  const int64_t per_group = (int64_t)GP * P.ntn;
   const int g = (int)(t / per_group);
   const int64_t k = t - (int64_t)g * per_group;
-  const int rows = min(GROUP_M, P.ntm - g * GROUP_M);
-  tm = g * GROUP_M + (int)(k % rows);
+  const int rows = min(GP, ntp - g * GP);
+  const int tp = g * GP + (int)(k % rows);
   tn = (int)(k / rows);
-  return !(P.sym && (int64_t)tn * BN + BN - 1 < (int64_t)tm * BM);
+  tm = tp * CLUSTER + rank;
+  const int tm0 = tp * CLUSTER;
+  return !(P.sym && (int64_t)tn * BN + BN - 1 < (int64_t)tm0 * BM);
 }
 
 __device__ __forceinline__ void named_sync(int id, int n) {
@@ -105,10 +115,12 @@ __device__ __forceinline__ bool named_any(int id, int n, bool v) {
   return r != 0;
 }
 
-// Persistent kernel, one CTA per SM, tiles t = blockIdx.x + k * gridDim.x.
-// Warp 0: TMA producer; warp 1: TMEM owner and MMA issuer; warps 2..9:
-// epilogue.  Two 256-column TMEM accumulators let the MMAs of the next tile
-// run while the epilogue drains the previous one.
+// Persistent kernel, one CTA per SM, clusters of two CTAs; cluster c takes
+// slots t = c + k * clusters.  Warp 0: TMA producer (its A tile, and half of
+// the shared B tile multicast to both CTAs); warp 1: TMEM owner and MMA
+// issuer (each stage is released to both producers); warps 2..9: epilogue.
+// Two 256-column TMEM accumulators let the MMAs of the next tile run while
+// the epilogue drains the previous one.
 __global__ void __launch_bounds__(THREADS, 1)
 k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
           const __grid_constant__ FcParams P) {
@@ -116,11 +128,14 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   GemmSmem& S = *reinterpret_cast<GemmSmem*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nk = P.kpad / BK;
-  const int64_t nslots = (int64_t)P.ntm * P.ntn;
+  const int rank = (int)tc::cluster_ctarank();
+  const int64_t cid = blockIdx.x / CLUSTER, ncl = gridDim.x / CLUSTER;
+  const int64_t nslots = (int64_t)((P.ntm + CLUSTER - 1) / CLUSTER) * P.ntn;
+  constexpr uint16_t ALL = (1u << CLUSTER) - 1;
   if (warp == 0 && lane == 0) {
     for (int s = 0; s < STAGES; ++s) {
       tc::mbar_init(&S.full[s], 1);
-      tc::mbar_init(&S.empty[s], 1);
+      tc::mbar_init(&S.empty[s], CLUSTER);  // both CTAs' MMAs must have read a stage
     }
     for (int a = 0; a < 2; ++a) {
       tc::mbar_init(&S.tfull[a], 1);
@@ -133,7 +148,8 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   }
   if (warp == 1) tc::tmem_alloc(&S.tslot, 512);
   tc::tc_fence_before();
-  __syncthreads();
+  // barriers initialised in both CTAs before any multicast reaches them
+  tc::cluster_sync();
   tc::tc_fence_after();
   const uint32_t tbase = S.tslot;
   bool ok = true;
@@ -141,9 +157,10 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
     if (lane == 0) {
       // TMA producer: the operand ring runs on across tiles
       int64_t kb_all = 0;
-      for (int64_t t = blockIdx.x; t < nslots && ok; t += gridDim.x) {
+      constexpr int BH = BN / CLUSTER;  // B rows this CTA loads for the cluster
+      for (int64_t t = cid; t < nslots && ok; t += ncl) {
         int tm, tn;
-        if (!tile_of(P, t, tm, tn)) continue;
+        if (!tile_of(P, t, rank, tm, tn)) continue;
         for (int kb = 0; kb < nk; ++kb, ++kb_all) {
           const int s = (int)(kb_all % STAGES);
           if (kb_all >= STAGES &&
@@ -152,9 +169,10 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
             ok = false;
             break;
           }
+          // own A tile plus the whole B tile (half from each CTA)
           tc::mbar_arrive_expect_tx(&S.full[s], (BM + BN) * BK * 2);
           tc::tma_load_2d(S.A[s], &ta, &S.full[s], kb * BK, tm * BM);
-          tc::tma_load_2d(S.B[s], &tb, &S.full[s], kb * BK, tn * BN);
+          tc::tma_load_2d_mc(S.B[s] + rank * BH * BK, &tb, &S.full[s], kb * BK, tn * BN + rank * BH, ALL);
         }
       }
       // every load issued has landed before the CTA may exit
@@ -168,9 +186,9 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
       int64_t kb_all = 0;
       int n = 0;  // tiles of this CTA so far
-      for (int64_t t = blockIdx.x; t < nslots && ok; t += gridDim.x) {
+      for (int64_t t = cid; t < nslots && ok; t += ncl) {
         int tm, tn;
-        if (!tile_of(P, t, tm, tn)) continue;
+        if (!tile_of(P, t, rank, tm, tn)) continue;
         const int acc = n & 1;
         if (n >= 2 && !tc::mbar_wait(&S.tempty[acc], (uint32_t)((n >> 1) & 1) ^ 1, WAIT_LIMIT)) {
           atomicOr(P.dstatus, NK_DEV_TIMEOUT);
@@ -191,7 +209,7 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k)
             tc::mma_bf16(tacc, tc::sdesc_k128(a0 + 32 * k), tc::sdesc_k128(b0 + 32 * k), idesc, (kb | k) != 0);
-          tc::mma_commit(&S.empty[s]);
+          tc::mma_commit_mc(&S.empty[s], ALL);  // the stage may be refilled by either CTA
         }
         if (!ok) break;
         tc::mma_commit(&S.tfull[acc]);
@@ -209,9 +227,9 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
     const int et = threadIdx.x - 64;  // 0 .. 32 * EPI_WARPS - 1
     const bool vec_ok = (P.ldk % 4 == 0) && ((reinterpret_cast<uintptr_t>(P.K) & 15) == 0);
     int n = 0;
-    for (int64_t t = blockIdx.x; t < nslots; t += gridDim.x) {
+    for (int64_t t = cid; t < nslots; t += ncl) {
       int tm, tn;
-      if (!tile_of(P, t, tm, tn)) continue;
+      if (!tile_of(P, t, rank, tm, tn)) continue;
       const int64_t m0 = (int64_t)tm * BM, n0 = (int64_t)tn * BN;
       // row and column factors of this tile into shared memory
       named_sync(1, 32 * EPI_WARPS);
@@ -302,7 +320,10 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
     }
   }
   tc::tc_fence_before();
-  __syncthreads();
+  __syncwarp();
+  // neither CTA leaves while the other may still multicast into it or
+  // arrive on its barriers
+  tc::cluster_sync();
   if (warp == 1) tc::tmem_dealloc(tbase, 512);
 }
 
@@ -414,7 +435,7 @@ cudaError_t nk_launch_fc_block(int depth, double sw2, double sb2, const float* X
   k_fc_q<<<grid(na * 32), 256, 0, st>>>(xa, na, d, depth, sw2, sb2, (float)(sw2 * inv2pi), qa, q1a);
   k_fc_q<<<grid(nb * 32), 256, 0, st>>>(xb, nb, d, depth, sw2, sb2, 1.f, qb, nullptr);
   CUtensorMap ta, tb;
-  if (!make_map(&ta, Ap, na, kpad, BM) || !make_map(&tb, Bp, nb, kpad, BN)) return cudaErrorInvalidValue;
+  if (!make_map(&ta, Ap, na, kpad, BM) || !make_map(&tb, Bp, nb, kpad, BN / CLUSTER)) return cudaErrorInvalidValue;
   FcParams P = {};
   P.M = na;
   P.N = nb;
@@ -432,13 +453,26 @@ cudaError_t nk_launch_fc_block(int depth, double sw2, double sb2, const float* X
   P.same = (Xa == Xb);
   P.selfoff = a0 - b0;
   P.q1a = q1a;
-  const int64_t slots = (int64_t)P.ntm * P.ntn;
+  const int64_t slots = (int64_t)((P.ntm + CLUSTER - 1) / CLUSTER) * P.ntn;
   const size_t smem = sizeof(GemmSmem) + 1024;
   cudaError_t e = cudaFuncSetAttribute(k_fc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   P.dstatus = dstatus;
   ++*launches;
-  const unsigned ctas = (unsigned)std::max<int64_t>(1, std::min<int64_t>(slots, sm));
-  k_fc_gram<<<ctas, THREADS, smem, st>>>(ta, tb, P);
+  const int64_t clusters = std::max<int64_t>(1, std::min<int64_t>(slots, sm / CLUSTER));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CLUSTER;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)(clusters * CLUSTER), 1, 1);
+  cfg.blockDim = dim3(THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, k_fc_gram, ta, tb, P);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

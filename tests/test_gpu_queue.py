@@ -119,3 +119,20 @@ def test_queue_rejects(h):
         h.block_queue([bad], convs, 2.0, 0.0)
     assert ei.value.status == NK_ERR_INVALID_ARG
     assert h.block_queue([], convs, 2.0, 0.0) == []
+
+
+def test_64x64_plain_path_matches_oracle(h):
+    """64x64 images (the larger problem of the mixed-resolution workload) have
+    no fused kernel; the layer-wise FP32 form computes them, here one row of
+    a 2 x 3 block against the oracle pair by pair."""
+    convs = (2, 1, 0)
+    x = nkdata.standardise(nkdata.images(3, 64, 3, 5, blur=True))[0].astype(np.float32)
+    X = torch.tensor(x, device="cuda")
+    q = h.self_diag(X, convs, 2.0, 0.0)
+    K = h.block(X, q, X, q, convs, 2.0, 0.0, prec="plain_fp32", a_range=(0, 1), b_range=(0, 3))
+    h.sync_status()
+    arch = oracle.Arch(convs)
+    for j in range(3):
+        want = float(oracle.kernels.myrtle_pair(arch, 2.0, 0.0, torch.tensor(x[0].astype(np.float64)),
+                                                torch.tensor(x[j].astype(np.float64))))
+        assert abs(float(K[0, j]) - want) <= 1e-5 * abs(want), (j, float(K[0, j]), want)
