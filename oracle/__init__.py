@@ -40,5 +40,5 @@ from .kernels import (  # noqa: F401
     myrtle_layers_pair,
     fc_nngp,
 )
-from .solve import cholesky_solve, pcg  # noqa: F401
+from .solve import cholesky_solve, pcg, pivchol_apply, pivoted_cholesky  # noqa: F401
 from .krr import krr_loss, krr_loss_and_grads  # noqa: F401

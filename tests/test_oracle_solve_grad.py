@@ -126,3 +126,71 @@ def test_euler_identities():
     # degree L = #weight layers in sigma_w^2
     L = arch.n_weight_layers
     assert abs(float(sw2.grad) - L * float(K) / 1.6) <= 1e-12 * abs(float(K))
+
+
+# --------------------------------------------------------------------------
+# Partial pivoted Cholesky preconditioner (Section 2: the paper's own)
+# --------------------------------------------------------------------------
+
+def test_pivoted_cholesky_full_rank_is_exact(gram):
+    from oracle import pivoted_cholesky
+
+    K, _ = gram
+    n = K.shape[0]
+    L, piv = pivoted_cholesky(K, n)
+    assert len(set(piv)) == len(piv)
+    # the greedy factor of an SPD matrix reproduces it (up to where the
+    # remaining diagonal vanishes at rounding level)
+    assert np.abs(L.T @ L - K).max() <= 1e-9 * np.abs(K).max()
+
+
+def test_pivoted_cholesky_pivots_are_greedy_schur_maxima(gram):
+    """Each pivot is the argmax of the diagonal of the Schur complement of
+    the previous pivots, computed here independently with a dense solve; the
+    residual K - L^T L vanishes on the pivot rows (interpolation)."""
+    from oracle import pivoted_cholesky
+
+    K, _ = gram
+    L, piv = pivoted_cholesky(K, 12)
+    assert len(piv) == 12 and len(set(piv)) == 12
+    for k in range(len(piv)):
+        P = piv[:k]
+        if k == 0:
+            S = np.diag(K).copy()
+        else:
+            KP = K[np.ix_(P, P)]
+            S = np.diag(K) - np.einsum("ij,ji->i", K[:, P], np.linalg.solve(KP, K[P, :]))
+        assert int(np.argmax(S)) == piv[k]
+    E = K - L.T @ L
+    assert np.abs(E[piv, :]).max() <= 1e-10 * np.abs(K).max()
+    # the remaining trace decreases with the rank
+    tr = [np.trace(K - pivoted_cholesky(K, r)[0].T @ pivoted_cholesky(K, r)[0]) for r in (1, 4, 12)]
+    assert tr[0] > tr[1] > tr[2] > 0
+
+
+def test_pivchol_apply_is_the_woodbury_inverse(gram):
+    from oracle import pivchol_apply, pivoted_cholesky
+
+    K, Y = gram
+    lam = 1e-3 * np.trace(K) / K.shape[0]
+    L, _ = pivoted_cholesky(K, 7)
+    M = L.T @ L + lam * np.eye(K.shape[0])
+    want = np.linalg.solve(M, Y)
+    assert np.allclose(pivchol_apply(L, lam, Y), want, rtol=1e-9, atol=1e-12 * np.abs(want).max())
+    assert np.allclose(pivchol_apply(L[:0], lam, Y), Y / lam)
+
+
+def test_pivchol_pcg_converges_and_beats_jacobi(gram):
+    K, Y = gram
+    n = K.shape[0]
+    lam = 1e-4 * np.trace(K) / n
+    Astar = cholesky_solve(K, Y, lam)
+    X, it_pc, rel = pcg(K, Y, lam, "pivchol", tol=1e-10, maxit=5000, rank=10)
+    assert rel.max() <= 1e-10
+    kappa = np.linalg.cond(K + lam * np.eye(n))
+    assert np.linalg.norm(X - Astar) / np.linalg.norm(Astar) <= kappa * 1e-10
+    _, it_j, _ = pcg(K, Y, lam, "jacobi", tol=1e-10, maxit=5000)
+    assert it_pc < it_j
+    # full rank: M = K + lam I, so CG needs a single step
+    _, it_full, rel_full = pcg(K, Y, lam, "pivchol", tol=1e-8, maxit=50, rank=n)
+    assert it_full <= 2 and rel_full.max() <= 1e-8
