@@ -331,18 +331,24 @@ def run_ours(args, rank, world, dist):
         extra["maxrel_plain_fp32_vs_plain_fp64"] = float(((res["plain_fp32"][1][:16, :16] - k16).abs()
                                                           / k16.abs()).max())
         extra["plain_tiles"] = f"{tile}x{tile} (fp32, mixed), 16x16 (fp64) train pairs"
-        # PCG: mixed vs plain FP64 on the same train block
-        for prec in ["mixed", "plain_fp64"]:
+        # PCG: mixed vs plain FP64 on the same train block, with the Jacobi
+        # preconditioner of the configuration and with the paper's pivoted
+        # Cholesky one (rank 100)
+        h.pcg_set_rank(100)
+        for pc, prec in [("jacobi", "mixed"), ("jacobi", "plain_fp64"), ("pivchol", "mixed"),
+                         ("pivchol", "plain_fp64")]:
             a, b = ev(), ev()
             a.record(stream)
-            _, its, rel = h.pcg_solve(Ktr, Y, -REL_LAMBDA, precond="jacobi", prec=prec, tol=1e-6,
+            _, its, rel = h.pcg_solve(Ktr, Y, -REL_LAMBDA, precond=pc, prec=prec, tol=1e-6,
                                       maxit=20000, A=A, allow_not_converged=True)
             b.record(stream)
             torch.cuda.synchronize()
             ms = a.elapsed_time(b)
-            extra[f"pcg_{prec}_iters"] = its
-            extra[f"pcg_{prec}_iters_per_s"] = its / (ms / 1e3)
-            extra[f"pcg_{prec}_relres"] = max(rel)
+            key = f"pcg_{prec}" if pc == "jacobi" else f"pcg_pivchol100_{prec}"
+            extra[f"{key}_iters"] = its
+            extra[f"{key}_ms"] = ms
+            extra[f"{key}_iters_per_s"] = its / (ms / 1e3)
+            extra[f"{key}_relres"] = max(rel)
     lam_used = h.last_lambda()
     if args.grad:
         extra.update(grad_leg(h, dev))

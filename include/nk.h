@@ -56,7 +56,7 @@ typedef enum {
 typedef enum { NK_PREC_PLAIN_FP64 = 0, NK_PREC_PLAIN_FP32 = 1, NK_PREC_MIXED = 2 } nk_prec;
 
 enum { NK_ACT_RELU = 0, NK_ACT_IDENTITY = 1 /* linear network, tests only */ };
-enum { NK_PRECOND_NONE = 0, NK_PRECOND_JACOBI = 1 };
+enum { NK_PRECOND_NONE = 0, NK_PRECOND_JACOBI = 1, NK_PRECOND_PIVCHOL = 2 };
 
 /* Myrtle-family architecture (Appendix A, Myrtle listing): n_stages stages;
  * stage s holds convs[s] layers of conv(filter x filter, SAME) + activation;
@@ -246,8 +246,18 @@ typedef struct {
 nk_status nk_block_queue(nk_handle* h, const nk_arch* arch, const nk_params* prm, int C,
                          const nk_block_task* tasks, int n_tasks, void* stream);
 
-/* Kernel-ridge solve (K + lambda I) A = Y by Jacobi-preconditioned CG, one CG
- * per column run in lock-step (Section 2 "Iterative solvers"; Appendix B.3).
+/* Rank of the partial pivoted Cholesky preconditioner (NK_PRECOND_PIVCHOL)
+ * used by later nk_pcg_solve calls on this handle (default 100; at most N is
+ * used).  rank in 1..1024, else NK_ERR_INVALID_ARG. */
+nk_status nk_pcg_set_rank(nk_handle* h, int rank);
+
+/* Kernel-ridge solve (K + lambda I) A = Y by preconditioned CG, one CG per
+ * column run in lock-step (Section 2 "Iterative solvers"; Appendix B.3).
+ *   precond: NK_PRECOND_NONE, NK_PRECOND_JACOBI (M = diag(K) + lambda) or
+ *   NK_PRECOND_PIVCHOL (Section 2's partial pivoted Cholesky: K ~ L^T L from
+ *   the rank (nk_pcg_set_rank) largest-remaining-diagonal pivots, built on
+ *   the device in FP64 for each call; M = L^T L + lambda I applied through
+ *   the Woodbury identity).
  *   K [N][ldk] float32 (device, symmetric), Y [N][R] float64 (device, row
  *   major), A [N][R] float64 (device, out).
  *   prec = NK_PREC_MIXED: iterative refinement: the true residual

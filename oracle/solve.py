@@ -32,17 +32,19 @@ def pivoted_cholesky(K, rank: int):
     step k takes the pivot i with the largest remaining diagonal d (the
     diagonal of the Schur complement of the pivots so far; the lowest index
     on ties), forms the row l_k = (K[i, :] - sum_{m<k} L[m, i] L[m, :]) /
-    sqrt(d[i]) and updates d -= l_k^2.  Stops early when the largest d is not
-    positive.  Returns (L [k][n], pivots [k]) with K ~ L^T L."""
+    sqrt(d[i]) and updates d -= l_k^2.  Stops early when the largest d is at
+    most 1e-12 of the largest diagonal of K (numerically exhausted rank).
+    Returns (L [k][n], pivots [k]) with K ~ L^T L."""
     K = np.asarray(K, dtype=np.float64)
     n = K.shape[0]
     rank = min(int(rank), n)
     d = np.diag(K).copy()
+    floor = 1e-12 * d.max() if n else 0.0
     L = np.zeros((rank, n))
     piv = []
     for k in range(rank):
         i = int(np.argmax(d))
-        if not d[i] > 0.0:
+        if not d[i] > floor:
             break
         row = K[i, :] - L[:k, i] @ L[:k, :]
         L[k] = row / np.sqrt(d[i])

@@ -19,13 +19,13 @@ NK_OK, NK_ERR_INVALID_ARG, NK_ERR_CUDA, NK_ERR_NUMERICAL = 0, 1, 2, 3
 NK_ERR_NOT_CONVERGED, NK_ERR_TIMEOUT, NK_ERR_NO_MEMORY, NK_ERR_UNSUPPORTED = 4, 5, 6, 7
 PREC = {"plain_fp64": 0, "plain_fp32": 1, "mixed": 2}
 ACT = {"relu": 0, "identity": 1}
-PRECOND = {"none": 0, "jacobi": 1}
+PRECOND = {"none": 0, "jacobi": 1, "pivchol": 2}
 
 # Every symbol include/nk.h declares (checked by a CPU test).
 EXPORTS = ["nk_create", "nk_destroy", "nk_status_string", "nk_last_error", "nk_sync_status",
            "nk_q_size", "nk_launch_count", "nk_last_lambda", "nk_self_diag", "nk_block", "nk_block_backward", "nk_fc_block",
            "nk_autotune",
-           "nk_autotune_set", "nk_block_fused_noalloc", "nk_block_queue", "nk_pcg_solve"]
+           "nk_autotune_set", "nk_block_fused_noalloc", "nk_block_queue", "nk_pcg_set_rank", "nk_pcg_solve"]
 
 
 class NkArch(ctypes.Structure):
@@ -107,6 +107,8 @@ def lib():
     L.nk_block_queue.argtypes = [c_void_p, POINTER(NkArch), POINTER(NkParams), c_int, POINTER(NkBlockTask),
                                  c_int, c_void_p]
     L.nk_block_queue.restype = c_int
+    L.nk_pcg_set_rank.argtypes = [c_void_p, c_int]
+    L.nk_pcg_set_rank.restype = c_int
     L.nk_pcg_solve.argtypes = [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_int, c_double, c_int,
                                c_int, c_double, c_int, c_int, c_void_p, POINTER(c_int),
                                c_void_p, c_void_p]

@@ -192,6 +192,10 @@ class Handle:
                                      c_void_p(_ptr(dsb2)), c_void_p(_stream()))
         self.check(st, "nk_block_backward")
 
+    def pcg_set_rank(self, rank: int):
+        """Rank of the pivoted Cholesky preconditioner (precond="pivchol")."""
+        self.check(lib().nk_pcg_set_rank(self._h, int(rank)), "nk_pcg_set_rank")
+
     def pcg_solve(self, K: torch.Tensor, Y: torch.Tensor, lam: float, precond: str = "jacobi",
                   prec: str = "mixed", tol: float = 1e-6, maxit: int = 10000, refine_max: int = 16,
                   A: Optional[torch.Tensor] = None, allow_not_converged: bool = False):

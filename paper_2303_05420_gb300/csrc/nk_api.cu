@@ -158,6 +158,7 @@ nk_status nk_create(nk_handle** out) {
   *out = nullptr;
   nk_handle* h = new nk_handle();
   memset(h, 0, sizeof(*h));
+  h->pcg_rank = 100;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
   if (e == cudaSuccess) e = cudaMalloc(&h->dstatus, sizeof(unsigned int));
@@ -512,6 +513,13 @@ nk_status nk_autotune_set(nk_handle* h, const nk_arch* arch, const nk_params* pr
   return NK_OK;
 }
 
+nk_status nk_pcg_set_rank(nk_handle* h, int rank) {
+  if (!h) return NK_ERR_INVALID_ARG;
+  if (rank < 1 || rank > 1024) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_set_rank: rank outside 1..1024");
+  h->pcg_rank = rank;
+  return NK_OK;
+}
+
 nk_status nk_pcg_solve(nk_handle* h, const float* K, int64_t ldk, int64_t N, const double* Y, int R,
                        double lambda, int precond, nk_prec prec, double tol, int maxit, int refine_max,
                        double* A, int* iters, double* relres, void* stream) {
@@ -523,7 +531,7 @@ nk_status nk_pcg_solve(nk_handle* h, const float* K, int64_t ldk, int64_t N, con
   if (!K || !Y || !A) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_solve: NULL pointer");
   if (ldk < N) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_solve: ldk < N");
   if (lambda != lambda) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_solve: lambda is NaN");
-  if (precond != NK_PRECOND_NONE && precond != NK_PRECOND_JACOBI)
+  if (precond != NK_PRECOND_NONE && precond != NK_PRECOND_JACOBI && precond != NK_PRECOND_PIVCHOL)
     return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_solve: unknown preconditioner");
   if (prec != NK_PREC_PLAIN_FP64 && prec != NK_PREC_PLAIN_FP32 && prec != NK_PREC_MIXED)
     return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_solve: unknown precision");

@@ -54,6 +54,7 @@ struct nk_handle {
   // PCG scratch
   void* pcg_ws;
   size_t pcg_bytes;
+  int pcg_rank;            // pivoted Cholesky preconditioner rank
 };
 
 nk_status nk_fail(nk_handle* h, nk_status s, const char* fmt, ...);

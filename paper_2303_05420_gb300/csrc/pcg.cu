@@ -353,6 +353,9 @@ __device__ __forceinline__ void finish_beta(double* sc, int R, int* flag) {
 
 // x += alpha p, r -= alpha q, z = M^{-1} r, r.z and r.r; the last block forms
 // beta and the activity flags.
+// JAC: the Jacobi preconditioner is applied here (z, r.z, and beta in the
+// last block); otherwise the preconditioner kernels that follow do it.
+template <bool JAC>
 __global__ void k_update(const double* __restrict__ minv, int64_t N, int R, double* __restrict__ X,
                          double* __restrict__ Rr, double* __restrict__ Z,
                          const double* __restrict__ P, const double* __restrict__ Q,
@@ -367,16 +370,42 @@ __global__ void k_update(const double* __restrict__ minv, int64_t N, int R, doub
     X[e] += alpha * P[e];
     const double rn = Rr[e] - alpha * Q[e];
     Rr[e] = rn;
-    const double z = minv[i] * rn;
-    Z[e] = z;
-    rz += rn * z;
+    if constexpr (JAC) {
+      const double z = minv[i] * rn;
+      Z[e] = z;
+      rz += rn * z;
+    }
     rr += rn * rn;
   }
-  double s = block_sum(rz, sh);
-  if (threadIdx.x == 0) atomicAdd(sc + SC_RZN * R + r, s);
+  double s;
+  if constexpr (JAC) {
+    s = block_sum(rz, sh);
+    if (threadIdx.x == 0) atomicAdd(sc + SC_RZN * R + r, s);
+  }
   s = block_sum(rr, sh);
   if (threadIdx.x == 0) atomicAdd(sc + SC_RR * R + r, s);
-  if (last_block(done)) finish_beta(sc, R, flag);
+  if constexpr (JAC) {
+    if (last_block(done)) finish_beta(sc, R, flag);
+  }
+}
+
+// Initialise a CG run for a preconditioner applied by separate kernels:
+// x = 0, r = B, B.B (z, p and r.z follow from the preconditioner kernels).
+__global__ void k_init_pc(const double* __restrict__ B, int64_t N, int R, double* __restrict__ X,
+                          double* __restrict__ Rr, double* __restrict__ sc) {
+  __shared__ double sh[32];
+  const int r = blockIdx.y;
+  double yy = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i * R + r;
+    const double b = B[e];
+    X[e] = 0.0;
+    Rr[e] = b;
+    yy += b * b;
+  }
+  const double s = block_sum(yy, sh);
+  if (threadIdx.x == 0) atomicAdd(sc + SC_YY * R + r, s);
 }
 
 __global__ void k_direction(int64_t N, int R, const double* __restrict__ Z, double* __restrict__ P,
@@ -451,6 +480,261 @@ __global__ void k_set_active(double* sc, int R, double tol2) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Partial pivoted Cholesky preconditioner (Section 2: the paper's own, after
+// Wang et al. 2019).  K ~ L^T L from `rank` greedy pivots (the largest
+// remaining diagonal d of the Schur complement, lowest index on ties; stop
+// once it falls to 1e-12 of K's largest diagonal), M = L^T L + lam I applied
+// by the Woodbury identity M^{-1} v = (v - L^T G^{-1} L v) / lam with
+// G = lam I + L L^T (rank x rank, FP64).  G^{-1} is formed once per solve
+// as W^T W with W = C^{-1}, C the Cholesky factor of G, so that it is
+// symmetric positive definite as computed.
+// ---------------------------------------------------------------------------
+struct PcState {
+  int stop;      // the rank is exhausted
+  int rank_eff;  // pivots taken
+  int piv;       // current pivot
+  int pad;
+  double invs;   // 1 / sqrt(d[piv])
+  double floor;  // 1e-12 * max diag K
+};
+
+// argmax of d (lowest index on ties) by one block; sets the next pivot or
+// marks the rank exhausted.
+__device__ void pc_select(const double* __restrict__ d, int64_t N, PcState* st) {
+  __shared__ double sv[32];
+  __shared__ int64_t si[32];
+  double best = -1.0;
+  int64_t bi = 0;
+  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+    const double v = __ldcg(d + j);
+    if (v > best) {
+      best = v;
+      bi = j;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > best || (ov == best && oi < bi)) {
+      best = ov;
+      bi = oi;
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sv[threadIdx.x >> 5] = best;
+    si[threadIdx.x >> 5] = bi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    best = sv[0];
+    bi = si[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (sv[w] > best || (sv[w] == best && si[w] < bi)) {
+        best = sv[w];
+        bi = si[w];
+      }
+    if (!(best > st->floor)) {
+      st->stop = 1;
+    } else {
+      st->piv = (int)bi;
+      st->invs = 1.0 / sqrt(best);
+    }
+  }
+}
+
+__global__ void k_pc_diag(const float* __restrict__ K, int64_t ldk, int64_t N, double* __restrict__ d,
+                          PcState* st) {
+  __shared__ double sh[32];
+  double mx = 0.0;
+  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+    const double v = (double)K[j * ldk + j];
+    d[j] = v;
+    mx = fmax(mx, v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sh[w]);
+    st->stop = 0;
+    st->rank_eff = 0;
+    st->floor = 1e-12 * m;
+  }
+  __syncthreads();
+  pc_select(d, N, st);
+}
+
+// row k of L: L[k][j] = (K[i][j] - sum_{m<k} L[m][i] L[m][j]) / sqrt(d[i]);
+// d[j] -= L[k][j]^2.  Rows past the exhausted rank are zero.
+__global__ void k_pc_row(const float* __restrict__ K, int64_t ldk, int64_t N, double* __restrict__ L,
+                         double* __restrict__ d, int k, PcState* st, int* done) {
+  const bool stop = st->stop != 0;
+  const int i = st->piv;
+  const double invs = st->invs;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    if (!stop) {
+      v = (double)K[(int64_t)i * ldk + j];
+      for (int m = 0; m < k; ++m) v -= L[(int64_t)m * N + i] * L[(int64_t)m * N + j];
+      v *= invs;
+      d[j] -= v * v;
+    }
+    L[(int64_t)k * N + j] = v;
+  }
+  // the last block picks the next pivot from the updated diagonal
+  if (last_block(done) && !stop) {
+    if (threadIdx.x == 0) st->rank_eff = k + 1;
+    pc_select(d, N, st);
+  }
+}
+
+// G = lam I + L L^T, lower triangle (one block per (a, b), a >= b)
+__global__ void k_pc_gram(const double* __restrict__ L, int r, int64_t N, double lam, double* __restrict__ G) {
+  __shared__ double sh[32];
+  const int a = blockIdx.x, b = blockIdx.y;
+  if (b > a) return;
+  double s = 0.0;
+  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) s += L[(int64_t)a * N + j] * L[(int64_t)b * N + j];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) {
+    if (a == b) s += lam;
+    G[a * r + b] = s;
+    G[b * r + a] = s;
+  }
+}
+
+// In place: G -> C (lower Cholesky factor), then Ginv = W^T W with W = C^{-1}
+// (one block; rank is small).  Work: W in `work` [r][r].
+__global__ void k_pc_factor(double* __restrict__ G, int r, double* __restrict__ W, double* __restrict__ Ginv) {
+  for (int k = 0; k < r; ++k) {
+    if (threadIdx.x == 0) G[k * r + k] = sqrt(fmax(G[k * r + k], 1e-300));
+    __syncthreads();
+    const double ckk = G[k * r + k];
+    for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) G[i * r + k] /= ckk;
+    __syncthreads();
+    for (int e = threadIdx.x; e < (r - k - 1) * (r - k - 1); e += blockDim.x) {
+      const int i = k + 1 + e / (r - k - 1), j = k + 1 + e % (r - k - 1);
+      if (j <= i) G[i * r + j] -= G[i * r + k] * G[j * r + k];
+    }
+    __syncthreads();
+  }
+  // W = C^{-1}: column c by forward substitution (one thread per column)
+  for (int c = threadIdx.x; c < r; c += blockDim.x) {
+    for (int i = 0; i < r; ++i) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int m = c; m < i; ++m) v -= G[i * r + m] * W[m * r + c];
+      W[i * r + c] = (i < c) ? 0.0 : v / G[i * r + i];
+    }
+  }
+  __syncthreads();
+  // Ginv[a][b] = sum_m W[m][a] W[m][b]
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int a = e / r, b = e % r;
+    double s = 0.0;
+    for (int m = (a > b ? a : b); m < r; ++m) s += W[m * r + a] * W[m * r + b];
+    Ginv[e] = s;
+  }
+}
+
+// T[m][col] = sum_j L[m][j] V[j][col] for one m per blockIdx.x and up to 16
+// columns per blockIdx.y.
+__global__ void k_pc_t(const double* __restrict__ L, int r, int64_t N, const double* __restrict__ V, int R,
+                       double* __restrict__ T) {
+  __shared__ double sh[32];
+  const int m = blockIdx.x;
+  const int c0 = blockIdx.y * 16, cn = min(16, R - c0);
+  double acc[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+    const double l = L[(int64_t)m * N + j];
+    const double* v = V + j * R + c0;
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+      if (c < cn) acc[c] += l * v[c];
+  }
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    if (c < cn) {
+      const double s = block_sum(acc[c], sh);
+      if (threadIdx.x == 0) T[m * R + c0 + c] = s;
+    }
+  }
+}
+
+// U = Ginv T, one thread per entry.
+__global__ void k_pc_u(const double* __restrict__ Ginv, int r, const double* __restrict__ T, int R,
+                       double* __restrict__ U) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= r * R) return;
+  const int a = e / R, col = e - a * R;
+  double s = 0.0;
+  for (int b = 0; b < r; ++b) s += Ginv[a * r + b] * T[b * R + col];
+  U[e] = s;
+}
+
+// Z = (V - L^T U) / lam and r.z per column.  init: r.z into SC_RZ and P = Z
+// (the first direction); otherwise r.z into SC_RZN and the last block forms
+// beta and the activity flags.  A block covers 32 rows j and up to 16
+// columns (blockIdx.y); its 8 warps split the sum over m (m = warp, warp + 8,
+// ...) and warp 0 adds the 8 partial sums, so no thread walks all `rank` terms.
+__global__ void __launch_bounds__(256) k_pc_z(const double* __restrict__ L, int r, int64_t N,
+                                              const double* __restrict__ V, int R, const double* __restrict__ U,
+                                              double lam, double* __restrict__ Z, double* __restrict__ P,
+                                              float* __restrict__ Pf, double* __restrict__ sc, int init, int* done,
+                                              int* flag) {
+  __shared__ double part[8][16][32];
+  const int jj = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int64_t j = (int64_t)blockIdx.x * 32 + jj;
+  const int c0 = blockIdx.y * 16, cn = min(16, R - c0);
+  double s[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) s[c] = 0.0;
+  if (j < N) {
+    for (int m = g; m < r; m += 8) {
+      const double l = L[(int64_t)m * N + j];
+      const double* u = U + m * R + c0;
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (c < cn) s[c] += l * u[c];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 16; ++c) part[g][c][jj] = s[c];
+  __syncthreads();
+  if (g == 0) {
+    const double il = 1.0 / lam;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      if (c >= cn) break;
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) t += part[w][c][jj];
+      double rz = 0.0;
+      if (j < N) {
+        const int64_t e = j * R + c0 + c;
+        const double v = V[e];
+        const double z = (v - t) * il;
+        Z[e] = z;
+        if (init) {
+          P[e] = z;
+          Pf[e] = (float)z;
+        }
+        rz = v * z;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) rz += __shfl_xor_sync(0xffffffffu, rz, o);
+      if (jj == 0) atomicAdd(sc + (init ? SC_RZ : SC_RZN) * R + c0 + c, rz);
+    }
+  }
+  if (!init && last_block(done)) finish_beta(sc, R, flag);
+}
+
 struct Pcg {
   int64_t N;
   int R;
@@ -465,9 +749,13 @@ struct Pcg {
   float* Pf;
   float *Xh, *Xl;    // double-FP32 split of the iterate (true residuals)
   int* flag;         // device: active columns after the last iteration
-  int* done;         // device: block arrival counters [2] (reset by the last block)
+  int* done;         // device: block arrival counters [4] (reset by the last block)
   int64_t* nlaunch;  // handle launch counter
+  // pivoted Cholesky preconditioner (pc_rank > 0; else Jacobi / none)
+  int pc_rank;
+  double *L, *Ginv, *T, *U;
 };
+
 
 template <bool F64>
 cudaError_t matvec(const Pcg& c, const void* Pin) {
@@ -541,6 +829,17 @@ inline dim3 vgrid(const Pcg& c) {
   return dim3((unsigned)std::max<int64_t>(1, b), (unsigned)c.R);
 }
 
+// z = M^{-1} r for the pivoted Cholesky preconditioner, r.z, and (init) the
+// first direction or (iteration) beta.
+void pc_apply(const Pcg& c, int init) {
+  c.nlaunch[0] += 3;
+  k_pc_t<<<dim3((unsigned)c.pc_rank, (unsigned)((c.R + 15) / 16)), 256, 0, c.st>>>(c.L, c.pc_rank, c.N, c.Rr,
+                                                                                c.R, c.T);
+  k_pc_u<<<(unsigned)((c.pc_rank * c.R + 127) / 128), 128, 0, c.st>>>(c.Ginv, c.pc_rank, c.T, c.R, c.U);
+  k_pc_z<<<dim3((unsigned)((c.N + 31) / 32), (unsigned)((c.R + 15) / 16)), 256, 0, c.st>>>(
+      c.L, c.pc_rank, c.N, c.Rr, c.R, c.U, c.lam, c.Z, c.P, c.Pf, c.sc, init, c.done + 3, c.flag);
+}
+
 // Q = (K + lam I) Xc with FP64 products and sums (exact_fp64) or with the
 // double-FP32 products and sums of k_matvec_df.
 cudaError_t apply_accurate(const Pcg& c, const double* Xc, bool exact_fp64) {
@@ -594,7 +893,14 @@ cudaError_t cg_iteration(const Pcg& c, double* Xc) {
   if (e != cudaSuccess) return e;
   c.nlaunch[0] += 3;
   k_reduce_dot<<<vgrid(c), 256, 0, c.st>>>(c.Qpart, c.S, c.N, c.R, c.P, c.lam, c.Q, c.sc, SC_PQ, c.done);
-  k_update<<<vgrid(c), 256, 0, c.st>>>(c.minv, c.N, c.R, Xc, c.Rr, c.Z, c.P, c.Q, c.sc, c.done + 1, c.flag);
+  if (c.pc_rank > 0) {
+    k_update<false><<<vgrid(c), 256, 0, c.st>>>(c.minv, c.N, c.R, Xc, c.Rr, c.Z, c.P, c.Q, c.sc, c.done + 1,
+                                                 c.flag);
+    pc_apply(c, 0);
+  } else {
+    k_update<true><<<vgrid(c), 256, 0, c.st>>>(c.minv, c.N, c.R, Xc, c.Rr, c.Z, c.P, c.Q, c.sc, c.done + 1,
+                                                c.flag);
+  }
   k_direction<<<vgrid(c), 256, 0, c.st>>>(c.N, c.R, c.Z, c.P, c.Pf, c.sc);
   return cudaGetLastError();
 }
@@ -646,7 +952,12 @@ cudaError_t cg_run(const Pcg& c, const double* B, double* Xc, double tol, int ma
   *c.nlaunch += 3;
   k_zero<<<1, 256, 0, c.st>>>(c.sc, (int64_t)SC_N * c.R);
   k_set_active<<<1, 256, 0, c.st>>>(c.sc, c.R, tol * tol);
-  k_init<<<vgrid(c), 256, 0, c.st>>>(B, c.minv, c.N, c.R, Xc, c.Rr, c.Z, c.P, c.Pf, c.sc);
+  if (c.pc_rank > 0) {
+    k_init_pc<<<vgrid(c), 256, 0, c.st>>>(B, c.N, c.R, Xc, c.Rr, c.sc);
+    pc_apply(c, 1);
+  } else {
+    k_init<<<vgrid(c), 256, 0, c.st>>>(B, c.minv, c.N, c.R, Xc, c.Rr, c.Z, c.P, c.Pf, c.sc);
+  }
   cudaError_t e = cudaSuccess;
   int it = 0;
   while (it < maxit) {
@@ -702,7 +1013,12 @@ nk_status nk_pcg_impl(nk_handle* h, const float* K, int64_t ldk, int64_t N, cons
   c.S = S;
   c.rows_per_split = (int)((N + S - 1) / S);
   const size_t NR = (size_t)N * R;
-  size_t bytes = NR * 8 * 7 + (size_t)S * NR * 8 + (size_t)N * 8 + SC_N * (size_t)R * 8 + NR * 4 * 3 + 14 * 256;
+  const int pr = (precond == NK_PRECOND_PIVCHOL) ? (int)std::min<int64_t>(std::max(h->pcg_rank, 1), N) : 0;
+  const size_t pc_bytes = pr ? ((size_t)pr * N * 8 + 3 * (size_t)pr * pr * 8 + 2 * (size_t)pr * R * 8 +
+                                (size_t)N * 8 + 64 + 8 * 256)
+                             : 0;
+  size_t bytes = NR * 8 * 7 + (size_t)S * NR * 8 + (size_t)N * 8 + SC_N * (size_t)R * 8 + NR * 4 * 3 + 14 * 256 +
+                 pc_bytes;
   if (bytes > h->pcg_bytes) {
     if (h->pcg_ws) cudaFree(h->pcg_ws);
     h->pcg_ws = nullptr;
@@ -728,7 +1044,20 @@ nk_status nk_pcg_impl(nk_handle* h, const float* K, int64_t ldk, int64_t N, cons
   c.Xh = (float*)take(NR * 4);
   c.Xl = (float*)take(NR * 4);
   c.flag = (int*)take(64);
-  c.done = c.flag + 4;  // same 64-byte slot: flag, pad, done[2]
+  c.done = c.flag + 4;  // same 64-byte slot: flag, pad, done[4]
+  double *pc_G = nullptr, *pc_W = nullptr, *pc_d = nullptr;
+  PcState* pc_st = nullptr;
+  c.pc_rank = pr;
+  if (pr) {
+    c.L = (double*)take((size_t)pr * N * 8);
+    pc_G = (double*)take((size_t)pr * pr * 8);
+    pc_W = (double*)take((size_t)pr * pr * 8);
+    c.Ginv = (double*)take((size_t)pr * pr * 8);
+    c.T = (double*)take((size_t)pr * R * 8);
+    c.U = (double*)take((size_t)pr * R * 8);
+    pc_d = (double*)take((size_t)N * 8);
+    pc_st = (PcState*)take(64);
+  }
   {
     const cudaError_t z = cudaMemsetAsync(c.flag, 0, 64, st);
     if (z != cudaSuccess) return nk_cuda_check(h, z, "pcg counters");
@@ -784,6 +1113,18 @@ nk_status nk_pcg_impl(nk_handle* h, const float* K, int64_t ldk, int64_t N, cons
   ++h->launches;
   k_minv<<<(unsigned)std::min<int64_t>((N + 255) / 256, 4 * c.sm), 256, 0, st>>>(
       K, ldk, N, lam, precond == NK_PRECOND_JACOBI, c.minv);
+  if (pr) {
+    // partial pivoted Cholesky of K, then G = lam I + L L^T and its inverse
+    const unsigned rows_grid = (unsigned)std::min<int64_t>((N + 255) / 256, 4 * c.sm);
+    h->launches += pr + 3;
+    k_pc_diag<<<1, 1024, 0, st>>>(K, ldk, N, pc_d, pc_st);
+    for (int k = 0; k < pr; ++k)
+      k_pc_row<<<rows_grid, 256, 0, st>>>(K, ldk, N, c.L, pc_d, k, pc_st, c.done + 2);
+    k_pc_gram<<<dim3((unsigned)pr, (unsigned)pr), 256, 0, st>>>(c.L, pr, N, lam, pc_G);
+    k_pc_factor<<<1, 256, 0, st>>>(pc_G, pr, pc_W, c.Ginv);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return finish(nk_cuda_check(h, e, "pcg preconditioner"));
+  }
   const bool f64 = prec == NK_PREC_PLAIN_FP64;
   double* Xc = prec == NK_PREC_MIXED ? D : A;
   int64_t per_block = 0;

@@ -194,6 +194,42 @@ def test_pcg_forms_many_columns(h, n, R):
     assert its_by["mixed"] <= 4 * its_by["plain_fp64"] + 16, its_by
 
 
+@pytest.mark.parametrize("rank", [10, 40, 128])
+def test_pcg_pivchol_matches_cholesky_and_oracle(h, rank):
+    """Section 2's partial pivoted Cholesky preconditioner: the solve reaches
+    1e-6 against Cholesky in both precisions; the FP64 form takes the
+    oracle's iteration count (same greedy pivots and Woodbury apply); at full
+    rank M = K + lambda I and one or two steps suffice."""
+    p = nkdata.image_problem(128, 32, 8, n_classes=10, blur=False)
+    X = _dev(p.x_train.astype(np.float32))
+    convs = (2, 1, 0)
+    q = h.self_diag(X, convs, 2.0, 0.0)
+    K = h.block(X, q, X, q, convs, 2.0, 0.0, prec="mixed", symmetric=True)
+    Kh = K.double().cpu().numpy()
+    lam = 1e-4 * np.trace(Kh) / Kh.shape[0]
+    Y = torch.tensor(p.y_train, device="cuda")
+    Astar = oracle.cholesky_solve(Kh, p.y_train, lam)
+    kappa = np.linalg.cond(Kh + lam * np.eye(len(Kh)))
+    _, it_or, _ = oracle.pcg(Kh, p.y_train, lam, "pivchol", tol=1e-6, maxit=5000, rank=rank)
+    h.pcg_set_rank(rank)
+    try:
+        for prec in ["plain_fp64", "mixed"]:
+            A, its, rel = h.pcg_solve(K, Y, lam, precond="pivchol", prec=prec, tol=1e-6, maxit=5000)
+            An = A.cpu().numpy()
+            r = p.y_train - (Kh + lam * np.eye(len(Kh))) @ An
+            rel_true = np.linalg.norm(r, axis=0) / np.linalg.norm(p.y_train, axis=0)
+            assert rel_true.max() <= 1e-6, (prec, rel_true.max())
+            # residuals far below tol are compared at the level of their own rounding
+            assert np.allclose(rel_true, rel, rtol=1e-3, atol=1e-9)
+            assert np.linalg.norm(An - Astar) / np.linalg.norm(Astar) <= kappa * 1e-6
+            if prec == "plain_fp64":
+                assert abs(its - it_or) <= 2 + it_or // 10, (its, it_or)
+                if rank == 128:
+                    assert its <= 2
+    finally:
+        h.pcg_set_rank(100)
+
+
 def test_pcg_not_converged_and_edge(h):
     from paper_2303_05420_gb300._lib import NK_ERR_NOT_CONVERGED, NkError
 
