@@ -174,8 +174,8 @@ nk_status nk_block_backward(nk_handle* h, const nk_arch* arch, const nk_params* 
                             void* dXb, double* dsw2, double* dsb2, void* stream);
 
 /* Autotuner for the fused (NK_PREC_MIXED) kernel, the block-tile queue's
- * launch shape (Figure 1, top: blocks are "batched further" to fit the
- * device).  Times each launch variant of the fused kernel for this
+ * launch shape (Figure 1, top: independent blocks are grouped so that each
+ * fills the device).  Times each launch variant of the fused kernel for this
  * architecture, image size, channel count and sigma_b2 == 0 or not, on a
  * synthetic 12 x 12 block of hashed images (allocated and freed here), and
  * caches the fastest in the handle; later nk_block calls with the same key

@@ -2,7 +2,7 @@
 
 Test infrastructure only.  Section 2 ("Iterative solvers") of the paper solves
 (K + lambda I) A = Y with conjugate gradients, one CG per label column run in
-lock-step (Appendix B.3: "the CG routine is fully vectorized over tasks"); it
+lock-step (Appendix B.3 vectorises its CG routine over the tasks); it
 cites Shewchuk's tutorial for CG.  The Jacobi preconditioner M = diag(K) +
 lambda is the one the benchmark configurations fix; the paper's own is the
 partial pivoted Cholesky preconditioner (Section 2, after Wang et al. 2019):
