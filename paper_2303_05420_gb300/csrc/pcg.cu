@@ -36,12 +36,16 @@ enum { SC_RZ = 0, SC_RZN, SC_PQ, SC_RR, SC_YY, SC_ACT, SC_ALPHA, SC_BETA, SC_ITE
 #define NK_MV_CHUNK 256
 #define NK_MV_THREADS 128
 
-template <int RB, bool F64, bool VEC>
+// MULTI: more than 16 right-hand sides, one group of 16 per blockIdx.z;
+// otherwise all R (<= RB) columns in one group.
+template <int RB, bool F64, bool VEC, bool MULTI = false>
 __global__ void __launch_bounds__(NK_MV_THREADS, (F64 && RB > 8) ? 2 : 4)
 k_matvec(const float* __restrict__ K, int64_t ldk, int64_t N, const void* __restrict__ Pin, int R,
-         int rc0, int rcnt, int rows_per_split, double* __restrict__ Qpart) {
+         int rows_per_split, double* __restrict__ Qpart) {
+  const int rc0 = MULTI ? (int)blockIdx.z * 16 : 0;
+  const int rcnt = MULTI ? min(16, R - rc0) : R;
   using T = typename std::conditional<F64, double, float>::type;
-  constexpr int U = F64 ? 2 : 8;  // rows per unrolled step
+  constexpr int U = F64 ? 2 : (RB > 10 ? 4 : 8);  // rows per unrolled step (registers)
   extern __shared__ double mv_sh[];
   const int tid = threadIdx.x;
   const int64_t i0 = ((int64_t)blockIdx.x * NK_MV_THREADS + tid) * 4;
@@ -145,9 +149,10 @@ constexpr size_t mv_smem() {
 template <int RB>
 __global__ void __launch_bounds__(NK_MV_THREADS, RB > 8 ? 3 : 4)
 k_matvec_df(const float* __restrict__ K, int64_t ldk, int64_t N, const float* __restrict__ Xh,
-            const float* __restrict__ Xl, int R, int rc0, int rcnt, int rows_per_split,
+            const float* __restrict__ Xl, int R, int rows_per_split,
             double* __restrict__ Qpart) {
   constexpr int CPT = 2;  // columns per thread
+  const int rc0 = blockIdx.z * 16, rcnt = min(16, R - rc0);  // column group
   const int tid = threadIdx.x;
   const int64_t i0 = ((int64_t)blockIdx.x * NK_MV_THREADS + tid) * CPT;
   const int64_t js = (int64_t)blockIdx.y * rows_per_split;
@@ -762,22 +767,31 @@ cudaError_t matvec(const Pcg& c, const void* Pin) {
   const bool vec = (c.ldk % 4 == 0) && ((reinterpret_cast<uintptr_t>(c.K) & 15) == 0);
   const int64_t colthreads = (c.N + 3) / 4;
   dim3 grid((unsigned)((colthreads + NK_MV_THREADS - 1) / NK_MV_THREADS), (unsigned)c.S);
-  for (int rc0 = 0; rc0 < c.R; rc0 += 16) {
-    const int rcnt = std::min(16, c.R - rc0);
+  grid.z = (unsigned)((c.R + 15) / 16);  // all column groups in one launch
+  if (c.R > 16) {
+    ++*c.nlaunch;
+    if (vec)
+      k_matvec<16, F64, true, true><<<grid, NK_MV_THREADS, mv_smem<16, F64>(), c.st>>>(
+          c.K, c.ldk, c.N, Pin, c.R, c.rows_per_split, c.Qpart);
+    else
+      k_matvec<16, F64, false, true><<<grid, NK_MV_THREADS, mv_smem<16, F64>(), c.st>>>(
+          c.K, c.ldk, c.N, Pin, c.R, c.rows_per_split, c.Qpart);
+    return cudaGetLastError();
+  }
+  const int rmax = c.R;
 #define NK_MV(RB)                                                                                  \
-  if (rcnt <= RB) {                                                                                \
+  if (rmax <= RB) {                                                                                \
     ++*c.nlaunch;                                                                                  \
     if (vec)                                                                                       \
       k_matvec<RB, F64, true><<<grid, NK_MV_THREADS, mv_smem<RB, F64>(), c.st>>>(                  \
-          c.K, c.ldk, c.N, Pin, c.R, rc0, rcnt, c.rows_per_split, c.Qpart);                        \
+          c.K, c.ldk, c.N, Pin, c.R, c.rows_per_split, c.Qpart);                                   \
     else                                                                                           \
       k_matvec<RB, F64, false><<<grid, NK_MV_THREADS, mv_smem<RB, F64>(), c.st>>>(                 \
-          c.K, c.ldk, c.N, Pin, c.R, rc0, rcnt, c.rows_per_split, c.Qpart);                        \
-    continue;                                                                                      \
+          c.K, c.ldk, c.N, Pin, c.R, c.rows_per_split, c.Qpart);                                   \
+    return cudaGetLastError();                                                                     \
   }
-    NK_MV(1) NK_MV(2) NK_MV(4) NK_MV(8) NK_MV(10) NK_MV(16)
+  NK_MV(1) NK_MV(2) NK_MV(4) NK_MV(8) NK_MV(10) NK_MV(16)
 #undef NK_MV
-  }
   return cudaGetLastError();
 }
 
@@ -797,23 +811,34 @@ int matvec_prepare(int R) {
                                                   mv_smem<RB, false>());
   NK_MV_ATTR(1) NK_MV_ATTR(2) NK_MV_ATTR(4) NK_MV_ATTR(8) NK_MV_ATTR(10) NK_MV_ATTR(16)
 #undef NK_MV_ATTR
+  cudaFuncSetAttribute(k_matvec<16, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)mv_smem<16, false>());
+  cudaFuncSetAttribute(k_matvec<16, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)mv_smem<16, false>());
   (void)cudaGetLastError();
   return std::max(occ, 1);
 }
 
-// Row splits S of the matvec: enough blocks for several waves, the number of
-// blocks chosen so that the last wave is nearly full, and at least 4R rows
-// (32 at least) per split so that the FP64 partial sums stay small next to K.
+// Row splits S of the matvec: two to eight waves of blocks, the number of
+// blocks chosen so that the last wave is nearly full; at least 32 rows per
+// split, and no more splits than keep the FP64 partial sums (S N R words)
+// within a quarter of K's bytes unless that would leave the GPU under one
+// wave (small systems: latency, not bytes, is what counts).
 int choose_splits(int64_t N, int R, int sm, int occ) {
   const int64_t colblocks = ((N + 3) / 4 + NK_MV_THREADS - 1) / NK_MV_THREADS;
+  const int64_t groups = (R + 15) / 16;
   const int64_t cap = (int64_t)sm * occ;  // resident blocks
-  const int64_t s_max = std::max<int64_t>(1, std::min<int64_t>(512, N / std::max(4 * R, 32)));
-  const int64_t s_lo = std::min<int64_t>(s_max, std::max<int64_t>(1, (2 * cap) / colblocks));
-  const int64_t s_hi = std::min<int64_t>(s_max, std::max<int64_t>(s_lo, (8 * cap) / colblocks));
+  const int64_t per_split = colblocks * groups;
+  const int64_t s_rows = std::max<int64_t>(1, std::min<int64_t>(512, N / 32));
+  const int64_t s_lo0 = std::max<int64_t>(1, (2 * cap) / per_split);
+  const int64_t s_hi0 = std::max<int64_t>(s_lo0, (8 * cap) / per_split);
+  const int64_t s_bytes = std::max<int64_t>(1, N / std::max(4 * R, 32));
+  const int64_t s_max = std::min<int64_t>(s_rows, std::max<int64_t>(s_bytes, s_lo0));
+  const int64_t s_lo = std::min(s_lo0, s_max), s_hi = std::min(s_hi0, s_max);
   int64_t best = s_lo;
   double best_eff = -1.0;
   for (int64_t S = s_lo; S <= s_hi; ++S) {
-    const double waves = (double)(colblocks * S) / (double)cap;
+    const double waves = (double)(per_split * S) / (double)cap;
     const double eff = waves / std::ceil(waves);
     if (eff > best_eff + 1e-3) {
       best_eff = eff;
@@ -853,19 +878,18 @@ cudaError_t apply_accurate(const Pcg& c, const double* Xc, bool exact_fp64) {
                   0, c.st>>>(NR, Xc, c.Xh, c.Xl);
     const int64_t colthreads = (c.N + 1) / 2;  // two columns per thread
     dim3 grid((unsigned)((colthreads + NK_MV_THREADS - 1) / NK_MV_THREADS), (unsigned)c.S);
-    for (int rc0 = 0; rc0 < c.R; rc0 += 16) {
-      const int rcnt = std::min(16, c.R - rc0);
-      ++*c.nlaunch;
-      if (rcnt <= 4)
-        k_matvec_df<4><<<grid, NK_MV_THREADS, 0, c.st>>>(c.K, c.ldk, c.N, c.Xh, c.Xl, c.R, rc0, rcnt,
-                                                         c.rows_per_split, c.Qpart);
-      else if (rcnt <= 10)
-        k_matvec_df<10><<<grid, NK_MV_THREADS, 0, c.st>>>(c.K, c.ldk, c.N, c.Xh, c.Xl, c.R, rc0, rcnt,
-                                                          c.rows_per_split, c.Qpart);
-      else
-        k_matvec_df<16><<<grid, NK_MV_THREADS, 0, c.st>>>(c.K, c.ldk, c.N, c.Xh, c.Xl, c.R, rc0, rcnt,
-                                                          c.rows_per_split, c.Qpart);
-    }
+    grid.z = (unsigned)((c.R + 15) / 16);  // all column groups in one launch
+    const int rmax = std::min(16, c.R);
+    ++*c.nlaunch;
+    if (rmax <= 4)
+      k_matvec_df<4><<<grid, NK_MV_THREADS, 0, c.st>>>(c.K, c.ldk, c.N, c.Xh, c.Xl, c.R, c.rows_per_split,
+                                                       c.Qpart);
+    else if (rmax <= 10)
+      k_matvec_df<10><<<grid, NK_MV_THREADS, 0, c.st>>>(c.K, c.ldk, c.N, c.Xh, c.Xl, c.R, c.rows_per_split,
+                                                        c.Qpart);
+    else
+      k_matvec_df<16><<<grid, NK_MV_THREADS, 0, c.st>>>(c.K, c.ldk, c.N, c.Xh, c.Xl, c.R, c.rows_per_split,
+                                                        c.Qpart);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
