@@ -107,6 +107,24 @@ def cpu_oracle_rate(n_workers: int, pairs_per_worker: int, hw: int, seed0: int =
     return pairs / max(times), pairs, max(times), wall
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks (a replicated job takes as long as its
+    slowest replica); x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world: int, units_per_replica: float, seconds: float) -> float:
+    """Whole-job units per second: each of the `world` replicas processes the
+    same workload (weak scaling, no data-path exchange)."""
+    return world * units_per_replica / seconds
+
+
 def load_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -267,13 +285,9 @@ def run_ours(args, rank, world, dist):
     clocks = sampler.stop()
     launches = h.launch_count() - launches0
     h.sync_status()
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
     ms_per_step = total_ms / args.steps
-    value = world * entries * args.steps / (total_ms / 1e3)
+    value = replica_throughput(world, entries * args.steps, total_ms / 1e3)
 
     # ---- end to end through host buffers (H2D inputs, D2H solution + test block)
     Ah = torch.empty_like(A, device="cpu").pin_memory()
@@ -292,7 +306,7 @@ def run_ours(args, rank, world, dist):
         b.record(stream)
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
-    e2e_val = world * entries / (statistics.mean(e2e_ms) / 1e3)
+    e2e_val = replica_throughput(world, entries, max_over_ranks(statistics.mean(e2e_ms), dist, dev) / 1e3)
 
     # ---- kernel-only roofline of the fused Myrtle kernel
     ops_entry = algorithmic_ops_per_entry(hw)

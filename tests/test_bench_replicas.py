@@ -1,0 +1,69 @@
+"""Host logic of the multi-GPU path (replicas: the method's blocks and solves
+shard into independent problems, so N GPUs run N copies with no data-path
+collective).  Two gloo ranks on the CPU check the max-over-ranks timing, the
+whole-job throughput, and that only rank 0 of the reference arm prints."""
+
+import io
+import json
+import os
+import socket
+import sys
+from contextlib import redirect_stdout
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, q):
+    import torch.distributed as dist
+
+    import bench
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        got = bench.max_over_ranks(10.0 + 5.0 * rank, dist, "cpu")
+        q.put((rank, got))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    res = dict(q.get(timeout=10) for _ in range(2))
+    assert res == {0: 15.0, 1: 15.0}
+
+
+def test_replica_throughput_and_single_rank():
+    import bench
+
+    assert bench.max_over_ranks(3.5, None, "cpu") == 3.5
+    assert bench.replica_throughput(4, 1000.0, 2.0) == 2000.0
+
+
+def test_reference_arm_other_ranks_print_nothing():
+    import bench
+
+    class A:
+        steps, warmup, config, ref_pairs = 1, 0, "headline", 1
+
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.run_reference(A(), rank=1, world=2)
+    assert buf.getvalue() == ""
