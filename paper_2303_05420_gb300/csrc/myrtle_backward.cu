@@ -78,13 +78,14 @@ __global__ void k_map_adj(const T* __restrict__ Kpre, T* __restrict__ d, T* __re
                           int64_t np, int HW, int64_t na, int64_t nb, int sym, int64_t pair0,
                           int64_t a0, int64_t b0, const double* __restrict__ qda,
                           const double* __restrict__ qdb, int64_t nq, int qoff) {
-  const int64_t HW2 = (int64_t)HW * HW, total = np * HW2;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t pr = e / HW2, rem = e - pr * HW2;
-    const int p = (int)(rem / HW), pp = (int)(rem - (int64_t)p * HW);
-    int64_t i, j;
-    pair_of(pair0 + pr, na, nb, sym, &i, &j);
+  // one pair per blockIdx.y step: its images are found once, not per entry
+  const int HW2 = HW * HW;
+  for (int64_t pr = blockIdx.y; pr < np; pr += gridDim.y) {
+   int64_t i, j;
+   pair_of(pair0 + pr, na, nb, sym, &i, &j);
+   for (int rem = blockIdx.x * blockDim.x + threadIdx.x; rem < HW2; rem += gridDim.x * blockDim.x) {
+    const int64_t e = pr * (int64_t)HW2 + rem;
+    const int p = rem / HW, pp = rem - p * HW;
     const T q1 = (T)qda[(a0 + i) * nq + qoff + p];
     const T q2 = (T)qdb[(b0 + j) * nq + qoff + pp];
     const T s = sqrt(q1 * q2);
@@ -104,6 +105,7 @@ __global__ void k_map_adj(const T* __restrict__ Kpre, T* __restrict__ d, T* __re
     }
     d[e] = dk;
     hbuf[e] = h;
+   }
   }
 }
 
@@ -156,13 +158,26 @@ __global__ void k_sigma_terms(const T* __restrict__ d, const T* __restrict__ Kpr
                               double sb2, double inv_sw2, double* __restrict__ dsw2,
                               double* __restrict__ dsb2) {
   __shared__ double r1[32], r2[32];
+  // sums in T over runs of at most 64 elements, added in FP64 (FP64
+  // arithmetic runs at 1/64 of the FP32 rate on this part)
   double a = 0.0, b = 0.0;
+  T ta = 0, tb = 0;
+  const T tsb2 = (T)sb2;
+  int run = 0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const double g = (double)d[e];
-    a += g * ((double)Kpre[e] - sb2);
-    b += g;
+    const T g = d[e];
+    ta += g * (Kpre[e] - tsb2);
+    tb += g;
+    if (++run == 64) {
+      a += (double)ta;
+      b += (double)tb;
+      ta = tb = 0;
+      run = 0;
+    }
   }
+  a += (double)ta;
+  b += (double)tb;
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_xor_sync(0xffffffffu, a, o);
     b += __shfl_xor_sync(0xffffffffu, b, o);
@@ -620,7 +635,7 @@ cudaError_t run_backward(const NkGeom& g, double sw2, double sb2, const float* X
         }
     }
     ++*launches;
-    k_input_cov<T><<<grid_for(np * (int64_t)P.hw0sq), 256, 0, st>>>(Xa, Xb, a0, b0, na, nb, sym, pair0, np,
+    k_input_cov<T><<<pair_grid(np, (int64_t)P.hw0sq), 256, 0, st>>>(Xa, Xb, a0, b0, na, nb, sym, pair0, np,
                                                                      g.Hs[0], g.Ws[0], g.C, cur);
     int layer = 0;
     for (int s = 0; s <= last_conv_stage; ++s) {
@@ -633,13 +648,13 @@ cudaError_t run_backward(const NkGeom& g, double sw2, double sb2, const float* X
       }
       for (int k = 0; k < g.convs[s]; ++k, ++layer) {
         ++*launches;
-        k_conv<T><<<grid_for(np * HW * HW), 256, 0, st>>>(cur, Kst[layer], np, H, W, g.filter, a_conv,
+        k_conv<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(cur, Kst[layer], np, H, W, g.filter, a_conv,
                                                           (T)sb2);
         e = cudaMemcpyAsync(nxt, Kst[layer], (size_t)np * HW * HW * sizeof(T), cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;
         if (relu) {
           ++*launches;
-          k_relu<T><<<grid_for(np * HW * HW), 256, 0, st>>>(nxt, np, (int)HW, na, nb, sym, pair0, a0, b0, qda,
+          k_relu<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(nxt, np, (int)HW, na, nb, sym, pair0, a0, b0, qda,
                                                             qdb, qsa, qsb, g.nq, g.layer_qoff[layer],
                                                             dstatus);
         }
@@ -663,7 +678,7 @@ cudaError_t run_backward(const NkGeom& g, double sw2, double sb2, const float* X
         --layer;
         if (relu) {
           *launches += 3;
-          k_map_adj<T><<<grid_for(np * HW * HW), 256, 0, st>>>(Kst[layer], cur, hbuf, np, (int)HW, na, nb, sym,
+          k_map_adj<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(Kst[layer], cur, hbuf, np, (int)HW, na, nb, sym,
                                                                pair0, a0, b0, qda, qdb, g.nq, g.layer_qoff[layer]);
           k_rowsum_q<T><<<grid_for(np * HW * 32), 256, 0, st>>>(hbuf, np, (int)HW, na, nb, sym, pair0, a0, qda,
                                                                 g.nq, g.layer_qoff[layer], dqa);
@@ -673,7 +688,7 @@ cudaError_t run_backward(const NkGeom& g, double sw2, double sb2, const float* X
         *launches += 2;
         k_sigma_terms<T><<<std::min(grid_for(np * HW * HW), 1024), 256, 0, st>>>(cur, Kst[layer], np * HW * HW,
                                                                                sb2, 1.0 / sw2, dsw2, dsb2);
-        k_conv<T><<<grid_for(np * HW * HW), 256, 0, st>>>(cur, nxt, np, H, W, g.filter, a_conv, (T)0);
+        k_conv<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(cur, nxt, np, H, W, g.filter, a_conv, (T)0);
         T* t = cur; cur = nxt; nxt = t;
       }
       if (s > 0) {

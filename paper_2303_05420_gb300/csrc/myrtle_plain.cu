@@ -30,7 +30,7 @@ cudaError_t run_plain(const NkGeom& g, double sw2, double sb2, const float* Xa, 
     T* cur = buf0;
     T* nxt = buf1;
     *launches += 2;  // input covariance + global average
-    k_input_cov<T><<<grid_for(np * HW0 * HW0), 256, 0, st>>>(Xa, Xb, a0, b0, na, nb, symmetric,
+    k_input_cov<T><<<pair_grid(np, HW0 * HW0), 256, 0, st>>>(Xa, Xb, a0, b0, na, nb, symmetric,
                                                              pair0, np, g.Hs[0], g.Ws[0], g.C, cur);
     int layer = 0;
     int H = g.Hs[0], W = g.Ws[0];
@@ -46,11 +46,11 @@ cudaError_t run_plain(const NkGeom& g, double sw2, double sb2, const float* Xa, 
       const int64_t HW = (int64_t)H * W;
       for (int k = 0; k < g.convs[s]; ++k, ++layer) {
         *launches += (g.act == NK_ACT_RELU) ? 2 : 1;
-        k_conv<T><<<grid_for(np * HW * HW), 256, 0, st>>>(cur, nxt, np, H, W, g.filter, a_conv,
+        k_conv<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(cur, nxt, np, H, W, g.filter, a_conv,
                                                           (T)sb2);
         T* t = cur; cur = nxt; nxt = t;
         if (g.act == NK_ACT_RELU)
-          k_relu<T><<<grid_for(np * HW * HW), 256, 0, st>>>(cur, np, (int)HW, na, nb, symmetric,
+          k_relu<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(cur, np, (int)HW, na, nb, symmetric,
                                                             pair0, a0, b0, qda, qdb, qsa, qsb,
                                                             g.nq, g.layer_qoff[layer], dstatus);
       }

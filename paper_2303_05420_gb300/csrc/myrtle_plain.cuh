@@ -32,42 +32,58 @@ template <typename T>
 __global__ void k_input_cov(const float* __restrict__ Xa, const float* __restrict__ Xb,
                             int64_t a0, int64_t b0, int64_t na, int64_t nb, int symmetric,
                             int64_t pair0, int64_t npairs, int H, int W, int C, T* __restrict__ out) {
-  const int64_t HW = (int64_t)H * W, HW2 = HW * HW;
-  const int64_t total = npairs * HW2;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t pr = e / HW2, rem = e - pr * HW2;
-    const int64_t p = rem / HW, pp = rem - p * HW;
+  const int HW = H * W, HW2 = HW * HW;
+  for (int64_t pr = blockIdx.y; pr < npairs; pr += gridDim.y) {
     int64_t i, j;
     pair_of(pair0 + pr, na, nb, symmetric, &i, &j);
-    const float* x = Xa + (a0 + i) * HW * C + p * C;
-    const float* y = Xb + (b0 + j) * HW * C + pp * C;
-    T acc = 0;
-    for (int c = 0; c < C; ++c) acc += (T)x[c] * (T)y[c];
-    out[e] = acc / (T)C;
+    const float* xa = Xa + (a0 + i) * (int64_t)HW * C;
+    const float* xb = Xb + (b0 + j) * (int64_t)HW * C;
+    for (int rem = blockIdx.x * blockDim.x + threadIdx.x; rem < HW2; rem += gridDim.x * blockDim.x) {
+      const int p = rem / HW, pp = rem - p * HW;
+      const float* x = xa + p * C;
+      const float* y = xb + pp * C;
+      T acc = 0;
+      for (int c = 0; c < C; ++c) acc += (T)x[c] * (T)y[c];
+      out[pr * (int64_t)HW2 + rem] = acc / (T)C;
+    }
   }
 }
 
 template <typename T>
 __global__ void k_conv(const T* __restrict__ in, T* __restrict__ out, int64_t npairs, int H, int W,
                        int filt, T a, T b) {
-  const int64_t HW = (int64_t)H * W, HW2 = HW * HW;
-  const int64_t total = npairs * HW2;
+  // one pair per blockIdx.y step, 32-bit index arithmetic inside a pair
+  const int HW = H * W;
+  const int HW2 = HW * HW;
   const int r = filt / 2;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t pr = e / HW2, rem = e - pr * HW2;
-    const int p = (int)(rem / HW), pp = (int)(rem - (int64_t)p * HW);
-    const int i = p / W, j = p % W, k = pp / W, l = pp % W;
-    T acc = 0;
-    for (int dy = -r; dy <= r; ++dy)
-      for (int dx = -r; dx <= r; ++dx) {
-        const int i2 = i + dy, j2 = j + dx, k2 = k + dy, l2 = l + dx;
-        if (i2 >= 0 && i2 < H && j2 >= 0 && j2 < W && k2 >= 0 && k2 < H && l2 >= 0 && l2 < W)
-          acc += in[pr * HW2 + (int64_t)(i2 * W + j2) * HW + k2 * W + l2];
+  for (int64_t pr = blockIdx.y; pr < npairs; pr += gridDim.y) {
+    const T* src = in + pr * (int64_t)HW2;
+    T* dst = out + pr * (int64_t)HW2;
+    for (int rem = blockIdx.x * blockDim.x + threadIdx.x; rem < HW2; rem += gridDim.x * blockDim.x) {
+      const int p = rem / HW, pp = rem - p * HW;
+      const int i = p / W, j = p - i * W, k = pp / W, l = pp - k * W;
+      T acc = 0;
+      for (int dy = -r; dy <= r; ++dy) {
+        const int i2 = i + dy, k2 = k + dy;
+        if (i2 < 0 || i2 >= H || k2 < 0 || k2 >= H) continue;
+        for (int dx = -r; dx <= r; ++dx) {
+          const int j2 = j + dx, l2 = l + dx;
+          if (j2 >= 0 && j2 < W && l2 >= 0 && l2 < W) acc += src[(i2 * W + j2) * HW + k2 * W + l2];
+        }
       }
-    out[e] = a * acc + b;
+      dst[rem] = a * acc + b;
+    }
   }
+}
+
+// Launch shape of the per-pair kernels: pairs along y, a pair's pixel pairs
+// along x.
+inline dim3 pair_grid(int64_t npairs, int64_t HW2) {
+  int64_t x = (HW2 + 255) / 256;
+  int64_t y = npairs;
+  if (y > 65535) y = 65535;
+  while (x * y > 152 * 64 && x > 1) x = (x + 1) / 2;
+  return dim3((unsigned)std::max<int64_t>(1, x), (unsigned)std::max<int64_t>(1, y));
 }
 
 // ReLU map with self-variances of the pair's two images at this layer.
@@ -77,13 +93,14 @@ __global__ void k_relu(T* __restrict__ K, int64_t npairs, int HW, int64_t na, in
                        const double* __restrict__ qda, const double* __restrict__ qdb,
                        const float* __restrict__ qsa, const float* __restrict__ qsb, int64_t nq,
                        int qoff, unsigned int* dstatus) {
-  const int64_t HW2 = (int64_t)HW * HW, total = npairs * HW2;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t pr = e / HW2, rem = e - pr * HW2;
-    const int p = (int)(rem / HW), pp = (int)(rem - (int64_t)p * HW);
-    int64_t i, j;
-    pair_of(pair0 + pr, na, nb, symmetric, &i, &j);
+  // one pair per blockIdx.y step: its images are found once, not per entry
+  const int HW2 = HW * HW;
+  for (int64_t pr = blockIdx.y; pr < npairs; pr += gridDim.y) {
+   int64_t i, j;
+   pair_of(pair0 + pr, na, nb, symmetric, &i, &j);
+   for (int rem = blockIdx.x * blockDim.x + threadIdx.x; rem < HW2; rem += gridDim.x * blockDim.x) {
+    const int64_t e = pr * (int64_t)HW2 + rem;
+    const int p = rem / HW, pp = rem - p * HW;
     if constexpr (sizeof(T) == 8) {
       const double q1 = qda[(a0 + i) * nq + qoff + p];
       const double q2 = qdb[(b0 + j) * nq + qoff + pp];
@@ -102,6 +119,7 @@ __global__ void k_relu(T* __restrict__ K, int64_t npairs, int HW, int64_t na, in
       }
       K[e] = v;
     }
+   }
   }
 }
 
