@@ -364,7 +364,7 @@ def run_ours(args, rank, world, dist):
             extra[f"{key}_iters_per_s"] = its / (ms / 1e3)
             extra[f"{key}_relres"] = max(rel)
     lam_used = h.last_lambda()
-    if args.grad:
+    if not args.skip_grad:
         extra.update(grad_leg(h, dev))
     if not args.skip_queue:
         extra.update(queue_leg(h, dev))
@@ -420,7 +420,7 @@ def grad_leg(h, dev):
     32x32 images (same generator), sigma_w^2 = 2, sigma_b^2 = 0.01: forward
     blocks K_ss (upper triangle) and K_ts by the fused kernel, loss in torch,
     gradients w.r.t. the support pixels, sigma_w^2 and sigma_b^2 by the FP32
-    layer-wise adjoint.  One untimed warm-up, one timed pass."""
+    layer-wise adjoint.  A small untimed warm-up (4 x 8), one timed pass."""
     import numpy as np
     import torch
 
@@ -435,26 +435,35 @@ def grad_leg(h, dev):
     Xt = torch.tensor(tgt.astype(np.float32), device=dev)
     h.autotune(convs, 2.0, 0.01, 32, 32, 3)
 
-    def once():
-        Xs = torch.tensor(sup.astype(np.float32), device=dev, requires_grad=True)
+    def once(ns, nt):
+        Xs = torch.tensor(sup[:ns].astype(np.float32), device=dev, requires_grad=True)
         s = torch.tensor(2.0, dtype=torch.float64, device=dev, requires_grad=True)
         b = torch.tensor(0.01, dtype=torch.float64, device=dev, requires_grad=True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
         Kss = nngp_block(Xs, Xs, s, b, convs, h, symmetric=True, prec="mixed", bprec="plain_fp32").double()
-        Kts = nngp_block(Xt, Xs, s, b, convs, h, prec="mixed", bprec="plain_fp32").double()
-        lam = 1e-6 * float(torch.trace(Kss)) / 100
-        A = torch.linalg.solve(Kss + lam * torch.eye(100, dtype=torch.float64, device=dev), ys)
-        L = 0.5 * ((Kts @ A - yt) ** 2).mean()
+        Kts = nngp_block(Xt[:nt], Xs, s, b, convs, h, prec="mixed", bprec="plain_fp32").double()
+        lam = 1e-6 * float(torch.trace(Kss.detach())) / ns
+        A = torch.linalg.solve(Kss + lam * torch.eye(ns, dtype=torch.float64, device=dev), ys[:ns])
+        L = 0.5 * ((Kts @ A - yt[:nt]) ** 2).mean()
+        ev[1].record()
         L.backward()
-        return float(L), float(s.grad), float(b.grad)
+        ev[2].record()
+        torch.cuda.synchronize()
+        return (float(L), float(s.grad), float(b.grad), ev[0].elapsed_time(ev[1]) / 1e3,
+                ev[1].elapsed_time(ev[2]) / 1e3)
 
-    once()
+    once(4, 8)  # loads every kernel; untimed
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    L, gs, gb = once()
+    L, gs, gb, t_fwd, t_bwd = once(100, 2048)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     entries = 100 * 101 // 2 + 2048 * 100
-    return {"grad_myrtle10_100x2048_s": dt, "grad_entries_per_s": entries / dt,
+    return {"grad_workload": "myrtle10_(3,3,3)_32x32_support100_target2048_krr_loss_fp32_adjoint",
+            "grad_myrtle10_100x2048_s": dt, "grad_entries_per_s": entries / dt,
+            "grad_forward_s": t_fwd, "grad_backward_s": t_bwd,
+            "grad_backward_entries_per_s": entries / t_bwd,
             "grad_loss": L, "grad_dsw2": gs, "grad_dsb2": gb}
 
 
@@ -671,8 +680,8 @@ def main():
     ap.add_argument("--fc-test", type=int, default=FC_N_TEST)
     ap.add_argument("--fc-only", action="store_true",
                     help="run only the FC leg (prints its keys as one JSON line)")
-    ap.add_argument("--grad", action="store_true",
-                    help="also time the Myrtle-10 kernel-ridge gradient (100 support x 2048 targets)")
+    ap.add_argument("--skip-grad", action="store_true",
+                    help="skip the Myrtle-10 kernel-ridge gradient leg (100 support x 2048 targets)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -266,3 +266,60 @@ def test_autotune_variants_agree(h):
         h.autotune_set(convs, 2.0, sb2, 32, 32, chosen)
     with pytest.raises(NkError):
         h.autotune_set((2, 1, 0), 2.0, 0.0, 32, 32, 3)
+
+
+@pytest.mark.parametrize("precond", ["none", "jacobi", "pivchol"])
+@pytest.mark.parametrize("prec", ["plain_fp64", "plain_fp32", "mixed"])
+def test_pcg_degenerate_cases(h, precond, prec):
+    """N = 1; a zero right-hand side next to a non-zero one; K with a leading
+    dimension larger than N; maxit = 0."""
+    from paper_2303_05420_gb300._lib import NK_ERR_NOT_CONVERGED, NkError
+
+    K = torch.tensor([[2.0]], device="cuda")
+    Y = torch.tensor([[4.0]], dtype=torch.float64, device="cuda")
+    A, its, rel = h.pcg_solve(K, Y, 2.0, precond=precond, prec=prec, tol=1e-10, maxit=10)
+    assert abs(float(A[0, 0]) - 1.0) <= 1e-6 and rel[0] <= 1e-10
+    n = 37
+    rng = np.random.default_rng(5)
+    B = rng.standard_normal((n, n))
+    Kh = (B @ B.T / n + np.eye(n)).astype(np.float32)
+    Kbig = torch.zeros((n, n + 11), device="cuda")
+    Kbig[:, :n] = torch.tensor(Kh, device="cuda")
+    Kv = Kbig[:, :n]  # leading dimension n + 11
+    Yh = np.stack([rng.standard_normal(n), np.zeros(n)], axis=1)
+    Y2 = torch.tensor(Yh, device="cuda")
+    tol = 1e-6 if prec == "plain_fp32" else 1e-9
+    A, its, rel = h.pcg_solve(Kv, Y2, 0.5, precond=precond, prec=prec, tol=tol, maxit=500)
+    want = np.linalg.solve(Kh.astype(np.float64) + 0.5 * np.eye(n), Yh)
+    assert np.allclose(A.cpu().numpy(), want, rtol=0, atol=20 * tol * np.abs(want).max())
+    assert rel[1] == 0.0 and float(A[:, 1].abs().max()) == 0.0
+    with pytest.raises(NkError) as ei:
+        h.pcg_solve(Kv, Y2, 0.5, precond=precond, prec=prec, tol=1e-9, maxit=0)
+    assert ei.value.status == NK_ERR_NOT_CONVERGED
+
+
+def test_pcg_rejects_bad_arguments(h):
+    import ctypes
+
+    from paper_2303_05420_gb300._lib import NK_ERR_INVALID_ARG, lib
+
+    K = torch.eye(4, device="cuda")
+    Y = torch.ones((4, 1), dtype=torch.float64, device="cuda")
+    A = torch.empty_like(Y)
+    its = ctypes.c_int(0)
+    rel = (ctypes.c_double * 1)()
+
+    def call(N=4, ldk=4, R=1, lam=1.0, precond=1, prec=2, tol=1e-6, maxit=10, refine=4):
+        return lib().nk_pcg_solve(h._h, ctypes.c_void_p(K.data_ptr()), ldk, N, ctypes.c_void_p(Y.data_ptr()), R,
+                                  lam, precond, prec, tol, maxit, refine, ctypes.c_void_p(A.data_ptr()),
+                                  ctypes.byref(its), ctypes.cast(rel, ctypes.c_void_p), None)
+
+    assert call() == 0
+    for kw in [dict(N=-1), dict(ldk=3), dict(R=-2), dict(R=257), dict(lam=float("nan")), dict(precond=3),
+               dict(prec=5), dict(tol=-1.0), dict(maxit=-1), dict(refine=-1)]:
+        assert call(**kw) == NK_ERR_INVALID_ARG, kw
+    assert call(N=0) == 0 and call(R=0) == 0
+    from paper_2303_05420_gb300._lib import NkError
+
+    with pytest.raises(NkError):
+        h.pcg_set_rank(0)
