@@ -648,8 +648,7 @@ cudaError_t run_backward(const NkGeom& g, double sw2, double sb2, const float* X
       }
       for (int k = 0; k < g.convs[s]; ++k, ++layer) {
         ++*launches;
-        k_conv<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(cur, Kst[layer], np, H, W, g.filter, a_conv,
-                                                          (T)sb2);
+        conv_layer<T>(cur, Kst[layer], np, H, W, g.filter, a_conv, (T)sb2, st);
         e = cudaMemcpyAsync(nxt, Kst[layer], (size_t)np * HW * HW * sizeof(T), cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;
         if (relu) {
@@ -688,7 +687,7 @@ cudaError_t run_backward(const NkGeom& g, double sw2, double sb2, const float* X
         *launches += 2;
         k_sigma_terms<T><<<std::min(grid_for(np * HW * HW), 1024), 256, 0, st>>>(cur, Kst[layer], np * HW * HW,
                                                                                sb2, 1.0 / sw2, dsw2, dsb2);
-        k_conv<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(cur, nxt, np, H, W, g.filter, a_conv, (T)0);
+        conv_layer<T>(cur, nxt, np, H, W, g.filter, a_conv, (T)0, st);
         T* t = cur; cur = nxt; nxt = t;
       }
       if (s > 0) {

@@ -46,8 +46,7 @@ cudaError_t run_plain(const NkGeom& g, double sw2, double sb2, const float* Xa, 
       const int64_t HW = (int64_t)H * W;
       for (int k = 0; k < g.convs[s]; ++k, ++layer) {
         *launches += (g.act == NK_ACT_RELU) ? 2 : 1;
-        k_conv<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(cur, nxt, np, H, W, g.filter, a_conv,
-                                                          (T)sb2);
+        conv_layer<T>(cur, nxt, np, H, W, g.filter, a_conv, (T)sb2, st);
         T* t = cur; cur = nxt; nxt = t;
         if (g.act == NK_ACT_RELU)
           k_relu<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(cur, np, (int)HW, na, nb, symmetric,

@@ -86,6 +86,73 @@ inline dim3 pair_grid(int64_t npairs, int64_t HW2) {
   return dim3((unsigned)std::max<int64_t>(1, x), (unsigned)std::max<int64_t>(1, y));
 }
 
+// The same 3x3 SAME conv, streamed: the diagonal stencil factors into a
+// 3-tap sum along the (j, l) diagonal of a fixed (i, k) plane and a 3-tap sum
+// over the planes (i - 1, k - 1), (i, k), (i + 1, k + 1), with the validity
+// masks factoring the same way.  A block walks one (i, k) diagonal of one
+// pair; the row-filtered planes of a sliding window of three live in shared
+// memory, so each input element is read three times (L1) instead of nine and
+// each output once.  smem: 3 W^2 elements of T.
+template <typename T>
+__global__ void __launch_bounds__(256) k_conv_diag(const T* __restrict__ in, T* __restrict__ out, int64_t npairs,
+                                                   int H, int W, T a, T b) {
+  extern __shared__ __align__(16) unsigned char conv_sm[];
+  T* sh = reinterpret_cast<T*>(conv_sm);
+  const int HW = H * W, W2 = W * W;
+  const int d = (int)blockIdx.x - (H - 1);  // k - i on this diagonal
+  const int i0 = d < 0 ? -d : 0;
+  const int i1 = (d > 0 ? H - d : H) - 1;   // last i with k = i + d < H
+  for (int64_t pr = blockIdx.y; pr < npairs; pr += gridDim.y) {
+    const T* src = in + pr * (int64_t)HW * HW;
+    T* dst = out + pr * (int64_t)HW * HW;
+    // row-filtered plane (ii, ii + d) into slot ii % 3
+    auto load = [&](int ii) {
+      const int kk = ii + d;
+      T* slot = sh + (ii % 3) * W2;
+      for (int e = threadIdx.x; e < W2; e += blockDim.x) {
+        const int j = e / W, l = e - j * W;
+        T v = src[(int64_t)(ii * W + j) * HW + kk * W + l];
+        if (j > 0 && l > 0) v += src[(int64_t)(ii * W + j - 1) * HW + kk * W + l - 1];
+        if (j + 1 < W && l + 1 < W) v += src[(int64_t)(ii * W + j + 1) * HW + kk * W + l + 1];
+        slot[e] = v;
+      }
+    };
+    __syncthreads();  // the previous pair's planes are no longer read
+    load(i0);
+    for (int i = i0; i <= i1; ++i) {
+      if (i + 1 <= i1) load(i + 1);
+      __syncthreads();
+      const T* cur = sh + (i % 3) * W2;
+      const T* prv = sh + ((i + 2) % 3) * W2;
+      const T* nxt = sh + ((i + 1) % 3) * W2;
+      const int k = i + d;
+      for (int e = threadIdx.x; e < W2; e += blockDim.x) {
+        T acc = cur[e];
+        if (i > i0) acc += prv[e];
+        if (i < i1) acc += nxt[e];
+        const int j = e / W, l = e - j * W;
+        dst[(int64_t)(i * W + j) * HW + k * W + l] = a * acc + b;
+      }
+      __syncthreads();  // slot (i + 2) % 3 is refilled next
+    }
+  }
+}
+
+// One 3x3 (or other odd) SAME conv layer on a chunk of pair tensors.
+template <typename T>
+inline void conv_layer(const T* in, T* out, int64_t np, int H, int W, int filt, T a, T b, cudaStream_t st) {
+  const size_t smem = (size_t)3 * W * W * sizeof(T);
+  if (filt == 3 && smem <= 200 * 1024) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_conv_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t y = np < 65535 ? np : 65535;
+    k_conv_diag<T><<<dim3((unsigned)(2 * H - 1), (unsigned)y), 256, smem, st>>>(in, out, np, H, W, a, b);
+  } else {
+    k_conv<T><<<pair_grid(np, (int64_t)H * W * H * W), 256, 0, st>>>(in, out, np, H, W, filt, a, b);
+  }
+}
+
+
 // ReLU map with self-variances of the pair's two images at this layer.
 template <typename T>
 __global__ void k_relu(T* __restrict__ K, int64_t npairs, int HW, int64_t na, int64_t nb,
