@@ -77,7 +77,15 @@ template <typename T>
 __global__ void k_map_adj(const T* __restrict__ Kpre, T* __restrict__ d, T* __restrict__ hbuf,
                           int64_t np, int HW, int64_t na, int64_t nb, int sym, int64_t pair0,
                           int64_t a0, int64_t b0, const double* __restrict__ qda,
-                          const double* __restrict__ qdb, int64_t nq, int qoff) {
+                          const double* __restrict__ qdb, int64_t nq, int qoff, double sb2, double inv_sw2,
+                          double* __restrict__ dsw2, double* __restrict__ dsb2) {
+  // the conv's sigma terms ride along: dsw2 += dK (K - sb2) / sw2, dsb2 += dK
+  // (sums in T over runs of at most 64 entries, added in FP64)
+  __shared__ double r1[32], r2[32];
+  double sa = 0.0, sbb = 0.0;
+  T ta = 0, tb = 0;
+  int run = 0;
+  const T tsb2 = (T)sb2;
   // one pair per blockIdx.y step: its images are found once, not per entry
   const int HW2 = HW * HW;
   for (int64_t pr = blockIdx.y; pr < np; pr += gridDim.y) {
@@ -105,7 +113,38 @@ __global__ void k_map_adj(const T* __restrict__ Kpre, T* __restrict__ d, T* __re
     }
     d[e] = dk;
     hbuf[e] = h;
+    ta += dk * (Kpre[e] - tsb2);
+    tb += dk;
+    if (++run == 64) {
+      sa += (double)ta;
+      sbb += (double)tb;
+      ta = tb = 0;
+      run = 0;
+    }
    }
+  }
+  sa += (double)ta;
+  sbb += (double)tb;
+  for (int o = 16; o > 0; o >>= 1) {
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    sbb += __shfl_xor_sync(0xffffffffu, sbb, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    r1[threadIdx.x >> 5] = sa;
+    r2[threadIdx.x >> 5] = sbb;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    sa = (threadIdx.x < (blockDim.x >> 5)) ? r1[threadIdx.x] : 0.0;
+    sbb = (threadIdx.x < (blockDim.x >> 5)) ? r2[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      sa += __shfl_xor_sync(0xffffffffu, sa, o);
+      sbb += __shfl_xor_sync(0xffffffffu, sbb, o);
+    }
+    if (threadIdx.x == 0) {
+      atomicAdd(dsw2, sa * inv_sw2);
+      atomicAdd(dsb2, sbb);
+    }
   }
 }
 
@@ -649,13 +688,15 @@ cudaError_t run_backward(const NkGeom& g, double sw2, double sb2, const float* X
       for (int k = 0; k < g.convs[s]; ++k, ++layer) {
         ++*launches;
         conv_layer<T>(cur, Kst[layer], np, H, W, g.filter, a_conv, (T)sb2, st);
-        e = cudaMemcpyAsync(nxt, Kst[layer], (size_t)np * HW * HW * sizeof(T), cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) return e;
         if (relu) {
+          // the pre-activation stays in Kst for the reverse sweep
           ++*launches;
-          k_relu<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(nxt, np, (int)HW, na, nb, sym, pair0, a0, b0, qda,
-                                                            qdb, qsa, qsb, g.nq, g.layer_qoff[layer],
+          k_relu<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(Kst[layer], nxt, np, (int)HW, na, nb, sym, pair0, a0,
+                                                            b0, qda, qdb, qsa, qsb, g.nq, g.layer_qoff[layer],
                                                             dstatus);
+        } else {
+          e = cudaMemcpyAsync(nxt, Kst[layer], (size_t)np * HW * HW * sizeof(T), cudaMemcpyDeviceToDevice, st);
+          if (e != cudaSuccess) return e;
         }
         T* t = cur; cur = nxt; nxt = t;
       }
@@ -678,15 +719,19 @@ cudaError_t run_backward(const NkGeom& g, double sw2, double sb2, const float* X
         if (relu) {
           *launches += 3;
           k_map_adj<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(Kst[layer], cur, hbuf, np, (int)HW, na, nb, sym,
-                                                               pair0, a0, b0, qda, qdb, g.nq, g.layer_qoff[layer]);
+                                                               pair0, a0, b0, qda, qdb, g.nq, g.layer_qoff[layer],
+                                                               sb2, 1.0 / sw2, dsw2, dsb2);
           k_rowsum_q<T><<<grid_for(np * HW * 32), 256, 0, st>>>(hbuf, np, (int)HW, na, nb, sym, pair0, a0, qda,
                                                                 g.nq, g.layer_qoff[layer], dqa);
           k_colsum_q<T><<<grid_for(np * HW), 256, 0, st>>>(hbuf, np, (int)HW, na, nb, sym, pair0, b0, qdb, g.nq,
                                                            g.layer_qoff[layer], dqb);
         }
-        *launches += 2;
-        k_sigma_terms<T><<<std::min(grid_for(np * HW * HW), 1024), 256, 0, st>>>(cur, Kst[layer], np * HW * HW,
-                                                                               sb2, 1.0 / sw2, dsw2, dsb2);
+        ++*launches;
+        if (!relu) {  // with a ReLU the map adjoint has added the sigma terms
+          ++*launches;
+          k_sigma_terms<T><<<std::min(grid_for(np * HW * HW), 1024), 256, 0, st>>>(cur, Kst[layer], np * HW * HW,
+                                                                                 sb2, 1.0 / sw2, dsw2, dsb2);
+        }
         conv_layer<T>(cur, nxt, np, H, W, g.filter, a_conv, (T)0, st);
         T* t = cur; cur = nxt; nxt = t;
       }

@@ -49,7 +49,7 @@ cudaError_t run_plain(const NkGeom& g, double sw2, double sb2, const float* Xa, 
         conv_layer<T>(cur, nxt, np, H, W, g.filter, a_conv, (T)sb2, st);
         T* t = cur; cur = nxt; nxt = t;
         if (g.act == NK_ACT_RELU)
-          k_relu<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(cur, np, (int)HW, na, nb, symmetric,
+          k_relu<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(cur, cur, np, (int)HW, na, nb, symmetric,
                                                             pair0, a0, b0, qda, qdb, qsa, qsb,
                                                             g.nq, g.layer_qoff[layer], dstatus);
       }

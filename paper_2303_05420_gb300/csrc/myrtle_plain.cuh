@@ -153,9 +153,10 @@ inline void conv_layer(const T* in, T* out, int64_t np, int H, int W, int filt, 
 }
 
 
-// ReLU map with self-variances of the pair's two images at this layer.
+// ReLU map with self-variances of the pair's two images at this layer,
+// K = map(Kin) (Kin may be K itself).
 template <typename T>
-__global__ void k_relu(T* __restrict__ K, int64_t npairs, int HW, int64_t na, int64_t nb,
+__global__ void k_relu(const T* Kin, T* K, int64_t npairs, int HW, int64_t na, int64_t nb,
                        int symmetric, int64_t pair0, int64_t a0, int64_t b0,
                        const double* __restrict__ qda, const double* __restrict__ qdb,
                        const float* __restrict__ qsa, const float* __restrict__ qsb, int64_t nq,
@@ -172,14 +173,14 @@ __global__ void k_relu(T* __restrict__ K, int64_t npairs, int HW, int64_t na, in
       const double q1 = qda[(a0 + i) * nq + qoff + p];
       const double q2 = qdb[(b0 + j) * nq + qoff + pp];
       if (!(q1 >= 0.0) || !(q2 >= 0.0)) atomicOr(dstatus, NK_DEV_NUMERICAL);
-      K[e] = nk_relu_map_f64(K[e], q1, q2);
+      K[e] = nk_relu_map_f64(Kin[e], q1, q2);
     } else {
       const float2 s1 = reinterpret_cast<const float2*>(qsa)[(a0 + i) * nq + qoff + p];
       const float2 s2 = reinterpret_cast<const float2*>(qsb)[(b0 + j) * nq + qoff + pp];
       const float s = s1.y * s2.y;
       float v = 0.f;
       if (s > 0.f) {
-        float c = K[e] * (s1.x * s2.x);
+        float c = Kin[e] * (s1.x * s2.x);
         c = fminf(fmaxf(c, -1.f), 1.f);
         v = s * (0.15915494309189533577f) *
             (sqrtf(fmaxf(1.f - c * c, 0.f)) + c * (NK_PI_F - acosf(c)));
