@@ -38,6 +38,9 @@ from .kernels import (  # noqa: F401
     myrtle_pair,
     myrtle_block,
     myrtle_layers_pair,
+    myrtle_ntk_pair,
+    myrtle_ntk_block,
+    relu_derivative_map,
     fc_nngp,
 )
 from .solve import cholesky_solve, pcg, pivchol_apply, pivoted_cholesky  # noqa: F401

@@ -185,6 +185,71 @@ def myrtle_layers_pair(arch: Arch, sw2, sb2, x, xp,
     return K, qs, pre
 
 
+def relu_derivative_map(K: torch.Tensor, q1: torch.Tensor, q2: torch.Tensor) -> torch.Tensor:
+    """E[relu'(u) relu'(v)] for centred Gaussians with variances q1, q2 and
+    covariance K: (pi - arccos c) / (2 pi), c = clamp(K / sqrt(q1 q2), -1, 1);
+    zero where q1 q2 = 0."""
+    s = torch.sqrt(q1 * q2)
+    pos = s > 0
+    s_safe = torch.where(pos, s, torch.ones_like(s))
+    c = torch.clamp(K / s_safe, -1.0, 1.0)
+    out = (math.pi - torch.arccos(c)) / (2.0 * math.pi)
+    return torch.where(pos, out, torch.zeros_like(out))
+
+
+def myrtle_ntk_pair(arch: Arch, sw2, sb2, x, xp, q_x: List[torch.Tensor], q_xp: List[torch.Tensor]):
+    """NNGP K and neural tangent kernel Theta of the Myrtle network on the
+    pair (x, x'), in the NTK parameterisation of the Appendix A listings
+    (stax's default: every weight and bias is a standard normal scaled in the
+    forward pass).  Differentiating the output with respect to the parameters
+    of a layer gives that layer's NNGP term, and the chain rule through a
+    ReLU multiplies by the derivative kernel, so:
+      input      Theta_0 = 0
+      conv       K' = sw2 A(Kt) + sb2,  Theta' = K' + sw2 A(Theta_t)
+                 (A the 3x3 SAME average on both pixels, divisor 9)
+      ReLU       Kt = relu_map(K),  Theta_t = Theta * E[relu' relu']
+      identity   Kt = K,  Theta_t = Theta
+      avg pool   the same linear pool on both
+      readout    K = sw2 mean Kt + sb2,  Theta = K + sw2 mean Theta_t.
+    Returns (K, Theta)."""
+    Kt = input_cov(x, xp)
+    Tt = torch.zeros_like(Kt)
+    li = 0
+    for s, n in enumerate(arch.convs):
+        if s > 0:
+            Kt = avgpool_pp(Kt)
+            Tt = avgpool_pp(Tt)
+        for _ in range(n):
+            K = conv_pp(Kt, sw2, sb2, arch.filt)
+            T = K + conv_pp(Tt, sw2, 0.0, arch.filt)
+            q1, q2 = q_x[li][:, :, None, None], q_xp[li][None, None, :, :]
+            if arch.act == "relu":
+                Kt = relu_map(K, q1, q2)
+                Tt = T * relu_derivative_map(K, q1, q2)
+            elif arch.act == "identity":
+                Kt, Tt = K, T
+            else:
+                raise ValueError(arch.act)
+            li += 1
+    Kout = sw2 * Kt.mean(dim=(-4, -3, -2, -1)) + sb2
+    Tout = Kout + sw2 * Tt.mean(dim=(-4, -3, -2, -1))
+    return Kout, Tout
+
+
+def myrtle_ntk_block(arch: Arch, sw2, sb2, Xa, Xb) -> Tuple[torch.Tensor, torch.Tensor]:
+    """(K, Theta) blocks for all pairs of Xa x Xb."""
+    Xa = torch.as_tensor(Xa, dtype=F64)
+    Xb = torch.as_tensor(Xb, dtype=F64)
+    qa = [myrtle_self_q(arch, sw2, sb2, x) for x in Xa]
+    qb = [myrtle_self_q(arch, sw2, sb2, x) for x in Xb]
+    K = torch.zeros((Xa.shape[0], Xb.shape[0]), dtype=F64)
+    T = torch.zeros_like(K)
+    for i in range(Xa.shape[0]):
+        for j in range(Xb.shape[0]):
+            K[i, j], T[i, j] = myrtle_ntk_pair(arch, sw2, sb2, Xa[i], Xb[j], qa[i], qb[j])
+    return K, T
+
+
 def myrtle_self_q(arch: Arch, sw2, sb2, x) -> List[torch.Tensor]:
     """Self-variances q_l(p) = K_l(p, p; x, x) at every activation layer,
     read off the diagonal of the FULL self tensor (no band)."""
