@@ -215,6 +215,21 @@ nk_status nk_block_fused_noalloc(const nk_arch* arch, const nk_params* prm,
                                  int H, int W, int C, float* K, int64_t ldk, int symmetric,
                                  void* stream, char* err_buf, size_t err_len);
 
+/* Neural tangent kernel block (the first widening of the hot path: the
+ * Myrtle NTK, Figure 1 computes NNGP and NTK kernels alike) together with
+ * the NNGP block, in the NTK parameterisation of the Appendix A listings
+ * (standard-normal parameters scaled in the forward pass):
+ *   Theta_0 = 0; conv: K' = sw2 A(Kt) + sb2, Theta' = K' + sw2 A(Theta_t);
+ *   ReLU: Kt = relu map of K, Theta_t = Theta (pi - arccos c) / (2 pi);
+ *   pools on both; readout K = sw2 mean Kt + sb2, Theta = K + sw2 mean Theta_t.
+ * Arguments as nk_block; K and Theta are [a1 - a0][ldk] outputs of the
+ * precision's type.  Layer-wise forms only: prec = NK_PREC_PLAIN_FP32 or
+ * NK_PREC_PLAIN_FP64 (NK_PREC_MIXED: NK_ERR_UNSUPPORTED, no fused NTK). */
+nk_status nk_block_ntk(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_prec prec,
+                       const float* Xa, const double* qda, const float* qsa, int64_t a0, int64_t a1,
+                       const float* Xb, const double* qdb, const float* qsb, int64_t b0, int64_t b1, int H,
+                       int W, int C, void* K, void* Theta, int64_t ldk, int symmetric, void* stream);
+
 /* One block of a kernel-block queue (nk_block_queue).  Images NHWC float32
  * of side H == W, self-variance pairs qs from nk_self_diag for that size,
  * output K[(i - a0) * ldk + (j - b0)] as in nk_block. */

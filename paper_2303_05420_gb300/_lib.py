@@ -25,7 +25,7 @@ PRECOND = {"none": 0, "jacobi": 1, "pivchol": 2}
 EXPORTS = ["nk_create", "nk_destroy", "nk_status_string", "nk_last_error", "nk_sync_status",
            "nk_q_size", "nk_launch_count", "nk_last_lambda", "nk_self_diag", "nk_block", "nk_block_backward", "nk_fc_block",
            "nk_autotune",
-           "nk_autotune_set", "nk_block_fused_noalloc", "nk_block_queue", "nk_pcg_set_rank", "nk_pcg_solve"]
+           "nk_autotune_set", "nk_block_fused_noalloc", "nk_block_queue", "nk_block_ntk", "nk_pcg_set_rank", "nk_pcg_solve"]
 
 
 class NkArch(ctypes.Structure):
@@ -104,6 +104,10 @@ def lib():
                                          c_int64, c_void_p, c_void_p, c_int64, c_int64, c_int, c_int,
                                          c_int, c_void_p, c_int64, c_int, c_void_p, c_char_p, c_size_t]
     L.nk_block_fused_noalloc.restype = c_int
+    L.nk_block_ntk.argtypes = [c_void_p, POINTER(NkArch), POINTER(NkParams), c_int, c_void_p, c_void_p, c_void_p,
+                               c_int64, c_int64, c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int, c_int,
+                               c_int, c_void_p, c_void_p, c_int64, c_int, c_void_p]
+    L.nk_block_ntk.restype = c_int
     L.nk_block_queue.argtypes = [c_void_p, POINTER(NkArch), POINTER(NkParams), c_int, POINTER(NkBlockTask),
                                  c_int, c_void_p]
     L.nk_block_queue.restype = c_int

@@ -123,6 +123,26 @@ class Handle:
         self.check(st, "nk_block")
         return out
 
+    def block_ntk(self, Xa: torch.Tensor, qa, Xb: torch.Tensor, qb, convs: Sequence[int], sw2: float,
+                  sb2: float, prec: str = "plain_fp32", a_range=None, b_range=None, symmetric: bool = False,
+                  filt: int = 3, act: str = "relu"):
+        """(K, Theta): NNGP and NTK blocks by the layer-wise forms (nk_block_ntk)."""
+        _, H, W, C = Xa.shape
+        a0, a1 = a_range if a_range is not None else (0, Xa.shape[0])
+        b0, b1 = b_range if b_range is not None else (0, Xb.shape[0])
+        dt = torch.float64 if prec == "plain_fp64" else torch.float32
+        K = torch.empty((a1 - a0, b1 - b0), dtype=dt, device=Xa.device)
+        T = torch.empty_like(K)
+        a = make_arch(convs, filt, act)
+        p = make_params(sw2, sb2)
+        st = lib().nk_block_ntk(self._h, byref(a), byref(p), _lib.PREC[prec],
+                                c_void_p(_ptr(Xa)), c_void_p(_ptr(qa[0])), c_void_p(_ptr(qa[1])), a0, a1,
+                                c_void_p(_ptr(Xb)), c_void_p(_ptr(qb[0])), c_void_p(_ptr(qb[1])), b0, b1,
+                                H, W, C, c_void_p(_ptr(K)), c_void_p(_ptr(T)), K.stride(0), int(symmetric),
+                                c_void_p(_stream()))
+        self.check(st, "nk_block_ntk")
+        return K, T
+
     def block_queue(self, tasks: Sequence[dict], convs: Sequence[int], sw2: float, sb2: float,
                     filt: int = 3) -> list:
         """Several MIXED kernel blocks, of image sides 8, 16 or 32, in one

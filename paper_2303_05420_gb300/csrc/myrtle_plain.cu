@@ -63,6 +63,66 @@ cudaError_t run_plain(const NkGeom& g, double sw2, double sb2, const float* Xa, 
   return cudaSuccess;
 }
 
+// Layer-wise NTK: the NNGP tensor K and the tangent tensor Theta side by side
+// (Theta_0 = 0; conv: Theta' = K' + a S(Theta_t); ReLU: Theta_t = Theta
+// E[relu' relu']; pools on both; readout Theta = K + sw2 mean Theta_t).
+template <typename T>
+cudaError_t run_plain_ntk(const NkGeom& g, double sw2, double sb2, const float* Xa, const double* qda,
+                          const float* qsa, int64_t a0, int64_t a1, const float* Xb, const double* qdb,
+                          const float* qsb, int64_t b0, int64_t b1, T* K, T* Th, int64_t ldk, int symmetric,
+                          void* ws, int64_t chunk, unsigned int* dstatus, cudaStream_t st, int64_t* launches) {
+  const int64_t na = a1 - a0, nb = b1 - b0;
+  const int64_t npairs_total = symmetric ? na * (na + 1) / 2 : na * nb;
+  const int64_t HW0 = (int64_t)g.Hs[0] * g.Ws[0];
+  T* kb0 = reinterpret_cast<T*>(ws);
+  T* kb1 = kb0 + chunk * HW0 * HW0;
+  T* tb0 = kb1 + chunk * HW0 * HW0;
+  T* tb1 = tb0 + chunk * HW0 * HW0;
+  const T a_conv = (T)(sw2 / (double)(g.filter * g.filter));
+  for (int64_t pair0 = 0; pair0 < npairs_total; pair0 += chunk) {
+    const int64_t np = (npairs_total - pair0 < chunk) ? npairs_total - pair0 : chunk;
+    T *kc = kb0, *kn = kb1, *tc = tb0, *tn = tb1;
+    *launches += 2;
+    k_input_cov<T><<<pair_grid(np, HW0 * HW0), 256, 0, st>>>(Xa, Xb, a0, b0, na, nb, symmetric, pair0, np,
+                                                             g.Hs[0], g.Ws[0], g.C, kc);
+    cudaError_t e = cudaMemsetAsync(tc, 0, (size_t)np * HW0 * HW0 * sizeof(T), st);
+    if (e != cudaSuccess) return e;
+    int layer = 0;
+    int H = g.Hs[0], W = g.Ws[0];
+    for (int s = 0; s < g.n_stages; ++s) {
+      if (s > 0) {
+        const unsigned grid = grid_for(np * (int64_t)(H / 2) * (W / 2) * (H / 2) * (W / 2));
+        *launches += 2;
+        k_pool<T><<<grid, 256, 0, st>>>(kc, kn, np, H, W);
+        k_pool<T><<<grid, 256, 0, st>>>(tc, tn, np, H, W);
+        T* t = kc; kc = kn; kn = t;
+        t = tc; tc = tn; tn = t;
+        H /= 2;
+        W /= 2;
+      }
+      const int64_t HW = (int64_t)H * W;
+      for (int k = 0; k < g.convs[s]; ++k, ++layer) {
+        *launches += 2;
+        conv_layer<T>(kc, kn, np, H, W, g.filter, a_conv, (T)sb2, st);
+        conv_layer<T>(tc, tn, np, H, W, g.filter, a_conv, (T)0, st, kn);  // + K'
+        T* t = kc; kc = kn; kn = t;
+        t = tc; tc = tn; tn = t;
+        if (g.act == NK_ACT_RELU) {
+          ++*launches;
+          k_relu_ntk<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(kc, tc, np, (int)HW, na, nb, symmetric, pair0,
+                                                                a0, b0, qda, qdb, qsa, qsb, g.nq,
+                                                                g.layer_qoff[layer], dstatus);
+        }
+      }
+    }
+    const int64_t HW = (int64_t)H * W;
+    k_gap_ntk<T><<<(unsigned)np, 256, 0, st>>>(kc, tc, HW * HW, na, nb, symmetric, pair0, sw2, sb2, K, Th, ldk);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace
 
 size_t nk_plain_ws_bytes(const NkGeom& g, int fp64, int64_t chunk) {
@@ -81,4 +141,17 @@ cudaError_t nk_launch_myrtle_plain(const NkGeom& g, int fp64, double sw2, double
                              reinterpret_cast<double*>(K), ldk, symmetric, ws, chunk, dstatus, st, launches);
   return run_plain<float>(g, sw2, sb2, Xa, qda, qsa, a0, a1, Xb, qdb, qsb, b0, b1,
                           reinterpret_cast<float*>(K), ldk, symmetric, ws, chunk, dstatus, st, launches);
+}
+
+cudaError_t nk_launch_myrtle_plain_ntk(const NkGeom& g, int fp64, double sw2, double sb2, const float* Xa,
+                                       const double* qda, const float* qsa, int64_t a0, int64_t a1,
+                                       const float* Xb, const double* qdb, const float* qsb, int64_t b0,
+                                       int64_t b1, void* K, void* Th, int64_t ldk, int symmetric, void* ws,
+                                       int64_t chunk, unsigned int* dstatus, cudaStream_t st, int64_t* launches) {
+  if (fp64)
+    return run_plain_ntk<double>(g, sw2, sb2, Xa, qda, qsa, a0, a1, Xb, qdb, qsb, b0, b1,
+                                 reinterpret_cast<double*>(K), reinterpret_cast<double*>(Th), ldk, symmetric, ws,
+                                 chunk, dstatus, st, launches);
+  return run_plain_ntk<float>(g, sw2, sb2, Xa, qda, qsa, a0, a1, Xb, qdb, qsb, b0, b1, reinterpret_cast<float*>(K),
+                              reinterpret_cast<float*>(Th), ldk, symmetric, ws, chunk, dstatus, st, launches);
 }

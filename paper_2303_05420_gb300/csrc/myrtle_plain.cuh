@@ -51,7 +51,7 @@ __global__ void k_input_cov(const float* __restrict__ Xa, const float* __restric
 
 template <typename T>
 __global__ void k_conv(const T* __restrict__ in, T* __restrict__ out, int64_t npairs, int H, int W,
-                       int filt, T a, T b) {
+                       int filt, T a, T b, const T* __restrict__ addend) {
   // one pair per blockIdx.y step, 32-bit index arithmetic inside a pair
   const int HW = H * W;
   const int HW2 = HW * HW;
@@ -71,7 +71,7 @@ __global__ void k_conv(const T* __restrict__ in, T* __restrict__ out, int64_t np
           if (j2 >= 0 && j2 < W && l2 >= 0 && l2 < W) acc += src[(i2 * W + j2) * HW + k2 * W + l2];
         }
       }
-      dst[rem] = a * acc + b;
+      dst[rem] = a * acc + b + (addend ? addend[pr * (int64_t)HW2 + rem] : (T)0);
     }
   }
 }
@@ -95,7 +95,7 @@ inline dim3 pair_grid(int64_t npairs, int64_t HW2) {
 // each output once.  smem: 3 W^2 elements of T.
 template <typename T>
 __global__ void __launch_bounds__(256) k_conv_diag(const T* __restrict__ in, T* __restrict__ out, int64_t npairs,
-                                                   int H, int W, T a, T b) {
+                                                   int H, int W, T a, T b, const T* __restrict__ addend) {
   extern __shared__ __align__(16) unsigned char conv_sm[];
   T* sh = reinterpret_cast<T*>(conv_sm);
   const int HW = H * W, W2 = W * W;
@@ -131,24 +131,27 @@ __global__ void __launch_bounds__(256) k_conv_diag(const T* __restrict__ in, T* 
         if (i > i0) acc += prv[e];
         if (i < i1) acc += nxt[e];
         const int j = e / W, l = e - j * W;
-        dst[(int64_t)(i * W + j) * HW + k * W + l] = a * acc + b;
+        const int64_t o = (int64_t)(i * W + j) * HW + k * W + l;
+        dst[o] = a * acc + b + (addend ? addend[pr * (int64_t)HW * HW + o] : (T)0);
       }
       __syncthreads();  // slot (i + 2) % 3 is refilled next
     }
   }
 }
 
-// One 3x3 (or other odd) SAME conv layer on a chunk of pair tensors.
+// One 3x3 (or other odd) SAME conv layer on a chunk of pair tensors:
+// out = a S(in) + b (+ addend, a tensor of the same shape, when not null).
 template <typename T>
-inline void conv_layer(const T* in, T* out, int64_t np, int H, int W, int filt, T a, T b, cudaStream_t st) {
+inline void conv_layer(const T* in, T* out, int64_t np, int H, int W, int filt, T a, T b, cudaStream_t st,
+                       const T* addend = nullptr) {
   const size_t smem = (size_t)3 * W * W * sizeof(T);
   if (filt == 3 && smem <= 200 * 1024) {
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(k_conv_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int64_t y = np < 65535 ? np : 65535;
-    k_conv_diag<T><<<dim3((unsigned)(2 * H - 1), (unsigned)y), 256, smem, st>>>(in, out, np, H, W, a, b);
+    k_conv_diag<T><<<dim3((unsigned)(2 * H - 1), (unsigned)y), 256, smem, st>>>(in, out, np, H, W, a, b, addend);
   } else {
-    k_conv<T><<<pair_grid(np, (int64_t)H * W * H * W), 256, 0, st>>>(in, out, np, H, W, filt, a, b);
+    k_conv<T><<<pair_grid(np, (int64_t)H * W * H * W), 256, 0, st>>>(in, out, np, H, W, filt, a, b, addend);
   }
 }
 
@@ -240,6 +243,97 @@ inline int grid_for(int64_t total) {
   if (g > 152 * 64) g = 152 * 64;
   if (g < 1) g = 1;
   return (int)g;
+}
+
+// NTK ReLU step (NTK parameterisation): Kt = map(K) in place and
+// Theta_t = Theta * E[relu' relu'] = Theta (pi - arccos c) / (2 pi).
+template <typename T>
+__global__ void k_relu_ntk(T* K, T* Th, int64_t npairs, int HW, int64_t na, int64_t nb, int symmetric,
+                           int64_t pair0, int64_t a0, int64_t b0, const double* __restrict__ qda,
+                           const double* __restrict__ qdb, const float* __restrict__ qsa,
+                           const float* __restrict__ qsb, int64_t nq, int qoff, unsigned int* dstatus) {
+  const int HW2 = HW * HW;
+  for (int64_t pr = blockIdx.y; pr < npairs; pr += gridDim.y) {
+    int64_t i, j;
+    pair_of(pair0 + pr, na, nb, symmetric, &i, &j);
+    for (int rem = blockIdx.x * blockDim.x + threadIdx.x; rem < HW2; rem += gridDim.x * blockDim.x) {
+      const int64_t e = pr * (int64_t)HW2 + rem;
+      const int p = rem / HW, pp = rem - p * HW;
+      if constexpr (sizeof(T) == 8) {
+        const double q1 = qda[(a0 + i) * nq + qoff + p];
+        const double q2 = qdb[(b0 + j) * nq + qoff + pp];
+        if (!(q1 >= 0.0) || !(q2 >= 0.0)) atomicOr(dstatus, NK_DEV_NUMERICAL);
+        const double s = sqrt(q1 * q2);
+        double kd = 0.0, kt = 0.0;
+        if (s > 0.0) {
+          double c = K[e] / s;
+          c = c < -1.0 ? -1.0 : (c > 1.0 ? 1.0 : c);
+          const double th = acos(c);
+          kt = s * NK_INV_2PI_D * (sqrt(fmax(1.0 - c * c, 0.0)) + c * (NK_PI_D - th));
+          kd = (NK_PI_D - th) * NK_INV_2PI_D;
+        }
+        K[e] = kt;
+        Th[e] *= kd;
+      } else {
+        const float2 s1 = reinterpret_cast<const float2*>(qsa)[(a0 + i) * nq + qoff + p];
+        const float2 s2 = reinterpret_cast<const float2*>(qsb)[(b0 + j) * nq + qoff + pp];
+        const float s = s1.y * s2.y;
+        float kt = 0.f, kd = 0.f;
+        if (s > 0.f) {
+          float c = K[e] * (s1.x * s2.x);
+          c = fminf(fmaxf(c, -1.f), 1.f);
+          const float th = acosf(c);
+          kt = s * 0.15915494309189533577f * (sqrtf(fmaxf(1.f - c * c, 0.f)) + c * (NK_PI_F - th));
+          kd = (NK_PI_F - th) * 0.15915494309189533577f;
+        }
+        K[e] = kt;
+        Th[e] *= kd;
+      }
+    }
+  }
+}
+
+// NTK readout: K = sw2 mean(Kt) + sb2, Theta = K + sw2 mean(Theta_t).
+template <typename T>
+__global__ void k_gap_ntk(const T* __restrict__ Kt, const T* __restrict__ Tt, int64_t HW2, int64_t na, int64_t nb,
+                          int symmetric, int64_t pair0, double sw2, double sb2, T* __restrict__ K,
+                          T* __restrict__ Th, int64_t ldk) {
+  __shared__ double r1[32], r2[32];
+  const int64_t pr = blockIdx.x;
+  double a = 0.0, b = 0.0;
+  for (int64_t e = threadIdx.x; e < HW2; e += blockDim.x) {
+    a += (double)Kt[pr * HW2 + e];
+    b += (double)Tt[pr * HW2 + e];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    r1[threadIdx.x >> 5] = a;
+    r2[threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    a = (threadIdx.x < (blockDim.x >> 5)) ? r1[threadIdx.x] : 0.0;
+    b = (threadIdx.x < (blockDim.x >> 5)) ? r2[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (threadIdx.x == 0) {
+      int64_t i, j;
+      pair_of(pair0 + pr, na, nb, symmetric, &i, &j);
+      const double kv = sw2 * (a / (double)HW2) + sb2;
+      const double tv = kv + sw2 * (b / (double)HW2);
+      K[i * ldk + j] = (T)kv;
+      Th[i * ldk + j] = (T)tv;
+      if (symmetric && i != j) {
+        K[j * ldk + i] = (T)kv;
+        Th[j * ldk + i] = (T)tv;
+      }
+    }
+  }
 }
 
 }  // namespace nkp

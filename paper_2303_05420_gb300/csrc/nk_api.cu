@@ -293,6 +293,49 @@ nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_p
   return nk_cuda_check(h, e, "nk_block plain launch");
 }
 
+nk_status nk_block_ntk(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_prec prec,
+                       const float* Xa, const double* qda, const float* qsa, int64_t a0, int64_t a1,
+                       const float* Xb, const double* qdb, const float* qsb, int64_t b0, int64_t b1, int H,
+                       int W, int C, void* K, void* Theta, int64_t ldk, int symmetric, void* stream) {
+  if (!h) return NK_ERR_INVALID_ARG;
+  NkGeom g;
+  const char* why = nullptr;
+  if (!nk_make_geom(arch, H, W, C, &g, &why)) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: %s", why);
+  if (!prm) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: params is NULL");
+  if (!(prm->sigma_w2 >= 0.0) || !(prm->sigma_b2 >= 0.0))
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: negative variance");
+  if (prec == NK_PREC_MIXED)
+    return nk_fail(h, NK_ERR_UNSUPPORTED, "nk_block_ntk: the NTK has the layer-wise forms only (PLAIN_FP32/FP64)");
+  if (prec != NK_PREC_PLAIN_FP64 && prec != NK_PREC_PLAIN_FP32)
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: unknown precision");
+  if (a0 < 0 || b0 < 0 || a1 < a0 || b1 < b0)
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: bad index range");
+  if (a1 == a0 || b1 == b0) return NK_OK;
+  if (!Xa || !Xb || !K || !Theta) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: NULL image or output");
+  if (ldk < b1 - b0) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: ldk < b1 - b0");
+  if (symmetric && (Xa != Xb || a0 != b0 || a1 != b1))
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: symmetric needs Xa == Xb and equal ranges");
+  const bool needq = (g.act == NK_ACT_RELU);
+  if (needq && prec == NK_PREC_PLAIN_FP64 && (!qda || !qdb))
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: PLAIN_FP64 needs qda and qdb");
+  if (needq && prec == NK_PREC_PLAIN_FP32 && (!qsa || !qsb))
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: PLAIN_FP32 needs qsa and qsb");
+  const int fp64 = (prec == NK_PREC_PLAIN_FP64);
+  const int64_t na = a1 - a0, nb = b1 - b0;
+  const int64_t npairs = symmetric ? na * (na + 1) / 2 : na * nb;
+  const size_t per_pair = 2 * nk_plain_ws_bytes(g, fp64, 1);
+  const size_t budget = (size_t)1 << 30;
+  int64_t chunk = (int64_t)std::max<size_t>(1, budget / per_pair);
+  chunk = std::min<int64_t>(chunk, npairs);
+  void* ws = nullptr;
+  nk_status s = nk_workspace(h, per_pair * chunk, &ws);
+  if (s != NK_OK) return s;
+  cudaError_t e = nk_launch_myrtle_plain_ntk(g, fp64, prm->sigma_w2, prm->sigma_b2, Xa, qda, qsa, a0, a1, Xb, qdb,
+                                             qsb, b0, b1, K, Theta, ldk, symmetric, ws, chunk, h->dstatus,
+                                             (cudaStream_t)stream, &h->launches);
+  return nk_cuda_check(h, e, "nk_block_ntk launch");
+}
+
 nk_status nk_block_queue(nk_handle* h, const nk_arch* arch, const nk_params* prm, int C,
                          const nk_block_task* tasks, int n_tasks, void* stream) {
   if (!h) return NK_ERR_INVALID_ARG;

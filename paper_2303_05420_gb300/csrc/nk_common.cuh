@@ -67,6 +67,13 @@ cudaError_t nk_launch_self_diag(const NkGeom& g, double sw2, double sb2, const f
                                 unsigned int* dstatus, cudaStream_t st);
 size_t nk_self_diag_ws_per_cta(const NkGeom& g);
 
+// Layer-wise Myrtle NTK block (K and Theta); workspace 2 * nk_plain_ws_bytes.
+cudaError_t nk_launch_myrtle_plain_ntk(const NkGeom& g, int fp64, double sw2, double sb2, const float* Xa,
+                                       const double* qda, const float* qsa, int64_t a0, int64_t a1,
+                                       const float* Xb, const double* qdb, const float* qsb, int64_t b0,
+                                       int64_t b1, void* K, void* Th, int64_t ldk, int symmetric, void* ws,
+                                       int64_t chunk, unsigned int* dstatus, cudaStream_t st, int64_t* launches);
+
 // Fused (MIXED) Myrtle block.  Returns cudaErrorNotSupported when the
 // architecture / size has no fused instantiation.
 cudaError_t nk_launch_myrtle_fused(const NkGeom& g, double sw2, double sb2, const float* Xa,
