@@ -345,6 +345,17 @@ def run_ours(args, rank, world, dist):
         extra["maxrel_plain_fp32_vs_plain_fp64"] = float(((res["plain_fp32"][1][:16, :16] - k16).abs()
                                                           / k16.abs()).max())
         extra["plain_tiles"] = f"{tile}x{tile} (fp32, mixed), 16x16 (fp64) train pairs"
+        # NTK (layer-wise FP32) on the same tile
+        h.block_ntk(X, q, X, q, CONVS, SW2, SB2, prec="plain_fp32", a_range=(0, tile), b_range=(tile, 2 * tile))
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        Kn, Tn = h.block_ntk(X, q, X, q, CONVS, SW2, SB2, prec="plain_fp32", a_range=(0, tile),
+                             b_range=(tile, 2 * tile))
+        b.record(stream)
+        torch.cuda.synchronize()
+        extra["ntk_plain_fp32_entries_per_s"] = tile * tile / (a.elapsed_time(b) / 1e3)
+        extra["ntk_over_nngp_mean"] = float((Tn.double() / Kn.double()).mean())
         # PCG: mixed vs plain FP64 on the same train block, with the Jacobi
         # preconditioner of the configuration and with the paper's pivoted
         # Cholesky one (rank 100)
