@@ -624,8 +624,26 @@ def fc_leg(h, dev, peaks, n=FC_N_TRAIN, m=FC_N_TEST):
                                     "frac": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
                                     "note": "K bytes per CG iteration / whole-solve time (includes the "
                                             "FP64 true residuals of the refinement)"}
-    del Ktr, Kte
+    # out of core: the same 10 GB kernel in pinned host memory, read by the
+    # matvec over the chip-to-chip link
+    del Kte
+    Kh = torch.empty(Ktr.shape, dtype=torch.float32).pin_memory()
+    Kh.copy_(Ktr)
+    del Ktr
     torch.cuda.empty_cache()
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    a.record(stream)
+    _, its, rel = h.pcg_solve(Kh, Y, -REL_LAMBDA, precond="jacobi", prec="mixed", tol=1e-6, maxit=5000, A=A,
+                              allow_not_converged=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    out["fc3_pcg_hostK_mixed_iters"] = its
+    out["fc3_pcg_hostK_mixed_ms"] = ms
+    out["fc3_pcg_hostK_mixed_relres"] = max(rel)
+    out["fc3_pcg_hostK_GBs"] = its * n * n * 4 / (ms / 1e3) / 1e9
+    del Kh
     return out
 
 

@@ -273,7 +273,10 @@ nk_status nk_pcg_set_rank(nk_handle* h, int rank);
  *   the rank (nk_pcg_set_rank) largest-remaining-diagonal pivots, built on
  *   the device in FP64 for each call; M = L^T L + lambda I applied through
  *   the Woodbury identity).
- *   K [N][ldk] float32 (device, symmetric), Y [N][R] float64 (device, row
+ *   K [N][ldk] float32 (symmetric; device memory, or pinned host memory the
+ *   device reads directly (cudaHostAlloc / cudaHostRegister; on a Grace
+ *   system over the chip-to-chip link): the solve is then out of core, for
+ *   kernels larger than HBM), Y [N][R] float64 (device, row
  *   major), A [N][R] float64 (device, out).
  *   prec = NK_PREC_MIXED: iterative refinement: the true residual
  *          Y - (K + lambda I) A is formed with FP64 products and sums, the

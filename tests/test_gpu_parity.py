@@ -323,3 +323,22 @@ def test_pcg_rejects_bad_arguments(h):
 
     with pytest.raises(NkError):
         h.pcg_set_rank(0)
+
+
+def test_pcg_out_of_core_host_K(h):
+    """K in pinned host memory, read by the kernels directly (out of core):
+    the same solution as with K in HBM, for the Jacobi and pivoted Cholesky
+    preconditioners."""
+    n = 1536
+    rng = np.random.default_rng(8)
+    B = rng.standard_normal((n, n + 32)).astype(np.float32)
+    Kh = (B @ B.T / n).astype(np.float32)
+    Kdev = torch.tensor(Kh, device="cuda")
+    Khost = torch.tensor(Kh).pin_memory()
+    Y = torch.tensor(rng.standard_normal((n, 4)), device="cuda")
+    for pc in ["jacobi", "pivchol"]:
+        Ad, itd, reld = h.pcg_solve(Kdev, Y, -1e-3, precond=pc, prec="mixed", tol=1e-8, maxit=5000)
+        Ah, ith, relh = h.pcg_solve(Khost, Y, -1e-3, precond=pc, prec="mixed", tol=1e-8, maxit=5000)
+        assert max(relh) <= 1e-8
+        assert abs(ith - itd) <= 2
+        assert torch.allclose(Ah, Ad, rtol=1e-7, atol=1e-9 * float(Ad.abs().max()))
