@@ -355,6 +355,21 @@ def run_ours(args, rank, world, dist):
         b.record(stream)
         torch.cuda.synchronize()
         extra["ntk_plain_fp32_entries_per_s"] = tile * tile / (a.elapsed_time(b) / 1e3)
+        # the 64x64 problem of the mixed-resolution workload (no fused kernel at
+        # 64x64): the layer-wise FP32 form on a 16 x 16 sample of pairs
+        x64 = nkdata.standardise(nkdata.images(32, 64, 3, nkdata.SEED_TRAIN, blur=True))[0]
+        X64 = torch.tensor(x64.astype(np.float32), device=dev)
+        q64 = h.self_diag(X64, CONVS, SW2, SB2)
+        h.block(X64, q64, X64, q64, CONVS, SW2, SB2, prec="plain_fp32", a_range=(0, 2), b_range=(16, 18))
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        h.block(X64, q64, X64, q64, CONVS, SW2, SB2, prec="plain_fp32", a_range=(0, 16), b_range=(16, 32))
+        b.record(stream)
+        torch.cuda.synchronize()
+        r64 = 256 / (a.elapsed_time(b) / 1e3)
+        extra["plain_fp32_64x64_entries_per_s"] = r64
+        extra["config5_64x64_block_s_extrapolated"] = (512 * 513 // 2 + 128 * 512) / r64
         extra["ntk_over_nngp_mean"] = float((Tn.double() / Kn.double()).mean())
         # PCG: mixed vs plain FP64 on the same train block, with the Jacobi
         # preconditioner of the configuration and with the paper's pivoted

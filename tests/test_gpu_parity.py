@@ -328,17 +328,32 @@ def test_pcg_rejects_bad_arguments(h):
 def test_pcg_out_of_core_host_K(h):
     """K in pinned host memory, read by the kernels directly (out of core):
     the same solution as with K in HBM, for the Jacobi and pivoted Cholesky
-    preconditioners."""
+    preconditioners.  The CG inner products accumulate with FP64 atomics, so
+    two solves round differently; each stops at relative residual <= tol, so
+    each lies within cond(K + lam I) * tol of the exact FP64 solution (per
+    column, relative), and the two within twice that of each other."""
     n = 1536
+    tol = 1e-8
     rng = np.random.default_rng(8)
     B = rng.standard_normal((n, n + 32)).astype(np.float32)
     Kh = (B @ B.T / n).astype(np.float32)
     Kdev = torch.tensor(Kh, device="cuda")
     Khost = torch.tensor(Kh).pin_memory()
-    Y = torch.tensor(rng.standard_normal((n, 4)), device="cuda")
+    Yh = rng.standard_normal((n, 4))
+    Y = torch.tensor(Yh, device="cuda")
+    K64 = Kh.astype(np.float64)
+    lam = 1e-3 * np.trace(K64) / n
+    w = np.linalg.eigvalsh(K64)
+    kappa = (w.max() + lam) / (w.min() + lam)
+    Astar = np.linalg.solve(K64 + lam * np.eye(n), Yh)
+    colrel = lambda A, Bm: np.linalg.norm(A - Bm, axis=0) / np.linalg.norm(Bm, axis=0)  # noqa: E731
     for pc in ["jacobi", "pivchol"]:
-        Ad, itd, reld = h.pcg_solve(Kdev, Y, -1e-3, precond=pc, prec="mixed", tol=1e-8, maxit=5000)
-        Ah, ith, relh = h.pcg_solve(Khost, Y, -1e-3, precond=pc, prec="mixed", tol=1e-8, maxit=5000)
-        assert max(relh) <= 1e-8
-        assert abs(ith - itd) <= 2
-        assert torch.allclose(Ah, Ad, rtol=1e-7, atol=1e-9 * float(Ad.abs().max()))
+        Ad, itd, reld = h.pcg_solve(Kdev, Y, -1e-3, precond=pc, prec="mixed", tol=tol, maxit=5000)
+        Ah, ith, relh = h.pcg_solve(Khost, Y, -1e-3, precond=pc, prec="mixed", tol=tol, maxit=5000)
+        assert max(relh) <= tol and max(reld) <= tol
+        # the rounding order also moves the refinement restarts by a few iterations
+        assert abs(ith - itd) <= max(2, 0.02 * itd)
+        Ad, Ah = Ad.cpu().numpy(), Ah.cpu().numpy()
+        assert colrel(Ah, Astar).max() <= kappa * tol
+        assert colrel(Ad, Astar).max() <= kappa * tol
+        assert colrel(Ah, Ad).max() <= 2 * kappa * tol
