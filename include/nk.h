@@ -125,9 +125,15 @@ nk_status nk_self_diag(nk_handle* h, const nk_arch* arch, const nk_params* prm,
  *   symmetric   nonzero when Xa == Xb and [a0,a1) == [b0,b1): only i <= j is
  *               evaluated and mirrored.
  * The Myrtle readout is K = sigma_w2 * mean_{P,P'} Kt(P, P') + sigma_b2
- * (GlobalAvgPool then Dense).  MIXED requires filter 3, ReLU, H = W in
- * {8, 16, 32}, C <= 3 and zero-conv stages only at the end; other valid
- * requests there return NK_ERR_UNSUPPORTED. */
+ * (GlobalAvgPool then Dense).  MIXED requires filter 3, ReLU, C <= 3 and
+ * zero-conv stages only at the end, with H = W in {8, 16, 32} and stage
+ * patterns (2,1,0) (2,1,1) (3,3,3) (1) (1,1,1), or H = W = 64 and (2,1,0) (1)
+ * (1,1); other valid requests there return NK_ERR_UNSUPPORTED.  At 64x64
+ * MIXED runs the tiled form: stage-0 tasks over row bands and groups of
+ * super-plane shifts, the pooled stage-1 tensor of each pair (4 MB) in a
+ * ring of slots in the handle's workspace (about 100 MB, allocated on first
+ * use), one stage-1 task per pair; device-side waits are bounded and report
+ * NK_ERR_TIMEOUT through nk_sync_status. */
 nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_prec prec,
                    const float* Xa, const double* qda, const float* qsa, int64_t a0, int64_t a1,
                    const float* Xb, const double* qdb, const float* qsb, int64_t b0, int64_t b1,
@@ -252,12 +258,15 @@ typedef struct {
  * independently and batched to fill the device), possibly of different image
  * sizes, in ONE persistent launch of the fused MIXED kernel.  Every block uses
  * the same architecture, parameters and channel count C; image sides 8, 16
- * or 32 (other sizes: NK_ERR_UNSUPPORTED).  A 32x32 pair is computed by a
- * 4-CTA cluster, a 16x16 or 8x8 pair by one CTA; larger images are queued
- * first.  Stream-ordered and asynchronous; allocates nothing, so it may be
- * captured in a CUDA graph (the handle's 64 KB scratch holds the
- * global-average slots: calls on one handle must be stream-ordered).
- * n_tasks in 0..NK_QUEUE_MAX; tasks is a host array. */
+ * or 32, or 64 and 32 (other mixes: NK_ERR_UNSUPPORTED).  Without 64x64
+ * blocks a 32x32 pair is computed by a 4-CTA cluster, a 16x16 or 8x8 pair by
+ * one CTA, and the launch allocates nothing (the handle's 64 KB scratch holds
+ * the global-average slots).  With 64x64 blocks every pair runs in the tiled
+ * form of nk_block (stage patterns (2,1,0) (1) (1,1)); its slot ring lives in
+ * the handle's workspace, which grows on the first such call, so make one
+ * call before capturing the queue in a CUDA graph.  Larger images are queued
+ * first.  Stream-ordered and asynchronous; calls on one handle must be
+ * stream-ordered.  n_tasks in 0..NK_QUEUE_MAX; tasks is a host array. */
 nk_status nk_block_queue(nk_handle* h, const nk_arch* arch, const nk_params* prm, int C,
                          const nk_block_task* tasks, int n_tasks, void* stream);
 

@@ -145,8 +145,8 @@ class Handle:
 
     def block_queue(self, tasks: Sequence[dict], convs: Sequence[int], sw2: float, sb2: float,
                     filt: int = 3) -> list:
-        """Several MIXED kernel blocks, of image sides 8, 16 or 32, in one
-        persistent launch (nk_block_queue).  Each task is a dict with keys
+        """Several MIXED kernel blocks, of image sides 8, 16 or 32, or 64 and
+        32 (the tiled form), in one persistent launch (nk_block_queue).  Each task is a dict with keys
         Xa, qa, Xb, qb (self_diag outputs), optional a_range, b_range,
         symmetric, out.  Returns the output tensors in task order."""
         if len(tasks) > _lib.NK_QUEUE_MAX:

@@ -6,7 +6,7 @@ bool nk_myrtle_fused_supported(const NkGeom& g) {
   if (g.filter != 3 || g.act != NK_ACT_RELU || g.C < 1 || g.C > 3) return false;
   if (g.Hs[0] != g.Ws[0]) return false;
   const int R0 = g.Hs[0];
-  if (R0 != 8 && R0 != 16 && R0 != 32) return false;
+  if (R0 != 8 && R0 != 16 && R0 != 32 && R0 != 64) return false;
   int c[3] = {0, 0, 0};
   for (int s = 0; s < g.n_stages; ++s) {
     if (s >= 3) {
@@ -15,6 +15,7 @@ bool nk_myrtle_fused_supported(const NkGeom& g) {
     }
     c[s] = g.convs[s];
   }
+  if (R0 == 64) return nkf::tiled_supported(c);
   const bool ok = (c[0] == 2 && c[1] == 1 && c[2] == 0) || (c[0] == 2 && c[1] == 1 && c[2] == 1) ||
                   (c[0] == 3 && c[1] == 3 && c[2] == 3) || (c[0] == 1 && c[1] == 0 && c[2] == 0) ||
                   (c[0] == 1 && c[1] == 1 && c[2] == 1);

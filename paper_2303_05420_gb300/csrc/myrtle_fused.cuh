@@ -887,6 +887,13 @@ cudaError_t dispatch_r16(const int c[3], bool bias, int variant, FusedParams& P,
 cudaError_t dispatch_r8(const int c[3], bool bias, int variant, FusedParams& P, int sm_count,
                         void* scratch, size_t scratch_bytes, cudaStream_t st);
 
+// Tiled form (myrtle_tiled.cu): 64x64 blocks, and queues mixing 64x64 and
+// 32x32 blocks (R[b] in {64, 32}, largest first) in one persistent launch.
+bool tiled_supported(const int c[3]);
+size_t tiled_ws_bytes(const int c[3], const int* R, const int64_t* npairs, int n, int sm_count);
+cudaError_t launch_tiled(const int c[3], bool bias, const int* R, const FusedParams* B, int n, int sm_count,
+                         void* ws, size_t ws_bytes, unsigned int* dstatus, cudaStream_t st);
+
 }  // namespace nkf
 
 // Kernel parameters of one block (myrtle_fused.cu).

@@ -69,6 +69,12 @@ extern "C" nk_status nk_block_fused_noalloc(const nk_arch* arch, const nk_params
             "nk_block_fused_noalloc: no fused kernel for this architecture / size (see nk_block)");
     return NK_ERR_UNSUPPORTED;
   }
+  if (g.Hs[0] == 64) {
+    // the 64x64 (tiled) form keeps its pooled stage-1 tensors in a ring of
+    // global slots of tens of MB: it needs nk_block and its workspace
+    set_err(err_buf, err_len, "nk_block_fused_noalloc: 64x64 images need nk_block (slot workspace)");
+    return NK_ERR_UNSUPPORTED;
+  }
   int dev = 0, sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);

@@ -267,8 +267,24 @@ nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_p
   if (prec == NK_PREC_MIXED) {
     if (!nk_myrtle_fused_supported(g))
       return nk_fail(h, NK_ERR_UNSUPPORTED,
-                     "nk_block MIXED: needs filter 3, ReLU, H == W in {8,16,32}, C <= 3 and one of "
-                     "the stage patterns (2,1,0) (2,1,1) (3,3,3) (1) (1,1,1)");
+                     "nk_block MIXED: needs filter 3, ReLU, C <= 3 and H == W in {8,16,32} with one of "
+                     "the stage patterns (2,1,0) (2,1,1) (3,3,3) (1) (1,1,1), or H == W == 64 with "
+                     "(2,1,0) (1) (1,1)");
+    if (g.Hs[0] == 64) {
+      const int c[3] = {g.convs[0], g.n_stages > 1 ? g.convs[1] : 0, g.n_stages > 2 ? g.convs[2] : 0};
+      nkf::FusedParams P = nk_fused_params(g, prm->sigma_w2, prm->sigma_b2, Xa, qsa, a0, a1, Xb, qsb, b0, b1,
+                                           (float*)K, ldk, symmetric);
+      const int R[1] = {64};
+      const int64_t np[1] = {P.npairs};
+      void* ws = nullptr;
+      const size_t need = nkf::tiled_ws_bytes(c, R, np, 1, h->sm_count);
+      nk_status s = nk_workspace(h, need, &ws);
+      if (s != NK_OK) return s;
+      h->launches += 1;
+      cudaError_t e = nkf::launch_tiled(c, prm->sigma_b2 != 0.0, R, &P, 1, h->sm_count, ws, h->ws_bytes,
+                                        h->dstatus, st);
+      return nk_cuda_check(h, e, "nk_block tiled launch");
+    }
     int key[8];
     tune_key(g, prm->sigma_b2 != 0.0, key);
     h->launches += 1;
@@ -369,8 +385,9 @@ nk_status nk_block_queue(nk_handle* h, const nk_arch* arch, const nk_params* prm
                      t);
     if (!nk_myrtle_fused_supported(g))
       return nk_fail(h, NK_ERR_UNSUPPORTED,
-                     "nk_block_queue task %d: needs filter 3, ReLU, H == W in {8,16,32}, C <= 3 and one of "
-                     "the stage patterns (2,1,0) (2,1,1) (3,3,3) (1) (1,1,1)", t);
+                     "nk_block_queue task %d: needs filter 3, ReLU, C <= 3 and H == W in {8,16,32} with one "
+                     "of the stage patterns (2,1,0) (2,1,1) (3,3,3) (1) (1,1,1), or 64 with (2,1,0) (1) (1,1)",
+                     t);
     c[0] = g.convs[0];
     c[1] = g.n_stages > 1 ? g.convs[1] : 0;
     c[2] = g.n_stages > 2 ? g.convs[2] : 0;
@@ -382,6 +399,30 @@ nk_status nk_block_queue(nk_handle* h, const nk_arch* arch, const nk_params* prm
   if (n == 0) return NK_OK;
   // largest images first (their items are the longest)
   std::stable_sort(items, items + n, [](const Item& x, const Item& y) { return x.R > y.R; });
+  if (items[0].R == 64) {
+    // 64x64 blocks: the tiled form, which also takes the 32x32 blocks
+    int R[NK_QUEUE_MAX];
+    int64_t np[NK_QUEUE_MAX];
+    nkf::FusedParams B[NK_QUEUE_MAX];
+    for (int b = 0; b < n; ++b) {
+      if (items[b].R != 64 && items[b].R != 32)
+        return nk_fail(h, NK_ERR_UNSUPPORTED,
+                       "nk_block_queue: a queue with 64x64 blocks takes 64x64 and 32x32 blocks only");
+      R[b] = items[b].R;
+      np[b] = items[b].P.npairs;
+      B[b] = items[b].P;
+    }
+    if (!nkf::tiled_supported(c))
+      return nk_fail(h, NK_ERR_UNSUPPORTED,
+                     "nk_block_queue: a queue with 64x64 blocks needs the stage pattern (2,1,0) (1) or (1,1)");
+    void* ws = nullptr;
+    nk_status s = nk_workspace(h, nkf::tiled_ws_bytes(c, R, np, n, h->sm_count), &ws);
+    if (s != NK_OK) return s;
+    h->launches += 1;
+    cudaError_t e = nkf::launch_tiled(c, prm->sigma_b2 != 0.0, R, B, n, h->sm_count, ws, h->ws_bytes, h->dstatus,
+                                      (cudaStream_t)stream);
+    return nk_cuda_check(h, e, "nk_block_queue tiled launch");
+  }
   nkf::QueueParams Q = {};
   Q.n = n;
   Q.item0[0] = 0;

@@ -103,12 +103,13 @@ def test_queue_in_cuda_graph(h):
 def test_queue_rejects(h):
     from paper_2303_05420_gb300._lib import NK_ERR_INVALID_ARG, NK_ERR_UNSUPPORTED, NkError
 
-    convs = (2, 1, 0)
+    # 64x64 images have the tiled form for (2,1,0) (test_gpu_tiled), not for (2,1,1)
     x64 = torch.zeros((2, 64, 64, 3), device="cuda")
-    q64 = h.self_diag(x64 + 1.0, convs, 2.0, 0.0)
+    q64 = h.self_diag(x64 + 1.0, (2, 1, 1), 2.0, 0.0)
     with pytest.raises(NkError) as ei:
-        h.block_queue([dict(Xa=x64, qa=q64, Xb=x64, qb=q64)], convs, 2.0, 0.0)
+        h.block_queue([dict(Xa=x64, qa=q64, Xb=x64, qb=q64)], (2, 1, 1), 2.0, 0.0)
     assert ei.value.status == NK_ERR_UNSUPPORTED
+    convs = (2, 1, 0)
     sets, X, q, tasks = _tasks(h, convs, 0.0)
     with pytest.raises(NkError) as ei:
         h.block_queue(tasks * 2, convs, 2.0, 0.0)
@@ -122,9 +123,9 @@ def test_queue_rejects(h):
 
 
 def test_64x64_plain_path_matches_oracle(h):
-    """64x64 images (the larger problem of the mixed-resolution workload) have
-    no fused kernel; the layer-wise FP32 form computes them, here one row of
-    a 2 x 3 block against the oracle pair by pair."""
+    """64x64 images (the larger problem of the mixed-resolution workload) in
+    the layer-wise FP32 form, here one row of a 2 x 3 block against the oracle
+    pair by pair (the tiled fused form is checked against this form)."""
     convs = (2, 1, 0)
     x = nkdata.standardise(nkdata.images(3, 64, 3, 5, blur=True))[0].astype(np.float32)
     X = torch.tensor(x, device="cuda")
