@@ -42,6 +42,8 @@ REL_LAMBDA = 1e-4
 CONFIGS = {
     "headline": dict(n_train=2048, n_test=512, hw=32, n_classes=10),
     "small": dict(n_train=64, n_test=16, hw=32, n_classes=10),
+    # a small 64x64 case (profiling the tiled form on a short launch)
+    "small64": dict(n_train=16, n_test=8, hw=64, n_classes=10),
 }
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
@@ -311,7 +313,8 @@ def run_ours(args, rank, world, dist):
     # ---- kernel-only roofline of the fused Myrtle kernel
     ops_entry = algorithmic_ops_per_entry(hw)
     blk_s = statistics.mean(blk_ms) / 1e3
-    # the block interval also holds nothing else: two fused launches
+    # the block interval holds the two fused launches (for the tiled form each
+    # after its workspace clear, about 50 MB here)
     achieved_tops = ops_entry * entries / blk_s / 1e12
     peak_clock = clocks.get("sm_max_mhz") or 2070.0
     peak_tops = SM_COUNT * FP32_LANES_PER_SM * peak_clock * 1e6 / 1e12
@@ -355,8 +358,8 @@ def run_ours(args, rank, world, dist):
         b.record(stream)
         torch.cuda.synchronize()
         extra["ntk_plain_fp32_entries_per_s"] = tile * tile / (a.elapsed_time(b) / 1e3)
-        # the 64x64 problem of the mixed-resolution workload (no fused kernel at
-        # 64x64): the layer-wise FP32 form on a 16 x 16 sample of pairs
+        # the 64x64 problem of the mixed-resolution workload in the layer-wise
+        # FP32 form, on a 16 x 16 sample of pairs (the fused form: queue leg)
         x64 = nkdata.standardise(nkdata.images(32, 64, 3, nkdata.SEED_TRAIN, blur=True))[0]
         X64 = torch.tensor(x64.astype(np.float32), device=dev)
         q64 = h.self_diag(X64, CONVS, SW2, SB2)
@@ -369,7 +372,7 @@ def run_ours(args, rank, world, dist):
         torch.cuda.synchronize()
         r64 = 256 / (a.elapsed_time(b) / 1e3)
         extra["plain_fp32_64x64_entries_per_s"] = r64
-        extra["config5_64x64_block_s_extrapolated"] = (512 * 513 // 2 + 128 * 512) / r64
+        extra["plain_fp32_64x64_blocks_s_extrapolated"] = (512 * 513 // 2 + 128 * 512) / r64
         extra["ntk_over_nngp_mean"] = float((Tn.double() / Kn.double()).mean())
         # PCG: mixed vs plain FP64 on the same train block, with the Jacobi
         # preconditioner of the configuration and with the paper's pivoted
@@ -425,7 +428,7 @@ def run_ours(args, rank, world, dist):
         "fused_variant": variant,
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "TFLOP/s",
                      "frac": achieved_tops / peak_tops, "traffic": None,
-                     "kernel": "k_myrtle_fused",
+                     "kernel": "k_myrtle_tiled" if variant == 3 else "k_myrtle_fused",
                      "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                     f"{peak_clock:.0f} MHz (FP32 ops/s)",
                      "ops_per_entry": ops_entry},
@@ -494,58 +497,55 @@ def grad_leg(h, dev):
 
 
 def queue_leg(h, dev):
-    """Mixed-resolution block queue (the 64x64 + 32x32 workload's structure
-    one octave down, the sizes the fused kernel covers): 512 train + 128 test
-    32x32 images (blur generator) and their 2x2-average 16x16 companions,
-    Myrtle-5 (2,1,0), sigma_w^2 = 2, sigma_b^2 = 0, 200 classes.  The four
-    blocks (train upper triangle and test block at each resolution) run as
-    one persistent launch captured in a CUDA graph; timed by replaying the
-    graph, beside the same blocks as four separate nk_block launches.  Then
-    the 200-right-hand-side MIXED PCG solve of the 32x32 train block."""
+    """The mixed-resolution workload at full size: 512 train + 128 test 64x64
+    images (blur generator) and their 2x2-average 32x32 companions, Myrtle-5
+    (2,1,0), sigma_w^2 = 2, sigma_b^2 = 0, 200 classes.  The four blocks
+    (train upper triangle and test block at each resolution) run as ONE
+    persistent launch of the tiled form, timed once directly (its first call
+    also sizes the slot workspace) and once as a replay of a CUDA graph
+    holding it; then the 200-right-hand-side MIXED PCG solve of the 64x64
+    train block."""
     import numpy as np
     import torch
 
     import nkdata
 
     n_tr, n_te = 512, 128
-    prob = nkdata.image_problem(n_tr, n_te, 32, n_classes=200, blur=True)
-    x32 = np.concatenate([prob.x_train, prob.x_test]).astype(np.float32)
-    x16 = nkdata.downsample2(np.concatenate([prob.x_train, prob.x_test])).astype(np.float32)
+    prob = nkdata.image_problem(n_tr, n_te, 64, n_classes=200, blur=True)
+    x64 = np.concatenate([prob.x_train, prob.x_test]).astype(np.float32)
+    x32 = nkdata.downsample2(np.concatenate([prob.x_train, prob.x_test])).astype(np.float32)
+    X64 = torch.tensor(x64, device=dev)
     X32 = torch.tensor(x32, device=dev)
-    X16 = torch.tensor(x16, device=dev)
+    q64 = h.self_diag(X64, CONVS, SW2, SB2)
     q32 = h.self_diag(X32, CONVS, SW2, SB2)
-    q16 = h.self_diag(X16, CONVS, SW2, SB2)
     tasks = []
-    for X, q in ((X32, q32), (X16, q16)):
+    for X, q in ((X64, q64), (X32, q32)):
         tasks.append(dict(Xa=X, qa=q, Xb=X, qb=q, a_range=(0, n_tr), b_range=(0, n_tr), symmetric=True,
                           out=torch.empty((n_tr, n_tr), dtype=torch.float32, device=dev)))
         tasks.append(dict(Xa=X, qa=q, Xb=X, qb=q, a_range=(n_tr, n_tr + n_te), b_range=(0, n_tr),
                           out=torch.empty((n_te, n_tr), dtype=torch.float32, device=dev)))
-    entries = 2 * (n_tr * (n_tr + 1) // 2 + n_te * n_tr)
-    h.block_queue(tasks, CONVS, SW2, SB2)
+    per_res = n_tr * (n_tr + 1) // 2 + n_te * n_tr
+    entries = 2 * per_res
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     torch.cuda.synchronize()
+    a, b = ev(), ev()
+    a.record(stream)
+    h.block_queue(tasks, CONVS, SW2, SB2)
+    b.record(stream)
+    torch.cuda.synchronize()
+    h.sync_status()
+    t_direct = a.elapsed_time(b) / 1e3
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, capture_error_mode="relaxed"):
         h.block_queue(tasks, CONVS, SW2, SB2)
-    stream = torch.cuda.current_stream()
-    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-    g.replay()
-    torch.cuda.synchronize()
     a, b = ev(), ev()
     a.record(stream)
     g.replay()
     b.record(stream)
     torch.cuda.synchronize()
-    t_queue = a.elapsed_time(b) / 1e3
-    a, b = ev(), ev()
-    a.record(stream)
-    for t in tasks:
-        h.block(t["Xa"], t["qa"], t["Xb"], t["qb"], CONVS, SW2, SB2, prec="mixed", a_range=t["a_range"],
-                b_range=t["b_range"], symmetric=t.get("symmetric", False), out=t["out"])
-    b.record(stream)
-    torch.cuda.synchronize()
-    t_sep = a.elapsed_time(b) / 1e3
     h.sync_status()
+    t_graph = a.elapsed_time(b) / 1e3
     Y = torch.tensor(prob.y_train, device=dev)
     a, b = ev(), ev()
     a.record(stream)
@@ -553,9 +553,11 @@ def queue_leg(h, dev):
                               maxit=20000, allow_not_converged=True)
     b.record(stream)
     torch.cuda.synchronize()
-    return {"queue_workload": "myrtle5_(2,1,0)_32x32+16x16_train512_test128_200cls_one_launch_graph",
-            "queue_entries": entries, "queue_graph_ms": 1e3 * t_queue,
-            "queue_entries_per_s": entries / t_queue, "queue_separate_launches_ms": 1e3 * t_sep,
+    # equivalent 32x32 work: a 64x64 entry is 16 times a 32x32 entry
+    return {"queue_workload": "myrtle5_(2,1,0)_64x64+32x32_train512_test128_200cls_one_launch_tiled",
+            "queue_entries": entries, "queue_direct_ms": 1e3 * t_direct, "queue_graph_ms": 1e3 * t_graph,
+            "queue_entries_per_s": entries / t_graph,
+            "queue_32x32_equivalent_entries_per_s": 17 * per_res / t_graph,
             "queue_pcg200_iters": its, "queue_pcg200_ms": a.elapsed_time(b),
             "queue_pcg200_relres": max(rel)}
 

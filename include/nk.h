@@ -185,9 +185,12 @@ nk_status nk_block_backward(nk_handle* h, const nk_arch* arch, const nk_params* 
  * architecture, image size, channel count and sigma_b2 == 0 or not, on a
  * synthetic 12 x 12 block of hashed images (allocated and freed here), and
  * caches the fastest in the handle; later nk_block calls with the same key
- * use it (without a tuned entry, variant 0).  Variants at 32x32: 0 = 768
- * threads x 8 row parts, 1 = 512 x 8, 2 = 512 x 4; other sizes have one.
- * *variant (may be NULL) receives the choice.  Synchronises `stream`. */
+ * use it.  Variants at 32x32: 0 = super-plane cluster kernel, 768 threads x
+ * 8 row parts, 1 = 512 x 8, 2 = 512 x 4, 3 = the tiled form of the 64x64
+ * blocks (stage patterns (2,1,0) (1) (1,1) only; it needs the handle's
+ * workspace, which grows on first use); other sizes have one.  Without a
+ * tuned entry nk_block uses variant 3 where it exists, else 0.  *variant
+ * (may be NULL) receives the choice.  Synchronises `stream`. */
 nk_status nk_autotune(nk_handle* h, const nk_arch* arch, const nk_params* prm, int H, int W, int C,
                       int* variant, void* stream);
 

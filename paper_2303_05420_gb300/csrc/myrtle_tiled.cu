@@ -26,11 +26,14 @@
 //    the last layer reduced into the global average and K written.
 //
 // Scheduling: one persistent CTA per SM pulls items from a global counter.
-// Pair g contributes its stage-0 tasks and, D pairs later in the item order,
-// the stage-1 task of pair g - D, which waits until pair g - D's stage-0
-// counter is full; a stage-0 task of pair g waits until the stage-1 task of
-// pair g - S (the slot's previous user, earlier in the order since S > D)
-// has cleared the slot.  Every wait is on an item claimed earlier, so the
+// The items are the stage-0 tasks of every pair, block by block, with the
+// stage-1 task of pair k merged in LAG stage-0 items (about two waves of the
+// grid) after the last stage-0 task of k, so that it rarely waits for them.
+// The 64x64 and the 32x32 pairs each own a ring of S_R slots; a stage-0 task
+// of pair g waits until the slot's previous user, pair g - S_R, has been
+// cleared by its stage-1 task, which S_R >= LAG / (tasks per pair) + 1 puts
+// earlier in the order (S_R = 2 LAG / (tasks per pair) + 2 puts it a LAG
+// earlier, so that it is normally done).  Every wait is on an item claimed earlier, so the
 // earliest unfinished item never waits and the queue drains.  Waits are
 // bounded: on a timeout the kernel raises NK_DEV_TIMEOUT and an abort flag
 // that makes every CTA stop taking items.
@@ -92,13 +95,17 @@ struct TiledParams {
   int R[QUEUE_MAX];               // image side of each block (64 or 32)
   int nt0[QUEUE_MAX];             // stage-0 tasks per pair of each block
   int64_t g0[QUEUE_MAX + 1];      // first pair index of each block
-  int64_t it0[QUEUE_MAX + 1];     // first item of each block
+  int64_t f0[QUEUE_MAX + 1];      // first stage-0 task index of each block
   FusedParams B[QUEUE_MAX];
   int64_t G;                      // pairs
-  int64_t nitems;                 // items (it0[n] + D)
-  int D, S;                       // stage-1 delay (pairs), slots
-  int64_t slot_floats;
-  float* slots;                   // [S][slot_floats]
+  int64_t G64;                    // pairs of 64x64 blocks (they come first)
+  int64_t T0;                     // stage-0 tasks
+  int64_t nitems;                 // T0 + G (stage 1 of two-stage nets) or T0
+  int64_t LAG;                    // stage-0 tasks between a pair's last one and its stage-1 task
+  int S[2];                       // slot rings of the 64x64 and the 32x32 pairs
+  int64_t ring_off[2];            // first float of each ring
+  int64_t slot_floats[2];         // (R / 2)^4
+  float* slots;
   int* cnt0;                      // [G] finished stage-0 tasks
   int* done1;                     // [G] stage 1 finished (slot cleared)
   double* gacc;                   // [G] global-average sums (single-stage nets)
@@ -375,11 +382,51 @@ __device__ __forceinline__ float4 ld_x(const float* p, int C, float s) {
   return make_float4(p[0] * s, C > 1 ? p[1] * s : 0.f, C > 2 ? p[2] * s : 0.f, 0.f);
 }
 
-// Locates pair g: block, and (i, j) within it.
+// Block of pair g.
 __device__ __forceinline__ int block_of(const TiledParams& Q, int64_t g) {
   int b = 0;
   while (b + 1 < Q.n && g >= Q.g0[b + 1]) ++b;
   return b;
+}
+
+// Slot of pair g (block b) in its resolution's ring, and the pair that used
+// it before (-1: none).
+__device__ __forceinline__ float* slot_of(const TiledParams& Q, int b, int64_t g, int64_t* prev) {
+  const int r = Q.R[b] == 64 ? 0 : 1;
+  const int64_t ord = r == 0 ? g : g - Q.G64;
+  *prev = ord >= Q.S[r] ? g - Q.S[r] : -1;
+  return Q.slots + Q.ring_off[r] + (ord % Q.S[r]) * Q.slot_floats[r];
+}
+
+// Position of pair k's stage-1 task in the item order: after stage-0 task
+// (last of k) + LAG, and after the k stage-1 tasks before it.
+__device__ __forceinline__ int64_t stage1_pos(const TiledParams& Q, int64_t k) {
+  const int b = block_of(Q, k);
+  int64_t x = Q.f0[b] + (k - Q.g0[b] + 1) * Q.nt0[b] + Q.LAG;
+  if (x > Q.T0) x = Q.T0;
+  return x + k;
+}
+
+// Item m -> stage-1 task of pair *k (returns 1) or stage-0 task index *k (0).
+__device__ int decode_item(const TiledParams& Q, bool two, int64_t m, int64_t* k) {
+  if (!two) {
+    *k = m;
+    return 0;
+  }
+  int64_t lo = 0, hi = Q.G;  // number of stage-1 tasks at positions <= m
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) / 2;
+    if (stage1_pos(Q, mid) <= m)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  if (lo > 0 && stage1_pos(Q, lo - 1) == m) {
+    *k = lo - 1;
+    return 1;
+  }
+  *k = m - lo;
+  return 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -402,12 +449,13 @@ __device__ void stage0_task(const TiledParams& Q, int b, int64_t g, int sub, uns
   const int s0 = b0 - N0 > 0 ? b0 - N0 : 0;
   const int s1 = b0 + G::B + N0 < R ? b0 + G::B + N0 : R;
   const int ty0 = yg * G::TY, tx0 = xg * G::TX;
-  float* slot = TWO ? Q.slots + (g % Q.S) * Q.slot_floats : nullptr;
+  int64_t prev = -1;
+  float* slot = TWO ? slot_of(Q, b, g, &prev) : nullptr;
 
   // the slot's previous pair must have been taken by its stage-1 task
   if (threadIdx.x == 0) {
     bool ok = true;
-    if (TWO && g >= Q.S) ok = wait_geq(Q, Q.done1 + (g - Q.S), 1);
+    if (TWO && prev >= 0) ok = wait_geq(Q, Q.done1 + prev, 1);
     *flag = ok ? 1 : 0;
   }
   float4* xs = reinterpret_cast<float4*>(smem + L::xs_off);
@@ -473,9 +521,9 @@ __device__ void stage0_task(const TiledParams& Q, int b, int64_t g, int sub, uns
     T.run(gap);
   }
   if constexpr (TWO) {
-    // publish this task's atomic adds, then count it (release by thread 0
-    // after the barrier, so that it covers every thread's adds)
-    __threadfence();
+    // publish this task's atomic adds, then count it: the barrier orders
+    // every thread's adds before thread 0's fence, which releases them
+    // together with the count
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
@@ -512,7 +560,8 @@ __device__ void stage1_task(const TiledParams& Q, int64_t g, unsigned char* smem
   int64_t i, j;
   pair_ij(g - Q.g0[b], P.na, P.nb, P.sym, &i, &j);
   const int64_t ia = P.a0 + i, ib = P.b0 + j;
-  float* slot = Q.slots + (g % Q.S) * Q.slot_floats;
+  int64_t prev = -1;
+  float* slot = slot_of(Q, b, g, &prev);
   if (threadIdx.x == 0) *flag = wait_geq(Q, Q.cnt0 + g, Q.nt0[b]) ? 1 : 0;
   float2* pt = reinterpret_cast<float2*>(smem + L::p_off);
   float2* qt = reinterpret_cast<float2*>(smem + L::q_off);
@@ -565,8 +614,8 @@ __device__ void stage1_task(const TiledParams& Q, int64_t g, unsigned char* smem
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) gap += __shfl_xor_sync(FULL, gap, o);
   if (lane == 0) red[warp] = gap;
-  // the cleared slot is published before the flag that frees it
-  __threadfence();
+  // the cleared slot is published before the flag that frees it (barrier,
+  // then thread 0's fence)
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
@@ -589,52 +638,85 @@ template <int N0, int N1, bool BIAS>
 __global__ void __launch_bounds__(THREADS, 1) k_myrtle_tiled(const __grid_constant__ TiledParams Q) {
   extern __shared__ __align__(16) unsigned char smem[];
   using SM = Smem<N0, N1>;
+  constexpr bool TWO = N1 > 0;
   double* red = reinterpret_cast<double*>(smem + SM::tables);
   int* flag = reinterpret_cast<int*>(smem + SM::tables + 16 * 8);
   long long* item_s = reinterpret_cast<long long*>(smem + SM::tables + 16 * 8 + 8);
-  const int64_t ibody = Q.it0[Q.n];
   for (;;) {
-    if (threadIdx.x == 0)
-      *item_s = *(volatile int*)Q.abort_flag ? (long long)Q.nitems : (long long)atomicAdd(Q.next, 1ull);
-    __syncthreads();
-    const int64_t item = *item_s;
-    __syncthreads();
-    if (item >= Q.nitems) break;
-    int64_t g1 = -1;
-    if (item < ibody) {
-      int b = 0;
-      while (b + 1 < Q.n && item >= Q.it0[b + 1]) ++b;
-      const int per = Q.nt0[b] + 1;
-      const int64_t k = item - Q.it0[b];
-      const int64_t g = Q.g0[b] + k / per;
-      const int sub = (int)(k % per);
-      if (sub < Q.nt0[b]) {
-        if (Q.R[b] == 64)
-          stage0_task<64, N0, N1, BIAS>(Q, b, g, sub, smem, red, flag);
-        else
-          stage0_task<32, N0, N1, BIAS>(Q, b, g, sub, smem, red, flag);
-      } else {
-        g1 = g - Q.D;
+    if (threadIdx.x == 0) {
+      const long long m =
+          *(volatile int*)Q.abort_flag ? (long long)Q.nitems : (long long)atomicAdd(Q.next, 1ull);
+      long long code = -1;  // stage-0 index k -> 2k; stage-1 pair k -> 2k + 1; -1 done
+      if (m < Q.nitems) {
+        int64_t k;
+        const int st1 = decode_item(Q, TWO, m, &k);
+        code = 2 * k + st1;
       }
-    } else {
-      g1 = Q.G - Q.D + (item - ibody);
+      *item_s = code;
     }
-    if constexpr (N1 > 0) {
-      if (g1 >= 0 && g1 < Q.G) {
-        if (Q.R[block_of(Q, g1)] == 64)
-          stage1_task<32, N0, N1, BIAS>(Q, g1, smem, red, flag);
-        else
-          stage1_task<16, N0, N1, BIAS>(Q, g1, smem, red, flag);
-      }
+    __syncthreads();
+    const long long code = *item_s;
+    __syncthreads();
+    if (code < 0) break;
+    const int64_t k = code >> 1;
+    if ((code & 1) == 0) {
+      int b = 0;
+      while (b + 1 < Q.n && k >= Q.f0[b + 1]) ++b;
+      const int64_t g = Q.g0[b] + (k - Q.f0[b]) / Q.nt0[b];
+      const int sub = (int)((k - Q.f0[b]) % Q.nt0[b]);
+      if (Q.R[b] == 64)
+        stage0_task<64, N0, N1, BIAS>(Q, b, g, sub, smem, red, flag);
+      else
+        stage0_task<32, N0, N1, BIAS>(Q, b, g, sub, smem, red, flag);
+    } else if constexpr (TWO) {
+      if (Q.R[block_of(Q, k)] == 64)
+        stage1_task<32, N0, N1, BIAS>(Q, k, smem, red, flag);
+      else
+        stage1_task<16, N0, N1, BIAS>(Q, k, smem, red, flag);
     }
     // the next item's staging overwrites the tables
     __syncthreads();
   }
 }
 
+// Host plan of a launch: item lag, slot rings and workspace layout.
+struct Plan {
+  int64_t LAG;
+  int S[2];
+  int64_t slot_floats[2], ring_off[2];
+  size_t slot_bytes, bytes;
+};
+
+inline Plan make_plan(bool two, const int* R, const int64_t* npairs, int n, int grid) {
+  Plan p = {};
+  p.LAG = 2 * (int64_t)grid;
+  int64_t G = 0;
+  bool has[2] = {false, false};
+  for (int b = 0; b < n; ++b) {
+    has[R[b] == 64 ? 0 : 1] = true;
+    G += npairs[b];
+  }
+  const int nt[2] = {G0<64>::NT0, G0<32>::NT0};
+  const int side[2] = {64, 32};
+  int64_t off = 0;
+  for (int r = 0; r < 2; ++r) {
+    const int64_t R1 = side[r] / 2;
+    // order alone needs S >= LAG / nt + 1; one more LAG of items between the
+    // slot's previous stage-1 task and its next user lets that task finish
+    // before it is waited for
+    p.S[r] = (two && has[r]) ? (int)((2 * p.LAG + nt[r] - 1) / nt[r]) + 2 : 1;
+    p.slot_floats[r] = (two && has[r]) ? R1 * R1 * R1 * R1 : 0;
+    p.ring_off[r] = off;
+    off += p.S[r] * p.slot_floats[r];
+  }
+  p.slot_bytes = (size_t)off * sizeof(float);
+  p.bytes = p.slot_bytes + (size_t)G * (2 * sizeof(int) + sizeof(double)) + 64;
+  return p;
+}
+
 template <int N0, int N1, bool BIAS>
-cudaError_t launch_t(TiledParams& Q, int sm_count, void* ws, size_t ws_bytes, cudaStream_t st,
-                     size_t* need_out) {
+cudaError_t launch_t(TiledParams& Q, const int64_t* npairs, int sm_count, void* ws, size_t ws_bytes,
+                     cudaStream_t st) {
   using SM = Smem<N0, N1>;
   auto kern = k_myrtle_tiled<N0, N1, BIAS>;
   static bool attr_set[64] = {false};
@@ -651,30 +733,25 @@ cudaError_t launch_t(TiledParams& Q, int sm_count, void* ws, size_t ws_bytes, cu
     attr_set[dev] = true;
   }
   const int grid = std::max(1, sm_count * per_sm[dev]);
-  // stage-1 delay and slot ring, in pairs: a stage-1 item comes about two
-  // waves of items after its pair's stage-0 items, and a slot is reused
-  // about two waves after its stage-1 item
-  int per_min = 1 << 30;
-  for (int b = 0; b < Q.n; ++b) per_min = std::min(per_min, Q.nt0[b] + 1);
-  Q.D = (N1 > 0) ? (2 * grid + per_min - 1) / per_min + 1 : 0;
-  Q.S = (N1 > 0) ? 2 * Q.D + 2 : 1;
-  Q.nitems = Q.it0[Q.n] + Q.D;
-  int R1max = 0;
-  for (int b = 0; b < Q.n; ++b) R1max = std::max(R1max, Q.R[b] / 2);
-  Q.slot_floats = (N1 > 0) ? (int64_t)R1max * R1max * R1max * R1max : 0;
-  const size_t slot_bytes = (size_t)Q.S * Q.slot_floats * sizeof(float);
+  constexpr bool TWO = N1 > 0;
+  const Plan p = make_plan(TWO, Q.R, npairs, Q.n, grid);
+  if (p.bytes > ws_bytes) return cudaErrorInvalidValue;
+  Q.LAG = p.LAG;
+  Q.nitems = Q.T0 + (TWO ? Q.G : 0);
   const size_t G = (size_t)Q.G;
-  const size_t need = slot_bytes + G * (2 * sizeof(int) + sizeof(double)) + 64;
-  *need_out = need;
-  if (need > ws_bytes) return cudaErrorInvalidValue;
-  char* p = reinterpret_cast<char*>(ws);
-  Q.slots = reinterpret_cast<float*>(p);
-  Q.gacc = reinterpret_cast<double*>(p + slot_bytes);
-  Q.cnt0 = reinterpret_cast<int*>(p + slot_bytes + G * sizeof(double));
+  char* c = reinterpret_cast<char*>(ws);
+  for (int r = 0; r < 2; ++r) {
+    Q.S[r] = p.S[r];
+    Q.slot_floats[r] = p.slot_floats[r];
+    Q.ring_off[r] = p.ring_off[r];
+  }
+  Q.slots = reinterpret_cast<float*>(c);
+  Q.gacc = reinterpret_cast<double*>(c + p.slot_bytes);
+  Q.cnt0 = reinterpret_cast<int*>(c + p.slot_bytes + G * sizeof(double));
   Q.done1 = Q.cnt0 + G;
-  Q.next = reinterpret_cast<unsigned long long*>(p + slot_bytes + G * (2 * sizeof(int) + sizeof(double)));
+  Q.next = reinterpret_cast<unsigned long long*>(c + p.slot_bytes + G * (2 * sizeof(int) + sizeof(double)));
   Q.abort_flag = reinterpret_cast<int*>(Q.next + 1);
-  cudaError_t e = cudaMemsetAsync(ws, 0, need, st);
+  cudaError_t e = cudaMemsetAsync(ws, 0, p.bytes, st);
   if (e != cudaSuccess) return e;
   kern<<<grid, THREADS, SM::bytes, st>>>(Q);
   return cudaGetLastError();
@@ -692,42 +769,35 @@ bool tiled_supported(const int c[3]) {
 size_t tiled_ws_bytes(const int c[3], const int* R, const int64_t* npairs, int n, int sm_count) {
   // an upper bound of what launch_tiled asks for (it runs one CTA per SM;
   // two are assumed here)
-  const int grid = 2 * sm_count;
-  int per_min = 1 << 30, R1max = 0;
-  int64_t G = 0;
-  for (int b = 0; b < n; ++b) {
-    per_min = std::min(per_min, (R[b] == 64 ? tiled::G0<64>::NT0 : tiled::G0<32>::NT0) + 1);
-    R1max = std::max(R1max, R[b] / 2);
-    G += npairs[b];
-  }
-  const int D = (c[1] > 0) ? (2 * grid + per_min - 1) / per_min + 1 : 0;
-  const int S = (c[1] > 0) ? 2 * D + 2 : 1;
-  const int64_t slot = (c[1] > 0) ? (int64_t)R1max * R1max * R1max * R1max : 0;
-  return (size_t)S * slot * 4 + (size_t)G * 16 + 64;
+  return tiled::make_plan(c[1] > 0, R, npairs, n, 2 * sm_count).bytes;
 }
 
 cudaError_t launch_tiled(const int c[3], bool bias, const int* R, const FusedParams* B, int n, int sm_count,
                          void* ws, size_t ws_bytes, unsigned int* dstatus, cudaStream_t st) {
   if (n < 1 || n > QUEUE_MAX || !tiled_supported(c)) return cudaErrorNotSupported;
   tiled::TiledParams Q = {};
+  int64_t np[QUEUE_MAX];
   Q.n = n;
   Q.g0[0] = 0;
-  Q.it0[0] = 0;
+  Q.f0[0] = 0;
   for (int b = 0; b < n; ++b) {
     if (R[b] != 64 && R[b] != 32) return cudaErrorNotSupported;
+    if (b > 0 && R[b] > R[b - 1]) return cudaErrorInvalidValue;  // 64x64 blocks first
     Q.R[b] = R[b];
     Q.nt0[b] = R[b] == 64 ? tiled::G0<64>::NT0 : tiled::G0<32>::NT0;
     Q.B[b] = B[b];
+    np[b] = B[b].npairs;
     Q.g0[b + 1] = Q.g0[b] + B[b].npairs;
-    Q.it0[b + 1] = Q.it0[b] + B[b].npairs * (Q.nt0[b] + 1);
+    Q.f0[b + 1] = Q.f0[b] + B[b].npairs * Q.nt0[b];
+    if (R[b] == 64) Q.G64 = Q.g0[b + 1];
   }
   Q.G = Q.g0[n];
+  Q.T0 = Q.f0[n];
   Q.dstatus = dstatus;
-  size_t need = 0;
 #define NK_T(a, b_)                                                                                   \
   if (c[0] == a && c[1] == b_)                                                                        \
-    return bias ? tiled::launch_t<a, b_, true>(Q, sm_count, ws, ws_bytes, st, &need)                  \
-                : tiled::launch_t<a, b_, false>(Q, sm_count, ws, ws_bytes, st, &need);
+    return bias ? tiled::launch_t<a, b_, true>(Q, np, sm_count, ws, ws_bytes, st)                     \
+                : tiled::launch_t<a, b_, false>(Q, np, sm_count, ws, ws_bytes, st);
   NK_T(2, 1) NK_T(1, 0) NK_T(1, 1)
 #undef NK_T
   return cudaErrorNotSupported;

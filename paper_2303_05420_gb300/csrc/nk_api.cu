@@ -104,10 +104,59 @@ void tune_key(const NkGeom& g, bool bias, int* key) {
   key[7] = bias ? 1 : 0;
 }
 
-int tune_lookup(const nk_handle* h, const int* key) {
+int tune_lookup(const nk_handle* h, const int* key, int fallback) {
   for (int i = 0; i < h->tune_n; ++i)
     if (memcmp(h->tune_key[i], key, sizeof(int) * 8) == 0) return h->tune_variant[i];
-  return 0;
+  return fallback;
+}
+
+// Stage pattern (first three stages) of a geometry.
+void stage_pattern(const NkGeom& g, int* c) {
+  c[0] = g.convs[0];
+  c[1] = g.n_stages > 1 ? g.convs[1] : 0;
+  c[2] = g.n_stages > 2 ? g.convs[2] : 0;
+}
+
+// Launch variants of the fused form at this size: at 32x32 the three
+// super-plane cluster launches, plus the tiled form (variant 3) where the
+// stage pattern has one; one variant elsewhere.
+bool fused_variant_valid(const NkGeom& g, int v) {
+  if (g.Hs[0] != 32) return v == 0;
+  if (v < 0 || v >= NK_FUSED_VARIANTS) return false;
+  int c[3];
+  stage_pattern(g, c);
+  return v < NK_TILED_VARIANT || nkf::tiled_supported(c);
+}
+
+// Default variant without a tuned entry: the tiled form where it exists
+// (measured faster than the cluster launches at 32x32), else variant 0.
+int fused_default_variant(const NkGeom& g) {
+  return fused_variant_valid(g, NK_TILED_VARIANT) ? NK_TILED_VARIANT : 0;
+}
+
+// One fused (MIXED) block: the tiled form at 64x64 and for variant 3, the
+// super-plane cluster kernel otherwise.
+nk_status fused_block(nk_handle* h, const NkGeom& g, const nk_params* prm, const float* Xa, const float* qsa,
+                      int64_t a0, int64_t a1, const float* Xb, const float* qsb, int64_t b0, int64_t b1, float* K,
+                      int64_t ldk, int symmetric, int variant, cudaStream_t st, const char* what) {
+  if (g.Hs[0] == 64 || variant == NK_TILED_VARIANT) {
+    int c[3];
+    stage_pattern(g, c);
+    nkf::FusedParams P = nk_fused_params(g, prm->sigma_w2, prm->sigma_b2, Xa, qsa, a0, a1, Xb, qsb, b0, b1, K,
+                                         ldk, symmetric);
+    const int R[1] = {g.Hs[0]};
+    const int64_t np[1] = {P.npairs};
+    void* ws = nullptr;
+    nk_status s = nk_workspace(h, nkf::tiled_ws_bytes(c, R, np, 1, h->sm_count), &ws);
+    if (s != NK_OK) return s;
+    h->launches += 1;
+    return nk_cuda_check(h, nkf::launch_tiled(c, prm->sigma_b2 != 0.0, R, &P, 1, h->sm_count, ws, h->ws_bytes,
+                                              h->dstatus, st), what);
+  }
+  h->launches += 1;
+  return nk_cuda_check(h, nk_launch_myrtle_fused(g, prm->sigma_w2, prm->sigma_b2, Xa, qsa, a0, a1, Xb, qsb, b0,
+                                                 b1, K, ldk, symmetric, h->sm_count, h->small_ws, 65536,
+                                                 variant, st), what);
 }
 
 void tune_store(nk_handle* h, const int* key, int v) {
@@ -270,28 +319,10 @@ nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_p
                      "nk_block MIXED: needs filter 3, ReLU, C <= 3 and H == W in {8,16,32} with one of "
                      "the stage patterns (2,1,0) (2,1,1) (3,3,3) (1) (1,1,1), or H == W == 64 with "
                      "(2,1,0) (1) (1,1)");
-    if (g.Hs[0] == 64) {
-      const int c[3] = {g.convs[0], g.n_stages > 1 ? g.convs[1] : 0, g.n_stages > 2 ? g.convs[2] : 0};
-      nkf::FusedParams P = nk_fused_params(g, prm->sigma_w2, prm->sigma_b2, Xa, qsa, a0, a1, Xb, qsb, b0, b1,
-                                           (float*)K, ldk, symmetric);
-      const int R[1] = {64};
-      const int64_t np[1] = {P.npairs};
-      void* ws = nullptr;
-      const size_t need = nkf::tiled_ws_bytes(c, R, np, 1, h->sm_count);
-      nk_status s = nk_workspace(h, need, &ws);
-      if (s != NK_OK) return s;
-      h->launches += 1;
-      cudaError_t e = nkf::launch_tiled(c, prm->sigma_b2 != 0.0, R, &P, 1, h->sm_count, ws, h->ws_bytes,
-                                        h->dstatus, st);
-      return nk_cuda_check(h, e, "nk_block tiled launch");
-    }
     int key[8];
     tune_key(g, prm->sigma_b2 != 0.0, key);
-    h->launches += 1;
-    cudaError_t e = nk_launch_myrtle_fused(g, prm->sigma_w2, prm->sigma_b2, Xa, qsa, a0, a1, Xb, qsb, b0,
-                                           b1, (float*)K, ldk, symmetric, h->sm_count, h->small_ws, 65536,
-                                           tune_lookup(h, key), st);
-    return nk_cuda_check(h, e, "nk_block fused launch");
+    return fused_block(h, g, prm, Xa, qsa, a0, a1, Xb, qsb, b0, b1, (float*)K, ldk, symmetric,
+                       tune_lookup(h, key, fused_default_variant(g)), st, "nk_block fused launch");
   }
   const int fp64 = (prec == NK_PREC_PLAIN_FP64);
   const int64_t na = a1 - a0, nb = b1 - b0;
@@ -517,8 +548,9 @@ nk_status nk_autotune(nk_handle* h, const nk_arch* arch, const nk_params* prm, i
   tune_key(g, prm->sigma_b2 != 0.0, key);
   const int nvar = (g.Hs[0] == 32) ? NK_FUSED_VARIANTS : 1;
   if (nvar == 1) {
-    tune_store(h, key, 0);
-    if (variant) *variant = 0;
+    const int v = fused_default_variant(g);
+    tune_store(h, key, v);
+    if (variant) *variant = v;
     return NK_OK;
   }
   cudaStream_t st = (cudaStream_t)stream;
@@ -549,13 +581,13 @@ nk_status nk_autotune(nk_handle* h, const nk_arch* arch, const nk_params* prm, i
   }
   float best_ms = 1e30f;
   for (int v = 0; v < nvar && e == cudaSuccess && ret == NK_OK; ++v) {
+    if (!fused_variant_valid(g, v)) continue;
     float ms_min = 1e30f;
-    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+    for (int rep = 0; rep < 4 && e == cudaSuccess && ret == NK_OK; ++rep) {
       e = cudaEventRecord(e0, st);
-      ++h->launches;
       if (e == cudaSuccess)
-        e = nk_launch_myrtle_fused(g, prm->sigma_w2, prm->sigma_b2, X, qs, 0, na, X, qs, na, n, K, nb, 0,
-                                   h->sm_count, h->small_ws, 65536, v, st);
+        ret = fused_block(h, g, prm, X, qs, 0, na, X, qs, na, n, K, nb, 0, v, st, "nk_autotune");
+      if (ret != NK_OK) break;
       if (e == cudaSuccess) e = cudaEventRecord(e1, st);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.f;
@@ -588,9 +620,10 @@ nk_status nk_autotune_set(nk_handle* h, const nk_arch* arch, const nk_params* pr
   const char* why = nullptr;
   if (!nk_make_geom(arch, H, W, C, &g, &why)) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_autotune_set: %s", why);
   if (!prm) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_autotune_set: params is NULL");
-  const int nvar = (g.Hs[0] == 32) ? NK_FUSED_VARIANTS : 1;
-  if (variant < 0 || variant >= nvar)
-    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_autotune_set: variant outside 0..%d", nvar - 1);
+  if (!fused_variant_valid(g, variant))
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_autotune_set: variant %d does not exist for this size and stage "
+                   "pattern (0..%d at 32x32, 3 = tiled for (2,1,0) (1) (1,1); 0 elsewhere)", variant,
+                   NK_FUSED_VARIANTS - 1);
   int key[8];
   tune_key(g, prm->sigma_b2 != 0.0, key);
   tune_store(h, key, variant);

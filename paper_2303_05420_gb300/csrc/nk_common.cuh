@@ -81,8 +81,10 @@ cudaError_t nk_launch_myrtle_fused(const NkGeom& g, double sw2, double sb2, cons
                                    const float* qsb, int64_t b0, int64_t b1, float* K,
                                    int64_t ldk, int symmetric, int sm_count, void* scratch,
                                    size_t scratch_bytes, int variant, cudaStream_t st);
-// Number of launch variants of the fused kernel at 32x32 (nk_autotune).
-#define NK_FUSED_VARIANTS 3
+// Number of launch variants of the fused form at 32x32 (nk_autotune): three
+// super-plane cluster launches and the tiled form.
+#define NK_FUSED_VARIANTS 4
+#define NK_TILED_VARIANT 3
 bool nk_myrtle_fused_supported(const NkGeom& g);
 
 // FC NNGP block on the tensor cores (fc_gram.cu).

@@ -253,19 +253,23 @@ def test_autotune_variants_agree(h):
 
     x = _imgs(6, 32, 4)
     X = _dev(x)
-    for convs, sb2 in [((2, 1, 0), 0.0), ((3, 3, 3), 0.01)]:
+    # (2,1,0) has the three cluster launches and the tiled form (3); (3,3,3)
+    # the cluster launches only
+    for convs, sb2, nvar in [((2, 1, 0), 0.0, 4), ((3, 3, 3), 0.01, 3)]:
         q = h.self_diag(X, convs, 2.0, sb2)
         chosen = h.autotune(convs, 2.0, sb2, 32, 32, 3)
-        assert 0 <= chosen < 3
+        assert 0 <= chosen < nvar
         ref = _oracle_block(convs, 2.0, sb2, x[:3], x[3:])
-        for v in range(3):
+        for v in range(nvar):
             h.autotune_set(convs, 2.0, sb2, 32, 32, v)
             K = h.block(X, q, X, q, convs, 2.0, sb2, prec="mixed", a_range=(0, 3), b_range=(3, 6))
             h.sync_status()
             assert _maxrel(K.double().cpu().numpy(), ref) <= TOL32, v
         h.autotune_set(convs, 2.0, sb2, 32, 32, chosen)
     with pytest.raises(NkError):
-        h.autotune_set((2, 1, 0), 2.0, 0.0, 32, 32, 3)
+        h.autotune_set((2, 1, 0), 2.0, 0.0, 32, 32, 4)
+    with pytest.raises(NkError):
+        h.autotune_set((3, 3, 3), 2.0, 0.0, 32, 32, 3)
 
 
 @pytest.mark.parametrize("precond", ["none", "jacobi", "pivchol"])

@@ -53,7 +53,10 @@ def test_queue_matches_blocks_and_oracle(h, convs, sb2):
     h.sync_status()
     from paper_2303_05420_gb300.api import Handle
 
-    h0 = Handle()  # fresh handle: launch variant 0, as the queue uses
+    h0 = Handle()
+    # the cluster launch variant 0, as the queue uses (at 32x32 the default
+    # of a fresh handle is the tiled form where the stage pattern has one)
+    h0.autotune_set(convs, 2.0, sb2, 32, 32, 0)
     for t, got in zip(tasks, outs):
         want = h0.block(t["Xa"], t["qa"], t["Xb"], t["qb"], convs, 2.0, sb2, prec="mixed",
                         a_range=t.get("a_range"), b_range=t.get("b_range"),

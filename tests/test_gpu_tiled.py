@@ -96,6 +96,7 @@ def test_tiled_queue_mixes_64_and_32(h, convs, sb2):
     from paper_2303_05420_gb300.api import Handle
 
     h0 = Handle()
+    h0.autotune_set(convs, 2.0, sb2, 32, 32, 0)
     for t, got in zip(tasks, outs):
         # 64x64: the tiled form alone; 32x32: the cluster super-plane kernel
         want = h0.block(t["Xa"], t["qa"], t["Xb"], t["qb"], convs, 2.0, sb2, prec="mixed",
