@@ -44,8 +44,11 @@
 namespace nkf {
 namespace tiled {
 
-constexpr int THREADS = 512;
-constexpr int NWARPS = THREADS / 32;
+// Threads per CTA: 512 with one CTA per SM wherever 64x64 blocks are present
+// (their tables take 194 KB); 256 with two CTAs per SM for 32x32-only
+// launches (97 KB each), so that one CTA's table staging and barriers
+// overlap the other's row streams.
+constexpr int MAX_WARPS = 16;
 constexpr long long WAIT_LIMIT = 1ll << 22;  // polls of ~0.25-1 us each
 
 // Stage-0 tiling at image side R: rows split into parts of four columns
@@ -432,7 +435,7 @@ __device__ int decode_item(const TiledParams& Q, bool two, int64_t m, int64_t* k
 // ---------------------------------------------------------------------------
 // Stage-0 task `sub` of pair g (block b).
 // ---------------------------------------------------------------------------
-template <int R, int N0, int N1, bool BIAS>
+template <int R, int N0, int N1, bool BIAS, int NT>
 __device__ void stage0_task(const TiledParams& Q, int b, int64_t g, int sub, unsigned char* smem, double* red,
                             int* flag) {
   using G = G0<R>;
@@ -469,7 +472,7 @@ __device__ void stage0_task(const TiledParams& Q, int b, int64_t g, int sub, uns
     const float2* qa = reinterpret_cast<const float2*>(P.qsa) + ia * P.nq;
     const float2* qb = reinterpret_cast<const float2*>(P.qsb) + ib * P.nq;
     const int np = (s1 - s0) * R;
-    for (int e = threadIdx.x; e < np; e += THREADS) {
+    for (int e = threadIdx.x; e < np; e += NT) {
       const int r = s0 + e / R, c = e % R;
       const int d = (r - s0) * G::SXP + (c / G::COLS) * (G::COLS + 1) + c % G::COLS;
       xs[d] = ld_x(xa + (r * R + c) * C, C, P.xscale);
@@ -480,7 +483,7 @@ __device__ void stage0_task(const TiledParams& Q, int b, int64_t g, int sub, uns
       }
     }
     const int nq = (s1 - s0 + G::TY - 1) * G::SQ;
-    for (int e = threadIdx.x; e < nq; e += THREADS) {
+    for (int e = threadIdx.x; e < nq; e += NT) {
       const int wr = e / G::SQ, wc = e - wr * G::SQ;
       const int r = (s0 + ty0 + wr) & (R - 1), c = (tx0 + wc) & (R - 1);
       xq[e] = ld_x(xb + (r * R + c) * C, C, 1.f);
@@ -496,7 +499,7 @@ __device__ void stage0_task(const TiledParams& Q, int b, int64_t g, int sub, uns
   double gap = 0.0;
   using BT = Band<R, G::NQ, N0, true, !TWO, BIAS, false, G::SXP, G::SQ, L::PL, L::QL>;
   static_assert(BT::COLS == G::COLS && BT::TYW == G::TYW, "split");
-  for (int w = warp; w < G::WT; w += NWARPS) {
+  for (int w = warp; w < G::WT; w += NT / 32) {
     BT T;
     const int txl = w / G::YW;
     const int tyw = (w % G::YW) * G::TYW + tyl;  // t_y - ty0
@@ -536,7 +539,7 @@ __device__ void stage0_task(const TiledParams& Q, int b, int64_t g, int sub, uns
     __syncthreads();
     if (threadIdx.x == 0) {
       double s = 0.0;
-      for (int w = 0; w < NWARPS; ++w) s += red[w];
+      for (int w = 0; w < NT / 32; ++w) s += red[w];
       atomicAdd(Q.gacc + g, s);
       __threadfence();
       const int old = atomicAdd(Q.cnt0 + g, 1);
@@ -551,7 +554,7 @@ __device__ void stage0_task(const TiledParams& Q, int b, int64_t g, int sub, uns
 // ---------------------------------------------------------------------------
 // Stage-1 task of pair g: the whole R1 stage on this CTA, then K.
 // ---------------------------------------------------------------------------
-template <int R1, int N0, int N1, bool BIAS>
+template <int R1, int N0, int N1, bool BIAS, int NT>
 __device__ void stage1_task(const TiledParams& Q, int64_t g, unsigned char* smem, double* red, int* flag) {
   using L = L1<R1, N1>;
   using SP = Split<R1>;
@@ -571,11 +574,11 @@ __device__ void stage1_task(const TiledParams& Q, int64_t g, unsigned char* smem
     for (int l = 0; l < N1; ++l) {
       const int Lr = N0 + l;
       const float f = P.fold[Lr];
-      for (int e = threadIdx.x; e < R1 * R1; e += THREADS) {
+      for (int e = threadIdx.x; e < R1 * R1; e += NT) {
         const float2 v = qa[P.qoff[Lr] + e];
         pt[l * L::PL + e] = make_float2(v.x, v.y * f);
       }
-      for (int e = threadIdx.x; e < R1 * 2 * R1; e += THREADS) {
+      for (int e = threadIdx.x; e < R1 * 2 * R1; e += NT) {
         const int row = e / (2 * R1), col = e - row * 2 * R1;
         qt[l * L::QL + row * L::S + col] = qb[P.qoff[Lr] + row * R1 + (col & (R1 - 1))];
       }
@@ -589,7 +592,7 @@ __device__ void stage1_task(const TiledParams& Q, int64_t g, unsigned char* smem
   using BT = Band<R1, SP::NQ, N1, false, true, BIAS, true, R1, L::S, L::PL, L::QL>;
   static_assert(BT::COLS == SP::COLS && BT::TYW == SP::TYW, "split");
   constexpr int NH = SP::WPT;
-  for (int task = warp; task < R1 * NH; task += NWARPS) {
+  for (int task = warp; task < R1 * NH; task += NT / 32) {
     BT T;
     T.t_x = task / NH;
     T.t_y = (task % NH) * SP::TYW + tyl;
@@ -619,29 +622,30 @@ __device__ void stage1_task(const TiledParams& Q, int64_t g, unsigned char* smem
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
-    for (int w = 0; w < NWARPS; ++w) s += red[w];
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
     store_entry(P, i, j, s);
     __threadfence();
     atomicExch(Q.done1 + g, 1);
   }
 }
 
-template <int N0, int N1>
+template <int N0, int N1, int RMAX>
 struct Smem {
-  static constexpr size_t s0 = std::max(L0<64, N0>::bytes, L0<32, N0>::bytes);
-  static constexpr size_t s1 = N1 > 0 ? std::max(L1<32, N1>::bytes, L1<16, N1>::bytes) : 0;
+  static constexpr size_t s0 = RMAX == 64 ? std::max(L0<64, N0>::bytes, L0<32, N0>::bytes) : L0<32, N0>::bytes;
+  static constexpr size_t s1 =
+      N1 > 0 ? (RMAX == 64 ? std::max(L1<32, N1>::bytes, L1<16, N1>::bytes) : L1<16, N1>::bytes) : 0;
   static constexpr size_t tables = std::max(s0, s1);
-  static constexpr size_t bytes = tables + 16 * 8 + 16;
+  static constexpr size_t bytes = tables + MAX_WARPS * 8 + 16;
 };
 
-template <int N0, int N1, bool BIAS>
-__global__ void __launch_bounds__(THREADS, 1) k_myrtle_tiled(const __grid_constant__ TiledParams Q) {
+template <int N0, int N1, bool BIAS, int NT, int RMAX>
+__global__ void __launch_bounds__(NT, 512 / NT) k_myrtle_tiled(const __grid_constant__ TiledParams Q) {
   extern __shared__ __align__(16) unsigned char smem[];
-  using SM = Smem<N0, N1>;
+  using SM = Smem<N0, N1, RMAX>;
   constexpr bool TWO = N1 > 0;
   double* red = reinterpret_cast<double*>(smem + SM::tables);
-  int* flag = reinterpret_cast<int*>(smem + SM::tables + 16 * 8);
-  long long* item_s = reinterpret_cast<long long*>(smem + SM::tables + 16 * 8 + 8);
+  int* flag = reinterpret_cast<int*>(smem + SM::tables + MAX_WARPS * 8);
+  long long* item_s = reinterpret_cast<long long*>(smem + SM::tables + MAX_WARPS * 8 + 8);
   for (;;) {
     if (threadIdx.x == 0) {
       const long long m =
@@ -664,15 +668,23 @@ __global__ void __launch_bounds__(THREADS, 1) k_myrtle_tiled(const __grid_consta
       while (b + 1 < Q.n && k >= Q.f0[b + 1]) ++b;
       const int64_t g = Q.g0[b] + (k - Q.f0[b]) / Q.nt0[b];
       const int sub = (int)((k - Q.f0[b]) % Q.nt0[b]);
-      if (Q.R[b] == 64)
-        stage0_task<64, N0, N1, BIAS>(Q, b, g, sub, smem, red, flag);
-      else
-        stage0_task<32, N0, N1, BIAS>(Q, b, g, sub, smem, red, flag);
+      if constexpr (RMAX == 64) {
+        if (Q.R[b] == 64)
+          stage0_task<64, N0, N1, BIAS, NT>(Q, b, g, sub, smem, red, flag);
+        else
+          stage0_task<32, N0, N1, BIAS, NT>(Q, b, g, sub, smem, red, flag);
+      } else {
+        stage0_task<32, N0, N1, BIAS, NT>(Q, b, g, sub, smem, red, flag);
+      }
     } else if constexpr (TWO) {
-      if (Q.R[block_of(Q, k)] == 64)
-        stage1_task<32, N0, N1, BIAS>(Q, k, smem, red, flag);
-      else
-        stage1_task<16, N0, N1, BIAS>(Q, k, smem, red, flag);
+      if constexpr (RMAX == 64) {
+        if (Q.R[block_of(Q, k)] == 64)
+          stage1_task<32, N0, N1, BIAS, NT>(Q, k, smem, red, flag);
+        else
+          stage1_task<16, N0, N1, BIAS, NT>(Q, k, smem, red, flag);
+      } else {
+        stage1_task<16, N0, N1, BIAS, NT>(Q, k, smem, red, flag);
+      }
     }
     // the next item's staging overwrites the tables
     __syncthreads();
@@ -714,11 +726,11 @@ inline Plan make_plan(bool two, const int* R, const int64_t* npairs, int n, int 
   return p;
 }
 
-template <int N0, int N1, bool BIAS>
+template <int N0, int N1, bool BIAS, int NT, int RMAX>
 cudaError_t launch_t(TiledParams& Q, const int64_t* npairs, int sm_count, void* ws, size_t ws_bytes,
                      cudaStream_t st) {
-  using SM = Smem<N0, N1>;
-  auto kern = k_myrtle_tiled<N0, N1, BIAS>;
+  using SM = Smem<N0, N1, RMAX>;
+  auto kern = k_myrtle_tiled<N0, N1, BIAS, NT, RMAX>;
   static bool attr_set[64] = {false};
   static int per_sm[64] = {0};
   int dev = 0;
@@ -727,7 +739,7 @@ cudaError_t launch_t(TiledParams& Q, const int64_t* npairs, int sm_count, void* 
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
     if (e != cudaSuccess) return e;
     int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, THREADS, SM::bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, SM::bytes);
     if (e != cudaSuccess) return e;
     per_sm[dev] = nb > 0 ? nb : 1;
     attr_set[dev] = true;
@@ -753,7 +765,7 @@ cudaError_t launch_t(TiledParams& Q, const int64_t* npairs, int sm_count, void* 
   Q.abort_flag = reinterpret_cast<int*>(Q.next + 1);
   cudaError_t e = cudaMemsetAsync(ws, 0, p.bytes, st);
   if (e != cudaSuccess) return e;
-  kern<<<grid, THREADS, SM::bytes, st>>>(Q);
+  kern<<<grid, NT, SM::bytes, st>>>(Q);
   return cudaGetLastError();
 }
 
@@ -767,9 +779,9 @@ bool tiled_supported(const int c[3]) {
 }
 
 size_t tiled_ws_bytes(const int c[3], const int* R, const int64_t* npairs, int n, int sm_count) {
-  // an upper bound of what launch_tiled asks for (it runs one CTA per SM;
-  // two are assumed here)
-  return tiled::make_plan(c[1] > 0, R, npairs, n, 2 * sm_count).bytes;
+  // an upper bound of what launch_tiled asks for (it runs one 512-thread or
+  // two 256-thread CTAs per SM; four are assumed here)
+  return tiled::make_plan(c[1] > 0, R, npairs, n, 4 * sm_count).bytes;
 }
 
 cudaError_t launch_tiled(const int c[3], bool bias, const int* R, const FusedParams* B, int n, int sm_count,
@@ -794,10 +806,15 @@ cudaError_t launch_tiled(const int c[3], bool bias, const int* R, const FusedPar
   Q.G = Q.g0[n];
   Q.T0 = Q.f0[n];
   Q.dstatus = dstatus;
+  const bool only32 = Q.G64 == 0;
 #define NK_T(a, b_)                                                                                   \
-  if (c[0] == a && c[1] == b_)                                                                        \
-    return bias ? tiled::launch_t<a, b_, true>(Q, np, sm_count, ws, ws_bytes, st)                     \
-                : tiled::launch_t<a, b_, false>(Q, np, sm_count, ws, ws_bytes, st);
+  if (c[0] == a && c[1] == b_) {                                                                      \
+    if (only32)                                                                                       \
+      return bias ? tiled::launch_t<a, b_, true, 256, 32>(Q, np, sm_count, ws, ws_bytes, st)          \
+                  : tiled::launch_t<a, b_, false, 256, 32>(Q, np, sm_count, ws, ws_bytes, st);        \
+    return bias ? tiled::launch_t<a, b_, true, 512, 64>(Q, np, sm_count, ws, ws_bytes, st)            \
+                : tiled::launch_t<a, b_, false, 512, 64>(Q, np, sm_count, ws, ws_bytes, st);          \
+  }
   NK_T(2, 1) NK_T(1, 0) NK_T(1, 1)
 #undef NK_T
   return cudaErrorNotSupported;
