@@ -14,7 +14,7 @@ that nk_map.cuh embeds.
 import mpmath as mp
 import numpy as np
 
-DEG = 6
+DEG = 5
 mp.mp.dps = 40
 
 

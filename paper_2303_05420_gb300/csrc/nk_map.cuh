@@ -43,19 +43,18 @@ __device__ __forceinline__ float nk_asin_small(float m) {
 }
 
 // Second form used by the kernels: J(c) = pi c + (1 - c)^{3/2} B(c) on
-// [0, 1], B a degree-6 polynomial fitted by csrc/fit_jpos.py (max absolute
-// error of J 3e-9 in float64; FP32 rounding dominates on the device).  One
-// square root and 9 FMA-pipe operations.  Correlations after a ReLU layer
+// [0, 1], B a degree-5 polynomial fitted by csrc/fit_jpos.py (max absolute
+// error of J 2.5e-8 in float64, below FP32 rounding of J in [1, pi]).  One
+// square root and 8 FMA-pipe operations.  Correlations after a ReLU layer
 // are >= 0 (a sum of non-negative terms), so every layer but the first uses
 // this form; the first uses J(c) = J(|c|) + pi min(c, 0).
 __device__ __forceinline__ float nk_B_poly(float c) {
-  float p = 3.246730975e-04f;
-  p = fmaf(p, c, -1.462184683e-03f);
-  p = fmaf(p, c, 3.599365081e-03f);
-  p = fmaf(p, c, -7.651096654e-03f);
-  p = fmaf(p, c, 1.879499484e-02f);
-  p = fmaf(p, c, -7.079588207e-02f);
-  p = fmaf(p, c, 9.999999970e-01f);
+  float p = -7.025579042e-04f;
+  p = fmaf(p, c, 2.948344719e-03f);
+  p = fmaf(p, c, -7.401106535e-03f);
+  p = fmaf(p, c, 1.875308504e-02f);
+  p = fmaf(p, c, -7.079342243e-02f);
+  p = fmaf(p, c, 9.999999749e-01f);
   return p;
 }
 
