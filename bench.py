@@ -394,7 +394,7 @@ def run_ours(args, rank, world, dist):
             extra[f"{key}_relres"] = max(rel)
     lam_used = h.last_lambda()
     if not args.skip_grad:
-        extra.update(grad_leg(h, dev))
+        extra.update(grad_leg(h, dev, args.grad_support, args.grad_targets))
     if not args.skip_queue:
         extra.update(queue_leg(h, dev))
     if not args.skip_fc:
@@ -444,9 +444,10 @@ def run_ours(args, rank, world, dist):
         print(json.dumps(line), flush=True)
 
 
-def grad_leg(h, dev):
+def grad_leg(h, dev, n_sup=100, n_tgt=2048):
     """Myrtle-10 kernel-ridge support-set loss, 100 support x 2048 target
-    32x32 images (same generator), sigma_w^2 = 2, sigma_b^2 = 0.01: forward
+    32x32 images (same generator; n_sup, n_tgt shrink it for profiling),
+    sigma_w^2 = 2, sigma_b^2 = 0.01: forward
     blocks K_ss (upper triangle) and K_ts by the fused kernel, loss in torch,
     gradients w.r.t. the support pixels, sigma_w^2 and sigma_b^2 by the FP32
     layer-wise adjoint.  A small untimed warm-up (4 x 8), one timed pass."""
@@ -485,12 +486,12 @@ def grad_leg(h, dev):
     once(4, 8)  # loads every kernel; untimed
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    L, gs, gb, t_fwd, t_bwd = once(100, 2048)
+    L, gs, gb, t_fwd, t_bwd = once(n_sup, n_tgt)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    entries = 100 * 101 // 2 + 2048 * 100
-    return {"grad_workload": "myrtle10_(3,3,3)_32x32_support100_target2048_krr_loss_fp32_adjoint",
-            "grad_myrtle10_100x2048_s": dt, "grad_entries_per_s": entries / dt,
+    entries = n_sup * (n_sup + 1) // 2 + n_tgt * n_sup
+    return {"grad_workload": f"myrtle10_(3,3,3)_32x32_support{n_sup}_target{n_tgt}_krr_loss_fp32_adjoint",
+            f"grad_myrtle10_{n_sup}x{n_tgt}_s": dt, "grad_entries_per_s": entries / dt,
             "grad_forward_s": t_fwd, "grad_backward_s": t_bwd,
             "grad_backward_entries_per_s": entries / t_bwd,
             "grad_loss": L, "grad_dsw2": gs, "grad_dsb2": gb}
@@ -726,6 +727,8 @@ def main():
     ap.add_argument("--fc-test", type=int, default=FC_N_TEST)
     ap.add_argument("--fc-only", action="store_true",
                     help="run only the FC leg (prints its keys as one JSON line)")
+    ap.add_argument("--grad-support", type=int, default=100, help="support images of the gradient leg")
+    ap.add_argument("--grad-targets", type=int, default=2048, help="target images of the gradient leg")
     ap.add_argument("--skip-grad", action="store_true",
                     help="skip the Myrtle-10 kernel-ridge gradient leg (100 support x 2048 targets)")
     args = ap.parse_args()

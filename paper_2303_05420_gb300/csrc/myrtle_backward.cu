@@ -73,11 +73,15 @@ __global__ void k_fill_pairs(T* __restrict__ buf, int64_t np, int64_t HW2, const
 }
 
 // ReLU-map adjoint, in place on d (dKt in, dK out); h = dKt (Kt - K J'/(2 pi)).
+// The FP32 form reads the FP32 (1/sqrt q, sqrt q) tables, as the forward map
+// does: no FP64 load, conversion or division per entry (FP64 runs at a small
+// fraction of the FP32 rate here and bounded this kernel when it did).
 template <typename T>
 __global__ void k_map_adj(const T* __restrict__ Kpre, T* __restrict__ d, T* __restrict__ hbuf,
                           int64_t np, int HW, int64_t na, int64_t nb, int sym, int64_t pair0,
                           int64_t a0, int64_t b0, const double* __restrict__ qda,
-                          const double* __restrict__ qdb, int64_t nq, int qoff, double sb2, double inv_sw2,
+                          const double* __restrict__ qdb, const float* __restrict__ qsa,
+                          const float* __restrict__ qsb, int64_t nq, int qoff, double sb2, double inv_sw2,
                           double* __restrict__ dsw2, double* __restrict__ dsb2) {
   // the conv's sigma terms ride along: dsw2 += dK (K - sb2) / sw2, dsb2 += dK
   // (sums in T over runs of at most 64 entries, added in FP64)
@@ -94,13 +98,20 @@ __global__ void k_map_adj(const T* __restrict__ Kpre, T* __restrict__ d, T* __re
    for (int rem = blockIdx.x * blockDim.x + threadIdx.x; rem < HW2; rem += gridDim.x * blockDim.x) {
     const int64_t e = pr * (int64_t)HW2 + rem;
     const int p = rem / HW, pp = rem - p * HW;
-    const T q1 = (T)qda[(a0 + i) * nq + qoff + p];
-    const T q2 = (T)qdb[(b0 + j) * nq + qoff + pp];
-    const T s = sqrt(q1 * q2);
+    T s, rs;  // sqrt(q q'), 1 / sqrt(q q')
+    if constexpr (sizeof(T) == 8) {
+      s = sqrt(qda[(a0 + i) * nq + qoff + p] * qdb[(b0 + j) * nq + qoff + pp]);
+      rs = s > 0.0 ? 1.0 / s : 0.0;
+    } else {
+      const float2 s1 = reinterpret_cast<const float2*>(qsa)[(a0 + i) * nq + qoff + p];
+      const float2 s2 = reinterpret_cast<const float2*>(qsb)[(b0 + j) * nq + qoff + pp];
+      s = s1.y * s2.y;
+      rs = s1.x * s2.x;
+    }
     T dk = 0, h = 0;
     if (s > (T)0) {
       const T K = Kpre[e];
-      T c = K / s;
+      T c = K * rs;
       c = c < (T)-1 ? (T)-1 : (c > (T)1 ? (T)1 : c);
       const T th = acos(c);
       const T J = sqrt(((T)1 - c * c) > (T)0 ? (T)1 - c * c : (T)0) + c * ((T)NK_PI_D - th);
@@ -719,8 +730,8 @@ cudaError_t run_backward(const NkGeom& g, double sw2, double sb2, const float* X
         if (relu) {
           *launches += 3;
           k_map_adj<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(Kst[layer], cur, hbuf, np, (int)HW, na, nb, sym,
-                                                               pair0, a0, b0, qda, qdb, g.nq, g.layer_qoff[layer],
-                                                               sb2, 1.0 / sw2, dsw2, dsb2);
+                                                               pair0, a0, b0, qda, qdb, qsa, qsb, g.nq,
+                                                               g.layer_qoff[layer], sb2, 1.0 / sw2, dsw2, dsb2);
           k_rowsum_q<T><<<grid_for(np * HW * 32), 256, 0, st>>>(hbuf, np, (int)HW, na, nb, sym, pair0, a0, qda,
                                                                 g.nq, g.layer_qoff[layer], dqa);
           k_colsum_q<T><<<grid_for(np * HW), 256, 0, st>>>(hbuf, np, (int)HW, na, nb, sym, pair0, b0, qdb, g.nq,
