@@ -93,16 +93,16 @@ def image_problem(n_train: int, n_test: int, hw: int, n_classes: int = 10,
     return ImageProblem(tr, te, y[:n_train], y[n_train:])
 
 
-# Benchmark configurations (sizes as the benchmark table states them).
-CONFIGS = {
-    1: dict(name="myrtle5_8x8_fp64", hw=8, n_train=128, n_test=32, n_classes=10,
-            blur=False, convs=(2, 1, 0), sw2=2.0, sb2=0.0),
-    2: dict(name="myrtle5_32x32", hw=32, n_train=2048, n_test=512, n_classes=10,
-            blur=True, convs=(2, 1, 0), sw2=2.0, sb2=0.0),
-    3: dict(name="myrtle10_32x32_grad", hw=32, n_train=100, n_test=2048, n_classes=10,
-            blur=True, convs=(3, 3, 3), sw2=2.0, sb2=0.01),
-    4: dict(name="fc3_3072", d=3072, n_train=50000, n_test=10000, n_classes=10,
-            sw2=2.0, sb2=0.01),
-    5: dict(name="myrtle5_64x64_queue", hw=64, n_train=512, n_test=128, n_classes=200,
-            blur=True, convs=(2, 1, 0), sw2=2.0, sb2=0.0),
+# Workloads, named by network, image size and purpose (synthetic stand-ins
+# with the shapes of the paper's experiments).
+WORKLOADS = {
+    "myrtle5_8x8_fp64": dict(hw=8, n_train=128, n_test=32, n_classes=10, blur=False, convs=(2, 1, 0),
+                             sw2=2.0, sb2=0.0),
+    "myrtle5_32x32": dict(hw=32, n_train=2048, n_test=512, n_classes=10, blur=True, convs=(2, 1, 0), sw2=2.0,
+                          sb2=0.0),
+    "myrtle10_32x32_grad": dict(hw=32, n_train=100, n_test=2048, n_classes=10, blur=True, convs=(3, 3, 3),
+                                sw2=2.0, sb2=0.01),
+    "fc3_3072": dict(d=3072, n_train=50000, n_test=10000, n_classes=10, sw2=2.0, sb2=0.01),
+    "myrtle5_64x64_queue": dict(hw=64, n_train=512, n_test=128, n_classes=200, blur=True, convs=(2, 1, 0),
+                                sw2=2.0, sb2=0.0),
 }

@@ -31,8 +31,8 @@ def test_golden_constants_match_configs():
     assert g["myrtle_listing"]["stage_convs"] == [3, 3, 3]
     layers = g["myrtle_listing"]["layers"]
     assert layers.count("conv") == 9 and layers.count("avgpool2") == 2
-    assert nkdata.CONFIGS[3]["convs"] == tuple(g["myrtle_listing"]["stage_convs"])
-    assert nkdata.CONFIGS[2]["sw2"] == g["myrtle_listing"]["W_std_squared"]
+    assert nkdata.WORKLOADS["myrtle10_32x32_grad"]["convs"] == tuple(g["myrtle_listing"]["stage_convs"])
+    assert nkdata.WORKLOADS["myrtle5_32x32"]["sw2"] == g["myrtle_listing"]["W_std_squared"]
     grid = np.concatenate([[0.0], np.logspace(g["ridge_grid"]["logspace_start"],
                                               g["ridge_grid"]["logspace_stop"],
                                               g["ridge_grid"]["logspace_num"])])
