@@ -40,6 +40,7 @@
 #include <algorithm>
 
 #include "myrtle_fused.cuh"
+#include "tiled_schedule.h"
 
 namespace nkf {
 namespace tiled {
@@ -66,6 +67,7 @@ struct G0 {
   static constexpr int SXP = R + NQ;          // p-side row stride: one pad after each part
   static constexpr int SQ = R + TX - 1;       // p'-side window columns (odd)
   static_assert(R % B == 0 && COLS % 2 == 0 && SQ % 2 == 1, "tiling");
+  static_assert(NT0 == sched::tasks_per_pair(R), "task count of the item order (tiled_schedule.h)");
 };
 
 template <int R, int N>
@@ -386,50 +388,14 @@ __device__ __forceinline__ float4 ld_x(const float* p, int C, float s) {
 }
 
 // Block of pair g.
-__device__ __forceinline__ int block_of(const TiledParams& Q, int64_t g) {
-  int b = 0;
-  while (b + 1 < Q.n && g >= Q.g0[b + 1]) ++b;
-  return b;
-}
+__device__ __forceinline__ int block_of(const TiledParams& Q, int64_t g) { return sched::block_of_pair(Q, g); }
 
 // Slot of pair g (block b) in its resolution's ring, and the pair that used
 // it before (-1: none).
 __device__ __forceinline__ float* slot_of(const TiledParams& Q, int b, int64_t g, int64_t* prev) {
-  const int r = Q.R[b] == 64 ? 0 : 1;
-  const int64_t ord = r == 0 ? g : g - Q.G64;
-  *prev = ord >= Q.S[r] ? g - Q.S[r] : -1;
-  return Q.slots + Q.ring_off[r] + (ord % Q.S[r]) * Q.slot_floats[r];
-}
-
-// Position of pair k's stage-1 task in the item order: after stage-0 task
-// (last of k) + LAG, and after the k stage-1 tasks before it.
-__device__ __forceinline__ int64_t stage1_pos(const TiledParams& Q, int64_t k) {
-  const int b = block_of(Q, k);
-  int64_t x = Q.f0[b] + (k - Q.g0[b] + 1) * Q.nt0[b] + Q.LAG;
-  if (x > Q.T0) x = Q.T0;
-  return x + k;
-}
-
-// Item m -> stage-1 task of pair *k (returns 1) or stage-0 task index *k (0).
-__device__ int decode_item(const TiledParams& Q, bool two, int64_t m, int64_t* k) {
-  if (!two) {
-    *k = m;
-    return 0;
-  }
-  int64_t lo = 0, hi = Q.G;  // number of stage-1 tasks at positions <= m
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) / 2;
-    if (stage1_pos(Q, mid) <= m)
-      lo = mid + 1;
-    else
-      hi = mid;
-  }
-  if (lo > 0 && stage1_pos(Q, lo - 1) == m) {
-    *k = lo - 1;
-    return 1;
-  }
-  *k = m - lo;
-  return 0;
+  int r;
+  const int64_t k = sched::slot(Q, b, g, &r, prev);
+  return Q.slots + Q.ring_off[r] + k * Q.slot_floats[r];
 }
 
 // ---------------------------------------------------------------------------
@@ -653,7 +619,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_myrtle_tiled(const __grid_cons
       long long code = -1;  // stage-0 index k -> 2k; stage-1 pair k -> 2k + 1; -1 done
       if (m < Q.nitems) {
         int64_t k;
-        const int st1 = decode_item(Q, TWO, m, &k);
+        const int st1 = sched::decode(Q, TWO, m, &k);
         code = 2 * k + st1;
       }
       *item_s = code;
@@ -664,10 +630,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_myrtle_tiled(const __grid_cons
     if (code < 0) break;
     const int64_t k = code >> 1;
     if ((code & 1) == 0) {
-      int b = 0;
-      while (b + 1 < Q.n && k >= Q.f0[b + 1]) ++b;
-      const int64_t g = Q.g0[b] + (k - Q.f0[b]) / Q.nt0[b];
-      const int sub = (int)((k - Q.f0[b]) % Q.nt0[b]);
+      int b, sub;
+      int64_t g;
+      sched::stage0_of(Q, k, &b, &g, &sub);
       if constexpr (RMAX == 64) {
         if (Q.R[b] == 64)
           stage0_task<64, N0, N1, BIAS, NT>(Q, b, g, sub, smem, red, flag);
@@ -691,41 +656,6 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_myrtle_tiled(const __grid_cons
   }
 }
 
-// Host plan of a launch: item lag, slot rings and workspace layout.
-struct Plan {
-  int64_t LAG;
-  int S[2];
-  int64_t slot_floats[2], ring_off[2];
-  size_t slot_bytes, bytes;
-};
-
-inline Plan make_plan(bool two, const int* R, const int64_t* npairs, int n, int grid) {
-  Plan p = {};
-  p.LAG = 2 * (int64_t)grid;
-  int64_t G = 0;
-  bool has[2] = {false, false};
-  for (int b = 0; b < n; ++b) {
-    has[R[b] == 64 ? 0 : 1] = true;
-    G += npairs[b];
-  }
-  const int nt[2] = {G0<64>::NT0, G0<32>::NT0};
-  const int side[2] = {64, 32};
-  int64_t off = 0;
-  for (int r = 0; r < 2; ++r) {
-    const int64_t R1 = side[r] / 2;
-    // order alone needs S >= LAG / nt + 1; one more LAG of items between the
-    // slot's previous stage-1 task and its next user lets that task finish
-    // before it is waited for
-    p.S[r] = (two && has[r]) ? (int)((2 * p.LAG + nt[r] - 1) / nt[r]) + 2 : 1;
-    p.slot_floats[r] = (two && has[r]) ? R1 * R1 * R1 * R1 : 0;
-    p.ring_off[r] = off;
-    off += p.S[r] * p.slot_floats[r];
-  }
-  p.slot_bytes = (size_t)off * sizeof(float);
-  p.bytes = p.slot_bytes + (size_t)G * (2 * sizeof(int) + sizeof(double)) + 64;
-  return p;
-}
-
 template <int N0, int N1, bool BIAS, int NT, int RMAX>
 cudaError_t launch_t(TiledParams& Q, const int64_t* npairs, int sm_count, void* ws, size_t ws_bytes,
                      cudaStream_t st) {
@@ -746,7 +676,7 @@ cudaError_t launch_t(TiledParams& Q, const int64_t* npairs, int sm_count, void* 
   }
   const int grid = std::max(1, sm_count * per_sm[dev]);
   constexpr bool TWO = N1 > 0;
-  const Plan p = make_plan(TWO, Q.R, npairs, Q.n, grid);
+  const sched::Plan p = sched::make_plan(TWO, Q.R, npairs, Q.n, grid);
   if (p.bytes > ws_bytes) return cudaErrorInvalidValue;
   Q.LAG = p.LAG;
   Q.nitems = Q.T0 + (TWO ? Q.G : 0);
@@ -781,7 +711,7 @@ bool tiled_supported(const int c[3]) {
 size_t tiled_ws_bytes(const int c[3], const int* R, const int64_t* npairs, int n, int sm_count) {
   // an upper bound of what launch_tiled asks for (it runs one 512-thread or
   // two 256-thread CTAs per SM; four are assumed here)
-  return tiled::make_plan(c[1] > 0, R, npairs, n, 4 * sm_count).bytes;
+  return (size_t)sched::make_plan(c[1] > 0, R, npairs, n, 4 * sm_count).bytes;
 }
 
 cudaError_t launch_tiled(const int c[3], bool bias, const int* R, const FusedParams* B, int n, int sm_count,
