@@ -13,11 +13,12 @@
 // So a pair is cut into independent stage-0 tasks and one stage-1 task:
 //
 //  * stage-0 task = (row band of B = 32 rows, group of TY = 16 shifts t_y,
-//    group of TX = 8 shifts t_x), 64 or 32 warp tasks of one t_x each.  A band streams its rows plus N0 halo rows
-//    on each inner side (the halo outputs are recomputed, not exchanged);
-//    the p-side tables cover the band's rows, the p'-side tables the window
-//    of rows (r + t_y) mod R and columns (c + t_x) mod R it touches.  At
-//    64x64 with two stage-0 layers the tables take 185 KB; 64 tasks a pair.
+//    group of TX = 8 shifts t_x), 64 or 32 warp tasks of one t_x each.  A
+//    band streams its rows plus N0 halo rows on each inner side (the halo
+//    outputs are recomputed, not exchanged); the p-side tables cover the
+//    band's rows, the p'-side tables the window of rows (r + t_y) mod R and
+//    columns (c + t_x) mod R it touches.  At 64x64 with two stage-0 layers
+//    the tables take 194 KB; 64 tasks a pair.
 //  * the pooled output goes into a per-pair slot in global memory (L2
 //    resident: a ring of S slots) by vector atomic adds; rows are paired in
 //    registers, columns too when t_x is even.
@@ -25,18 +26,19 @@
 //    from the slot (L2, bypassing L1) and cleared for the slot's next pair,
 //    the last layer reduced into the global average and K written.
 //
-// Scheduling: one persistent CTA per SM pulls items from a global counter.
-// The items are the stage-0 tasks of every pair, block by block, with the
-// stage-1 task of pair k merged in LAG stage-0 items (about two waves of the
-// grid) after the last stage-0 task of k, so that it rarely waits for them.
-// The 64x64 and the 32x32 pairs each own a ring of S_R slots; a stage-0 task
-// of pair g waits until the slot's previous user, pair g - S_R, has been
-// cleared by its stage-1 task, which S_R >= LAG / (tasks per pair) + 1 puts
-// earlier in the order (S_R = 2 LAG / (tasks per pair) + 2 puts it a LAG
-// earlier, so that it is normally done).  Every wait is on an item claimed earlier, so the
-// earliest unfinished item never waits and the queue drains.  Waits are
-// bounded: on a timeout the kernel raises NK_DEV_TIMEOUT and an abort flag
-// that makes every CTA stop taking items.
+// Scheduling (tiled_schedule.h): one or two persistent CTAs per SM pull
+// items from a global counter.  The items are the stage-0 tasks of every
+// pair, block by block, with the stage-1 task of pair k merged in LAG
+// stage-0 items (about two waves of the grid) after the last stage-0 task of
+// k, so that it rarely waits for them.  The 64x64 and the 32x32 pairs each
+// own a ring of S_R slots; a stage-0 task of pair g waits until the slot's
+// previous user, pair g - S_R, has been cleared by its stage-1 task, which
+// S_R >= LAG / (tasks per pair) + 1 puts earlier in the order (S_R = 2 LAG /
+// (tasks per pair) + 2 puts it a LAG earlier, so that it is normally done).
+// Every wait is on an item claimed earlier, so the earliest unfinished item
+// never waits and the queue drains.  Waits are bounded: on a timeout the
+// kernel raises NK_DEV_TIMEOUT and an abort flag that makes every CTA stop
+// taking items.
 #include <algorithm>
 
 #include "myrtle_fused.cuh"
