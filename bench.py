@@ -97,6 +97,35 @@ def _oracle_worker(args):
     return time.perf_counter() - t0
 
 
+def cpu_pcg_rate(n: int = 2048, r: int = 10, d: int = 3072):
+    """The oracle's textbook Jacobi PCG (float64 numpy, BLAS threads as numpy
+    starts them) on a kernel matrix the oracle computes itself: the depth-3
+    FC ReLU NNGP (sigma_w^2 = 2, sigma_b^2 = 0.01) of n random rows of
+    dimension d; r right-hand sides, lambda = 1e-4 tr(K)/n, tol 1e-6.  Only
+    the solve is timed.  The CPU counterpart of the PCG iterations/s."""
+    import numpy as np
+
+    import nkdata
+    import oracle
+
+    X = nkdata.fc_rows(n, d, seed=nkdata.SEED_TRAIN).astype(np.float64)
+    K = oracle.fc_nngp(X, X, 2.0, 0.01, depth=3).numpy()
+    lam = 1e-4 * float(np.trace(K)) / n
+    Y = nkdata.labels(n, r)
+    total_its, solves, relmax = 0, 0, 0.0
+    t0 = time.perf_counter()
+    while solves == 0 or time.perf_counter() - t0 < 1.0:  # repeated solves, about a second
+        _, iters, rel = oracle.pcg(K, Y, lam, precond="jacobi", tol=1e-6, maxit=20000)
+        total_its += int(iters)
+        solves += 1
+        relmax = max(relmax, float(np.max(rel)))
+    dt = time.perf_counter() - t0
+    return {"iters_per_s": total_its / dt, "iters": total_its // solves, "solves": solves, "seconds": dt,
+            "relres": relmax, "kind": "oracle",
+            "sample": f"Jacobi PCG, {r} right-hand sides, N = {n} (FC3 NNGP of {n} random rows of dimension "
+                      f"{d}, float64 numpy), tol 1e-6, solved {solves} times"}
+
+
 def cpu_oracle_rate(n_workers: int, pairs_per_worker: int, hw: int, seed0: int = 100):
     ctx = mp.get_context("spawn")
     with ctx.Pool(n_workers) as pool:
@@ -209,6 +238,7 @@ def run_ours(args, rank, world, dist):
 
     # CPU oracle baseline first: its spawn pool starts before any CUDA call
     cpu = None
+    cpu_pcg = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = host_cores()
         rate, pairs, tmax, wall = cpu_oracle_rate(cores, args.cpu_pairs, hw)
@@ -216,6 +246,7 @@ def run_ours(args, rank, world, dist):
                "sample": f"{pairs} Myrtle-5 32x32 pixel-pair recursions ({args.cpu_pairs} per process, "
                          f"{cores} spawned processes x 1 thread, float64 torch CPU); self-variances "
                          f"precomputed outside the timed loop; {tmax:.1f} s"}
+        cpu_pcg = cpu_pcg_rate()
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
@@ -438,6 +469,7 @@ def run_ours(args, rank, world, dist):
         "gpu_launches": launches,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "cpu_pcg_baseline": cpu_pcg,
     }
     line.update(extra)
     if rank == 0:
