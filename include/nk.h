@@ -131,9 +131,13 @@ nk_status nk_self_diag(nk_handle* h, const nk_arch* arch, const nk_params* prm,
  * (1,1); other valid requests there return NK_ERR_UNSUPPORTED.  At 64x64
  * MIXED runs the tiled form: stage-0 tasks over row bands and groups of
  * super-plane shifts, the pooled stage-1 tensor of each pair (4 MB) in a
- * ring of slots in the handle's workspace (about 100 MB, allocated on first
- * use), one stage-1 task per pair; device-side waits are bounded and report
- * NK_ERR_TIMEOUT through nk_sync_status. */
+ * ring of slots in the handle's workspace, one stage-1 task per pair; the
+ * workspace holds the ring (sized for four CTAs per SM: about 170 MB with
+ * 64x64 pairs, 250 MB when 32x32 blocks share the queue, 80 MB with 32x32
+ * pairs only) plus 16 bytes per pair of the block, and is allocated on first
+ * use.  The same form is the default at
+ * 32x32 for these stage patterns (see nk_autotune).  Device-side waits are
+ * bounded and report NK_ERR_TIMEOUT through nk_sync_status. */
 nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_prec prec,
                    const float* Xa, const double* qda, const float* qsa, int64_t a0, int64_t a1,
                    const float* Xb, const double* qdb, const float* qsb, int64_t b0, int64_t b1,
