@@ -41,6 +41,8 @@ from .kernels import (  # noqa: F401
     myrtle_ntk_pair,
     myrtle_ntk_block,
     relu_derivative_map,
+    erf_map,
+    erf_derivative_map,
     fc_nngp,
 )
 from .solve import cholesky_solve, pcg, pivchol_apply, pivoted_cholesky  # noqa: F401

@@ -29,7 +29,9 @@ class Arch:
     listing: one conv, two more, pool, three, pool, three, GAP, Dense; the
     first stage therefore holds three convs).  ``filt`` is the square filter
     size (3 in the paper; 1 is used by a test reduction).  ``act`` is "relu"
-    (the paper) or "identity" (a test-only linear network).
+    (the paper's Myrtle listings), "erf" (one of the activations of the
+    paper's architecture search, Appendix on tuning the Myrtle architecture)
+    or "identity" (a test-only linear network).
     """
 
     convs: Tuple[int, ...] = (2, 1, 0)
@@ -86,9 +88,32 @@ def relu_map(K: torch.Tensor, q1: torch.Tensor, q2: torch.Tensor) -> torch.Tenso
     return torch.where(pos, out, torch.zeros_like(out))
 
 
+# --------------------------------------------------------------------------
+# Erf map (stax.Erf: the activation erf(x))
+# --------------------------------------------------------------------------
+
+
+def erf_map(K: torch.Tensor, q1: torch.Tensor, q2: torch.Tensor) -> torch.Tensor:
+    """E[erf(u) erf(v)] for centred Gaussians (u, v) with variances q1, q2 and
+    covariance K: (2 / pi) arcsin(2 K / sqrt((1 + 2 q1)(1 + 2 q2))), the
+    closed form of the Gaussian integral of the error function (Williams,
+    1997).  Zero at K = 0; the argument stays inside [-1, 1] because
+    |K| <= sqrt(q1 q2)."""
+    return (2.0 / math.pi) * torch.arcsin(2.0 * K / torch.sqrt((1.0 + 2.0 * q1) * (1.0 + 2.0 * q2)))
+
+
+def erf_derivative_map(K: torch.Tensor, q1: torch.Tensor, q2: torch.Tensor) -> torch.Tensor:
+    """E[erf'(u) erf'(v)], erf'(x) = (2 / sqrt(pi)) exp(-x^2), for centred
+    Gaussians with variances q1, q2 and covariance K:
+    (4 / pi) / sqrt((1 + 2 q1)(1 + 2 q2) - 4 K^2)."""
+    return (4.0 / math.pi) / torch.sqrt((1.0 + 2.0 * q1) * (1.0 + 2.0 * q2) - 4.0 * K * K)
+
+
 def _activate(arch: Arch, K, q1, q2):
     if arch.act == "relu":
         return relu_map(K, q1, q2)
+    if arch.act == "erf":
+        return erf_map(K, q1, q2)
     if arch.act == "identity":
         return K
     raise ValueError(arch.act)
@@ -208,6 +233,7 @@ def myrtle_ntk_pair(arch: Arch, sw2, sb2, x, xp, q_x: List[torch.Tensor], q_xp: 
       conv       K' = sw2 A(Kt) + sb2,  Theta' = K' + sw2 A(Theta_t)
                  (A the 3x3 SAME average on both pixels, divisor 9)
       ReLU       Kt = relu_map(K),  Theta_t = Theta * E[relu' relu']
+      Erf        Kt = erf_map(K),   Theta_t = Theta * E[erf' erf']
       identity   Kt = K,  Theta_t = Theta
       avg pool   the same linear pool on both
       readout    K = sw2 mean Kt + sb2,  Theta = K + sw2 mean Theta_t.
@@ -226,6 +252,9 @@ def myrtle_ntk_pair(arch: Arch, sw2, sb2, x, xp, q_x: List[torch.Tensor], q_xp: 
             if arch.act == "relu":
                 Kt = relu_map(K, q1, q2)
                 Tt = T * relu_derivative_map(K, q1, q2)
+            elif arch.act == "erf":
+                Kt = erf_map(K, q1, q2)
+                Tt = T * erf_derivative_map(K, q1, q2)
             elif arch.act == "identity":
                 Kt, Tt = K, T
             else:
