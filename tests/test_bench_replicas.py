@@ -67,3 +67,30 @@ def test_reference_arm_other_ranks_print_nothing():
     with redirect_stdout(buf):
         bench.run_reference(A(), rank=1, world=2)
     assert buf.getvalue() == ""
+
+
+def test_reference_arm_line_on_cpu():
+    """Rank 0 of the reference arm (the FP64 oracle on the host cores) prints
+    one JSON line with the keys the measurement contract names."""
+    import json
+
+    import bench
+
+    class A:
+        steps, warmup, config, ref_pairs = 1, 0, "headline", 1
+
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.run_reference(A(), rank=0, world=1)
+    lines = [ln for ln in buf.getvalue().splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ["impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"]:
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "entries/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert "workload" in d["config"]
