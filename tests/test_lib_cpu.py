@@ -64,3 +64,24 @@ def test_q_size_host_logic(libnk):
     bad = make_arch((0, 1))
     assert libnk.nk_q_size(ctypes.byref(bad), 8, 8) == -1
     assert libnk.nk_q_size(ctypes.byref(make_arch((2,), filt=5)), 8, 8) == -1
+
+
+def test_header_compiles_and_links_as_c(libnk, tmp_path):
+    """include/nk.h compiles as C99 and libnk links from a C program that
+    calls the host-only entry points (tests/c_abi_check.c)."""
+    import shutil
+    import subprocess
+
+    from paper_2303_05420_gb300 import _lib
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    libdir = os.path.dirname(_lib.LIB_PATH)
+    exe = str(tmp_path / "c_abi_check")
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c_abi_check.c"), "-o", exe, "-L", libdir, "-lnk",
+                    "-Wl,-rpath," + libdir], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stdout + out.stderr
+    assert out.stdout.strip() == "ok"
