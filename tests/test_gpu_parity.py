@@ -118,12 +118,12 @@ def test_block_empty_and_invalid(h):
         h.block(Y, qy, Y, qy, convs, 2.0, 0.0, prec="mixed")
 
 
-@pytest.mark.parametrize("convs", [(2, 1, 0), (3, 3, 3), (2, 1, 1), (1,)])
-def test_block_32x32_sampled_pairs(h, convs):
+@pytest.mark.parametrize("convs,sb2", [((2, 1, 0), 0.0), ((2, 1, 0), 0.01), ((3, 3, 3), 0.01), ((2, 1, 1), 0.0),
+                                       ((1,), 0.1)])
+def test_block_32x32_sampled_pairs(h, convs, sb2):
     """(2,1,0) and (1) run the tiled form at 32x32 by default ((1): its
     single-stage path, the global average taken in the stage-0 tasks), the
-    others the cluster kernel."""
-    sb2 = {(3, 3, 3): 0.01, (1,): 0.1}.get(convs, 0.0)
+    others the cluster kernel; sb2 > 0 takes the kernels' bias branch."""
     xa = _imgs(6, 32, 0)
     xb = _imgs(4, 32, 1)
     Xa, Xb = _dev(xa), _dev(xb)
