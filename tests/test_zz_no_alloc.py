@@ -75,3 +75,18 @@ def test_noalloc_rejects_bad_arguments_with_a_message():
     assert st == _lib.NK_ERR_UNSUPPORTED and "no fused kernel" in msg
     st, msg = _call(L, (2, 1, 0), 0.0, X, qs, (0, 2), (1, 2), 12, out, True)
     assert st == _lib.NK_ERR_INVALID_ARG and msg
+
+
+def test_noalloc_rejects_64x64():
+    """64x64 images need the tiled form, whose slot ring lives in a handle's
+    workspace: the allocation-free entry point refuses them before any work."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_05420_gb300 import _lib
+
+    L = _lib.lib()
+    X = torch.zeros((2, 64, 64, 3), device="cuda")
+    qs = torch.zeros((2, 2 * 64 * 64 + 32 * 32, 2), device="cuda")
+    out = torch.zeros((2, 2), device="cuda")
+    st, msg = _call(L, (2, 1, 0), 0.0, X, qs, (0, 2), (0, 2), 64, out, False)
+    assert st == _lib.NK_ERR_UNSUPPORTED and "64x64" in msg
