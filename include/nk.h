@@ -191,7 +191,7 @@ nk_status nk_block_backward(nk_handle* h, const nk_arch* arch, const nk_params* 
  * caches the fastest in the handle; later nk_block calls with the same key
  * use it.  Variants at 32x32: 0 = super-plane cluster kernel, 768 threads x
  * 8 row parts, 1 = 512 x 8, 2 = 512 x 4, 3 = the tiled form of the 64x64
- * blocks (stage patterns (2,1,0) (1) (1,1) only; it needs the handle's
+ * blocks (stage patterns (2,1,0) and (1) at 32x32; it needs the handle's
  * workspace, which grows on first use); other sizes have one.  Without a
  * tuned entry nk_block uses variant 3 where it exists, else 0.  *variant
  * (may be NULL) receives the choice.  Synchronises `stream`. */

@@ -622,7 +622,7 @@ nk_status nk_autotune_set(nk_handle* h, const nk_arch* arch, const nk_params* pr
   if (!prm) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_autotune_set: params is NULL");
   if (!fused_variant_valid(g, variant))
     return nk_fail(h, NK_ERR_INVALID_ARG, "nk_autotune_set: variant %d does not exist for this size and stage "
-                   "pattern (0..%d at 32x32, 3 = tiled for (2,1,0) (1) (1,1); 0 elsewhere)", variant,
+                   "pattern (0..%d at 32x32, 3 = tiled for (2,1,0) and (1); 0 elsewhere)", variant,
                    NK_FUSED_VARIANTS - 1);
   int key[8];
   tune_key(g, prm->sigma_b2 != 0.0, key);
