@@ -476,6 +476,44 @@ def run_ours(args, rank, world, dist):
         print(json.dumps(line), flush=True)
 
 
+def adjoint_layerwise_bytes(convs, hw: int, esize: int = 4) -> int:
+    """Bytes the layer-wise adjoint (nk_block_backward, FP32) moves through
+    HBM per image pair, counting each pass over a pixel-pair tensor once
+    (E_s = (hw / 2^s)^4 elements at stage s): forward recomputation -- input
+    covariance write, per conv layer the conv's read and write and the ReLU
+    map's read and write, pools, the readout mean; reverse sweep -- the seed
+    fill, per layer the map adjoint (reads the stored pre-activation and the
+    gradient, writes the gradient and the q-gradient terms), the two q sums
+    (each reads those terms) and the conv adjoint's read and write, the pool
+    adjoints, and the two input adjoints."""
+    last = max(s for s, n in enumerate(convs) if n > 0)
+    E = [(hw >> s) ** 4 for s in range(last + 1)]
+    tot = E[0]
+    for s in range(last + 1):
+        if s > 0:
+            tot += E[s - 1] + E[s]
+        tot += 4 * convs[s] * E[s]
+    tot += 2 * E[last]
+    for s in range(last, -1, -1):
+        tot += 8 * convs[s] * E[s]
+        if s > 0:
+            tot += E[s] + E[s - 1]
+    tot += 2 * E[0]
+    return esize * tot
+
+
+def adjoint_roofline(seconds: float, n_pairs: int, peaks: dict, convs=(3, 3, 3), hw: int = 32) -> dict:
+    """Achieved HBM bandwidth of the layer-wise adjoint under the traffic
+    model above, against the measured copy bandwidth."""
+    per_pair = adjoint_layerwise_bytes(convs, hw)
+    gbs = per_pair * n_pairs / seconds / 1e9
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "bytes_per_pair": per_pair, "traffic": None,
+            "note": "layer-wise traffic model (each pixel-pair tensor pass read or written once) x pairs / "
+                    "backward time, against the measured copy bandwidth"}
+
+
 def grad_leg(h, dev, n_sup=100, n_tgt=2048):
     """Myrtle-10 kernel-ridge support-set loss, 100 support x 2048 target
     32x32 images (same generator; n_sup, n_tgt shrink it for profiling),
@@ -526,6 +564,7 @@ def grad_leg(h, dev, n_sup=100, n_tgt=2048):
             f"grad_myrtle10_{n_sup}x{n_tgt}_s": dt, "grad_entries_per_s": entries / dt,
             "grad_forward_s": t_fwd, "grad_backward_s": t_bwd,
             "grad_backward_entries_per_s": entries / t_bwd,
+            "grad_adjoint_hbm": adjoint_roofline(t_bwd, entries, load_peaks()),
             "grad_loss": L, "grad_dsw2": gs, "grad_dsb2": gb}
 
 

@@ -94,3 +94,19 @@ def test_reference_arm_line_on_cpu():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]
+
+
+def test_adjoint_traffic_model():
+    """The adjoint's traffic model counts 41 stage-0 tensor passes per pair of
+    a three-stage net (1 input covariance, 12 forward, 1 pool, 1 pool adjoint,
+    24 reverse, 2 input adjoints) and scales with the pair count and time."""
+    import bench
+
+    E0, E1, E2 = 32 ** 4, 16 ** 4, 8 ** 4
+    b = bench.adjoint_layerwise_bytes((3, 3, 3), 32)
+    assert b == 4 * (41 * E0 + 40 * E1 + 40 * E2)
+    # a single-stage net: input cov, conv+relu, mean, fill, reverse, input adjoints
+    assert bench.adjoint_layerwise_bytes((1,), 8) == 4 * (1 + 4 + 2 + 8 + 2) * 8 ** 4
+    r = bench.adjoint_roofline(2.0, 1000, {"hbm_gbs": 5000.0})
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - b * 1000 / 2.0 / 1e9) < 1e-9 and abs(r["frac"] - r["achieved"] / 5000.0) < 1e-12
