@@ -43,6 +43,8 @@ from .kernels import (  # noqa: F401
     relu_derivative_map,
     erf_map,
     erf_derivative_map,
+    cv_pair,
+    cv_block,
     fc_nngp,
 )
 from .solve import cholesky_solve, pcg, pivchol_apply, pivoted_cholesky  # noqa: F401

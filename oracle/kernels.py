@@ -320,6 +320,39 @@ def myrtle_block(arch: Arch, sw2, sb2, Xa, Xb, symmetric: bool = False,
 # --------------------------------------------------------------------------
 
 
+def cv_pair(sw2, sb2, x, xp, depth: int = 8, filt: int = 3, act: str = "relu") -> torch.Tensor:
+    """NNGP of the CV8 listing (Appendix A): ``depth`` conv(filt x filt, SAME)
+    + activation layers, then Flatten and a Dense readout.  The readout's
+    weights are independent per position, so only the diagonal of the last
+    post-activation tensor enters: K = sw2 mean_p Kt_L(p, p) + sb2.  The
+    whole pixel-pair tensor is carried through every layer (the plain
+    definition); self-variances from the full self tensors."""
+    arch = Arch((depth,), filt, act)
+    x = torch.as_tensor(x, dtype=F64)
+    xp = torch.as_tensor(xp, dtype=F64)
+    qx = myrtle_self_q(arch, sw2, sb2, x)
+    qxp = myrtle_self_q(arch, sw2, sb2, xp)
+    Kt = input_cov(x, xp)
+    for layer in range(depth):
+        K = conv_pp(Kt, sw2, sb2, filt)
+        Kt = _activate(arch, K, qx[layer][:, :, None, None], qxp[layer][None, None, :, :])
+    H, W = Kt.shape[0], Kt.shape[1]
+    i = torch.arange(H)[:, None]
+    j = torch.arange(W)[None, :]
+    return sw2 * Kt[i, j, i, j].mean() + sb2
+
+
+def cv_block(Xa, Xb, sw2, sb2, depth: int = 8, filt: int = 3, act: str = "relu") -> torch.Tensor:
+    """CV8-style NNGP for all pairs of Xa x Xb."""
+    Xa = torch.as_tensor(Xa, dtype=F64)
+    Xb = torch.as_tensor(Xb, dtype=F64)
+    K = torch.zeros((Xa.shape[0], Xb.shape[0]), dtype=F64)
+    for a in range(Xa.shape[0]):
+        for b in range(Xb.shape[0]):
+            K[a, b] = cv_pair(sw2, sb2, Xa[a], Xb[b], depth, filt, act)
+    return K
+
+
 def fc_nngp(X1, X2, sw2, sb2, depth: int = 3, act: str = "relu") -> torch.Tensor:
     """FC NNGP: K_0 = x.x'/d; K = sw2 K_0 + sb2; then ``depth`` times
     K <- sw2 * relu_map(K) + sb2 (Dense(512)+Relu x depth, Dense readout)."""
