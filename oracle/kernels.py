@@ -31,12 +31,19 @@ class Arch:
     size (3 in the paper; 1 is used by a test reduction).  ``act`` is "relu"
     (the paper's Myrtle listings), "erf" (one of the activations of the
     paper's architecture search, Appendix on tuning the Myrtle architecture)
-    or "identity" (a test-only linear network).
+    or "identity" (a test-only linear network).  ``norm`` is "none" (the
+    Myrtle listings) or "layer": a LayerNorm over every axis of each image's
+    hidden representation (pixels and channels, as in the tuned Myrtle
+    listing) between each conv and its activation.  At infinite width the
+    channel mean of a centred pre-activation vanishes and its mean square over
+    pixels and channels tends to m = mean_p q(p), so the normalised covariance
+    is K(p, p') / sqrt(m m') and the normalised self-variances q / m.
     """
 
     convs: Tuple[int, ...] = (2, 1, 0)
     filt: int = 3
     act: str = "relu"
+    norm: str = "none"
 
     @property
     def n_weight_layers(self) -> int:
@@ -184,8 +191,8 @@ def myrtle_layers_pair(arch: Arch, sw2, sb2, x, xp,
 
     Returns (K, qs, pre) with K the kernel value (Appendix A readout:
     Dense(W_std, b_std) after GlobalAvgPool: K = sw2 * mean Kt + sb2), qs the
-    list of q used at each activation and pre the list of pre-activation
-    tensors.
+    list of self-variances of each conv's output (before a LayerNorm) and pre
+    the list of the activations' input tensors.
     """
     self_pair = q_x is None
     qs: List[torch.Tensor] = []
@@ -197,13 +204,19 @@ def myrtle_layers_pair(arch: Arch, sw2, sb2, x, xp,
             Kt = avgpool_pp(Kt)
         for _ in range(n):
             K = conv_pp(Kt, sw2, sb2, arch.filt)
-            pre.append(K)
             if self_pair:
                 q = _diag(K)
                 q1, q2 = q, q
             else:
                 q1, q2 = q_x[li], q_xp[li]
             qs.append(q1)
+            if arch.norm == "layer":
+                m1, m2 = q1.mean(), q2.mean()
+                K = K / torch.sqrt(m1 * m2)
+                q1, q2 = q1 / m1, q2 / m2
+            elif arch.norm != "none":
+                raise ValueError(arch.norm)
+            pre.append(K)
             Kt = _activate(arch, K, q1[:, :, None, None], q2[None, None, :, :])
             li += 1
     K = sw2 * Kt.mean(dim=(-4, -3, -2, -1)) + sb2
@@ -249,6 +262,11 @@ def myrtle_ntk_pair(arch: Arch, sw2, sb2, x, xp, q_x: List[torch.Tensor], q_xp: 
             K = conv_pp(Kt, sw2, sb2, arch.filt)
             T = K + conv_pp(Tt, sw2, 0.0, arch.filt)
             q1, q2 = q_x[li][:, :, None, None], q_xp[li][None, None, :, :]
+            if arch.norm == "layer":
+                # a deterministic per-image scale in the limit: K and Theta alike
+                m1, m2 = q_x[li].mean(), q_xp[li].mean()
+                K, T = K / torch.sqrt(m1 * m2), T / torch.sqrt(m1 * m2)
+                q1, q2 = q1 / m1, q2 / m2
             if arch.act == "relu":
                 Kt = relu_map(K, q1, q2)
                 Tt = T * relu_derivative_map(K, q1, q2)
