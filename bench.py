@@ -126,6 +126,18 @@ def cpu_pcg_rate(n: int = 2048, r: int = 10, d: int = 3072):
                       f"{d}, float64 numpy), tol 1e-6, solved {solves} times"}
 
 
+def cpu_baseline_line(rate: float, pairs: int, seconds: float, cores: int, pairs_per_process: int,
+                      workload_entries: int) -> dict:
+    """The cpu_baseline object: the oracle's all-core rate on the bounded
+    sample, per core, and the time the whole workload would take at that rate
+    (extrapolated, not measured)."""
+    return {"value": rate, "unit": "entries/s", "cores": cores, "kind": "oracle",
+            "per_core": rate / cores, "workload_extrapolated_s": workload_entries / rate,
+            "sample": f"{pairs} Myrtle-5 32x32 pixel-pair recursions ({pairs_per_process} per process, "
+                      f"{cores} spawned processes x 1 thread, float64 torch CPU); self-variances "
+                      f"precomputed outside the timed loop; {seconds:.1f} s"}
+
+
 def cpu_oracle_rate(n_workers: int, pairs_per_worker: int, hw: int, seed0: int = 100):
     ctx = mp.get_context("spawn")
     with ctx.Pool(n_workers) as pool:
@@ -242,10 +254,7 @@ def run_ours(args, rank, world, dist):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = host_cores()
         rate, pairs, tmax, wall = cpu_oracle_rate(cores, args.cpu_pairs, hw)
-        cpu = {"value": rate, "unit": "entries/s", "cores": cores, "kind": "oracle",
-               "sample": f"{pairs} Myrtle-5 32x32 pixel-pair recursions ({args.cpu_pairs} per process, "
-                         f"{cores} spawned processes x 1 thread, float64 torch CPU); self-variances "
-                         f"precomputed outside the timed loop; {tmax:.1f} s"}
+        cpu = cpu_baseline_line(rate, pairs, tmax, cores, args.cpu_pairs, n_tr * (n_tr + 1) // 2 + n_te * n_tr)
         cpu_pcg = cpu_pcg_rate()
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))

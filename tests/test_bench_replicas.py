@@ -110,3 +110,12 @@ def test_adjoint_traffic_model():
     r = bench.adjoint_roofline(2.0, 1000, {"hbm_gbs": 5000.0})
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert abs(r["achieved"] - b * 1000 / 2.0 / 1e9) < 1e-9 and abs(r["frac"] - r["achieved"] / 5000.0) < 1e-12
+
+
+def test_cpu_baseline_line():
+    import bench
+
+    d = bench.cpu_baseline_line(160.0, 320, 2.0, 16, 20, 3146752)
+    assert d["value"] == 160.0 and d["unit"] == "entries/s" and d["cores"] == 16 and d["kind"] == "oracle"
+    assert d["per_core"] == 10.0 and abs(d["workload_extrapolated_s"] - 3146752 / 160.0) < 1e-9
+    assert "320 Myrtle-5 32x32" in d["sample"] and "2.0 s" in d["sample"]
