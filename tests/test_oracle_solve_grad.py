@@ -168,6 +168,36 @@ def test_pivoted_cholesky_pivots_are_greedy_schur_maxima(gram):
     assert tr[0] > tr[1] > tr[2] > 0
 
 
+def test_pivoted_cholesky_stops_at_the_rank_of_a_rank_deficient_gram():
+    """K = V^T V of r < n vectors has rank r: after r exact pivots the Schur
+    complement is zero, and in float64 its computed diagonal is rounding noise
+    (about k u max diag K after k steps).  The factor must stop at exactly r
+    pivots and reproduce K; a stop rule of d > 0 would pivot on that noise
+    (rank above r, rows divided by the square root of a rounding error), and
+    a floor far above rounding would stop before r on a matrix whose last
+    real pivot is small (second case: smallest pivot about 1e-9 of the
+    largest diagonal, which must still be taken)."""
+    from oracle import pivoted_cholesky
+
+    rng = np.random.default_rng(12)
+    n = 40
+    for r in (1, 7, 25):
+        V = rng.standard_normal((r, n))
+        K = V.T @ V
+        L, piv = pivoted_cholesky(K, n)
+        assert len(piv) == r, (r, len(piv))
+        assert np.isfinite(L).all()
+        assert np.abs(L.T @ L - K).max() <= 1e-12 * np.abs(K).max()
+    # full rank with one small direction: every one of the n pivots is real
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    ev = np.ones(n)
+    ev[-1] = 1e-9
+    K = (Q * ev) @ Q.T
+    L, piv = pivoted_cholesky(K, n)
+    assert len(piv) == n
+    assert np.abs(L.T @ L - K).max() <= 1e-12 * np.abs(K).max()
+
+
 def test_pivchol_apply_is_the_woodbury_inverse(gram):
     from oracle import pivchol_apply, pivoted_cholesky
 
