@@ -6,27 +6,35 @@
 // The Gram X_a X_b^T is the one dense contraction of the method (d = 3072
 // for the CIFAR-shaped inputs).  It runs as a BF16 tcgen05 GEMM with FP32
 // accumulation in TMEM on split operands: x = x_hi + x_lo (BF16 each), and
-// x . x' ~ hi.hi' + hi.lo' + lo.hi' is one GEMM over a tripled K with
-// A' = [hi | hi | lo] and B' = [hi' | lo' | hi'] (zero-padded to a multiple
-// of 64).  Persistent clusters of two CTAs (one per SM) walk pairs of
-// vertically adjacent 128 x 256 output tiles in a grouped raster (16 tile rows
-// at a time, so that concurrent clusters share B tiles in L2); the two CTAs
-// of a cluster share the B tile, each loading half of it by TMA multicast
-// into both, which halves B's L2-to-SM traffic.  Operand tiles (128 x 64 and 256 x 64 BF16) arrive by TMA with
-// 128-byte swizzle through a 4-stage mbarrier ring; one thread issues the
-// MMAs into one of two 256-column TMEM accumulators while eight epilogue warps
-// drain the other: each reads 32 rows x 128 columns from TMEM, applies the whole
-// arc-cosine recursion layer by layer over 32 entries at a time (column
-// factors staged in shared memory) and stores 16 bytes of a K row per lane.  The
-// self-variances q_l of each row follow the closed diagonal recursion
-// q_1 = sw2 |x|^2/d + sb2, q_{l+1} = sw2 q_l / 2 + sb2 (FP64).
-// Symmetric blocks run only tiles touching the upper triangle and store each
-// entry at (i, j) and (j, i).  The tensor core's FP32 accumulator rounds
-// once per 16-element MMA step; for a sum of 3d positive products (a row
-// with itself) those roundings drift one way, about 2e-5 relative at
-// d = 3072, so self pairs take their K_1 from the FP64 norm; rows that are
-// near copies of each other keep a bias of that order.  Every mbarrier wait is bounded; on a timeout
-// the kernel records NK_DEV_TIMEOUT and skips its stores.
+// x . x' ~ hi.lo' + lo.hi' + hi.hi' is one GEMM over a tripled K with
+// A' = [hi | lo | hi] and B' = [lo' | hi' | hi'] (zero-padded to a multiple
+// of 64).  Persistent CTAs (one per SM) walk the 128 x 128 output tiles in a
+// grouped raster (16 tile rows at a time, so that concurrent CTAs share B
+// tiles in L2).  Operand tiles (128 x 64 BF16 each) arrive by TMA with
+// 128-byte swizzle through a 6-stage mbarrier ring; one thread issues the
+// MMAs while eight epilogue warps drain the previous tile: each reads 32 rows
+// x 64 columns from TMEM, applies the whole arc-cosine recursion layer by
+// layer over 32 entries at a time (column factors staged in shared memory)
+// and stores 16 bytes of a K row per lane.  The self-variances q_l of each
+// row follow the closed diagonal recursion q_1 = sw2 |x|^2/d + sb2,
+// q_{l+1} = sw2 q_l / 2 + sb2 (FP64).  Symmetric blocks run only tiles
+// touching the upper triangle and store each entry at (i, j) and (j, i).
+//
+// Accumulation accuracy.  The tensor core adds each 16-element MMA step to
+// the FP32 accumulator with a rounding that always goes toward zero, so for
+// a sum of 3d products of one sign (a row with itself or with a near copy of
+// itself) the errors add up one way: about 2e-5 relative at d = 3072 when
+// the large hi.hi' products come first.  Two measures bring that under
+// 5e-6: the small hi.lo' and lo.hi' products come first, while the running
+// sum is still small, and each tile accumulates its even and odd 64-wide K
+// blocks into two separate TMEM accumulators (two chunk sums, each half as
+// long, added in FP32 by the epilogue).  TMEM holds 2 tiles x 2 chunks x 128
+// columns (all 512).  Self pairs still take K_1 from the FP64 norm.
+//
+// Every mbarrier wait of the pipeline is bounded by the handle's wait limit;
+// on a timeout the kernel records NK_DEV_TIMEOUT and skips its stores, and
+// before exit it waits (with a fixed generous bound) for its own TMA loads
+// and MMAs in flight, then frees TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -38,12 +46,12 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 6;
 constexpr int GROUP_M = 16;     // tile rows per raster group (L2 reuse of B)
-constexpr int CLUSTER = 2;      // CTAs sharing each B tile (TMA multicast)
-constexpr int EPI_WARPS = 8;    // two per TMEM lane quarter, 128 columns each
+constexpr int NCHUNK = 2;       // accumulators per tile (even / odd K blocks)
+constexpr int EPI_WARPS = 8;    // two per TMEM lane quarter, 64 columns each
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
-constexpr uint32_t WAIT_LIMIT = 1u << 26;
+constexpr uint32_t DRAIN_LIMIT = 1u << 26;  // waits for own copies / MMAs before exit
 constexpr int MAX_DEPTH = 8;
 
 struct GemmSmem {
@@ -70,6 +78,7 @@ struct FcParams {
   int sym;
   int ntm, ntn;          // tiles along M and N
   unsigned int* dstatus;
+  uint32_t wait_limit;   // polls of a pipeline mbarrier wait before it gives up
   // self pairs (same image on both sides: Xa == Xb and a0 + i == b0 + j)
   // take K_1 = sw2 |x|^2/d + sb2 from the FP64 norm instead of the Gram
   int same;
@@ -77,24 +86,17 @@ struct FcParams {
   const float* q1a;      // [M]
 };
 
-// Tile slot t of the grouped raster over pair rows: a pair row is CLUSTER
-// consecutive tile rows that share every B tile (one per CTA of a cluster);
-// GROUP_M tile rows at a time, column by column, so that the clusters running
-// together share B tiles in L2.  Returns this CTA's tile, and false when the
-// cluster's first tile has no entry on or above the diagonal of a symmetric
-// block (both CTAs then skip the slot).
-__device__ __forceinline__ bool tile_of(const FcParams& P, int64_t t, int rank, int& tm, int& tn) {
-  constexpr int GP = GROUP_M / CLUSTER;  // pair rows per group
-  const int ntp = (P.ntm + CLUSTER - 1) / CLUSTER;
-  const int64_t per_group = (int64_t)GP * P.ntn;
+// Tile slot t of the grouped raster: GROUP_M tile rows at a time, column by
+// column, so that the CTAs running together share B tiles in L2.  False
+// when the tile has no entry on or above the diagonal of a symmetric block.
+__device__ __forceinline__ bool tile_of(const FcParams& P, int64_t t, int& tm, int& tn) {
+  const int64_t per_group = (int64_t)GROUP_M * P.ntn;
   const int g = (int)(t / per_group);
   const int64_t k = t - (int64_t)g * per_group;
-  const int rows = min(GP, ntp - g * GP);
-  const int tp = g * GP + (int)(k % rows);
+  const int rows = min(GROUP_M, P.ntm - g * GROUP_M);
+  tm = g * GROUP_M + (int)(k % rows);
   tn = (int)(k / rows);
-  tm = tp * CLUSTER + rank;
-  const int tm0 = tp * CLUSTER;
-  return !(P.sym && (int64_t)tn * BN + BN - 1 < (int64_t)tm0 * BM);
+  return !(P.sym && (int64_t)tn * BN + BN - 1 < (int64_t)tm * BM);
 }
 
 __device__ __forceinline__ void named_sync(int id, int n) {
@@ -115,12 +117,11 @@ __device__ __forceinline__ bool named_any(int id, int n, bool v) {
   return r != 0;
 }
 
-// Persistent kernel, one CTA per SM, clusters of two CTAs; cluster c takes
-// slots t = c + k * clusters.  Warp 0: TMA producer (its A tile, and half of
-// the shared B tile multicast to both CTAs); warp 1: TMEM owner and MMA
-// issuer (each stage is released to both producers); warps 2..9: epilogue.
-// Two 256-column TMEM accumulators let the MMAs of the next tile run while
-// the epilogue drains the previous one.
+// Persistent kernel, one CTA per SM; CTA c takes tile slots t = c + k * CTAs.
+// Warp 0: TMA producer; warp 1: TMEM owner and MMA issuer; warps 2..9:
+// epilogue.  Tile n uses TMEM columns [(n & 1) * 256, +256): chunk 0 (even K
+// blocks) in the first 128, chunk 1 (odd K blocks) in the next 128, so the
+// MMAs of the next tile run while the epilogue drains the previous one.
 __global__ void __launch_bounds__(THREADS, 1)
 k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
           const __grid_constant__ FcParams P) {
@@ -128,14 +129,12 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   GemmSmem& S = *reinterpret_cast<GemmSmem*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nk = P.kpad / BK;
-  const int rank = (int)tc::cluster_ctarank();
-  const int64_t cid = blockIdx.x / CLUSTER, ncl = gridDim.x / CLUSTER;
-  const int64_t nslots = (int64_t)((P.ntm + CLUSTER - 1) / CLUSTER) * P.ntn;
-  constexpr uint16_t ALL = (1u << CLUSTER) - 1;
+  const int64_t cta = blockIdx.x, ncta = gridDim.x;
+  const int64_t nslots = (int64_t)P.ntm * P.ntn;
   if (warp == 0 && lane == 0) {
     for (int s = 0; s < STAGES; ++s) {
       tc::mbar_init(&S.full[s], 1);
-      tc::mbar_init(&S.empty[s], CLUSTER);  // both CTAs' MMAs must have read a stage
+      tc::mbar_init(&S.empty[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
       tc::mbar_init(&S.tfull[a], 1);
@@ -148,8 +147,7 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   }
   if (warp == 1) tc::tmem_alloc(&S.tslot, 512);
   tc::tc_fence_before();
-  // barriers initialised in both CTAs before any multicast reaches them
-  tc::cluster_sync();
+  __syncthreads();
   tc::tc_fence_after();
   const uint32_t tbase = S.tslot;
   bool ok = true;
@@ -157,27 +155,25 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
     if (lane == 0) {
       // TMA producer: the operand ring runs on across tiles
       int64_t kb_all = 0;
-      constexpr int BH = BN / CLUSTER;  // B rows this CTA loads for the cluster
-      for (int64_t t = cid; t < nslots && ok; t += ncl) {
+      for (int64_t t = cta; t < nslots && ok; t += ncta) {
         int tm, tn;
-        if (!tile_of(P, t, rank, tm, tn)) continue;
+        if (!tile_of(P, t, tm, tn)) continue;
         for (int kb = 0; kb < nk; ++kb, ++kb_all) {
           const int s = (int)(kb_all % STAGES);
           if (kb_all >= STAGES &&
-              !tc::mbar_wait(&S.empty[s], (uint32_t)((kb_all / STAGES) & 1) ^ 1, WAIT_LIMIT)) {
+              !tc::mbar_wait(&S.empty[s], (uint32_t)((kb_all / STAGES) & 1) ^ 1, P.wait_limit)) {
             atomicOr(P.dstatus, NK_DEV_TIMEOUT);
             ok = false;
             break;
           }
-          // own A tile plus the whole B tile (half from each CTA)
           tc::mbar_arrive_expect_tx(&S.full[s], (BM + BN) * BK * 2);
           tc::tma_load_2d(S.A[s], &ta, &S.full[s], kb * BK, tm * BM);
-          tc::tma_load_2d_mc(S.B[s] + rank * BH * BK, &tb, &S.full[s], kb * BK, tn * BN + rank * BH, ALL);
+          tc::tma_load_2d(S.B[s], &tb, &S.full[s], kb * BK, tn * BN);
         }
       }
       // every load issued has landed before the CTA may exit
       for (int64_t k = std::max<int64_t>(0, kb_all - STAGES); k < kb_all; ++k)
-        if (!tc::mbar_wait(&S.full[k % STAGES], (uint32_t)((k / STAGES) & 1), WAIT_LIMIT))
+        if (!tc::mbar_wait(&S.full[k % STAGES], (uint32_t)((k / STAGES) & 1), DRAIN_LIMIT))
           atomicOr(P.dstatus, NK_DEV_TIMEOUT);
     }
   } else if (warp == 1) {
@@ -186,30 +182,32 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
       int64_t kb_all = 0;
       int n = 0;  // tiles of this CTA so far
-      for (int64_t t = cid; t < nslots && ok; t += ncl) {
+      for (int64_t t = cta; t < nslots && ok; t += ncta) {
         int tm, tn;
-        if (!tile_of(P, t, rank, tm, tn)) continue;
+        if (!tile_of(P, t, tm, tn)) continue;
         const int acc = n & 1;
-        if (n >= 2 && !tc::mbar_wait(&S.tempty[acc], (uint32_t)((n >> 1) & 1) ^ 1, WAIT_LIMIT)) {
+        if (n >= 2 && !tc::mbar_wait(&S.tempty[acc], (uint32_t)((n >> 1) & 1) ^ 1, P.wait_limit)) {
           atomicOr(P.dstatus, NK_DEV_TIMEOUT);
           ok = false;
           break;
         }
         tc::tc_fence_after();
-        const uint32_t tacc = tbase + (uint32_t)(acc * BN);
+        const uint32_t tacc = tbase + (uint32_t)(acc * NCHUNK * BN);
         for (int kb = 0; kb < nk; ++kb, ++kb_all) {
           const int s = (int)(kb_all % STAGES);
-          if (!tc::mbar_wait(&S.full[s], (uint32_t)((kb_all / STAGES) & 1), WAIT_LIMIT)) {
+          if (!tc::mbar_wait(&S.full[s], (uint32_t)((kb_all / STAGES) & 1), P.wait_limit)) {
             atomicOr(P.dstatus, NK_DEV_TIMEOUT);
             ok = false;
             break;
           }
           tc::tc_fence_after();
           const uint32_t a0 = tc::smem_addr(S.A[s]), b0 = tc::smem_addr(S.B[s]);
+          const uint32_t tch = tacc + (uint32_t)((kb & 1) * BN);  // chunk of this K block
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k)
-            tc::mma_bf16(tacc, tc::sdesc_k128(a0 + 32 * k), tc::sdesc_k128(b0 + 32 * k), idesc, (kb | k) != 0);
-          tc::mma_commit_mc(&S.empty[s], ALL);  // the stage may be refilled by either CTA
+            tc::mma_bf16(tch, tc::sdesc_k128(a0 + 32 * k), tc::sdesc_k128(b0 + 32 * k), idesc,
+                         (kb >= NCHUNK) || (k != 0));
+          tc::mma_commit(&S.empty[s]);  // the stage may be refilled once these MMAs have read it
         }
         if (!ok) break;
         tc::mma_commit(&S.tfull[acc]);
@@ -217,19 +215,20 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       }
       // all MMAs issued by this thread complete before TMEM is released
       tc::mma_commit(&S.done);
-      if (!tc::mbar_wait(&S.done, 0, WAIT_LIMIT)) atomicOr(P.dstatus, NK_DEV_TIMEOUT);
+      if (!tc::mbar_wait(&S.done, 0, DRAIN_LIMIT)) atomicOr(P.dstatus, NK_DEV_TIMEOUT);
     }
   } else {
     // epilogue: TMEM lane quarter q holds tile rows 32q .. 32q+31; the two
-    // warps of a quarter take columns [0, 128) and [128, 256)
+    // warps of a quarter take columns [0, 64) and [64, 128)
     const int q = warp & 3;
     const int cbeg = ((warp - 2) >> 2) * (BN / 2);
     const int et = threadIdx.x - 64;  // 0 .. 32 * EPI_WARPS - 1
     const bool vec_ok = (P.ldk % 4 == 0) && ((reinterpret_cast<uintptr_t>(P.K) & 15) == 0);
+    const bool two = nk > 1;  // chunk 1 holds the odd K blocks (none when nk == 1)
     int n = 0;
-    for (int64_t t = cid; t < nslots; t += ncl) {
+    for (int64_t t = cta; t < nslots; t += ncta) {
       int tm, tn;
-      if (!tile_of(P, t, rank, tm, tn)) continue;
+      if (!tile_of(P, t, tm, tn)) continue;
       const int64_t m0 = (int64_t)tm * BM, n0 = (int64_t)tn * BN;
       // row and column factors of this tile into shared memory
       named_sync(1, 32 * EPI_WARPS);
@@ -243,7 +242,7 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       }
       named_sync(1, 32 * EPI_WARPS);
       const int acc = n & 1;
-      const bool got = tc::mbar_wait(&S.tfull[acc], (uint32_t)((n >> 1) & 1), WAIT_LIMIT);
+      const bool got = tc::mbar_wait(&S.tfull[acc], (uint32_t)((n >> 1) & 1), P.wait_limit);
       // the epilogue warps leave together (they share named barriers)
       if (named_any(2, 32 * EPI_WARPS, !got)) {
         atomicOr(P.dstatus, NK_DEV_TIMEOUT);
@@ -255,12 +254,18 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       const bool rowok = i < P.M;
       const float self_k1 = (rowok && P.same) ? P.q1a[i] : 0.f;
       const float2* qr = S.qa + row * P.depth;
-      const uint32_t taddr = tbase + (uint32_t)(acc * BN) + ((uint32_t)(32 * q) << 16);
+      const uint32_t taddr = tbase + (uint32_t)(acc * NCHUNK * BN) + ((uint32_t)(32 * q) << 16);
       for (int c0 = cbeg; c0 < cbeg + BN / 2; c0 += 32) {
         float v[32];
         tc::tmem_ld32(taddr + (uint32_t)c0, v);
+        if (two) {
+          float w[32];
+          tc::tmem_ld32(taddr + (uint32_t)(BN + c0), w);
+#pragma unroll
+          for (int e = 0; e < 32; ++e) v[e] += w[e];
+        }
         if (c0 + 32 == cbeg + BN / 2) {
-          // this warp's part of the accumulator is free for a later tile
+          // this warp's part of the accumulators is free for a later tile
           tc::tc_fence_before();
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(&S.tempty[acc]);
@@ -320,14 +325,13 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
     }
   }
   tc::tc_fence_before();
-  __syncwarp();
-  // neither CTA leaves while the other may still multicast into it or
-  // arrive on its barriers
-  tc::cluster_sync();
+  __syncthreads();
+  tc::tc_fence_after();
   if (warp == 1) tc::tmem_dealloc(tbase, 512);
 }
 
-// A' = [hi | hi | lo] (role a) or B' = [hi | lo | hi] (role b), zero-padded to kpad.
+// A' = [hi | lo | hi] (role a) or B' = [lo | hi | hi] (role b), zero-padded to
+// kpad: the small cross products hi.lo' and lo.hi' come first in K'.
 __global__ void k_split_bf16(const float* __restrict__ X, int64_t rows, int d, int kpad, int role_b,
                              __nv_bfloat16* __restrict__ out) {
   const int64_t total = rows * (int64_t)kpad;
@@ -340,7 +344,7 @@ __global__ void k_split_bf16(const float* __restrict__ X, int64_t rows, int d, i
       const int seg = k / d, c = k - seg * d;
       const float x = X[r * d + c];
       const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-      const bool want_lo = role_b ? (seg == 1) : (seg == 2);
+      const bool want_lo = role_b ? (seg == 0) : (seg == 1);
       v = want_lo ? __bfloat162float(__float2bfloat16_rn(x - __bfloat162float(hi))) : __bfloat162float(hi);
     }
     out[e] = __float2bfloat16_rn(v);
@@ -382,7 +386,8 @@ EncodeTiledFn encode_fn() {
   if (!fn) {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
       fn = (EncodeTiledFn)p;
   }
@@ -411,7 +416,8 @@ size_t nk_fc_ws_bytes(int64_t na, int64_t nb, int d, int depth) {
 
 cudaError_t nk_launch_fc_block(int depth, double sw2, double sb2, const float* Xa, int64_t a0, int64_t a1,
                                const float* Xb, int64_t b0, int64_t b1, int d, float* K, int64_t ldk, int sym,
-                               void* ws, int sm, unsigned int* dstatus, cudaStream_t st, int64_t* launches) {
+                               void* ws, int sm, unsigned int* dstatus, uint32_t wait_limit, cudaStream_t st,
+                               int64_t* launches) {
   const int64_t na = a1 - a0, nb = b1 - b0;
   const int kpad = (int)((3 * (int64_t)d + BK - 1) / BK * BK);
   char* w = reinterpret_cast<char*>(ws);
@@ -435,7 +441,7 @@ cudaError_t nk_launch_fc_block(int depth, double sw2, double sb2, const float* X
   k_fc_q<<<grid(na * 32), 256, 0, st>>>(xa, na, d, depth, sw2, sb2, (float)(sw2 * inv2pi), qa, q1a);
   k_fc_q<<<grid(nb * 32), 256, 0, st>>>(xb, nb, d, depth, sw2, sb2, 1.f, qb, nullptr);
   CUtensorMap ta, tb;
-  if (!make_map(&ta, Ap, na, kpad, BM) || !make_map(&tb, Bp, nb, kpad, BN / CLUSTER)) return cudaErrorInvalidValue;
+  if (!make_map(&ta, Ap, na, kpad, BM) || !make_map(&tb, Bp, nb, kpad, BN)) return cudaErrorInvalidValue;
   FcParams P = {};
   P.M = na;
   P.N = nb;
@@ -453,26 +459,14 @@ cudaError_t nk_launch_fc_block(int depth, double sw2, double sb2, const float* X
   P.same = (Xa == Xb);
   P.selfoff = a0 - b0;
   P.q1a = q1a;
-  const int64_t slots = (int64_t)((P.ntm + CLUSTER - 1) / CLUSTER) * P.ntn;
+  P.wait_limit = wait_limit;
+  const int64_t slots = (int64_t)P.ntm * P.ntn;
   const size_t smem = sizeof(GemmSmem) + 1024;
   cudaError_t e = cudaFuncSetAttribute(k_fc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   P.dstatus = dstatus;
   ++*launches;
-  const int64_t clusters = std::max<int64_t>(1, std::min<int64_t>(slots, sm / CLUSTER));
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CLUSTER;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3((unsigned)(clusters * CLUSTER), 1, 1);
-  cfg.blockDim = dim3(THREADS, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, k_fc_gram, ta, tb, P);
-  if (e != cudaSuccess) return e;
+  const unsigned ctas = (unsigned)std::max<int64_t>(1, std::min<int64_t>(slots, sm));
+  k_fc_gram<<<ctas, THREADS, smem, st>>>(ta, tb, P);
   return cudaGetLastError();
 }
