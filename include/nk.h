@@ -150,8 +150,10 @@ nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_p
  * for rows i in [a0, a1) of Xa and j in [b0, b1) of Xb (row-major [n][d]
  * float32, device), into K[i - a0][j - b0] (float32, leading dimension
  * ldk).  The Gram is a split-BF16 tcgen05 GEMM (x = hi + lo, three BF16
- * products per pair of elements, FP32 accumulation in TMEM) with the
- * recursion fused into its epilogue; the per-row self-variances are FP64.
+ * products per pair of elements, FP32 accumulation in TMEM, the small
+ * cross products first and even / odd K blocks in two accumulators added by
+ * the epilogue) with the recursion fused into its epilogue; the per-row
+ * self-variances are FP64.
  * symmetric: Xa == Xb, equal ranges; tiles below the diagonal are skipped and
  * each entry is stored at (i, j) and (j, i).  depth 0..8.  Uses a handle
  * workspace of (na + nb) * 6 d bytes for the split operands.  A device wait
@@ -206,16 +208,17 @@ nk_status nk_autotune_set(nk_handle* h, const nk_arch* arch, const nk_params* pr
 
 /* Fused (NK_PREC_MIXED) kernel block that allocates no device memory and
  * needs no handle.  The paper has no counterpart: this entry point exists for
- * callers that cannot call cudaMalloc when they need a block -- code being
- * recorded into a CUDA graph, a process whose device memory is reserved up
- * front by its own allocator, a plugin whose host framework owns all device
- * memory -- since nk_create allocates.  Arguments and results are those of
+ * callers that cannot call cudaMalloc when they need a block -- a process
+ * whose device memory is reserved up front by its own allocator and which
+ * forbids new device allocations while it serves, or a plugin whose host
+ * framework owns all device memory -- since nk_create allocates.  Arguments and results are those of
  * nk_block with prec = NK_PREC_MIXED (qsa / qsb from nk_self_diag, computed
  * beforehand); the launch variant is 0.  The kernel's scratch (two
  * accumulator slots of 12 bytes per 4-CTA or 1-CTA cluster) is a fixed
  * 16 KB device array inside the library, shared by all calls on a device:
- *   - the first call on a device looks up that array's device address with
- *     the device current; make that first call before any stream capture;
+ *   - the first call on a device (and the first after that device's
+ *     context was reset) looks up the array's device address with the
+ *     device current; make that first call before any stream capture;
  *   - each call clears the slots it uses (stream-ordered) before its kernel;
  *   - calls whose kernels overlap on the GPU (unordered streams) race on the
  *     array; order them on one stream;
@@ -277,6 +280,20 @@ typedef struct {
 nk_status nk_block_queue(nk_handle* h, const nk_arch* arch, const nk_params* prm, int C,
                          const nk_block_task* tasks, int n_tasks, void* stream);
 
+/* Bound of every device-side wait of later calls on this handle (Section 2:
+ * kernel blocks are computed by independent, preemption-safe routines, so a
+ * block that cannot finish must end with an error, never hang).  The tiled
+ * MIXED kernel waits for earlier items of its queue (each poll about
+ * 0.25-1 us; default 2^22 polls, seconds); the FC kernel's pipeline waits on
+ * its mbarriers (each poll a bounded try_wait; default 2^26 polls).  A wait
+ * that runs out sets NK_ERR_TIMEOUT (read by nk_sync_status), the kernel
+ * stops taking work, and the results of that call are undefined; the handle
+ * stays usable.  The waits a kernel makes before it exits, for its own copies
+ * and tensor-core operations in flight, keep a fixed bound.
+ *   polls >= 0: the bound in polls (0: give up at the first unmet check);
+ *   polls < 0: the defaults. */
+nk_status nk_set_wait_limit(nk_handle* h, int64_t polls);
+
 /* Rank of the partial pivoted Cholesky preconditioner (NK_PRECOND_PIVCHOL)
  * used by later nk_pcg_solve calls on this handle (default 100; at most N is
  * used).  rank in 1..1024, else NK_ERR_INVALID_ARG. */
@@ -295,8 +312,9 @@ nk_status nk_pcg_set_rank(nk_handle* h, int rank);
  *   kernels larger than HBM), Y [N][R] float64 (device, row
  *   major), A [N][R] float64 (device, out).
  *   prec = NK_PREC_MIXED: iterative refinement: the true residual
- *          Y - (K + lambda I) A is formed with FP64 products and sums, the
- *          correction is solved by CG with FP32 K@P (FP32 chunks of 256
+ *          Y - (K + lambda I) A is formed in double-FP32 arithmetic (exact
+ *          FP32 products and two-float sums, about 2^-48 relative per step),
+ *          the correction is solved by CG with FP32 K@P (FP32 chunks of 256
  *          products summed in FP64) and FP64 vectors and scalars, A += D
  *          (at most refine_max corrections);
  *   prec = NK_PREC_PLAIN_FP32: FP32 K@P, FP64 vectors and scalars, no

@@ -25,7 +25,8 @@ PRECOND = {"none": 0, "jacobi": 1, "pivchol": 2}
 EXPORTS = ["nk_create", "nk_destroy", "nk_status_string", "nk_last_error", "nk_sync_status",
            "nk_q_size", "nk_launch_count", "nk_last_lambda", "nk_self_diag", "nk_block", "nk_block_backward", "nk_fc_block",
            "nk_autotune",
-           "nk_autotune_set", "nk_block_fused_noalloc", "nk_block_queue", "nk_block_ntk", "nk_pcg_set_rank", "nk_pcg_solve"]
+           "nk_autotune_set", "nk_block_fused_noalloc", "nk_block_queue", "nk_block_ntk", "nk_set_wait_limit", "nk_pcg_set_rank",
+           "nk_pcg_solve"]
 
 
 class NkArch(ctypes.Structure):
@@ -111,6 +112,8 @@ def lib():
     L.nk_block_queue.argtypes = [c_void_p, POINTER(NkArch), POINTER(NkParams), c_int, POINTER(NkBlockTask),
                                  c_int, c_void_p]
     L.nk_block_queue.restype = c_int
+    L.nk_set_wait_limit.argtypes = [c_void_p, c_int64]
+    L.nk_set_wait_limit.restype = c_int
     L.nk_pcg_set_rank.argtypes = [c_void_p, c_int]
     L.nk_pcg_set_rank.restype = c_int
     L.nk_pcg_solve.argtypes = [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_int, c_double, c_int,

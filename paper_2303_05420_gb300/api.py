@@ -212,6 +212,10 @@ class Handle:
                                      c_void_p(_ptr(dsb2)), c_void_p(_stream()))
         self.check(st, "nk_block_backward")
 
+    def set_wait_limit(self, polls: int):
+        """Bound of the device-side waits of later calls (polls; < 0: defaults)."""
+        self.check(lib().nk_set_wait_limit(self._h, int(polls)), "nk_set_wait_limit")
+
     def pcg_set_rank(self, rank: int):
         """Rank of the pivoted Cholesky preconditioner (precond="pivchol")."""
         self.check(lib().nk_pcg_set_rank(self._h, int(rank)), "nk_pcg_set_rank")

@@ -891,8 +891,10 @@ cudaError_t dispatch_r8(const int c[3], bool bias, int variant, FusedParams& P, 
 // 32x32 blocks (R[b] in {64, 32}, largest first) in one persistent launch.
 bool tiled_supported(const int c[3]);
 size_t tiled_ws_bytes(const int c[3], const int* R, const int64_t* npairs, int n, int sm_count);
+// wait_limit: polls of a dependency wait before it gives up (NK_DEV_TIMEOUT).
 cudaError_t launch_tiled(const int c[3], bool bias, const int* R, const FusedParams* B, int n, int sm_count,
-                         void* ws, size_t ws_bytes, unsigned int* dstatus, cudaStream_t st);
+                         void* ws, size_t ws_bytes, unsigned int* dstatus, long long wait_limit,
+                         cudaStream_t st);
 
 }  // namespace nkf
 

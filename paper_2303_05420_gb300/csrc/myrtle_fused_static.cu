@@ -2,11 +2,10 @@
 // not allocate device memory.
 //
 // Some callers cannot call cudaMalloc at the point where they need a kernel
-// block: code recording a CUDA graph (allocation is not a capturable
-// operation), a serving process whose memory is reserved up front by its own
-// allocator and forbids new device allocations while it runs, or a plugin
-// whose host framework owns all device memory.  nk_block needs an nk_handle,
-// and nk_create allocates.  This entry point takes no handle and allocates
+// block: a serving process whose device memory is reserved up front by its
+// own allocator and which forbids new device allocations while it runs, or a
+// plugin whose host framework owns all device memory.  nk_block needs an
+// nk_handle, and nk_create allocates.  This entry point takes no handle and allocates
 // nothing: the only scratch the fused kernel needs -- two per-cluster slots
 // holding the global-average sum (8 bytes) and an arrival counter (4 bytes)
 // -- lives in a fixed file-scope device array below.
@@ -16,7 +15,10 @@
 // (stream-ordered memset) before the launch.  Two calls whose kernels overlap
 // on the GPU (different streams, no ordering between them) use the same
 // slots and race; order them on one stream or serialise them.
+#include <cuda.h>
 #include <stdio.h>
+
+#include <mutex>
 
 #include "myrtle_fused.cuh"
 
@@ -28,11 +30,68 @@ namespace {
 constexpr size_t kNoallocScratchBytes = 16384;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-// Device address of g_noalloc_scratch for each device ordinal, looked up on
-// the first call made with that device current.  In host code the array's
-// name is only a host-side stand-in, never a device address.
+// Device address of g_noalloc_scratch for each device ordinal, looked up
+// with that device current by the first call on it, and again whenever the
+// device's current context is not the one the address was taken in (after a
+// cudaDeviceReset the module is loaded anew and the array may move).
+// Contexts are told apart by their process-unique ids (cuCtxGetId).  In host
+// code the array's name is only a host-side stand-in, never a device
+// address.  The table is shared by all host threads, under g_mu.
 constexpr int kMaxDevices = 64;
-void* g_noalloc_addr[kMaxDevices];
+struct ScratchAddr {
+  unsigned long long ctx_id;  // 0: none recorded
+  void* addr;
+};
+std::mutex g_mu;
+ScratchAddr g_addr[kMaxDevices];
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Id of the calling thread's current context; 0 when there is none or the
+// driver does not tell (the caller then looks the address up every time).
+// Called with g_mu held.
+unsigned long long current_ctx_id() {
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool resolved = false;
+  if (!resolved) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_cur = (CtxGetCurrentFn)p;
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (CtxGetIdFn)p;
+    resolved = true;
+  }
+  if (!get_cur || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_cur(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// The scratch array's device address for device `dev` (current).
+cudaError_t scratch_address(int dev, void** out) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  unsigned long long id = current_ctx_id();
+  ScratchAddr& s = g_addr[dev];
+  if (id == 0 || s.ctx_id != id || !s.addr) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    // the lookup makes the device's primary context current if none was
+    id = current_ctx_id();
+    s.ctx_id = id;
+    s.addr = p;
+  }
+  *out = s.addr;
+  return cudaSuccess;
+}
 
 void set_err(char* buf, size_t len, const char* msg) {
   if (buf && len) snprintf(buf, len, "%s", msg);
@@ -86,15 +145,13 @@ extern "C" nk_status nk_block_fused_noalloc(const nk_arch* arch, const nk_params
     set_err(err_buf, err_len, "nk_block_fused_noalloc: device ordinal above 63");
     return NK_ERR_INVALID_ARG;
   }
-  // one-time set-up per device, with that device current
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) {
-      set_err(err_buf, err_len, cudaGetErrorString(e));
-      return NK_ERR_CUDA;
-    }
-    g_noalloc_addr[dev] = p;
+  // set-up once per device (and context), with that device current
+  void* scratch = nullptr;
+  e = scratch_address(dev, &scratch);
+  if (e != cudaSuccess) {
+    set_err(err_buf, err_len, cudaGetErrorString(e));
+    (void)cudaGetLastError();
+    return NK_ERR_CUDA;
   }
   // the launch uses at most one cluster per SM; reject a GPU whose clusters
   // would not fit the fixed array
@@ -107,7 +164,7 @@ extern "C" nk_status nk_block_fused_noalloc(const nk_arch* arch, const nk_params
     return NK_ERR_INVALID_ARG;
   }
   e = nk_launch_myrtle_fused(g, prm->sigma_w2, prm->sigma_b2, Xa, qsa, a0, a1, Xb, qsb, b0, b1, K, ldk,
-                             symmetric, sm, g_noalloc_addr[dev], kNoallocScratchBytes, 0,
+                             symmetric, sm, scratch, kNoallocScratchBytes, 0,
                              (cudaStream_t)stream);
   if (e != cudaSuccess) {
     set_err(err_buf, err_len, cudaGetErrorString(e));

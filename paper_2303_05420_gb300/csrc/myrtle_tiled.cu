@@ -38,7 +38,8 @@
 // Every wait is on an item claimed earlier, so the earliest unfinished item
 // never waits and the queue drains.  Waits are bounded: on a timeout the
 // kernel raises NK_DEV_TIMEOUT and an abort flag that makes every CTA stop
-// taking items.
+// taking items.  The bound is the handle's wait limit (nk_set_wait_limit;
+// 2^22 polls, seconds, by default).
 #include <algorithm>
 
 #include "myrtle_fused.cuh"
@@ -52,7 +53,6 @@ namespace tiled {
 // launches (97 KB each), so that one CTA's table staging and barriers
 // overlap the other's row streams.
 constexpr int MAX_WARPS = 16;
-constexpr long long WAIT_LIMIT = 1ll << 22;  // polls of ~0.25-1 us each
 
 // Stage-0 tiling at image side R: rows split into parts of four columns
 // (lane = part * TYW + t_y - ty0), as in the 32x32 super-plane kernel.
@@ -119,6 +119,7 @@ struct TiledParams {
   unsigned long long* next;       // item counter
   int* abort_flag;
   unsigned int* dstatus;
+  long long wait_limit;           // polls (~0.25-1 us each) before a wait gives up
 };
 
 __device__ __forceinline__ void red_v4(float* a, float x, float y, float z, float w) {
@@ -140,7 +141,7 @@ __device__ bool wait_geq(const TiledParams& Q, const int* p, int v) {
   for (long long it = 0;; ++it) {
     if (ld_acquire(p) >= v) return true;
     if (*(volatile int*)Q.abort_flag) return false;
-    if (it > WAIT_LIMIT) {
+    if (it > Q.wait_limit) {
       atomicOr(Q.dstatus, NK_DEV_TIMEOUT);
       atomicExch(Q.abort_flag, 1);
       return false;
@@ -717,7 +718,8 @@ size_t tiled_ws_bytes(const int c[3], const int* R, const int64_t* npairs, int n
 }
 
 cudaError_t launch_tiled(const int c[3], bool bias, const int* R, const FusedParams* B, int n, int sm_count,
-                         void* ws, size_t ws_bytes, unsigned int* dstatus, cudaStream_t st) {
+                         void* ws, size_t ws_bytes, unsigned int* dstatus, long long wait_limit,
+                         cudaStream_t st) {
   if (n < 1 || n > QUEUE_MAX || !tiled_supported(c)) return cudaErrorNotSupported;
   tiled::TiledParams Q = {};
   int64_t np[QUEUE_MAX];
@@ -738,6 +740,7 @@ cudaError_t launch_tiled(const int c[3], bool bias, const int* R, const FusedPar
   Q.G = Q.g0[n];
   Q.T0 = Q.f0[n];
   Q.dstatus = dstatus;
+  Q.wait_limit = wait_limit;
   const bool only32 = Q.G64 == 0;
 #define NK_T(a, b_)                                                                                   \
   if (c[0] == a && c[1] == b_) {                                                                      \

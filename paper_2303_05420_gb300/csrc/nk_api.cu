@@ -134,6 +134,15 @@ int fused_default_variant(const NkGeom& g) {
   return fused_variant_valid(g, NK_TILED_VARIANT) ? NK_TILED_VARIANT : 0;
 }
 
+// Bounds of the device waits of the two kernels that wait (nk_set_wait_limit).
+long long tiled_wait_limit(const nk_handle* h) {
+  return h->wait_polls < 0 ? NK_TILED_WAIT_DEFAULT : h->wait_polls;
+}
+uint32_t fc_wait_limit(const nk_handle* h) {
+  if (h->wait_polls < 0) return NK_FC_WAIT_DEFAULT;
+  return h->wait_polls > 0xFFFFFFFFll ? 0xFFFFFFFFu : (uint32_t)h->wait_polls;
+}
+
 // One fused (MIXED) block: the tiled form at 64x64 and for variant 3, the
 // super-plane cluster kernel otherwise.
 nk_status fused_block(nk_handle* h, const NkGeom& g, const nk_params* prm, const float* Xa, const float* qsa,
@@ -151,7 +160,7 @@ nk_status fused_block(nk_handle* h, const NkGeom& g, const nk_params* prm, const
     if (s != NK_OK) return s;
     h->launches += 1;
     return nk_cuda_check(h, nkf::launch_tiled(c, prm->sigma_b2 != 0.0, R, &P, 1, h->sm_count, ws, h->ws_bytes,
-                                              h->dstatus, st), what);
+                                              h->dstatus, tiled_wait_limit(h), st), what);
   }
   h->launches += 1;
   return nk_cuda_check(h, nk_launch_myrtle_fused(g, prm->sigma_w2, prm->sigma_b2, Xa, qsa, a0, a1, Xb, qsb, b0,
@@ -208,6 +217,7 @@ nk_status nk_create(nk_handle** out) {
   nk_handle* h = new nk_handle();
   memset(h, 0, sizeof(*h));
   h->pcg_rank = 100;
+  h->wait_polls = -1;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
   if (e == cudaSuccess) e = cudaMalloc(&h->dstatus, sizeof(unsigned int));
@@ -451,7 +461,7 @@ nk_status nk_block_queue(nk_handle* h, const nk_arch* arch, const nk_params* prm
     if (s != NK_OK) return s;
     h->launches += 1;
     cudaError_t e = nkf::launch_tiled(c, prm->sigma_b2 != 0.0, R, B, n, h->sm_count, ws, h->ws_bytes, h->dstatus,
-                                      (cudaStream_t)stream);
+                                      tiled_wait_limit(h), (cudaStream_t)stream);
     return nk_cuda_check(h, e, "nk_block_queue tiled launch");
   }
   nkf::QueueParams Q = {};
@@ -529,7 +539,8 @@ nk_status nk_fc_block(nk_handle* h, int depth, const nk_params* prm, const float
   nk_status s = nk_workspace(h, nk_fc_ws_bytes(a1 - a0, b1 - b0, d, depth), &ws);
   if (s != NK_OK) return s;
   cudaError_t e = nk_launch_fc_block(depth, prm->sigma_w2, prm->sigma_b2, Xa, a0, a1, Xb, b0, b1, d, K, ldk,
-                                     symmetric, ws, h->sm_count, h->dstatus, (cudaStream_t)stream, &h->launches);
+                                     symmetric, ws, h->sm_count, h->dstatus, fc_wait_limit(h), (cudaStream_t)stream,
+                                     &h->launches);
   if (e == cudaErrorInvalidValue) return nk_fail(h, NK_ERR_CUDA, "nk_fc_block: tensor map encoding failed");
   return nk_cuda_check(h, e, "nk_fc_block");
 }
@@ -627,6 +638,12 @@ nk_status nk_autotune_set(nk_handle* h, const nk_arch* arch, const nk_params* pr
   int key[8];
   tune_key(g, prm->sigma_b2 != 0.0, key);
   tune_store(h, key, variant);
+  return NK_OK;
+}
+
+nk_status nk_set_wait_limit(nk_handle* h, int64_t polls) {
+  if (!h) return NK_ERR_INVALID_ARG;
+  h->wait_polls = polls < 0 ? -1 : (long long)polls;
   return NK_OK;
 }
 

@@ -55,7 +55,14 @@ struct nk_handle {
   void* pcg_ws;
   size_t pcg_bytes;
   int pcg_rank;            // pivoted Cholesky preconditioner rank
+  long long wait_polls;    // bound of device waits (nk_set_wait_limit); < 0: defaults
 };
+
+// Default bounds of the device-side waits: polls of the tiled kernel's
+// dependency waits (each about 0.25-1 us) and of the FC kernel's mbarrier
+// waits (each a try_wait of up to a few us).
+#define NK_TILED_WAIT_DEFAULT (1ll << 22)
+#define NK_FC_WAIT_DEFAULT (1u << 26)
 
 nk_status nk_fail(nk_handle* h, nk_status s, const char* fmt, ...);
 nk_status nk_cuda_check(nk_handle* h, cudaError_t e, const char* what);
@@ -91,7 +98,8 @@ bool nk_myrtle_fused_supported(const NkGeom& g);
 size_t nk_fc_ws_bytes(int64_t na, int64_t nb, int d, int depth);
 cudaError_t nk_launch_fc_block(int depth, double sw2, double sb2, const float* Xa, int64_t a0, int64_t a1,
                                const float* Xb, int64_t b0, int64_t b1, int d, float* K, int64_t ldk, int sym,
-                               void* ws, int sm, unsigned int* dstatus, cudaStream_t st, int64_t* launches);
+                               void* ws, int sm, unsigned int* dstatus, uint32_t wait_limit, cudaStream_t st,
+                               int64_t* launches);
 
 // Adjoint of the Myrtle block (layer-wise, FP32 or FP64 pixel-pair tensors).
 size_t nk_backward_ws_bytes(const NkGeom& g, int fp64, int64_t npairs, int64_t na, int64_t nb, int sym,

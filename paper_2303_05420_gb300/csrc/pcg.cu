@@ -11,7 +11,9 @@
 // (row-split partials reduced in FP64 by the next kernel).  CG scalars
 // (alpha, beta, r.z, p.Ap) are FP64.  NK_PREC_MIXED wraps FP32-matvec inner
 // solves in an FP64 iterative-refinement loop whose true residual is formed
-// with FP64 products and sums.
+// in double-FP32 arithmetic (k_matvec_df: exact FP32 products and two-float
+// TwoSum accumulation, about 2^-48 relative per step) on the FP32 units;
+// PLAIN_FP64 keeps native FP64 products throughout.
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>

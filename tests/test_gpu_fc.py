@@ -121,3 +121,73 @@ def test_fc3_fullsize_properties_and_pcg(h, fc_full):
     assert rel_true.max() <= 1e-6
     assert np.allclose(rel_true, rel, rtol=1e-3, atol=1e-9)
     assert abs(lam - 1e-4 * float(torch.diagonal(Ktr).double().sum()) / 50000) <= 1e-10 * lam
+
+
+def _near_copies(n, d, eps, seed):
+    """Rows x and x + eps z (both scaled to norm sqrt(d)): what data
+    augmentation produces, and the case where the Gram is a sum of 3d
+    products of one sign."""
+    x = nkdata.fc_rows(n, d, seed=seed)
+    z = np.random.default_rng(seed + 100).standard_normal((n, d))
+    y = x + eps * z
+    y *= np.sqrt(d) / np.linalg.norm(y, axis=1, keepdims=True)
+    return x.astype(np.float32), y.astype(np.float32)
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-2])
+def test_fc3_near_duplicate_rows(h, eps):
+    """K(x, x + eps z) at d = 3072 within 1e-5 of the oracle: the tensor
+    core's accumulator rounds toward zero, and for near copies every product
+    has one sign; the kernel's order of K' and its two chunk accumulators keep
+    the drift under the bar.  Also a symmetric block over [x; x + eps z], where
+    the near copies sit off the diagonal."""
+    xa, xb = _near_copies(256, 3072, eps, seed=5)
+    Xa, Xb = torch.tensor(xa, device="cuda"), torch.tensor(xb, device="cuda")
+    K = h.fc_block(Xa, Xb, 2.0, 0.01, depth=3)
+    h.sync_status()
+    want = oracle.fc_nngp(xa.astype(np.float64), xb.astype(np.float64), 2.0, 0.01, depth=3).numpy()
+    got = K.double().cpu().numpy()
+    assert _maxrel(got, want) <= 1e-5
+    # the near-copy pairs themselves (the diagonal of this block)
+    assert float(np.max(np.abs(np.diag(got) - np.diag(want)) / np.abs(np.diag(want)))) <= 1e-5
+    xs = np.concatenate([xa[:128], xb[:128]])
+    Xs = torch.tensor(xs, device="cuda")
+    Ks = h.fc_block(Xs, Xs, 2.0, 0.01, depth=3, symmetric=True)
+    h.sync_status()
+    wants = oracle.fc_nngp(xs.astype(np.float64), xs.astype(np.float64), 2.0, 0.01, depth=3).numpy()
+    assert _maxrel(Ks.double().cpu().numpy(), wants) <= 1e-5
+
+
+def test_fc_gram_near_duplicates_depth0(h):
+    """depth 0 exposes the Gram itself: x . x' / d for near copies within
+    5e-6 relative (the whole sum drifts one way)."""
+    xa, xb = _near_copies(200, 3072, 1e-3, seed=6)
+    K = h.fc_block(torch.tensor(xa, device="cuda"), torch.tensor(xb, device="cuda"), 1.0, 0.0, depth=0)
+    h.sync_status()
+    want = xa.astype(np.float64) @ xb.astype(np.float64).T / 3072
+    got = K.double().cpu().numpy()
+    d = np.abs(np.diag(got) - np.diag(want)) / np.abs(np.diag(want))
+    assert float(d.max()) <= 5e-6, float(d.max())
+
+
+def test_fc_wait_limit_runs_out_and_the_handle_recovers(h):
+    """A wait limit of 0 polls makes the first unmet mbarrier wait of the FC
+    kernel give up: the launch returns, nk_sync_status reports
+    NK_ERR_TIMEOUT, and with the default limit restored the next call on the
+    same handle is correct.  No wait is left unbounded."""
+    from paper_2303_05420_gb300._lib import NK_ERR_TIMEOUT, NkError
+
+    x = nkdata.fc_rows(300, 3072, seed=4).astype(np.float32)
+    X = torch.tensor(x, device="cuda")
+    h.set_wait_limit(0)
+    try:
+        h.fc_block(X, X, 2.0, 0.01, depth=3, symmetric=True)
+        with pytest.raises(NkError) as ei:
+            h.sync_status()
+        assert ei.value.status == NK_ERR_TIMEOUT
+    finally:
+        h.set_wait_limit(-1)
+    K = h.fc_block(X, X, 2.0, 0.01, depth=3, symmetric=True)
+    h.sync_status()
+    want = oracle.fc_nngp(x.astype(np.float64), x.astype(np.float64), 2.0, 0.01, depth=3).numpy()
+    assert _maxrel(K.double().cpu().numpy(), want) <= 1e-5

@@ -98,3 +98,49 @@ def test_fullsize_pcg_pivchol(headline):
     assert rel_true.max() <= 1e-6
     _, it_p64, _ = h.pcg_solve(Ktr, Y, -1e-4, precond="pivchol", prec="plain_fp64", tol=1e-6, maxit=20000)
     assert it_p64 < it_j / 2, (it_p64, it_j)
+
+
+def _sym_pair(idx, n):
+    """(i, j) of upper-triangle pair number idx in the row-major order the
+    kernels walk (row i holds pairs (i, i), (i, i + 1), ..., (i, n - 1))."""
+    i = 0
+    while idx >= n - i:
+        idx -= n - i
+        i += 1
+    return i, i + idx
+
+
+def test_fullsize_contiguous_subblocks(headline):
+    """Contiguous 16 x 16 sub-blocks of the full-size blocks, entry by entry:
+    one crossing the train block's diagonal at its end, one in its interior,
+    and the last rows and columns of the test block."""
+    h, x, p, Ktr, Kte = headline
+    arch = oracle.Arch((2, 1, 0))
+    xd = x.astype(np.float64)
+    Kt, Ke = Ktr.double().cpu().numpy(), Kte.double().cpu().numpy()
+    cases = [(Kt, slice(2032, 2048), slice(2032, 2048), xd[2032:2048], xd[2032:2048]),
+             (Kt, slice(1000, 1016), slice(1100, 1116), xd[1000:1016], xd[1100:1116]),
+             (Ke, slice(496, 512), slice(2032, 2048), xd[2048 + 496:2560], xd[2032:2048])]
+    for K, ri, cj, xa, xb in cases:
+        want = oracle.myrtle_block(arch, 2.0, 0.0, xa, xb).numpy()
+        got = K[ri, cj]
+        err = float(np.max(np.abs(got - want) / np.abs(want)))
+        assert err <= 1e-5, (ri, cj, err)
+
+
+def test_fullsize_item_order_positions(headline):
+    """Pairs at the start, middle and end of the train block's item order,
+    and pairs one and two slot-ring lengths apart (the 32x32 launch of two
+    CTAs per SM keeps 154 slots; pairs g and g + 154 share one)."""
+    h, x, p, Ktr, Kte = headline
+    arch = oracle.Arch((2, 1, 0))
+    xs = torch.tensor(x.astype(np.float64))
+    G = 2048 * 2049 // 2
+    idx = [0, 1, 2, G // 2, G // 2 + 1, G - 2, G - 1, 100000, 100000 + 154, 100000 + 308]
+    Kt = Ktr.cpu().numpy()
+    for g in idx:
+        i, j = _sym_pair(g, 2048)
+        qi = oracle.myrtle_self_q(arch, 2.0, 0.0, xs[i])
+        qj = oracle.myrtle_self_q(arch, 2.0, 0.0, xs[j])
+        want, _, _ = oracle.kernels.myrtle_layers_pair(arch, 2.0, 0.0, xs[i], xs[j], qi, qj)
+        assert abs(float(Kt[i, j]) - float(want)) <= 1e-5 * abs(float(want)), (g, i, j, Kt[i, j], float(want))

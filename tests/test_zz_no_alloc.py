@@ -1,8 +1,9 @@
 """The allocation-free kernel-block entry point against nk_block.
 
 nk_block_fused_noalloc serves callers that cannot allocate device memory when
-they need a block (graph capture, pre-reserved memory, host-owned memory):
-it takes no handle and keeps its scratch in a fixed device array.  This test
+they need a block (a process whose device memory is reserved up front by its
+own allocator, a plugin whose host framework owns all device memory): it
+takes no handle and keeps its scratch in a fixed device array.  This test
 calls it through the C ABI twice in a row (the second call reuses the array
 the first left behind) and checks both results against nk_block's fused path
 at the kernel-entry tolerance.  It lives in a file collected last, and works
