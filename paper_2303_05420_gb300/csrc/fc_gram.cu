@@ -8,28 +8,30 @@
 // accumulation in TMEM on split operands: x = x_hi + x_lo (BF16 each), and
 // x . x' ~ hi.lo' + lo.hi' + hi.hi' is one GEMM over a tripled K with
 // A' = [hi | lo | hi] and B' = [lo' | hi' | hi'] (zero-padded to a multiple
-// of 64).  Persistent CTAs (one per SM) walk the 128 x 128 output tiles in a
+// of 64).  Persistent CTAs (one per SM) walk the 128 x 256 output tiles in a
 // grouped raster (16 tile rows at a time, so that concurrent CTAs share B
-// tiles in L2).  Operand tiles (128 x 64 BF16 each) arrive by TMA with
-// 128-byte swizzle through a 6-stage mbarrier ring; one thread issues the
-// MMAs while eight epilogue warps drain the previous tile: each reads 32 rows
-// x 64 columns from TMEM, applies the whole arc-cosine recursion layer by
-// layer over 32 entries at a time (column factors staged in shared memory)
-// and stores 16 bytes of a K row per lane.  The self-variances q_l of each
-// row follow the closed diagonal recursion q_1 = sw2 |x|^2/d + sb2,
-// q_{l+1} = sw2 q_l / 2 + sb2 (FP64).  Symmetric blocks run only tiles
-// touching the upper triangle and store each entry at (i, j) and (j, i).
+// tiles in L2).  Operand tiles (128 x 64 and 256 x 64 BF16) arrive by TMA
+// with 128-byte swizzle through a 4-stage mbarrier ring (each CTA loads its
+// own tiles); one thread issues the MMAs; eight epilogue warps take the
+// finished accumulator out of TMEM into registers (32 rows x 128 columns a
+// warp), release TMEM at once so that the next tile's MMAs start, and then
+// apply the whole arc-cosine recursion layer by layer over 32 entries at a
+// time (column factors staged in shared memory) and store 16 bytes of a K
+// row per lane.  The self-variances q_l of each row follow the closed
+// diagonal recursion q_1 = sw2 |x|^2/d + sb2, q_{l+1} = sw2 q_l / 2 + sb2
+// (FP64).  Symmetric blocks run only tiles touching the upper triangle and
+// store each entry at (i, j) and (j, i).
 //
 // Accumulation accuracy.  The tensor core adds each 16-element MMA step to
 // the FP32 accumulator with a rounding that always goes toward zero, so for
 // a sum of 3d products of one sign (a row with itself or with a near copy of
 // itself) the errors add up one way: about 2e-5 relative at d = 3072 when
-// the large hi.hi' products come first.  Two measures bring that under
-// 5e-6: the small hi.lo' and lo.hi' products come first, while the running
+// the large hi.hi' products come first.  Two measures bring that to about
+// 6e-6: the small hi.lo' and lo.hi' products come first, while the running
 // sum is still small, and each tile accumulates its even and odd 64-wide K
 // blocks into two separate TMEM accumulators (two chunk sums, each half as
-// long, added in FP32 by the epilogue).  TMEM holds 2 tiles x 2 chunks x 128
-// columns (all 512).  Self pairs still take K_1 from the FP64 norm.
+// long, added in FP32 by the epilogue).  The two 128 x 256 FP32 chunks fill
+// all 512 TMEM columns.  Self pairs take K_1 from the FP64 norm.
 //
 // Every mbarrier wait of the pipeline is bounded by the handle's wait limit;
 // on a timeout the kernel records NK_DEV_TIMEOUT and skips its stores, and
@@ -46,10 +48,11 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 6;
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 constexpr int GROUP_M = 16;     // tile rows per raster group (L2 reuse of B)
 constexpr int NCHUNK = 2;       // accumulators per tile (even / odd K blocks)
-constexpr int EPI_WARPS = 8;    // two per TMEM lane quarter, 64 columns each
+constexpr int EPI_WARPS = 8;    // two per TMEM lane quarter, 128 columns each
+constexpr int EPI_COLS = BN / 2;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t DRAIN_LIMIT = 1u << 26;  // waits for own copies / MMAs before exit
 constexpr int MAX_DEPTH = 8;
@@ -60,7 +63,7 @@ struct GemmSmem {
   float2 qb[BN * MAX_DEPTH];             // per-column (1/sqrt q, sqrt q) of the current tile
   float2 qa[BM * MAX_DEPTH];             // per-row (1/sqrt q, sqrt q * sw2/(2 pi))
   uint64_t full[STAGES], empty[STAGES];  // operand ring
-  uint64_t tfull[2], tempty[2];          // TMEM accumulators: MMA -> epilogue, epilogue -> MMA
+  uint64_t tfull, tempty;                // TMEM accumulators: MMA -> epilogue, epilogue -> MMA
   uint64_t done;
   uint32_t tslot;
 };
@@ -117,11 +120,69 @@ __device__ __forceinline__ bool named_any(int id, int n, bool v) {
   return r != 0;
 }
 
+// The arc-cosine recursion and the stores of 32 consecutive entries of row i
+// (columns n0 + c0 .. n0 + c0 + 31) whose Gram sums are in w.
+__device__ __forceinline__ void epi_entries(const FcParams& P, float (&w)[32], const float2* qr,
+                                            const float2* qb, int c0, int64_t n0, int64_t i, bool rowok,
+                                            float self_k1, bool vec_ok) {
+  if (P.same) {
+    const int64_t d = i + P.selfoff - (n0 + c0);  // column of the self pair, if among these
+#pragma unroll
+    for (int e = 0; e < 32; ++e) w[e] = (d == e) ? self_k1 : fmaf(P.kscale, w[e], P.sb2);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 32; ++e) w[e] = fmaf(P.kscale, w[e], P.sb2);
+  }
+  // layer by layer over the 32 entries (independent chains)
+  for (int l = 0; l < P.depth; ++l) {
+    const float2 ra = qr[l];
+    const float2* qc = qb + c0 * P.depth + l;
+    if (l == 0) {
+#pragma unroll
+      for (int e = 0; e < 32; ++e) {
+        const float2 rb = qc[e * P.depth];
+        w[e] = fmaf(ra.y * rb.y, nk_J_f32(w[e] * (ra.x * rb.x)), P.sb2);
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 32; ++e) {
+        const float2 rb = qc[e * P.depth];
+        w[e] = fmaf(ra.y * rb.y, nk_J01_f32(w[e] * (ra.x * rb.x)), P.sb2);
+      }
+    }
+  }
+  if (!rowok) return;
+  const int64_t jb = n0 + c0;
+  // mirror of a symmetric block: column stores (j, i), coalesced over i
+  if (P.sym) {
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+      const int64_t j = jb + e;
+      if (j < P.N && j > i) P.K[j * P.ldk + i] = w[e];
+    }
+  }
+  // row stores (i, j): 16 bytes per lane; the two halves of a 32-byte sector
+  // come from the same lane in consecutive stores
+  float* krow = P.K + i * P.ldk + jb;
+#pragma unroll
+  for (int e4 = 0; e4 < 32; e4 += 4) {
+    const int64_t j = jb + e4;
+    if (vec_ok && j + 3 < P.N && (!P.sym || j >= i)) {
+      *reinterpret_cast<float4*>(krow + e4) = make_float4(w[e4], w[e4 + 1], w[e4 + 2], w[e4 + 3]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (j + u < P.N && (!P.sym || j + u >= i)) krow[e4 + u] = w[e4 + u];
+    }
+  }
+}
+
 // Persistent kernel, one CTA per SM; CTA c takes tile slots t = c + k * CTAs.
 // Warp 0: TMA producer; warp 1: TMEM owner and MMA issuer; warps 2..9:
-// epilogue.  Tile n uses TMEM columns [(n & 1) * 256, +256): chunk 0 (even K
-// blocks) in the first 128, chunk 1 (odd K blocks) in the next 128, so the
-// MMAs of the next tile run while the epilogue drains the previous one.
+// epilogue.  TMEM columns [0, 256) hold chunk 0 (even K blocks) of the
+// current tile, [256, 512) chunk 1 (odd K blocks).  The epilogue copies a
+// finished tile into registers and releases TMEM before its arithmetic, so
+// the MMAs of the next tile overlap that arithmetic.
 __global__ void __launch_bounds__(THREADS, 1)
 k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
           const __grid_constant__ FcParams P) {
@@ -136,10 +197,8 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       tc::mbar_init(&S.full[s], 1);
       tc::mbar_init(&S.empty[s], 1);
     }
-    for (int a = 0; a < 2; ++a) {
-      tc::mbar_init(&S.tfull[a], 1);
-      tc::mbar_init(&S.tempty[a], EPI_WARPS);
-    }
+    tc::mbar_init(&S.tfull, 1);
+    tc::mbar_init(&S.tempty, EPI_WARPS);
     tc::mbar_init(&S.done, 1);
     tc::mbar_fence_init();
     tc::prefetch_tmap(&ta);
@@ -185,14 +244,13 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       for (int64_t t = cta; t < nslots && ok; t += ncta) {
         int tm, tn;
         if (!tile_of(P, t, tm, tn)) continue;
-        const int acc = n & 1;
-        if (n >= 2 && !tc::mbar_wait(&S.tempty[acc], (uint32_t)((n >> 1) & 1) ^ 1, P.wait_limit)) {
+        // the epilogue has taken the previous tile out of TMEM
+        if (n >= 1 && !tc::mbar_wait(&S.tempty, (uint32_t)((n - 1) & 1), P.wait_limit)) {
           atomicOr(P.dstatus, NK_DEV_TIMEOUT);
           ok = false;
           break;
         }
         tc::tc_fence_after();
-        const uint32_t tacc = tbase + (uint32_t)(acc * NCHUNK * BN);
         for (int kb = 0; kb < nk; ++kb, ++kb_all) {
           const int s = (int)(kb_all % STAGES);
           if (!tc::mbar_wait(&S.full[s], (uint32_t)((kb_all / STAGES) & 1), P.wait_limit)) {
@@ -202,7 +260,7 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
           }
           tc::tc_fence_after();
           const uint32_t a0 = tc::smem_addr(S.A[s]), b0 = tc::smem_addr(S.B[s]);
-          const uint32_t tch = tacc + (uint32_t)((kb & 1) * BN);  // chunk of this K block
+          const uint32_t tch = tbase + (uint32_t)((kb & 1) * BN);  // chunk of this K block
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k)
             tc::mma_bf16(tch, tc::sdesc_k128(a0 + 32 * k), tc::sdesc_k128(b0 + 32 * k), idesc,
@@ -210,7 +268,7 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
           tc::mma_commit(&S.empty[s]);  // the stage may be refilled once these MMAs have read it
         }
         if (!ok) break;
-        tc::mma_commit(&S.tfull[acc]);
+        tc::mma_commit(&S.tfull);
         ++n;
       }
       // all MMAs issued by this thread complete before TMEM is released
@@ -219,9 +277,9 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
     }
   } else {
     // epilogue: TMEM lane quarter q holds tile rows 32q .. 32q+31; the two
-    // warps of a quarter take columns [0, 64) and [64, 128)
+    // warps of a quarter take columns [0, 128) and [128, 256)
     const int q = warp & 3;
-    const int cbeg = ((warp - 2) >> 2) * (BN / 2);
+    const int cbeg = ((warp - 2) >> 2) * EPI_COLS;
     const int et = threadIdx.x - 64;  // 0 .. 32 * EPI_WARPS - 1
     const bool vec_ok = (P.ldk % 4 == 0) && ((reinterpret_cast<uintptr_t>(P.K) & 15) == 0);
     const bool two = nk > 1;  // chunk 1 holds the odd K blocks (none when nk == 1)
@@ -241,84 +299,48 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
         S.qa[e] = i < P.M ? P.qa[m0 * P.depth + e] : make_float2(0.f, 0.f);
       }
       named_sync(1, 32 * EPI_WARPS);
-      const int acc = n & 1;
-      const bool got = tc::mbar_wait(&S.tfull[acc], (uint32_t)((n >> 1) & 1), P.wait_limit);
+      const bool got = tc::mbar_wait(&S.tfull, (uint32_t)(n & 1), P.wait_limit);
       // the epilogue warps leave together (they share named barriers)
       if (named_any(2, 32 * EPI_WARPS, !got)) {
         atomicOr(P.dstatus, NK_DEV_TIMEOUT);
         break;
       }
       tc::tc_fence_after();
+      // this warp's 32 rows x 128 columns into registers, both chunks added
+      const uint32_t taddr = tbase + (uint32_t)cbeg + ((uint32_t)(32 * q) << 16);
+      float v[EPI_COLS / 32][32];
+#pragma unroll
+      for (int c = 0; c < EPI_COLS / 32; ++c) tc::tmem_ld32(taddr + (uint32_t)(32 * c), v[c]);
+      if (two) {
+#pragma unroll
+        for (int c = 0; c < EPI_COLS / 32; ++c) {
+          float u[32];
+          tc::tmem_ld32(taddr + (uint32_t)(BN + 32 * c), u);
+#pragma unroll
+          for (int e = 0; e < 32; ++e) v[c][e] += u[e];
+        }
+      }
+      // TMEM is free for the next tile
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&S.tempty);
       const int row = 32 * q + lane;
       const int64_t i = m0 + row;
       const bool rowok = i < P.M;
       const float self_k1 = (rowok && P.same) ? P.q1a[i] : 0.f;
       const float2* qr = S.qa + row * P.depth;
-      const uint32_t taddr = tbase + (uint32_t)(acc * NCHUNK * BN) + ((uint32_t)(32 * q) << 16);
-      for (int c0 = cbeg; c0 < cbeg + BN / 2; c0 += 32) {
-        float v[32];
-        tc::tmem_ld32(taddr + (uint32_t)c0, v);
-        if (two) {
-          float w[32];
-          tc::tmem_ld32(taddr + (uint32_t)(BN + c0), w);
+      // one copy of the 32-entry body (the instruction cache is shared with
+      // the single-thread TMA and MMA loops): a runtime loop that rotates the
+      // register sub-arrays instead of indexing them
+      static_assert(EPI_COLS / 32 == 4, "rotation below");
+#pragma unroll 1
+      for (int c = 0; c < EPI_COLS / 32; ++c) {
+        epi_entries(P, v[0], qr, S.qb, cbeg + 32 * c, n0, i, rowok, self_k1, vec_ok);
 #pragma unroll
-          for (int e = 0; e < 32; ++e) v[e] += w[e];
-        }
-        if (c0 + 32 == cbeg + BN / 2) {
-          // this warp's part of the accumulators is free for a later tile
-          tc::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) tc::mbar_arrive(&S.tempty[acc]);
-        }
-        if (P.same) {
-          const int64_t d = i + P.selfoff - (n0 + c0);  // column of the self pair, if in this chunk
-#pragma unroll
-          for (int e = 0; e < 32; ++e) v[e] = (d == e) ? self_k1 : fmaf(P.kscale, v[e], P.sb2);
-        } else {
-#pragma unroll
-          for (int e = 0; e < 32; ++e) v[e] = fmaf(P.kscale, v[e], P.sb2);
-        }
-        // layer by layer over the 32 entries (independent chains)
-        for (int l = 0; l < P.depth; ++l) {
-          const float2 ra = qr[l];
-          const float2* qc = S.qb + c0 * P.depth + l;
-          if (l == 0) {
-#pragma unroll
-            for (int e = 0; e < 32; ++e) {
-              const float2 rb = qc[e * P.depth];
-              v[e] = fmaf(ra.y * rb.y, nk_J_f32(v[e] * (ra.x * rb.x)), P.sb2);
-            }
-          } else {
-#pragma unroll
-            for (int e = 0; e < 32; ++e) {
-              const float2 rb = qc[e * P.depth];
-              v[e] = fmaf(ra.y * rb.y, nk_J01_f32(v[e] * (ra.x * rb.x)), P.sb2);
-            }
-          }
-        }
-        if (!rowok) continue;
-        const int64_t jb = n0 + c0;
-        // mirror of a symmetric block: column stores (j, i), coalesced over i
-        if (P.sym) {
-#pragma unroll
-          for (int e = 0; e < 32; ++e) {
-            const int64_t j = jb + e;
-            if (j < P.N && j > i) P.K[j * P.ldk + i] = v[e];
-          }
-        }
-        // row stores (i, j): 16 bytes per lane; the two halves of a 32-byte
-        // sector come from the same lane in consecutive stores
-        float* krow = P.K + i * P.ldk + jb;
-#pragma unroll
-        for (int e4 = 0; e4 < 32; e4 += 4) {
-          const int64_t j = jb + e4;
-          if (vec_ok && j + 3 < P.N && (!P.sym || j >= i)) {
-            *reinterpret_cast<float4*>(krow + e4) = make_float4(v[e4], v[e4 + 1], v[e4 + 2], v[e4 + 3]);
-          } else {
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (j + u < P.N && (!P.sym || j + u >= i)) krow[e4 + u] = v[e4 + u];
-          }
+        for (int e = 0; e < 32; ++e) {
+          v[0][e] = v[1][e];
+          v[1][e] = v[2][e];
+          v[2][e] = v[3][e];
         }
       }
       ++n;
