@@ -55,19 +55,32 @@ typedef enum {
  *  NK_PREC_PLAIN_FP64 the same in FP64; K is double*. */
 typedef enum { NK_PREC_PLAIN_FP64 = 0, NK_PREC_PLAIN_FP32 = 1, NK_PREC_MIXED = 2 } nk_prec;
 
-enum { NK_ACT_RELU = 0, NK_ACT_IDENTITY = 1 /* linear network, tests only */ };
+/* Activations: the ReLU of the Myrtle listings (Appendix A), the identity
+ * (a linear network, tests only) and Erf, one of the activations of the
+ * paper's architecture search (Appendix on tuning the Myrtle architecture;
+ * stax.Erf also serves its graph-network listing). */
+enum { NK_ACT_RELU = 0, NK_ACT_IDENTITY = 1, NK_ACT_ERF = 2 };
+/* Normalisation between each conv and its activation: none (the Myrtle
+ * listings) or the tuned Myrtle listing's LayerNorm over pixels and channels
+ * of each image (stax.LayerNorm(axis=(1, 2, 3))). */
+enum { NK_NORM_NONE = 0, NK_NORM_LAYER = 1 };
 enum { NK_PRECOND_NONE = 0, NK_PRECOND_JACOBI = 1, NK_PRECOND_PIVCHOL = 2 };
 
 /* Myrtle-family architecture (Appendix A, Myrtle listing): n_stages stages;
- * stage s holds convs[s] layers of conv(filter x filter, SAME) + activation;
- * a 2x2 stride-2 average pool sits between consecutive stages; the last
- * stage ends in a global average pool and a Dense readout.
- * Myrtle-10 = {3, {3,3,3}}; the Myrtle-5 of the benchmark = {3, {2,1,0}}. */
+ * stage s holds convs[s] layers of conv(filter x filter, SAME) [+ norm] +
+ * activation; a 2x2 stride-2 average pool sits between consecutive stages;
+ * the last stage ends in a global average pool and a Dense readout.
+ * Myrtle-10 = {3, {3,3,3}}; the Myrtle-5 of the benchmark = {3, {2,1,0}}.
+ * With norm = NK_NORM_LAYER each layer's covariance is divided by
+ * sqrt(m m'), m = the pixel mean of that layer's self-variances of each
+ * image (the infinite-width limit of a LayerNorm over pixels and channels),
+ * and the activation sees the self-variances q / m. */
 typedef struct {
   int n_stages;   /* 1..4 */
   int convs[4];   /* convs[0] >= 1 */
   int filter;     /* 3 (paper) or 1 */
-  int activation; /* NK_ACT_RELU or NK_ACT_IDENTITY */
+  int activation; /* NK_ACT_RELU, NK_ACT_ERF or NK_ACT_IDENTITY */
+  int norm;       /* NK_NORM_NONE or NK_NORM_LAYER (not with NK_ACT_IDENTITY) */
 } nk_arch;
 
 /* sigma_w^2 = W_std^2 and sigma_b^2 = b_std^2 of every Conv / Dense layer
@@ -89,8 +102,9 @@ nk_status nk_last_error(nk_handle* h, char* buf, size_t len);
 nk_status nk_sync_status(nk_handle* h, void* stream);
 
 /* Number of per-image self-variance entries: the sum over activation layers
- * l of H_l * W_l (H_l, W_l the resolution of layer l's stage).  Returns -1 for
- * an invalid architecture or size. */
+ * l of H_l * W_l (H_l, W_l the resolution of layer l's stage), plus one
+ * entry per layer (its LayerNorm divisor m_l) with NK_NORM_LAYER.  Returns -1
+ * for an invalid architecture or size. */
 int64_t nk_q_size(const nk_arch* arch, int H, int W);
 
 /* Number of CUDA kernels launched through this handle since nk_create (a
@@ -101,14 +115,23 @@ int64_t nk_launch_count(nk_handle* h);
 double nk_last_lambda(nk_handle* h);
 
 /* Per-pixel self-variances q_l(p) = K_l(p, p; x, x) for every image and every
- * activation layer (needed by the ReLU map, stax.Relu in Appendix A).
+ * activation layer (needed by the activation maps, stax.Relu / stax.Erf in
+ * Appendix A), q_l being the conv's output before any LayerNorm.
  *   X   [n][H][W][C] float32 (device)
- *   qd  [n][nq] float64 (device, out): q, layer-major then row-major pixels
- *   qs  [n][nq][2] float32 (device, out, may be NULL): (1/sqrt(q), sqrt(q)),
- *       (0, 0) where q == 0
+ *   qd  [n][nq] float64 (device, out): q, layer-major then row-major pixels;
+ *       with NK_NORM_LAYER the last n_layers entries of a row are the
+ *       divisors m_l = mean_p q_l(p)
+ *   qs  [n][nq][2] float32 (device, out, may be NULL): the per-pixel factors
+ *       (a, b) with which every kernel evaluates the activation of a pixel
+ *       pair from its un-normalised covariance K:
+ *         ReLU: a = 1/sqrt(q), b = sqrt(q / m): Kt = b b' J(K a a') / (2 pi),
+ *               (0, 0) where q == 0;
+ *         Erf:  a = sqrt(2 / (m + 2 q)), b = 1: Kt = b b' (2/pi) asin(K a a');
+ *       m = 1 without a norm.
  * with nq = nk_q_size(arch, H, W).  Computed in FP64 from the banded self
  * covariance K_l(p, p + D; x, x), |D| <= r_s per stage (r = 0 at the last
- * stage with an activation, r_prev = 2 r + 1 across each pool). */
+ * stage with an activation, r_prev = 2 r + 1 across each pool).  m <= 0 (an
+ * all-zero representation under a LayerNorm) is NK_ERR_NUMERICAL. */
 nk_status nk_self_diag(nk_handle* h, const nk_arch* arch, const nk_params* prm,
                        const float* X, int64_t n, int H, int W, int C,
                        double* qd, float* qs, void* stream);
@@ -125,10 +148,13 @@ nk_status nk_self_diag(nk_handle* h, const nk_arch* arch, const nk_params* prm,
  *   symmetric   nonzero when Xa == Xb and [a0,a1) == [b0,b1): only i <= j is
  *               evaluated and mirrored.
  * The Myrtle readout is K = sigma_w2 * mean_{P,P'} Kt(P, P') + sigma_b2
- * (GlobalAvgPool then Dense).  MIXED requires filter 3, ReLU, C <= 3 and
- * zero-conv stages only at the end, with H = W in {8, 16, 32} and stage
+ * (GlobalAvgPool then Dense).  MIXED requires filter 3, C <= 3 and
+ * zero-conv stages only at the end; with ReLU H = W in {8, 16, 32} and stage
  * patterns (2,1,0) (2,1,1) (3,3,3) (1) (1,1,1), or H = W = 64 and (2,1,0) (1)
- * (1,1); other valid requests there return NK_ERR_UNSUPPORTED.  At 64x64
+ * (1,1); with Erf the tiled form only: H = W in {32, 64} and (2,1,0) (1)
+ * (1,1); either with or without a LayerNorm.  Other valid requests there
+ * return NK_ERR_UNSUPPORTED; the layer-wise PLAIN forms take every
+ * architecture.  At 64x64
  * MIXED runs the tiled form: stage-0 tasks over row bands and groups of
  * super-plane shifts, the pooled stage-1 tensor of each pair (4 MB) in a
  * ring of slots in the handle's workspace, one stage-1 task per pair; the
@@ -177,7 +203,8 @@ nk_status nk_fc_block(nk_handle* h, int depth, const nk_params* prm, const float
  *              tables (required unless PLAIN_FP64).
  *   symmetric  the block is the upper triangle of Xa x Xa: dK[i][j] and
  *              dK[j][i] both count for that entry; dXa must equal dXb.
- * Needs sigma_w2 > 0 and C <= 4.  The forward tensors of each layer are
+ * Needs sigma_w2 > 0, C <= 4, ReLU or identity and no norm (other
+ * architectures: NK_ERR_UNSUPPORTED).  The forward tensors of each layer are
  * recomputed per chunk of pairs and kept in the handle's workspace. */
 nk_status nk_block_backward(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_prec prec,
                             const float* Xa, const double* qda, const float* qsa, int64_t a0, int64_t a1,
@@ -239,7 +266,7 @@ nk_status nk_block_fused_noalloc(const nk_arch* arch, const nk_params* prm,
  *   ReLU: Kt = relu map of K, Theta_t = Theta (pi - arccos c) / (2 pi);
  *   pools on both; readout K = sw2 mean Kt + sb2, Theta = K + sw2 mean Theta_t.
  * Arguments as nk_block; K and Theta are [a1 - a0][ldk] outputs of the
- * precision's type.  Layer-wise forms only: prec = NK_PREC_PLAIN_FP32 or
+ * precision's type.  ReLU or identity, no norm.  Layer-wise forms only: prec = NK_PREC_PLAIN_FP32 or
  * NK_PREC_PLAIN_FP64 (NK_PREC_MIXED: NK_ERR_UNSUPPORTED, no fused NTK). */
 nk_status nk_block_ntk(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_prec prec,
                        const float* Xa, const double* qda, const float* qsa, int64_t a0, int64_t a1,

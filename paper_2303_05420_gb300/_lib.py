@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(HERE, "libnk.so")
 NK_OK, NK_ERR_INVALID_ARG, NK_ERR_CUDA, NK_ERR_NUMERICAL = 0, 1, 2, 3
 NK_ERR_NOT_CONVERGED, NK_ERR_TIMEOUT, NK_ERR_NO_MEMORY, NK_ERR_UNSUPPORTED = 4, 5, 6, 7
 PREC = {"plain_fp64": 0, "plain_fp32": 1, "mixed": 2}
-ACT = {"relu": 0, "identity": 1}
+ACT = {"relu": 0, "identity": 1, "erf": 2}
+NORM = {"none": 0, "layer": 1}
 PRECOND = {"none": 0, "jacobi": 1, "pivchol": 2}
 
 # Every symbol include/nk.h declares (checked by a CPU test).
@@ -30,7 +31,8 @@ EXPORTS = ["nk_create", "nk_destroy", "nk_status_string", "nk_last_error", "nk_s
 
 
 class NkArch(ctypes.Structure):
-    _fields_ = [("n_stages", c_int), ("convs", c_int * 4), ("filter", c_int), ("activation", c_int)]
+    _fields_ = [("n_stages", c_int), ("convs", c_int * 4), ("filter", c_int), ("activation", c_int),
+                ("norm", c_int)]
 
 
 class NkParams(ctypes.Structure):
@@ -124,13 +126,14 @@ def lib():
     return L
 
 
-def make_arch(convs, filt: int = 3, act: str = "relu") -> NkArch:
+def make_arch(convs, filt: int = 3, act: str = "relu", norm: str = "none") -> NkArch:
     a = NkArch()
     a.n_stages = len(convs)
     for i in range(4):
         a.convs[i] = convs[i] if i < len(convs) else 0
     a.filter = filt
     a.activation = ACT[act]
+    a.norm = NORM[norm]
     return a
 
 

@@ -66,11 +66,11 @@ class Handle:
         return int(lib().nk_q_size(byref(a), H, W))
 
     def self_diag(self, X: torch.Tensor, convs: Sequence[int], sw2: float, sb2: float,
-                  filt: int = 3, act: str = "relu") -> Tuple[torch.Tensor, torch.Tensor]:
+                  filt: int = 3, act: str = "relu", norm: str = "none") -> Tuple[torch.Tensor, torch.Tensor]:
         """X [n, H, W, C] float32 CUDA -> (qd [n, nq] float64, qs [n, nq, 2] float32)."""
         assert X.is_cuda and X.dtype == torch.float32 and X.is_contiguous()
         n, H, W, C = X.shape
-        a = make_arch(convs, filt, act)
+        a = make_arch(convs, filt, act, norm)
         p = make_params(sw2, sb2)
         nq = int(lib().nk_q_size(byref(a), H, W))
         if nq < 0:
@@ -83,10 +83,10 @@ class Handle:
         return qd, qs
 
     def autotune(self, convs: Sequence[int], sw2: float, sb2: float, H: int, W: int, C: int = 3,
-                 filt: int = 3) -> int:
+                 filt: int = 3, act: str = "relu", norm: str = "none") -> int:
         """Times the fused-kernel launch variants for this shape; caches and
         returns the chosen variant."""
-        a = make_arch(convs, filt)
+        a = make_arch(convs, filt, act, norm)
         p = make_params(sw2, sb2)
         v = c_int(0)
         st = lib().nk_autotune(self._h, byref(a), byref(p), H, W, C, byref(v), c_void_p(_stream()))
@@ -103,7 +103,8 @@ class Handle:
     def block(self, Xa: torch.Tensor, qa: Tuple[torch.Tensor, torch.Tensor], Xb: torch.Tensor,
               qb: Tuple[torch.Tensor, torch.Tensor], convs: Sequence[int], sw2: float, sb2: float,
               prec: str = "mixed", a_range=None, b_range=None, symmetric: bool = False,
-              out: Optional[torch.Tensor] = None, filt: int = 3, act: str = "relu") -> torch.Tensor:
+              out: Optional[torch.Tensor] = None, filt: int = 3, act: str = "relu",
+              norm: str = "none") -> torch.Tensor:
         """K[i - a0, j - b0] = NNGP(Xa[i], Xb[j]) over the given index ranges."""
         assert Xa.is_cuda and Xb.is_cuda and Xa.dtype == torch.float32 and Xb.dtype == torch.float32
         _, H, W, C = Xa.shape
@@ -113,7 +114,7 @@ class Handle:
         if out is None:
             out = torch.empty((a1 - a0, b1 - b0), dtype=dt, device=Xa.device)
         assert out.dtype == dt and out.stride(1) == 1
-        a = make_arch(convs, filt, act)
+        a = make_arch(convs, filt, act, norm)
         p = make_params(sw2, sb2)
         st = lib().nk_block(self._h, byref(a), byref(p), _lib.PREC[prec],
                             c_void_p(_ptr(Xa)), c_void_p(_ptr(qa[0])), c_void_p(_ptr(qa[1])), a0, a1,

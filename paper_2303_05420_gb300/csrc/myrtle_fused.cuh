@@ -892,7 +892,9 @@ cudaError_t dispatch_r8(const int c[3], bool bias, int variant, FusedParams& P, 
 bool tiled_supported(const int c[3]);
 size_t tiled_ws_bytes(const int c[3], const int* R, const int64_t* npairs, int n, int sm_count);
 // wait_limit: polls of a dependency wait before it gives up (NK_DEV_TIMEOUT).
-cudaError_t launch_tiled(const int c[3], bool bias, const int* R, const FusedParams* B, int n, int sm_count,
+// act: NK_ACT_RELU or NK_ACT_ERF (the map of every activation layer).
+cudaError_t launch_tiled(const int c[3], bool bias, int act, const int* R, const FusedParams* B, int n,
+                         int sm_count,
                          void* ws, size_t ws_bytes, unsigned int* dstatus, long long wait_limit,
                          cudaStream_t st);
 

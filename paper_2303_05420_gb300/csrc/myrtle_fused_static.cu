@@ -123,7 +123,8 @@ extern "C" nk_status nk_block_fused_noalloc(const nk_arch* arch, const nk_params
     set_err(err_buf, err_len, "nk_block_fused_noalloc: NULL pointer");
     return NK_ERR_INVALID_ARG;
   }
-  if (!nk_myrtle_fused_supported(g)) {
+  const int pat[3] = {g.convs[0], g.n_stages > 1 ? g.convs[1] : 0, g.n_stages > 2 ? g.convs[2] : 0};
+  if (!nk_myrtle_fused_supported(g) || g.act != NK_ACT_RELU || !nk_cluster_pattern(pat)) {
     set_err(err_buf, err_len,
             "nk_block_fused_noalloc: no fused kernel for this architecture / size (see nk_block)");
     return NK_ERR_UNSUPPORTED;

@@ -6,7 +6,8 @@
 // average pool + Dense readout).  Pairs are processed in chunks.  It handles
 // every architecture nk_block accepts (any filter, identity activation,
 // zero-conv stages) and serves as the baseline the fused path is measured
-// against.  FP32 uses CUDA's acosf / sqrtf; FP64 uses acos / sqrt.
+// against.  FP32 uses CUDA's acosf / asinf / sqrtf; FP64 uses acos / asin /
+// sqrt.  Activations ReLU, Erf or identity, with or without a LayerNorm.
 #include "myrtle_plain.cuh"
 
 namespace {
@@ -45,13 +46,14 @@ cudaError_t run_plain(const NkGeom& g, double sw2, double sb2, const float* Xa, 
       }
       const int64_t HW = (int64_t)H * W;
       for (int k = 0; k < g.convs[s]; ++k, ++layer) {
-        *launches += (g.act == NK_ACT_RELU) ? 2 : 1;
+        const bool act = (g.act == NK_ACT_RELU || g.act == NK_ACT_ERF);
+        *launches += act ? 2 : 1;
         conv_layer<T>(cur, nxt, np, H, W, g.filter, a_conv, (T)sb2, st);
         T* t = cur; cur = nxt; nxt = t;
-        if (g.act == NK_ACT_RELU)
-          k_relu<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(cur, cur, np, (int)HW, na, nb, symmetric,
-                                                            pair0, a0, b0, qda, qdb, qsa, qsb,
-                                                            g.nq, g.layer_qoff[layer], dstatus);
+        if (act)
+          k_act<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(
+              cur, np, (int)HW, na, nb, symmetric, pair0, a0, b0, qda, qdb, qsa, qsb, g.nq, g.layer_qoff[layer],
+              g.act, g.norm == NK_NORM_LAYER ? g.nq_base + layer : -1, dstatus);
       }
     }
     const int64_t HW = (int64_t)H * W;

@@ -156,6 +156,54 @@ inline void conv_layer(const T* in, T* out, int64_t np, int H, int W, int filt, 
 }
 
 
+// Activation of the forward layer-wise form, in place: ReLU or Erf, with or
+// without the LayerNorm before it.  FP64 reads the self-variances q and (with
+// a norm) the divisors m of both images from qd and maps the normalised
+// K / sqrt(m m') with q / m, q' / m'; FP32 uses the factor tables qs of
+// nk_self_diag, which carry the norm: ReLU b b' J(K a a') / (2 pi), Erf
+// (2/pi) asin(K a a').
+template <typename T>
+__global__ void k_act(T* K, int64_t npairs, int HW, int64_t na, int64_t nb, int symmetric, int64_t pair0,
+                      int64_t a0, int64_t b0, const double* __restrict__ qda, const double* __restrict__ qdb,
+                      const float* __restrict__ qsa, const float* __restrict__ qsb, int64_t nq, int qoff,
+                      int act, int moff, unsigned int* dstatus) {
+  const int HW2 = HW * HW;
+  for (int64_t pr = blockIdx.y; pr < npairs; pr += gridDim.y) {
+    int64_t i, j;
+    pair_of(pair0 + pr, na, nb, symmetric, &i, &j);
+    const int64_t ra = (a0 + i) * nq, rb = (b0 + j) * nq;
+    for (int rem = blockIdx.x * blockDim.x + threadIdx.x; rem < HW2; rem += gridDim.x * blockDim.x) {
+      const int64_t e = pr * (int64_t)HW2 + rem;
+      const int p = rem / HW, pp = rem - p * HW;
+      if constexpr (sizeof(T) == 8) {
+        double q1 = qda[ra + qoff + p], q2 = qdb[rb + qoff + pp];
+        if (!(q1 >= 0.0) || !(q2 >= 0.0)) atomicOr(dstatus, NK_DEV_NUMERICAL);
+        double k = K[e];
+        if (moff >= 0) {
+          const double m1 = qda[ra + moff], m2 = qdb[rb + moff];
+          k /= sqrt(m1 * m2);
+          q1 /= m1;
+          q2 /= m2;
+        }
+        K[e] = (act == NK_ACT_ERF) ? nk_erf_map_f64(k, q1, q2) : nk_relu_map_f64(k, q1, q2);
+      } else {
+        const float2 s1 = reinterpret_cast<const float2*>(qsa)[ra + qoff + p];
+        const float2 s2 = reinterpret_cast<const float2*>(qsb)[rb + qoff + pp];
+        const float s = s1.y * s2.y;
+        float c = K[e] * (s1.x * s2.x);
+        c = fminf(fmaxf(c, -1.f), 1.f);
+        float v = 0.f;
+        if (act == NK_ACT_ERF) {
+          v = s * 0.63661977236758134308f * asinf(c);
+        } else if (s > 0.f) {
+          v = s * (0.15915494309189533577f) * (sqrtf(fmaxf(1.f - c * c, 0.f)) + c * (NK_PI_F - acosf(c)));
+        }
+        K[e] = v;
+      }
+    }
+  }
+}
+
 // ReLU map with self-variances of the pair's two images at this layer,
 // K = map(Kin) (Kin may be K itself).
 template <typename T>

@@ -49,8 +49,13 @@ bool nk_make_geom(const nk_arch* arch, int H, int W, int C, NkGeom* g, const cha
   if (!arch) { *why = "arch is NULL"; return false; }
   if (arch->n_stages < 1 || arch->n_stages > NK_MAX_STAGES) { *why = "n_stages outside 1..4"; return false; }
   if (arch->filter != 1 && arch->filter != 3) { *why = "filter must be 1 or 3"; return false; }
-  if (arch->activation != NK_ACT_RELU && arch->activation != NK_ACT_IDENTITY) {
+  if (arch->activation != NK_ACT_RELU && arch->activation != NK_ACT_IDENTITY && arch->activation != NK_ACT_ERF) {
     *why = "unknown activation";
+    return false;
+  }
+  if (arch->norm != NK_NORM_NONE && arch->norm != NK_NORM_LAYER) { *why = "unknown norm"; return false; }
+  if (arch->norm == NK_NORM_LAYER && arch->activation == NK_ACT_IDENTITY) {
+    *why = "a LayerNorm needs the ReLU or Erf activation";
     return false;
   }
   if (arch->convs[0] < 1) { *why = "the first stage needs at least one conv"; return false; }
@@ -58,6 +63,7 @@ bool nk_make_geom(const nk_arch* arch, int H, int W, int C, NkGeom* g, const cha
   g->n_stages = arch->n_stages;
   g->filter = arch->filter;
   g->act = arch->activation;
+  g->norm = arch->norm;
   g->C = C;
   int h = H, w = W, nl = 0, off = 0;
   g->last_act_stage = -1;
@@ -81,7 +87,8 @@ bool nk_make_geom(const nk_arch* arch, int H, int W, int C, NkGeom* g, const cha
     if (arch->convs[s] > 0) g->last_act_stage = s;
   }
   g->n_layers = nl;
-  g->nq = off;
+  g->nq_base = off;
+  g->nq = off + (g->norm == NK_NORM_LAYER ? nl : 0);
   g->gap_stage = g->n_stages - 1;
   int r = 0;
   for (int s = g->last_act_stage; s >= 0; --s) {
@@ -125,7 +132,8 @@ bool fused_variant_valid(const NkGeom& g, int v) {
   if (v < 0 || v >= NK_FUSED_VARIANTS) return false;
   int c[3];
   stage_pattern(g, c);
-  return v < NK_TILED_VARIANT || nkf::tiled_supported(c);
+  if (v == NK_TILED_VARIANT) return nkf::tiled_supported(c);
+  return g.act == NK_ACT_RELU && nk_cluster_pattern(c);  // the cluster launches
 }
 
 // Default variant without a tuned entry: the tiled form where it exists
@@ -159,8 +167,8 @@ nk_status fused_block(nk_handle* h, const NkGeom& g, const nk_params* prm, const
     nk_status s = nk_workspace(h, nkf::tiled_ws_bytes(c, R, np, 1, h->sm_count), &ws);
     if (s != NK_OK) return s;
     h->launches += 1;
-    return nk_cuda_check(h, nkf::launch_tiled(c, prm->sigma_b2 != 0.0, R, &P, 1, h->sm_count, ws, h->ws_bytes,
-                                              h->dstatus, tiled_wait_limit(h), st), what);
+    return nk_cuda_check(h, nkf::launch_tiled(c, prm->sigma_b2 != 0.0, g.act, R, &P, 1, h->sm_count, ws,
+                                              h->ws_bytes, h->dstatus, tiled_wait_limit(h), st), what);
   }
   h->launches += 1;
   return nk_cuda_check(h, nk_launch_myrtle_fused(g, prm->sigma_w2, prm->sigma_b2, Xa, qsa, a0, a1, Xb, qsb, b0,
@@ -326,9 +334,9 @@ nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_p
   if (prec == NK_PREC_MIXED) {
     if (!nk_myrtle_fused_supported(g))
       return nk_fail(h, NK_ERR_UNSUPPORTED,
-                     "nk_block MIXED: needs filter 3, ReLU, C <= 3 and H == W in {8,16,32} with one of "
-                     "the stage patterns (2,1,0) (2,1,1) (3,3,3) (1) (1,1,1), or H == W == 64 with "
-                     "(2,1,0) (1) (1,1)");
+                     "nk_block MIXED: needs filter 3, C <= 3 and, with ReLU, H == W in {8,16,32} with one "
+                     "of the stage patterns (2,1,0) (2,1,1) (3,3,3) (1) (1,1,1), or H == W in {32,64} with "
+                     "(2,1,0) (1) (1,1); with Erf H == W in {32,64} and (2,1,0) (1) (1,1)");
     int key[8];
     tune_key(g, prm->sigma_b2 != 0.0, key);
     return fused_block(h, g, prm, Xa, qsa, a0, a1, Xb, qsb, b0, b1, (float*)K, ldk, symmetric,
@@ -363,6 +371,8 @@ nk_status nk_block_ntk(nk_handle* h, const nk_arch* arch, const nk_params* prm, 
     return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: negative variance");
   if (prec == NK_PREC_MIXED)
     return nk_fail(h, NK_ERR_UNSUPPORTED, "nk_block_ntk: the NTK has the layer-wise forms only (PLAIN_FP32/FP64)");
+  if (g.act == NK_ACT_ERF || g.norm != NK_NORM_NONE)
+    return nk_fail(h, NK_ERR_UNSUPPORTED, "nk_block_ntk: ReLU or identity without a norm only");
   if (prec != NK_PREC_PLAIN_FP64 && prec != NK_PREC_PLAIN_FP32)
     return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: unknown precision");
   if (a0 < 0 || b0 < 0 || a1 < a0 || b1 < b0)
@@ -409,6 +419,7 @@ nk_status nk_block_queue(nk_handle* h, const nk_arch* arch, const nk_params* prm
   } items[NK_QUEUE_MAX];
   int n = 0;
   int c[3] = {0, 0, 0};
+  int act = NK_ACT_RELU;
   for (int t = 0; t < n_tasks; ++t) {
     const nk_block_task& T = tasks[t];
     NkGeom g;
@@ -426,12 +437,14 @@ nk_status nk_block_queue(nk_handle* h, const nk_arch* arch, const nk_params* prm
                      t);
     if (!nk_myrtle_fused_supported(g))
       return nk_fail(h, NK_ERR_UNSUPPORTED,
-                     "nk_block_queue task %d: needs filter 3, ReLU, C <= 3 and H == W in {8,16,32} with one "
-                     "of the stage patterns (2,1,0) (2,1,1) (3,3,3) (1) (1,1,1), or 64 with (2,1,0) (1) (1,1)",
+                     "nk_block_queue task %d: needs filter 3, C <= 3 and, with ReLU, H == W in {8,16,32} with "
+                     "one of the stage patterns (2,1,0) (2,1,1) (3,3,3) (1) (1,1,1), or 64 with (2,1,0) (1) "
+                     "(1,1); with Erf 64x64 and 32x32 blocks of (2,1,0) (1) (1,1)",
                      t);
     c[0] = g.convs[0];
     c[1] = g.n_stages > 1 ? g.convs[1] : 0;
     c[2] = g.n_stages > 2 ? g.convs[2] : 0;
+    act = g.act;
     items[n].R = T.H;
     items[n].P = nk_fused_params(g, prm->sigma_w2, prm->sigma_b2, T.Xa, T.qsa, T.a0, T.a1, T.Xb, T.qsb, T.b0,
                                  T.b1, T.K, T.ldk, T.symmetric);
@@ -460,10 +473,14 @@ nk_status nk_block_queue(nk_handle* h, const nk_arch* arch, const nk_params* prm
     nk_status s = nk_workspace(h, nkf::tiled_ws_bytes(c, R, np, n, h->sm_count), &ws);
     if (s != NK_OK) return s;
     h->launches += 1;
-    cudaError_t e = nkf::launch_tiled(c, prm->sigma_b2 != 0.0, R, B, n, h->sm_count, ws, h->ws_bytes, h->dstatus,
-                                      tiled_wait_limit(h), (cudaStream_t)stream);
+    cudaError_t e = nkf::launch_tiled(c, prm->sigma_b2 != 0.0, act, R, B, n, h->sm_count, ws, h->ws_bytes,
+                                      h->dstatus, tiled_wait_limit(h), (cudaStream_t)stream);
     return nk_cuda_check(h, e, "nk_block_queue tiled launch");
   }
+  if (act != NK_ACT_RELU || !nk_cluster_pattern(c))
+    return nk_fail(h, NK_ERR_UNSUPPORTED,
+                   "nk_block_queue: without 64x64 blocks the queue takes ReLU networks of the patterns (2,1,0) "
+                   "(2,1,1) (3,3,3) (1) (1,1,1)");
   nkf::QueueParams Q = {};
   Q.n = n;
   Q.item0[0] = 0;
@@ -495,6 +512,8 @@ nk_status nk_block_backward(nk_handle* h, const nk_arch* arch, const nk_params* 
   if (prec != NK_PREC_PLAIN_FP64 && prec != NK_PREC_PLAIN_FP32 && prec != NK_PREC_MIXED)
     return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_backward: unknown precision");
   if (C > 4) return nk_fail(h, NK_ERR_UNSUPPORTED, "nk_block_backward: C > 4");
+  if (g.act == NK_ACT_ERF || g.norm != NK_NORM_NONE)
+    return nk_fail(h, NK_ERR_UNSUPPORTED, "nk_block_backward: ReLU or identity without a norm only");
   if (a0 < 0 || b0 < 0 || a1 < a0 || b1 < b0)
     return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_backward: bad index range");
   if (a1 == a0 || b1 == b0) return NK_OK;

@@ -21,13 +21,15 @@ struct NkGeom {
   int convs[NK_MAX_STAGES];
   int filter;
   int act;
+  int norm;           // NK_NORM_NONE / NK_NORM_LAYER
   int C;
   int Hs[NK_MAX_STAGES];
   int Ws[NK_MAX_STAGES];
   int n_layers;
   int layer_stage[NK_MAX_LAYERS];
   int layer_qoff[NK_MAX_LAYERS];
-  int nq;
+  int nq;             // per-image stride of qd / qs: nq_base + (norm ? n_layers : 0)
+  int nq_base;        // sum over layers of H_l W_l; the LayerNorm divisors m_l follow at nq_base + l
   int last_act_stage;  // last stage holding an activation layer (-1: none)
   int gap_stage;       // the stage whose activations feed the global average pool
   int radius[NK_MAX_STAGES];  // self-covariance band radius needed per stage
@@ -93,6 +95,7 @@ cudaError_t nk_launch_myrtle_fused(const NkGeom& g, double sw2, double sb2, cons
 #define NK_FUSED_VARIANTS 4
 #define NK_TILED_VARIANT 3
 bool nk_myrtle_fused_supported(const NkGeom& g);
+bool nk_cluster_pattern(const int c[3]);
 
 // FC NNGP block on the tensor cores (fc_gram.cu).
 size_t nk_fc_ws_bytes(int64_t na, int64_t nb, int d, int depth);

@@ -102,6 +102,27 @@ __device__ __forceinline__ float nk_dJ_f32(float c) {
   return NK_HALF_PI_F + copysignf(asa, c);
 }
 
+// asin(c) in FP32 for c in [-1, 1] (clamped): asin|c| = asin_small(|c|) for
+// |c| <= 1/sqrt(2), else pi/2 - asin_small(sqrt(1 - c^2)); the sign of c.
+// The Erf map's argument 2K / sqrt((m + 2q)(m' + 2q')) stays below
+// 2q / (1 + 2q) < 1 in magnitude, where asin is well conditioned.
+__device__ __forceinline__ float nk_asin_f32(float c) {
+  c = fminf(fmaxf(c, -1.f), 1.f);
+  const float a = fabsf(c);
+  const float sn = nk_sqrt_approx(fmaf(-c, c, 1.f));
+  const float m = fminf(a, sn);
+  const float as = nk_asin_small(m);
+  return copysignf((a > sn) ? (NK_HALF_PI_F - as) : as, c);
+}
+
+// Erf map in FP64: E[erf(u) erf(v)] = (2/pi) asin(2 K / sqrt((1 + 2 q1)(1 + 2 q2)))
+// for centred Gaussians with variances q1, q2 and covariance K.
+__device__ __forceinline__ double nk_erf_map_f64(double K, double q1, double q2) {
+  double c = 2.0 * K / sqrt((1.0 + 2.0 * q1) * (1.0 + 2.0 * q2));
+  c = fmin(fmax(c, -1.0), 1.0);
+  return (2.0 / NK_PI_D) * asin(c);
+}
+
 // J(c) in FP64 with the CUDA double-precision arccos.
 __device__ __forceinline__ double nk_J_f64(double c) {
   c = fmin(fmax(c, -1.0), 1.0);

@@ -12,6 +12,13 @@
 // One CTA per image (grid-stride over images); planes of the current stage
 // live in a per-CTA global workspace (at most 49 planes of H*W doubles), the
 // image and the current q in shared memory.
+//
+// Activations: ReLU (arc-cosine map) or Erf, E[erf(u) erf(v)] =
+// (2/pi) asin(2 K / sqrt((1 + 2 q)(1 + 2 q'))).  With a LayerNorm between
+// conv and activation (the tuned Myrtle listing), the layer's band is divided
+// by m = mean_p q(p) of this image before the activation, which then sees
+// the self-variances q / m (the infinite-width limit of normalising over
+// pixels and channels); m is written after the layer's q values.
 #include "nk_common.cuh"
 #include "nk_map.cuh"
 
@@ -25,6 +32,7 @@ k_self_diag(NkGeom g, double sw2, double sb2, const float* __restrict__ X, int64
   const int H0 = g.Hs[0], W0 = g.Ws[0], C = g.C;
   double* xs = sh;                      // [H0*W0*C]
   double* qsh = sh + (size_t)H0 * W0 * C;  // [H0*W0]
+  double* red = qsh + (size_t)H0 * W0;     // [33]: warp sums, then m
   double* bufA = ws + (size_t)blockIdx.x * 2 * ws_half;
   double* bufB = bufA + ws_half;
   const int tid = threadIdx.x, bd = blockDim.x;
@@ -106,28 +114,55 @@ k_self_diag(NkGeom g, double sw2, double sb2, const float* __restrict__ X, int64
         __syncthreads();
         const int center = r * D + r;
         const int off = g.layer_qoff[layer];
+        // LayerNorm divisor m = mean_p q(p) (1 without a norm)
+        double m = 1.0;
+        if (g.norm == NK_NORM_LAYER) {
+          double s = 0.0;
+          for (int p = tid; p < HW; p += bd) s += B[(size_t)center * HW + p];
+          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          if ((tid & 31) == 0) red[tid >> 5] = s;
+          __syncthreads();
+          if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (bd >> 5); ++w) t += red[w];
+            t /= (double)HW;
+            qd[img * (int64_t)g.nq + g.nq_base + layer] = t;
+            if (qs) reinterpret_cast<float2*>(qs)[img * (int64_t)g.nq + g.nq_base + layer] = make_float2(0.f, 0.f);
+            if (!(t > 0.0)) {
+              atomicOr(dstatus, NK_DEV_NUMERICAL);
+              t = 1.0;  // results are flagged; keep them finite
+            }
+            red[32] = t;
+          }
+          __syncthreads();
+          m = red[32];
+        }
         for (int p = tid; p < HW; p += bd) {
           const double q = B[(size_t)center * HW + p];
-          qsh[p] = q;
+          qsh[p] = q / m;
           qd[img * (int64_t)g.nq + off + p] = q;
           if (!(q >= 0.0)) atomicOr(dstatus, NK_DEV_NUMERICAL);
           if (qs) {
             float2 o = make_float2(0.f, 0.f);
-            if (q > 0.0) {
-              const double sq = sqrt(q);
-              o = make_float2((float)(1.0 / sq), (float)sq);
+            if (g.act == NK_ACT_ERF) {
+              o = make_float2((float)sqrt(2.0 / (m + 2.0 * q)), 1.f);
+            } else if (q > 0.0) {
+              o = make_float2((float)(1.0 / sqrt(q)), (float)sqrt(q / m));
             }
             reinterpret_cast<float2*>(qs)[img * (int64_t)g.nq + off + p] = o;
           }
         }
         __syncthreads();
-        if (g.act == NK_ACT_RELU) {
+        if (g.act == NK_ACT_RELU || g.act == NK_ACT_ERF) {
+          const double inv_m = 1.0 / m;
           for (int idx = tid; idx < np * HW; idx += bd) {
             const int pl = idx / HW, p = idx - pl * HW;
             const int dy = pl / D - r, dx = pl % D - r;
             const int i = p / W, j = p - (p / W) * W;
-            if (i + dy >= 0 && i + dy < H && j + dx >= 0 && j + dx < W)
-              B[idx] = nk_relu_map_f64(B[idx], qsh[p], qsh[(i + dy) * W + j + dx]);
+            if (i + dy >= 0 && i + dy < H && j + dx >= 0 && j + dx < W) {
+              const double Kn = B[idx] * inv_m, q1 = qsh[p], q2 = qsh[(i + dy) * W + j + dx];
+              B[idx] = (g.act == NK_ACT_RELU) ? nk_relu_map_f64(Kn, q1, q2) : nk_erf_map_f64(Kn, q1, q2);
+            }
           }
           __syncthreads();
         }
@@ -155,7 +190,7 @@ cudaError_t nk_launch_self_diag(const NkGeom& g, double sw2, double sb2, const f
                                 unsigned int* dstatus, cudaStream_t st) {
   if (n <= 0 || g.last_act_stage < 0) return cudaSuccess;
   const size_t half = nk_self_diag_ws_per_cta(g) / sizeof(double) / 2;
-  const size_t smem = (size_t)g.Hs[0] * g.Ws[0] * (g.C + 1) * sizeof(double);
+  const size_t smem = ((size_t)g.Hs[0] * g.Ws[0] * (g.C + 1) + 33) * sizeof(double);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_self_diag, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

@@ -64,6 +64,13 @@ def test_q_size_host_logic(libnk):
     bad = make_arch((0, 1))
     assert libnk.nk_q_size(ctypes.byref(bad), 8, 8) == -1
     assert libnk.nk_q_size(ctypes.byref(make_arch((2,), filt=5)), 8, 8) == -1
+    # Erf keeps the layout; a LayerNorm appends one divisor per layer
+    assert libnk.nk_q_size(ctypes.byref(make_arch((2, 1, 0), act="erf")), 32, 32) == 2 * 1024 + 256
+    assert libnk.nk_q_size(ctypes.byref(make_arch((2, 1, 0), norm="layer")), 32, 32) == 2 * 1024 + 256 + 3
+    assert libnk.nk_q_size(ctypes.byref(make_arch((3, 3, 3), act="erf", norm="layer")), 16, 16) == \
+        3 * (256 + 64 + 16) + 9
+    # a LayerNorm needs an activation
+    assert libnk.nk_q_size(ctypes.byref(make_arch((2, 1, 0), act="identity", norm="layer")), 8, 8) == -1
 
 
 def test_header_compiles_and_links_as_c(libnk, tmp_path):
