@@ -64,6 +64,11 @@ enum { NK_ACT_RELU = 0, NK_ACT_IDENTITY = 1, NK_ACT_ERF = 2 };
  * listings) or the tuned Myrtle listing's LayerNorm over pixels and channels
  * of each image (stax.LayerNorm(axis=(1, 2, 3))). */
 enum { NK_NORM_NONE = 0, NK_NORM_LAYER = 1 };
+/* Readout after the last conv layer: GlobalAvgPool then Dense (the Myrtle
+ * listings) or Flatten then Dense (the CV8 listing, Appendix A).  A Flatten
+ * readout's weights are independent per pixel, so only the pixel pairs p = p'
+ * of the last layer enter: K = sigma_w2 mean_p Kt(p, p) + sigma_b2. */
+enum { NK_READOUT_GAP = 0, NK_READOUT_FLATTEN = 1 };
 enum { NK_PRECOND_NONE = 0, NK_PRECOND_JACOBI = 1, NK_PRECOND_PIVCHOL = 2 };
 
 /* Myrtle-family architecture (Appendix A, Myrtle listing): n_stages stages;
@@ -81,6 +86,7 @@ typedef struct {
   int filter;     /* 3 (paper) or 1 */
   int activation; /* NK_ACT_RELU, NK_ACT_ERF or NK_ACT_IDENTITY */
   int norm;       /* NK_NORM_NONE or NK_NORM_LAYER (not with NK_ACT_IDENTITY) */
+  int readout;    /* NK_READOUT_GAP or NK_READOUT_FLATTEN (no norm) */
 } nk_arch;
 
 /* sigma_w^2 = W_std^2 and sigma_b^2 = b_std^2 of every Conv / Dense layer
@@ -152,9 +158,12 @@ nk_status nk_self_diag(nk_handle* h, const nk_arch* arch, const nk_params* prm,
  * zero-conv stages only at the end; with ReLU H = W in {8, 16, 32} and stage
  * patterns (2,1,0) (2,1,1) (3,3,3) (1) (1,1,1), or H = W = 64 and (2,1,0) (1)
  * (1,1); with Erf the tiled form only: H = W in {32, 64} and (2,1,0) (1)
- * (1,1); either with or without a LayerNorm.  Other valid requests there
- * return NK_ERR_UNSUPPORTED; the layer-wise PLAIN forms take every
- * architecture.  At 64x64
+ * (1,1); either with or without a LayerNorm.  With NK_READOUT_FLATTEN
+ * (the CV8 listing: one stage of convs, no pools) MIXED carries only the
+ * p = p' diagonal of each pair, which the diagonal stencil keeps closed: H
+ * in {8, 16, 32}, W <= 32, ReLU or Erf, C <= 4; one warp per pair, FP32
+ * recursion, FP64 readout sum.  Other valid requests there return
+ * NK_ERR_UNSUPPORTED; the layer-wise PLAIN forms take every architecture.  At 64x64
  * MIXED runs the tiled form: stage-0 tasks over row bands and groups of
  * super-plane shifts, the pooled stage-1 tensor of each pair (4 MB) in a
  * ring of slots in the handle's workspace, one stage-1 task per pair; the

@@ -20,6 +20,7 @@ NK_ERR_NOT_CONVERGED, NK_ERR_TIMEOUT, NK_ERR_NO_MEMORY, NK_ERR_UNSUPPORTED = 4, 
 PREC = {"plain_fp64": 0, "plain_fp32": 1, "mixed": 2}
 ACT = {"relu": 0, "identity": 1, "erf": 2}
 NORM = {"none": 0, "layer": 1}
+READOUT = {"gap": 0, "flatten": 1}
 PRECOND = {"none": 0, "jacobi": 1, "pivchol": 2}
 
 # Every symbol include/nk.h declares (checked by a CPU test).
@@ -32,7 +33,7 @@ EXPORTS = ["nk_create", "nk_destroy", "nk_status_string", "nk_last_error", "nk_s
 
 class NkArch(ctypes.Structure):
     _fields_ = [("n_stages", c_int), ("convs", c_int * 4), ("filter", c_int), ("activation", c_int),
-                ("norm", c_int)]
+                ("norm", c_int), ("readout", c_int)]
 
 
 class NkParams(ctypes.Structure):
@@ -126,7 +127,7 @@ def lib():
     return L
 
 
-def make_arch(convs, filt: int = 3, act: str = "relu", norm: str = "none") -> NkArch:
+def make_arch(convs, filt: int = 3, act: str = "relu", norm: str = "none", readout: str = "gap") -> NkArch:
     a = NkArch()
     a.n_stages = len(convs)
     for i in range(4):
@@ -134,6 +135,7 @@ def make_arch(convs, filt: int = 3, act: str = "relu", norm: str = "none") -> Nk
     a.filter = filt
     a.activation = ACT[act]
     a.norm = NORM[norm]
+    a.readout = READOUT[readout]
     return a
 
 

@@ -104,7 +104,7 @@ class Handle:
               qb: Tuple[torch.Tensor, torch.Tensor], convs: Sequence[int], sw2: float, sb2: float,
               prec: str = "mixed", a_range=None, b_range=None, symmetric: bool = False,
               out: Optional[torch.Tensor] = None, filt: int = 3, act: str = "relu",
-              norm: str = "none") -> torch.Tensor:
+              norm: str = "none", readout: str = "gap") -> torch.Tensor:
         """K[i - a0, j - b0] = NNGP(Xa[i], Xb[j]) over the given index ranges."""
         assert Xa.is_cuda and Xb.is_cuda and Xa.dtype == torch.float32 and Xb.dtype == torch.float32
         _, H, W, C = Xa.shape
@@ -114,7 +114,7 @@ class Handle:
         if out is None:
             out = torch.empty((a1 - a0, b1 - b0), dtype=dt, device=Xa.device)
         assert out.dtype == dt and out.stride(1) == 1
-        a = make_arch(convs, filt, act, norm)
+        a = make_arch(convs, filt, act, norm, readout)
         p = make_params(sw2, sb2)
         st = lib().nk_block(self._h, byref(a), byref(p), _lib.PREC[prec],
                             c_void_p(_ptr(Xa)), c_void_p(_ptr(qa[0])), c_void_p(_ptr(qa[1])), a0, a1,

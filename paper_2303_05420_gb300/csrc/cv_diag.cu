@@ -1,0 +1,166 @@
+// NNGP blocks of conv networks with a Flatten readout (the CV8 listing of
+// Appendix A: eight conv(3x3, SAME) + ReLU layers, Flatten, Dense) by the
+// diagonal recursion, NK_PREC_MIXED.
+//
+// The conv stencil of the NNGP recursion moves both pixels of a pair by the
+// same offset, so the offset p' - p of a pixel pair never changes; without
+// pools nothing else mixes offsets.  The Flatten readout's Dense weights are
+// independent per pixel, so only the pairs p' = p of the last layer enter:
+//   K(x, x') = sw2 mean_p Kt_L(p, p) + sb2,
+// and the whole recursion closes on the H x W diagonal of each pair:
+//   K_1(p) = sw2/(9 C) sum_delta x(p + delta) . x'(p + delta) + sb2,
+//   K_{l+1}(p) = sw2/9 sum_delta Kt_l(p + delta) + sb2,   Kt_l = map(K_l),
+// with zero padding at the borders and the activation's per-pixel factors
+// (nk_self_diag's tables) of both images at the same pixel.  That is H W
+// values per pair and layer instead of (H W)^2.
+//
+// One warp per pair: lane = image column, the rows of the column in
+// registers.  The vertical taps of the 3x3 box are register neighbours, the
+// horizontal taps two shuffles; the per-pixel tables are read row by row
+// (each row a coalesced 256-byte load per image).  FP32 recursion, the final
+// mean summed in FP64.  Consecutive warps take consecutive pairs, so the warps
+// of a CTA mostly share the image of side a in L1.
+#include "myrtle_plain.cuh"
+
+namespace {
+
+constexpr int CV_WARPS = 8;
+
+struct CvParams {
+  const float* Xa;
+  const float* Xb;
+  const float2* qa;  // [n][nq] per-pixel factors (a, b) of side a
+  const float2* qb;
+  int64_t a0, na, b0, nb, npairs;
+  int sym;
+  int W, C, L;       // image width (<= 32), channels, conv layers
+  int nq;
+  int act;
+  float xscale;      // sw2 / (9 C)
+  float cscale;      // sw2 / 9
+  float sb2;
+  float fold;        // 1/(2 pi) (ReLU) or 2/pi (Erf)
+  double out_scale;  // sw2 / (H W)
+  double out_bias;   // sb2
+  float* K;
+  int64_t ldk;
+};
+
+template <int H>
+__device__ __forceinline__ void box3(const float (&v)[H], float (&k)[H], int lane, int W, float a, float b) {
+  float s[H];
+#pragma unroll
+  for (int r = 0; r < H; ++r) s[r] = v[r] + (r > 0 ? v[r - 1] : 0.f) + (r + 1 < H ? v[r + 1] : 0.f);
+#pragma unroll
+  for (int r = 0; r < H; ++r) {
+    const float up = __shfl_up_sync(0xffffffffu, s[r], 1);
+    const float dn = __shfl_down_sync(0xffffffffu, s[r], 1);
+    const float h = s[r] + (lane > 0 ? up : 0.f) + (lane + 1 < W ? dn : 0.f);
+    k[r] = fmaf(a, h, b);
+  }
+}
+
+template <int H>
+__global__ void __launch_bounds__(32 * CV_WARPS) k_cv_diag(const __grid_constant__ CvParams P) {
+  const int lane = threadIdx.x & 31;
+  const bool col = lane < P.W;
+  const int64_t nw = (int64_t)gridDim.x * CV_WARPS;
+  for (int64_t pr = (int64_t)blockIdx.x * CV_WARPS + (threadIdx.x >> 5); pr < P.npairs; pr += nw) {
+    int64_t i, j;
+    nkp::pair_of(pr, P.na, P.nb, P.sym, &i, &j);
+    const int64_t ia = P.a0 + i, ib = P.b0 + j;
+    const float* xa = P.Xa + ia * (int64_t)H * P.W * P.C;
+    const float* xb = P.Xb + ib * (int64_t)H * P.W * P.C;
+    // channel contraction at every pixel of the column
+    float v[H], k[H];
+#pragma unroll
+    for (int r = 0; r < H; ++r) {
+      float u = 0.f;
+      if (col) {
+        const float* pa = xa + ((int64_t)r * P.W + lane) * P.C;
+        const float* pb = xb + ((int64_t)r * P.W + lane) * P.C;
+        for (int c = 0; c < P.C; ++c) u = fmaf(pa[c], pb[c], u);
+      }
+      v[r] = u;
+    }
+    const float2* ta = P.qa + ia * (int64_t)P.nq;
+    const float2* tb = P.qb + ib * (int64_t)P.nq;
+    for (int l = 0; l < P.L; ++l) {
+      box3<H>(v, k, lane, P.W, l == 0 ? P.xscale : P.cscale, P.sb2);
+      const float2* la = ta + (int64_t)l * H * P.W;
+      const float2* lb = tb + (int64_t)l * H * P.W;
+#pragma unroll
+      for (int r = 0; r < H; ++r) {
+        float o = 0.f;
+        if (col) {
+          const float2 fa = la[r * P.W + lane], fb = lb[r * P.W + lane];
+          const float c = k[r] * (fa.x * fb.x);
+          float m;
+          if (P.act == NK_ACT_ERF)
+            m = nk_asin_f32(c);
+          else
+            m = (l == 0) ? nk_J_f32(c) : nk_J01_f32(c);  // after a ReLU layer every K_l >= 0
+          o = (fa.y * fb.y) * P.fold * m;
+        }
+        v[r] = o;
+      }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int r = 0; r < H; ++r) s += (double)v[r];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      const float out = (float)(P.out_scale * s + P.out_bias);
+      P.K[i * P.ldk + j] = out;
+      if (P.sym && i != j) P.K[j * P.ldk + i] = out;
+    }
+  }
+}
+
+}  // namespace
+
+bool nk_cv_supported(const NkGeom& g) {
+  return g.readout == NK_READOUT_FLATTEN && g.n_stages == 1 && g.filter == 3 &&
+         (g.act == NK_ACT_RELU || g.act == NK_ACT_ERF) && g.norm == NK_NORM_NONE && g.C >= 1 && g.C <= 4 &&
+         (g.Hs[0] == 8 || g.Hs[0] == 16 || g.Hs[0] == 32) && g.Ws[0] >= 1 && g.Ws[0] <= 32;
+}
+
+cudaError_t nk_launch_cv_diag(const NkGeom& g, double sw2, double sb2, const float* Xa, const float* qsa,
+                              int64_t a0, int64_t a1, const float* Xb, const float* qsb, int64_t b0, int64_t b1,
+                              float* K, int64_t ldk, int symmetric, int sm_count, cudaStream_t st) {
+  if (!nk_cv_supported(g)) return cudaErrorNotSupported;
+  CvParams P = {};
+  P.Xa = Xa;
+  P.Xb = Xb;
+  P.qa = reinterpret_cast<const float2*>(qsa);
+  P.qb = reinterpret_cast<const float2*>(qsb);
+  P.a0 = a0;
+  P.na = a1 - a0;
+  P.b0 = b0;
+  P.nb = b1 - b0;
+  P.sym = symmetric;
+  P.npairs = symmetric ? P.na * (P.na + 1) / 2 : P.na * P.nb;
+  if (P.npairs <= 0) return cudaSuccess;
+  P.W = g.Ws[0];
+  P.C = g.C;
+  P.L = g.convs[0];
+  P.nq = g.nq;
+  P.act = g.act;
+  P.xscale = (float)(sw2 / (9.0 * g.C));
+  P.cscale = (float)(sw2 / 9.0);
+  P.sb2 = (float)sb2;
+  P.fold = g.act == NK_ACT_ERF ? 0.63661977236758134308f : 0.15915494309189533577f;
+  P.out_scale = sw2 / ((double)g.Hs[0] * g.Ws[0]);
+  P.out_bias = sb2;
+  P.K = K;
+  P.ldk = ldk;
+  const int64_t want = (P.npairs + CV_WARPS - 1) / CV_WARPS;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count * 16));
+  switch (g.Hs[0]) {
+    case 8: k_cv_diag<8><<<grid, 32 * CV_WARPS, 0, st>>>(P); break;
+    case 16: k_cv_diag<16><<<grid, 32 * CV_WARPS, 0, st>>>(P); break;
+    default: k_cv_diag<32><<<grid, 32 * CV_WARPS, 0, st>>>(P); break;
+  }
+  return cudaGetLastError();
+}

@@ -14,6 +14,7 @@ bool nk_cluster_pattern(const int c[3]) {
 // third must be empty (pool then global average equals global average).
 bool nk_myrtle_fused_supported(const NkGeom& g) {
   if (g.filter != 3 || (g.act != NK_ACT_RELU && g.act != NK_ACT_ERF) || g.C < 1 || g.C > 3) return false;
+  if (g.readout != NK_READOUT_GAP) return false;
   if (g.Hs[0] != g.Ws[0]) return false;
   const int R0 = g.Hs[0];
   if (R0 != 8 && R0 != 16 && R0 != 32 && R0 != 64) return false;

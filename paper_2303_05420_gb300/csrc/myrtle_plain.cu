@@ -57,8 +57,10 @@ cudaError_t run_plain(const NkGeom& g, double sw2, double sb2, const float* Xa, 
       }
     }
     const int64_t HW = (int64_t)H * W;
-    k_gap<T><<<(unsigned)np, 256, 0, st>>>(cur, HW * HW, na, nb, symmetric, pair0, (T)sw2, (T)sb2,
-                                           K, ldk);
+    if (g.readout == NK_READOUT_FLATTEN)
+      k_flatten<T><<<(unsigned)np, 256, 0, st>>>(cur, (int)HW, na, nb, symmetric, pair0, (T)sw2, (T)sb2, K, ldk);
+    else
+      k_gap<T><<<(unsigned)np, 256, 0, st>>>(cur, HW * HW, na, nb, symmetric, pair0, (T)sw2, (T)sb2, K, ldk);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -286,6 +286,32 @@ __global__ void k_gap(const T* __restrict__ in, int64_t HW2, int64_t na, int64_t
   }
 }
 
+// Flatten + Dense readout (the CV8 listing): K = sw2 mean_p Kt(p, p) + sb2,
+// the pixel pairs p' = p of each pair's last tensor (HW x HW), summed in FP64.
+template <typename T>
+__global__ void k_flatten(const T* __restrict__ in, int HW, int64_t na, int64_t nb, int symmetric,
+                          int64_t pair0, T sw2, T sb2, T* __restrict__ K, int64_t ldk) {
+  __shared__ double red[32];
+  const int64_t pr = blockIdx.x;
+  const int64_t HW2 = (int64_t)HW * HW;
+  double acc = 0.0;
+  for (int p = threadIdx.x; p < HW; p += blockDim.x) acc += (double)in[pr * HW2 + (int64_t)p * HW + p];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) {
+      int64_t i, j;
+      pair_of(pair0 + pr, na, nb, symmetric, &i, &j);
+      const T v = (T)((double)sw2 * (acc / (double)HW) + (double)sb2);
+      K[i * ldk + j] = v;
+      if (symmetric && i != j) K[j * ldk + i] = v;
+    }
+  }
+}
+
 inline int grid_for(int64_t total) {
   int64_t g = (total + 255) / 256;
   if (g > 152 * 64) g = 152 * 64;

@@ -58,12 +58,18 @@ bool nk_make_geom(const nk_arch* arch, int H, int W, int C, NkGeom* g, const cha
     *why = "a LayerNorm needs the ReLU or Erf activation";
     return false;
   }
+  if (arch->readout != NK_READOUT_GAP && arch->readout != NK_READOUT_FLATTEN) { *why = "unknown readout"; return false; }
+  if (arch->readout == NK_READOUT_FLATTEN && arch->norm != NK_NORM_NONE) {
+    *why = "a Flatten readout is supported without a norm only";
+    return false;
+  }
   if (arch->convs[0] < 1) { *why = "the first stage needs at least one conv"; return false; }
   if (H < 1 || W < 1 || C < 1) { *why = "H, W and C must be positive"; return false; }
   g->n_stages = arch->n_stages;
   g->filter = arch->filter;
   g->act = arch->activation;
   g->norm = arch->norm;
+  g->readout = arch->readout;
   g->C = C;
   int h = H, w = W, nl = 0, off = 0;
   g->last_act_stage = -1;
@@ -331,6 +337,16 @@ nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_p
   if (needq && prec != NK_PREC_PLAIN_FP64 && (!qsa || !qsb))
     return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block: FP32 paths need qsa and qsb");
   cudaStream_t st = (cudaStream_t)stream;
+  if (prec == NK_PREC_MIXED && g.readout == NK_READOUT_FLATTEN) {
+    if (!nk_cv_supported(g))
+      return nk_fail(h, NK_ERR_UNSUPPORTED,
+                     "nk_block MIXED with a Flatten readout: needs one stage of filter-3 convs, ReLU or Erf, "
+                     "H in {8,16,32}, W <= 32, C <= 4");
+    h->launches += 1;
+    return nk_cuda_check(h, nk_launch_cv_diag(g, prm->sigma_w2, prm->sigma_b2, Xa, qsa, a0, a1, Xb, qsb, b0, b1,
+                                              (float*)K, ldk, symmetric, h->sm_count, st),
+                         "nk_block flatten-readout launch");
+  }
   if (prec == NK_PREC_MIXED) {
     if (!nk_myrtle_fused_supported(g))
       return nk_fail(h, NK_ERR_UNSUPPORTED,
@@ -371,8 +387,8 @@ nk_status nk_block_ntk(nk_handle* h, const nk_arch* arch, const nk_params* prm, 
     return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: negative variance");
   if (prec == NK_PREC_MIXED)
     return nk_fail(h, NK_ERR_UNSUPPORTED, "nk_block_ntk: the NTK has the layer-wise forms only (PLAIN_FP32/FP64)");
-  if (g.act == NK_ACT_ERF || g.norm != NK_NORM_NONE)
-    return nk_fail(h, NK_ERR_UNSUPPORTED, "nk_block_ntk: ReLU or identity without a norm only");
+  if (g.act == NK_ACT_ERF || g.norm != NK_NORM_NONE || g.readout != NK_READOUT_GAP)
+    return nk_fail(h, NK_ERR_UNSUPPORTED, "nk_block_ntk: ReLU or identity, no norm, global-average readout only");
   if (prec != NK_PREC_PLAIN_FP64 && prec != NK_PREC_PLAIN_FP32)
     return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: unknown precision");
   if (a0 < 0 || b0 < 0 || a1 < a0 || b1 < b0)
@@ -512,8 +528,9 @@ nk_status nk_block_backward(nk_handle* h, const nk_arch* arch, const nk_params* 
   if (prec != NK_PREC_PLAIN_FP64 && prec != NK_PREC_PLAIN_FP32 && prec != NK_PREC_MIXED)
     return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_backward: unknown precision");
   if (C > 4) return nk_fail(h, NK_ERR_UNSUPPORTED, "nk_block_backward: C > 4");
-  if (g.act == NK_ACT_ERF || g.norm != NK_NORM_NONE)
-    return nk_fail(h, NK_ERR_UNSUPPORTED, "nk_block_backward: ReLU or identity without a norm only");
+  if (g.act == NK_ACT_ERF || g.norm != NK_NORM_NONE || g.readout != NK_READOUT_GAP)
+    return nk_fail(h, NK_ERR_UNSUPPORTED,
+                   "nk_block_backward: ReLU or identity, no norm, global-average readout only");
   if (a0 < 0 || b0 < 0 || a1 < a0 || b1 < b0)
     return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_backward: bad index range");
   if (a1 == a0 || b1 == b0) return NK_OK;

@@ -22,6 +22,7 @@ struct NkGeom {
   int filter;
   int act;
   int norm;           // NK_NORM_NONE / NK_NORM_LAYER
+  int readout;        // NK_READOUT_GAP / NK_READOUT_FLATTEN
   int C;
   int Hs[NK_MAX_STAGES];
   int Ws[NK_MAX_STAGES];
@@ -96,6 +97,12 @@ cudaError_t nk_launch_myrtle_fused(const NkGeom& g, double sw2, double sb2, cons
 #define NK_TILED_VARIANT 3
 bool nk_myrtle_fused_supported(const NkGeom& g);
 bool nk_cluster_pattern(const int c[3]);
+
+// Flatten-readout (CV8) block by the diagonal recursion (cv_diag.cu).
+bool nk_cv_supported(const NkGeom& g);
+cudaError_t nk_launch_cv_diag(const NkGeom& g, double sw2, double sb2, const float* Xa, const float* qsa,
+                              int64_t a0, int64_t a1, const float* Xb, const float* qsb, int64_t b0, int64_t b1,
+                              float* K, int64_t ldk, int symmetric, int sm_count, cudaStream_t st);
 
 // FC NNGP block on the tensor cores (fc_gram.cu).
 size_t nk_fc_ws_bytes(int64_t na, int64_t nb, int d, int depth);
