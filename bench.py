@@ -45,8 +45,8 @@ CONFIGS = {
     # a small 64x64 case (profiling the tiled form on a short launch)
     "small64": dict(n_train=16, n_test=8, hw=64, n_classes=10),
 }
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
+FP32_LANES_PER_SM = 128  # the derived fallback when no probe file exists
+PEAKS_PROBE = os.path.join(ROOT, "profiles", "peaks_probe.json")
 
 
 def algorithmic_ops_per_entry(hw: int, convs=CONVS, C: int = 3) -> float:
@@ -174,6 +174,29 @@ def load_peaks() -> dict:
             return json.load(f)
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+def load_probe() -> dict:
+    """Rates measured by `bench.py --probe-peaks` on this GPU type (nk_probe),
+    stored per SM and cycle so that they scale with the clock a run saw."""
+    try:
+        with open(PEAKS_PROBE) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def fp32_peak(sm_count: int, clock_mhz: float) -> tuple:
+    """FP32 lane-operations per second at this clock: the probed FMA issue
+    rate per SM and cycle when a probe file exists, else the unit count."""
+    pr = load_probe()
+    per = pr.get("fp32_fma_per_sm_per_cycle")
+    if per:
+        return (sm_count * per * clock_mhz * 1e6 / 1e12,
+                f"probed: {per:.1f} FP32 lane-FMAs per SM per cycle (nk_probe, {pr.get('gpu', '?')}) x "
+                f"{sm_count} SMs x {clock_mhz:.0f} MHz")
+    return (sm_count * FP32_LANES_PER_SM * clock_mhz * 1e6 / 1e12,
+            f"derived: {sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x {clock_mhz:.0f} MHz (FP32 ops/s)")
 
 
 def host_cores() -> int:
@@ -356,8 +379,9 @@ def run_ours(args, rank, world, dist):
     # the block interval holds the two fused launches (for the tiled form each
     # after its workspace clear, about 50 MB here)
     achieved_tops = ops_entry * entries / blk_s / 1e12
-    peak_clock = clocks.get("sm_max_mhz") or 2070.0
-    peak_tops = SM_COUNT * FP32_LANES_PER_SM * peak_clock * 1e6 / 1e12
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    run_clock = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    peak_tops, peak_source = fp32_peak(sm_count, run_clock)
 
     # ---- plain layer-wise forms on sample tiles, at equal accuracy
     extra = {}
@@ -433,6 +457,10 @@ def run_ours(args, rank, world, dist):
             extra[f"{key}_iters_per_s"] = its / (ms / 1e3)
             extra[f"{key}_relres"] = max(rel)
     lam_used = h.last_lambda()
+    if not args.skip_plain:
+        extra.update(config1_leg(h, dev))
+        extra.update(erf_leg(h, dev))
+        extra.update(cv8_leg(h, dev))
     if not args.skip_grad:
         extra.update(grad_leg(h, dev, args.grad_support, args.grad_targets))
     if not args.skip_queue:
@@ -459,6 +487,7 @@ def run_ours(args, rank, world, dist):
                                 "PCG FP32 matvec + FP64 scalars + FP64 refinement",
                    "l2": "256 MB buffer written between timed steps"},
         "pcg_iters_per_s": statistics.mean(iters) / (statistics.mean(pcg_ms) / 1e3),
+        "pcg_l2": pcg_l2_roofline(n_tr, statistics.mean(iters), statistics.mean(pcg_ms) / 1e3),
         "pcg_iters": iters[-1],
         "pcg_relres": rels[-1],
         "lambda": lam_used,
@@ -469,9 +498,7 @@ def run_ours(args, rank, world, dist):
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "TFLOP/s",
                      "frac": achieved_tops / peak_tops, "traffic": None,
                      "kernel": "k_myrtle_tiled" if variant == 3 else "k_myrtle_fused",
-                     "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
-                                    f"{peak_clock:.0f} MHz (FP32 ops/s)",
-                     "ops_per_entry": ops_entry},
+                     "peak_source": peak_source, "ops_per_entry": ops_entry},
         "e2e": {"value": e2e_val, "unit": "entries/s",
                 "h2d_bytes_per_step": Xh.numel() * 4 + Yh.numel() * 8,
                 "d2h_bytes_per_step": Ah.numel() * 8 + Kteh.numel() * 4},
@@ -481,8 +508,26 @@ def run_ours(args, rank, world, dist):
         "cpu_pcg_baseline": cpu_pcg,
     }
     line.update(extra)
+    # the figures the metric compares, last in the line (a truncated tail of
+    # the output keeps them)
+    keys = ["mixed_over_plain_fp32", "plain_fp32_entries_per_s", "plain_fp64_entries_per_s", "pcg_iters_per_s",
+            "pcg_mixed_iters_per_s", "pcg_plain_fp64_iters_per_s", "fc3_gram_ms", "grad_backward_s",
+            "queue_graph_ms", "erf_entries_per_s", "cv8_entries_per_s", "config1_entries_per_s"]
+    line["summary"] = {"value": value, "e2e": e2e_val, "roofline_frac": achieved_tops / peak_tops,
+                       **{k: line.get(k) for k in keys if k in line}}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def pcg_l2_roofline(n: int, iters: float, seconds: float) -> dict:
+    """The headline solve's K (n^2 FP32, 16 MB at n = 2048) stays in L2: K
+    bytes per CG iteration x iterations / solve time (refinement sweeps
+    included), against the probed L2 read bandwidth."""
+    gbs = 4.0 * n * n * iters / seconds / 1e9
+    peak = load_probe().get("l2_read_GBs")
+    return {"bound": "l2", "achieved": gbs, "unit": "GB/s", "peak": peak, "frac": gbs / peak if peak else None,
+            "note": "K bytes per iteration / whole-solve time against the probed L2 read bandwidth; the "
+                    "iteration is latency-bound at this size (four dependent launches)"}
 
 
 def adjoint_layerwise_bytes(convs, hw: int, esize: int = 4) -> int:
@@ -643,6 +688,156 @@ def queue_leg(h, dev):
             "queue_pcg200_relres": max(rel)}
 
 
+def config1_leg(h, dev):
+    """The small FP64 configuration: Myrtle-5 (2,1,0), sigma_w^2 = 2,
+    sigma_b^2 = 0, 128 train + 32 test 8x8x3 images (N(0,1), standardised per
+    channel), 10 classes (one-hot minus 0.1): the full 128 x 128 and 32 x 128
+    blocks in PLAIN_FP64 and the FP64 Jacobi PCG solve with lambda =
+    1e-4 tr(K)/N.  One untimed warm-up, then one timed pass."""
+    import numpy as np
+    import torch
+
+    import nkdata
+
+    prob = nkdata.image_problem(128, 32, 8, n_classes=10, blur=False)
+    X = torch.tensor(np.concatenate([prob.x_train, prob.x_test]).astype(np.float32), device=dev)
+    Y = torch.tensor(prob.y_train, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def once():
+        q = h.self_diag(X, CONVS, SW2, SB2)
+        Ktr = h.block(X, q, X, q, CONVS, SW2, SB2, prec="plain_fp64", a_range=(0, 128), b_range=(0, 128))
+        Kte = h.block(X, q, X, q, CONVS, SW2, SB2, prec="plain_fp64", a_range=(128, 160), b_range=(0, 128))
+        return Ktr, Kte
+
+    Ktr, _ = once()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(stream)
+    Ktr, Kte = once()
+    ev[1].record(stream)
+    K32 = Ktr.float().contiguous()
+    _, its, rel = h.pcg_solve(K32, Y, -REL_LAMBDA, precond="jacobi", prec="plain_fp64", tol=1e-6, maxit=20000,
+                              allow_not_converged=True)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    t_blk = ev[0].elapsed_time(ev[1]) / 1e3
+    t_pcg = ev[1].elapsed_time(ev[2]) / 1e3
+    return {"config1_workload": "myrtle5_(2,1,0)_8x8_train128_test32_fp64_full_blocks_jacobi_pcg",
+            "config1_entries_per_s": (128 * 128 + 32 * 128) / t_blk, "config1_blocks_ms": 1e3 * t_blk,
+            "config1_pcg_iters": its, "config1_pcg_iters_per_s": its / t_pcg, "config1_pcg_relres": max(rel)}
+
+
+def erf_leg(h, dev):
+    """The Erf activation (the tuned-Myrtle options) on the headline workload:
+    Myrtle-5 (2,1,0) with Erf, sigma_w^2 = 2, sigma_b^2 = 0, the 2048-image
+    symmetric train block in the tiled fused form (MIXED)."""
+    import numpy as np
+    import torch
+
+    import nkdata
+
+    prob = nkdata.image_problem(2048, 512, 32, n_classes=10, blur=True)
+    X = torch.tensor(prob.x_train.astype(np.float32), device=dev)
+    q = h.self_diag(X, CONVS, SW2, SB2, act="erf")
+    K = torch.empty((2048, 2048), dtype=torch.float32, device=dev)
+    h.block(X, q, X, q, CONVS, SW2, SB2, prec="mixed", act="erf", symmetric=True, a_range=(0, 256),
+            b_range=(0, 256), out=K[:256, :256])
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    h.block(X, q, X, q, CONVS, SW2, SB2, prec="mixed", act="erf", symmetric=True, out=K)
+    b.record()
+    torch.cuda.synchronize()
+    h.sync_status()
+    t = a.elapsed_time(b) / 1e3
+    return {"erf_workload": "myrtle5_(2,1,0)_erf_32x32_train2048_symmetric_mixed_tiled",
+            "erf_entries_per_s": 2048 * 2049 / 2 / t, "erf_block_ms": 1e3 * t}
+
+
+def cv8_leg(h, dev):
+    """The CV8 listing (eight conv + ReLU layers, Flatten, Dense; sigma_w^2 = 2,
+    sigma_b^2 = 0.01) on the headline images: the 2048 symmetric train block
+    and the 512 x 2048 test block by the diagonal recursion (MIXED), and the
+    layer-wise FP32 form on a 16 x 16 sample for comparison."""
+    import numpy as np
+    import torch
+
+    import nkdata
+
+    prob = nkdata.image_problem(2048, 512, 32, n_classes=10, blur=True)
+    X = torch.tensor(np.concatenate([prob.x_train, prob.x_test]).astype(np.float32), device=dev)
+    convs, sb2 = (8,), 0.01
+    q = h.self_diag(X, convs, SW2, sb2)
+    Ktr = torch.empty((2048, 2048), dtype=torch.float32, device=dev)
+    Kte = torch.empty((512, 2048), dtype=torch.float32, device=dev)
+
+    def blocks():
+        h.block(X, q, X, q, convs, SW2, sb2, prec="mixed", readout="flatten", a_range=(0, 2048),
+                b_range=(0, 2048), symmetric=True, out=Ktr)
+        h.block(X, q, X, q, convs, SW2, sb2, prec="mixed", readout="flatten", a_range=(2048, 2560),
+                b_range=(0, 2048), out=Kte)
+
+    blocks()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    blocks()
+    ev[1].record()
+    ev[2].record()
+    Kp = h.block(X, q, X, q, convs, SW2, sb2, prec="plain_fp32", readout="flatten", a_range=(0, 16),
+                 b_range=(16, 32))
+    ev[3].record()
+    torch.cuda.synchronize()
+    h.sync_status()
+    t = ev[0].elapsed_time(ev[1]) / 1e3
+    tp = ev[2].elapsed_time(ev[3]) / 1e3
+    entries = 2048 * 2049 // 2 + 512 * 2048
+    return {"cv8_workload": "cv8_relu_32x32_train2048_test512_flatten_mixed_diagonal",
+            "cv8_entries_per_s": entries / t, "cv8_blocks_ms": 1e3 * t,
+            "cv8_plain_fp32_entries_per_s": 256 / tp,
+            "cv8_maxrel_mixed_vs_plain_fp32": float(((Ktr[:16, 16:32] - Kp).abs() / Kp.abs()).max())}
+
+
+def probe_peaks(path: str):
+    """Measures the peak rates the roofline fractions divide by (nk_probe:
+    FP32 and FP64 FMA issue, L2-resident and HBM reads) with the SM clocks
+    sampled during the probes, and writes them per SM and cycle to `path`."""
+    import torch
+
+    from paper_2303_05420_gb300.api import probe
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    props = torch.cuda.get_device_properties(dev)
+    sm = props.multi_processor_count
+    probe("fp32_fma", 1 << 10)  # context and module load
+    sampler = ClockSampler(0)
+    sampler.start()
+    res = {}
+    for name in ("fp32_fma", "fp64_fma", "l2_read", "hbm_read"):
+        best = (0.0, 0.0)
+        for _ in range(3):
+            r, ms = probe(name)
+            if r > best[0]:
+                best = (r, ms)
+        res[name] = best
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz")
+    out = {"gpu": props.name, "sm_count": sm, "clocks": clocks,
+           "fp32_fma_per_s": res["fp32_fma"][0], "fp64_fma_per_s": res["fp64_fma"][0],
+           "l2_read_GBs": res["l2_read"][0] / 1e9, "hbm_read_GBs": res["hbm_read"][0] / 1e9,
+           "fp32_fma_per_sm_per_cycle": res["fp32_fma"][0] / (sm * mhz * 1e6) if mhz else None,
+           "fp64_fma_per_sm_per_cycle": res["fp64_fma"][0] / (sm * mhz * 1e6) if mhz else None,
+           "how": "nk_probe (CUDA events, best of 3 after a warm-up): 8 independent FMA chains per thread at "
+                  "2048 threads per SM; float4 reads bypassing L1 of a 32 MB (L2) and a 1 GB (HBM) buffer; "
+                  "per-cycle rates divide by the median SM clock sampled during the probes"}
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps(out), flush=True)
+
+
 FC_N_TRAIN, FC_N_TEST, FC_D, FC_DEPTH = 50000, 10000, 3072, 3
 FC_SW2, FC_SB2 = 2.0, 0.01  # the FC3 listing's W_std = sqrt 2, b_std = 0.1
 
@@ -698,9 +893,11 @@ def fc_leg(h, dev, peaks, n=FC_N_TRAIN, m=FC_N_TEST):
                             "peak": peaks.get("bf16_tflops"),
                             "frac": (3 * alg / t_gram / 1e12) / peaks["bf16_tflops"]
                             if peaks.get("bf16_tflops") else None,
+                            "frac_algorithmic": (alg / t_gram / 1e12) / peaks["bf16_tflops"]
+                            if peaks.get("bf16_tflops") else None,
                             "note": "achieved = 2 d flops per unique entry (algorithmic); frac = "
                                     "tensor-pipe BF16 rate (3 products per split-BF16 entry) of measured "
-                                    "burst bf16 peak"}}
+                                    "burst bf16 peak; frac_algorithmic = achieved of the same peak"}}
     for prec in ["mixed", "plain_fp64"]:
         torch.cuda.synchronize()
         a, b = ev(), ev()
@@ -792,7 +989,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="nk", choices=["nk", "reference"])
     ap.add_argument("--config", default="headline", choices=sorted(CONFIGS))
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-pairs", type=int, default=20)
     ap.add_argument("--ref-pairs", type=int, default=4)
     ap.add_argument("--skip-plain", action="store_true")
@@ -811,7 +1008,12 @@ def main():
     ap.add_argument("--grad-targets", type=int, default=2048, help="target images of the gradient leg")
     ap.add_argument("--skip-grad", action="store_true",
                     help="skip the Myrtle-10 kernel-ridge gradient leg (100 support x 2048 targets)")
+    ap.add_argument("--probe-peaks", default=None, metavar="PATH",
+                    help="measure the peak rates (nk_probe) and write them to PATH as JSON, then exit")
     args = ap.parse_args()
+    if args.probe_peaks:
+        probe_peaks(args.probe_peaks)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -28,7 +28,8 @@ EXPORTS = ["nk_create", "nk_destroy", "nk_status_string", "nk_last_error", "nk_s
            "nk_q_size", "nk_launch_count", "nk_last_lambda", "nk_self_diag", "nk_block", "nk_block_backward", "nk_fc_block",
            "nk_autotune",
            "nk_autotune_set", "nk_block_fused_noalloc", "nk_block_queue", "nk_block_ntk", "nk_set_wait_limit", "nk_pcg_set_rank",
-           "nk_pcg_solve"]
+           "nk_pcg_solve", "nk_probe"]
+PROBE = {"fp32_fma": 0, "fp64_fma": 1, "l2_read": 2, "hbm_read": 3}
 
 
 class NkArch(ctypes.Structure):
@@ -123,6 +124,8 @@ def lib():
                                c_int, c_double, c_int, c_int, c_void_p, POINTER(c_int),
                                c_void_p, c_void_p]
     L.nk_pcg_solve.restype = c_int
+    L.nk_probe.argtypes = [c_int, c_int64, POINTER(c_double), POINTER(c_double), c_void_p]
+    L.nk_probe.restype = c_int
     _LIB = L
     return L
 

@@ -244,6 +244,16 @@ class Handle:
         return A, its.value, [rel[i] for i in range(R)]
 
 
+def probe(which: str, work: int = 0) -> Tuple[float, float]:
+    """(rate per second, kernel ms) of a machine probe (nk_probe): "fp32_fma"
+    and "fp64_fma" in lane-FMAs/s, "l2_read" and "hbm_read" in bytes/s."""
+    rate, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = lib().nk_probe(_lib.PROBE[which], int(work), byref(rate), byref(ms), c_void_p(_stream()))
+    if st != 0:
+        raise NkError(st, f"nk_probe {which}")
+    return rate.value, ms.value
+
+
 _DEFAULT: Optional[Handle] = None
 
 

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include "nk.h"
+#include "nk_probe.h"
 
 static int fails = 0;
 #define CHECK(cond)                                   \
@@ -27,7 +28,7 @@ int main(void) {
       (const void*)&nk_block,          (const void*)&nk_block_backward,   (const void*)&nk_fc_block,
       (const void*)&nk_autotune,       (const void*)&nk_autotune_set,     (const void*)&nk_block_fused_noalloc,
       (const void*)&nk_block_ntk,      (const void*)&nk_block_queue,      (const void*)&nk_pcg_set_rank,
-      (const void*)&nk_set_wait_limit,
+      (const void*)&nk_set_wait_limit, (const void*)&nk_probe,
       (const void*)&nk_pcg_solve,
   };
   for (size_t i = 0; i < sizeof(fns) / sizeof(fns[0]); ++i) CHECK(fns[i] != NULL);
