@@ -531,27 +531,39 @@ def pcg_l2_roofline(n: int, iters: float, seconds: float) -> dict:
 
 
 def adjoint_layerwise_bytes(convs, hw: int, esize: int = 4) -> int:
-    """Bytes the layer-wise adjoint (nk_block_backward, FP32) moves through
-    HBM per image pair, counting each pass over a pixel-pair tensor once
-    (E_s = (hw / 2^s)^4 elements at stage s): forward recomputation -- input
-    covariance write, per conv layer the conv's read and write and the ReLU
-    map's read and write, pools, the readout mean; reverse sweep -- the seed
-    fill, per layer the map adjoint (reads the stored pre-activation and the
-    gradient, writes the gradient and the q-gradient terms), the two q sums
-    (each reads those terms) and the conv adjoint's read and write, the pool
-    adjoints, and the two input adjoints."""
+    """Bytes the layer-fused adjoint (nk_block_backward, FP32) moves through
+    HBM per image pair (E_s = (hw / 2^s)^4 elements at stage s).  Forward:
+    the first layer writes its pre-activation (the input covariance is formed
+    on load), every later layer reads the previous one (mapped on load) and
+    writes its own, each pool reads the previous stage's last tensor and
+    writes the pooled one, the readout reads the last.  Reverse, per layer:
+    the stored pre-activation, the incoming gradient (none for the readout's
+    constant, the next stage's tensor through the pool adjoint, else this
+    stage's) and the outgoing gradient, plus the q-term partial sums (two
+    H^2 W buffers written and read); the input adjoints read the last
+    gradient twice.  Stage patterns without empty middle stages."""
     last = max(s for s, n in enumerate(convs) if n > 0)
     E = [(hw >> s) ** 4 for s in range(last + 1)]
-    tot = E[0]
+    Wd = [hw >> s for s in range(last + 1)]
+    tot = 0
+    first = True
     for s in range(last + 1):
         if s > 0:
             tot += E[s - 1] + E[s]
-        tot += 4 * convs[s] * E[s]
-    tot += 2 * E[last]
+        for _ in range(convs[s]):
+            tot += E[s] if first else 2 * E[s]
+            first = False
+    tot += E[last]
+    const = True
     for s in range(last, -1, -1):
-        tot += 8 * convs[s] * E[s]
-        if s > 0:
-            tot += E[s] + E[s - 1]
+        for k in range(convs[s] - 1, -1, -1):
+            tot += 2 * E[s] + 4 * E[s] // Wd[s]
+            if const:
+                const = False
+            elif k == convs[s] - 1:
+                tot += E[s + 1]
+            else:
+                tot += E[s]
     tot += 2 * E[0]
     return esize * tot
 
@@ -564,8 +576,8 @@ def adjoint_roofline(seconds: float, n_pairs: int, peaks: dict, convs=(3, 3, 3),
     peak = float(peaks.get("hbm_gbs", 6800.0))
     return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
             "bytes_per_pair": per_pair, "traffic": None,
-            "note": "layer-wise traffic model (each pixel-pair tensor pass read or written once) x pairs / "
-                    "backward time, against the measured copy bandwidth"}
+            "note": "layer-fused traffic model (adjoint_layerwise_bytes) x pairs / backward time, against the "
+                    "measured copy bandwidth; the passes are issue-bound, not bandwidth-bound"}
 
 
 def grad_leg(h, dev, n_sup=100, n_tgt=2048):

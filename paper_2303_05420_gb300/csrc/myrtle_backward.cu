@@ -1,5 +1,5 @@
-// nk_block_backward: adjoint of the Myrtle NNGP kernel block (plain layer-wise
-// form, FP32 or FP64).
+// nk_block_backward: adjoint of the Myrtle NNGP kernel block (layer-wise form,
+// FP32 or FP64).
 //
 // For a block K[i][j] = NNGP(Xa[i], Xb[j]) and an upstream gradient dK, it
 // accumulates dL/dXa, dL/dXb, dL/dsigma_w^2 and dL/dsigma_b^2 (+=), the
@@ -15,8 +15,20 @@
 // The self-variances q_l(p) = K_l(p,p;x,x) depend on x, sw2 and sb2 through
 // the banded self recursion; their gradients dq are reduced per pixel here
 // and pushed through the adjoint of that recursion (FP64) at the end.
-// Forward pixel-pair tensors of each layer are recomputed per chunk of pairs
-// and kept in HBM for the reverse sweep.
+//
+// Layer-fused passes.  Every pass over a pixel-pair tensor is one streamed
+// 3x3 diagonal stencil (k_conv_fused) whose input transform is applied while
+// a plane is loaded: forward, the input covariance (first layer) or the
+// previous layer's map of the stored pre-activation; reverse, the map adjoint
+// of this layer's stored pre-activation and the incoming gradient, which is
+// read from a full tensor, from the next stage's gradient through the pool
+// adjoint (index / 2, value / 16), or as the pair's readout constant.  The
+// reverse pass also takes the sigma sums and, per plane, the row and column
+// sums of the map's q-terms (small partial buffers, reduced per pixel after
+// the pass).  Only the pre-activation of each layer is stored (HBM); per pair
+// and stage-0 layer that is one write forward, two reads and one write in
+// reverse.  The next plane's loads are issued into registers before the
+// current plane's barriers, so their latency overlaps the stencil work.
 #include <algorithm>
 
 #include "myrtle_plain.cuh"
@@ -47,206 +59,419 @@ __global__ void k_pair_seed(const T* __restrict__ dK, int64_t lddk, const T* __r
   }
 }
 
-// mean of each pair's tensor (the forward value before the readout)
+// ---------------------------------------------------------------------------
+// Layer-fused streamed stencil.
+// ---------------------------------------------------------------------------
+enum { CIN_COV = 0, CIN_PLAIN = 1, CIN_MAP = 2, CIN_ADJ = 3 };
+enum { G_TENSOR = 0, G_POOLED = 1, G_CONST = 2 };
+
 template <typename T>
-__global__ void k_pair_mean(const T* __restrict__ in, int64_t HW2, T* __restrict__ out) {
+struct FArgs {
+  int64_t np, pair0, na, nb, a0, b0;
+  int sym, H, W;
+  const T* src;            // CIN_PLAIN / CIN_MAP: input tensor; CIN_ADJ: this layer's pre-activation
+  const float* Xa;         // CIN_COV: the images
+  const float* Xb;
+  int C;
+  int relu;                // CIN_MAP / CIN_ADJ: ReLU map (else identity)
+  const double* qda;       // self-variances (FP64 form) and their FP32 tables
+  const double* qdb;
+  const float* qsa;
+  const float* qsb;
+  int64_t nq;
+  int qoff;                // layer offset in the q rows (of the layer whose map is applied)
+  const T* gsrc;           // CIN_ADJ: gradient of this layer's post-activation
+  int gmode;               // G_TENSOR: same layout; G_POOLED: the next stage's tensor; G_CONST: [np]
+  T* out;                  // a S(v) + b of the transformed input v
+  T a, b;
+  T* prow;                 // CIN_ADJ: [np][H][H][W] per-plane row sums of the q-terms h
+  T* pcol;                 //          [np][H][H][W] per-plane column sums
+  double sb2, inv_sw2;
+  double* dsw2;
+  double* dsb2;
+};
+
+// The activation's scale factors of pixel p (image a) and p' (image b):
+// s = sqrt(q q'), rs = 1 / sqrt(q q').
+template <typename T>
+__device__ __forceinline__ void act_scale(const FArgs<T>& A, int64_t ia, int64_t ib, int p, int pp, T& s, T& rs) {
+  if constexpr (sizeof(T) == 8) {
+    s = sqrt(A.qda[ia * A.nq + A.qoff + p] * A.qdb[ib * A.nq + A.qoff + pp]);
+    rs = s > 0.0 ? 1.0 / s : 0.0;
+  } else {
+    const float2 s1 = reinterpret_cast<const float2*>(A.qsa)[ia * A.nq + A.qoff + p];
+    const float2 s2 = reinterpret_cast<const float2*>(A.qsb)[ib * A.nq + A.qoff + pp];
+    s = s1.y * s2.y;
+    rs = s1.x * s2.x;
+  }
+}
+
+// Raw input of element (p, p') = ((ii, jj), (kk, ll)) of pair pr: k, and
+// (reverse) the incoming gradient g.  W is the stage width.
+template <typename T, int MODE, int W>
+__device__ __forceinline__ void fetch_el(const FArgs<T>& A, int64_t pr, int64_t ia, int64_t ib, int ii, int jj,
+                                         int kk, int ll, T& k, T& g) {
+  const int HW = A.H * W;
+  const int p = ii * W + jj, pp = kk * W + ll;
+  if constexpr (MODE == CIN_COV) {
+    const float* xa = A.Xa + (ia * HW + p) * (int64_t)A.C;
+    const float* xb = A.Xb + (ib * HW + pp) * (int64_t)A.C;
+    T acc = 0;
+    for (int c = 0; c < A.C; ++c) acc += (T)xa[c] * (T)xb[c];
+    k = acc / (T)A.C;
+  } else {
+    k = A.src[pr * (int64_t)HW * HW + (int64_t)p * HW + pp];
+  }
+  if constexpr (MODE == CIN_ADJ) {
+    if (A.gmode == G_TENSOR) {
+      g = A.gsrc[pr * (int64_t)HW * HW + (int64_t)p * HW + pp];
+    } else if (A.gmode == G_POOLED) {
+      constexpr int Wn = W / 2;
+      const int HWn = (A.H >> 1) * Wn;
+      const int P = (ii >> 1) * Wn + (jj >> 1), PP = (kk >> 1) * Wn + (ll >> 1);
+      g = A.gsrc[pr * (int64_t)HWn * HWn + (int64_t)P * HWn + PP] * (T)(1.0 / 16.0);
+    } else {
+      g = A.gsrc[pr];
+    }
+  }
+}
+
+// The transform of one element: input covariance / plain value, the map, or
+// the map adjoint (h = its q-term, sa / sb the sigma sums).  FP32 evaluates J
+// and J' = pi - arccos c by the library's polynomial forms (nk_map.cuh), FP64
+// by acos.
+template <typename T>
+__device__ __forceinline__ void J_dJ(T c, T& J, T& dJ) {
+  if constexpr (sizeof(T) == 8) {
+    c = c < -1.0 ? -1.0 : (c > 1.0 ? 1.0 : c);
+    const double th = acos(c);
+    J = sqrt(fmax(1.0 - c * c, 0.0)) + c * (NK_PI_D - th);
+    dJ = NK_PI_D - th;
+  } else {
+    nk_J_dJ_f32(c, J, dJ);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T J_only(T c) {
+  if constexpr (sizeof(T) == 8) {
+    c = c < -1.0 ? -1.0 : (c > 1.0 ? 1.0 : c);
+    return sqrt(fmax(1.0 - c * c, 0.0)) + c * (NK_PI_D - acos(c));
+  } else {
+    return nk_J_f32(c);
+  }
+}
+
+template <typename T, int MODE>
+__device__ __forceinline__ T xform(const FArgs<T>& A, int64_t ia, int64_t ib, int p, int pp, T k, T g, T& h, T& sa,
+                                   T& sb) {
+  if constexpr (MODE == CIN_COV || MODE == CIN_PLAIN) {
+    return k;
+  } else {
+    const T inv2pi = (T)NK_INV_2PI_D;
+    if constexpr (MODE == CIN_MAP) {
+      if (!A.relu) return k;
+      T s, rs;
+      act_scale(A, ia, ib, p, pp, s, rs);
+      if (!(s > (T)0)) return (T)0;
+      return s * inv2pi * J_only<T>(k * rs);
+    } else {
+      T dk = g;
+      h = 0;
+      if (A.relu) {
+        dk = 0;
+        T s, rs;
+        act_scale(A, ia, ib, p, pp, s, rs);
+        if (s > (T)0) {
+          T J, dJ;
+          J_dJ<T>(k * rs, J, dJ);
+          const T Kt = s * inv2pi * J;
+          dk = g * dJ * inv2pi;
+          h = g * (Kt - k * dJ * inv2pi);
+        }
+      }
+      sa += dk * (k - (T)A.sb2);
+      sb += dk;
+      return dk;
+    }
+  }
+}
+
+// One block per (group of NPB pairs, diagonal d = k - i of the (i, k)
+// image-row planes); planes (i, i + d) of every pair of the group are
+// transformed, row-filtered along their (j, l) diagonal into a ring of
+// three, and each output plane sums three of them.  The loads of plane s + 2
+// are issued while plane s is processed (two register buffers), so about two
+// steps of work cover their latency.  W (the stage width) is a compile-time
+// constant and each thread's in-plane coordinates (jj, ll) are fixed, so the
+// per-element index arithmetic is a few adds.  Reverse: the q-terms' row sums
+// of a plane are warp shuffles when a warp covers a row (W >= 32), the column
+// sums per-thread partials reduced across warps; smaller stages reduce from
+// shared memory.
+template <typename T, int MODE, int W, int NPB>
+__global__ void __launch_bounds__(256) k_conv_fused(const __grid_constant__ FArgs<T> A) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  T* sh = reinterpret_cast<T*>(fsm);
+  constexpr int W2 = W * W, EPT = W2 > 256 ? W2 / 256 : 1;
+  constexpr bool WIDE = W >= 32;          // a warp covers (part of) one row
+  constexpr int RPW = WIDE ? W / 32 : 1;  // warps per row
+  constexpr int CG = WIDE ? 256 / W : 1;  // row groups of the column partials
+  const int H = A.H, HW = H * W;
+  T* slot = sh;                  // [NPB][3][W2] row-filtered planes
+  T* raw = sh + 3 * NPB * W2;    // [NPB][W2] transformed plane
+  T* hs = raw + NPB * W2;        // [NPB][W2] q-terms (narrow stages) / row and column partials (wide)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int d = (int)blockIdx.x - (H - 1);
+  const int i0 = d < 0 ? -d : 0;
+  const int i1 = (d > 0 ? H - d : H) - 1;
+  int jj_[EPT], ll_[EPT];
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    const int e = tid + u * 256;
+    jj_[u] = e / W;
+    ll_[u] = e % W;
+  }
+  double dsa = 0.0, dsb = 0.0;
+  for (int64_t pg = (int64_t)blockIdx.y * NPB; pg < A.np; pg += (int64_t)gridDim.y * NPB) {
+    int64_t ia[NPB], ib[NPB];
+    bool ok[NPB];
+#pragma unroll
+    for (int b = 0; b < NPB; ++b) {
+      ok[b] = pg + b < A.np;
+      int64_t i = 0, j = 0;
+      if (ok[b]) pair_of(A.pair0 + pg + b, A.na, A.nb, A.sym, &i, &j);
+      ia[b] = A.a0 + i;
+      ib[b] = A.b0 + j;
+    }
+    T k0[NPB][EPT], g0[NPB][EPT], k1[NPB][EPT], g1[NPB][EPT];
+    auto fetch = [&](int ii, T (&rk)[NPB][EPT], T (&rg)[NPB][EPT]) {
+      const int kk = ii + d;
+#pragma unroll
+      for (int b = 0; b < NPB; ++b)
+#pragma unroll
+        for (int u = 0; u < EPT; ++u) {
+          rk[b][u] = 0;
+          rg[b][u] = 0;
+          if (ok[b] && tid + u * 256 < W2)
+            fetch_el<T, MODE, W>(A, pg + b, ia[b], ib[b], ii, jj_[u], kk, ll_[u], rk[b][u], rg[b][u]);
+        }
+    };
+    // one step: transform plane s from (rk, rg), refill them with plane s + 2,
+    // row-filter plane s, reduce its q-terms, output plane s - 1
+    auto step = [&](int s, T (&rk)[NPB][EPT], T (&rg)[NPB][EPT]) {
+      if (s <= i1) {
+        const int kk = s + d;
+        T sa = 0, sb = 0;
+#pragma unroll
+        for (int b = 0; b < NPB; ++b) {
+          T colp = 0;
+#pragma unroll
+          for (int u = 0; u < EPT; ++u) {
+            const int e = tid + u * 256;
+            if (e < W2) {
+              T h = 0;
+              raw[b * W2 + e] = xform<T, MODE>(A, ia[b], ib[b], s * W + jj_[u], kk * W + ll_[u], rk[b][u], rg[b][u],
+                                               h, sa, sb);
+              if constexpr (MODE == CIN_ADJ) {
+                if constexpr (WIDE) {
+                  colp += h;
+                  T r = h;
+#pragma unroll
+                  for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+                  if (lane == 0) hs[b * W2 + jj_[u] * RPW + ll_[u] / 32] = r;  // row partial
+                } else {
+                  hs[b * W2 + e] = h;
+                }
+              }
+            }
+          }
+          if constexpr (MODE == CIN_ADJ && WIDE) hs[b * W2 + W * RPW + (tid / W) * W + ll_[0]] = colp;
+        }
+        dsa += (double)sa;
+        dsb += (double)sb;
+        if (s + 2 <= i1) fetch(s + 2, rk, rg);  // in flight during the next two steps
+      }
+      __syncthreads();
+      if (s <= i1) {
+        for (int e = tid; e < NPB * W2; e += 256) {
+          const int b = e / W2, f = e - b * W2;
+          const int jj = f / W, ll = f - jj * W;
+          const T* r = raw + b * W2;
+          T v = r[f];
+          if (jj > 0 && ll > 0) v += r[f - W - 1];
+          if (jj + 1 < W && ll + 1 < W) v += r[f + W + 1];
+          slot[(b * 3 + s % 3) * W2 + f] = v;
+        }
+        if constexpr (MODE == CIN_ADJ) {
+          const int kk = s + d;
+          for (int t = tid; t < NPB * 2 * W; t += 256) {
+            const int b = t / (2 * W), r = t - b * 2 * W;
+            if (!ok[b]) continue;
+            const T* hb = hs + b * W2;
+            T v = 0;
+            if constexpr (WIDE) {
+              if (r < W) {
+#pragma unroll
+                for (int c = 0; c < RPW; ++c) v += hb[r * RPW + c];
+              } else {
+#pragma unroll
+                for (int g = 0; g < CG; ++g) v += hb[W * RPW + g * W + (r - W)];
+              }
+            } else {
+              // skewed row reads avoid bank conflicts; column reads are consecutive
+              if (r < W) {
+                for (int l = 0; l < W; ++l) v += hb[r * W + ((l + r) & (W - 1))];
+              } else {
+                for (int jj = 0; jj < W; ++jj) v += hb[jj * W + (r - W)];
+              }
+            }
+            const int64_t base = (((pg + b) * H + s) * (int64_t)H + kk) * W;
+            if (r < W)
+              A.prow[base + r] = v;
+            else
+              A.pcol[base + r - W] = v;
+          }
+        }
+      }
+      __syncthreads();
+      if (s - 1 >= i0) {
+        const int io = s - 1, ko = io + d;
+        for (int e = tid; e < NPB * W2; e += 256) {
+          const int b = e / W2, f = e - b * W2;
+          if (!ok[b]) continue;
+          const T* sl = slot + b * 3 * W2;
+          T acc = sl[(io % 3) * W2 + f];
+          if (io > i0) acc += sl[((io + 2) % 3) * W2 + f];
+          if (io < i1) acc += sl[((io + 1) % 3) * W2 + f];
+          const int jj = f / W, ll = f - jj * W;
+          A.out[(pg + b) * (int64_t)HW * HW + (int64_t)(io * W + jj) * HW + ko * W + ll] = A.a * acc + A.b;
+        }
+      }
+    };
+    __syncthreads();  // the previous group's planes are no longer read
+    fetch(i0, k0, g0);
+    if (i0 + 1 <= i1) fetch(i0 + 1, k1, g1);
+    int s = i0;
+    for (; s + 1 <= i1 + 1; s += 2) {
+      step(s, k0, g0);
+      step(s + 1, k1, g1);
+    }
+    if (s <= i1 + 1) step(s, k0, g0);
+  }
+  if constexpr (MODE == CIN_ADJ) {
+    __shared__ double r1[8], r2[8];
+    for (int o = 16; o > 0; o >>= 1) {
+      dsa += __shfl_xor_sync(0xffffffffu, dsa, o);
+      dsb += __shfl_xor_sync(0xffffffffu, dsb, o);
+    }
+    if (lane == 0) {
+      r1[warp] = dsa;
+      r2[warp] = dsb;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double x = 0.0, y = 0.0;
+      for (int w = 0; w < 8; ++w) {
+        x += r1[w];
+        y += r2[w];
+      }
+      if (x != 0.0 || y != 0.0) {
+        atomicAdd(A.dsw2, x * A.inv_sw2);
+        atomicAdd(A.dsb2, y);
+      }
+    }
+  }
+}
+
+// Forward pool with the map of the previous layer applied on load:
+// out(P, P') = 1/16 sum_{a,b} map(src(2P + a, 2P' + b)) at output H x W.
+template <typename T>
+__global__ void k_pool_map(const FArgs<T> A, int Ho, int Wo) {
+  const int Hi = 2 * Ho, Wi = 2 * Wo;
+  const int64_t HWi = (int64_t)Hi * Wi, HWo = (int64_t)Ho * Wo;
+  const int64_t total = A.np * HWo * HWo;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pr = e / (HWo * HWo), rem = e - pr * HWo * HWo;
+    const int P = (int)(rem / HWo), PP = (int)(rem - (int64_t)P * HWo);
+    int64_t i, j;
+    pair_of(A.pair0 + pr, A.na, A.nb, A.sym, &i, &j);
+    const int64_t ia = A.a0 + i, ib = A.b0 + j;
+    const int I = P / Wo, J = P % Wo, K2 = PP / Wo, L = PP % Wo;
+    T acc = 0, h = 0, sa = 0, sb = 0;
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) {
+        const int p = (2 * I + a) * Wi + 2 * J + b;
+        for (int c = 0; c < 2; ++c)
+          for (int dd = 0; dd < 2; ++dd) {
+            const int pp = (2 * K2 + c) * Wi + 2 * L + dd;
+            const T k = A.src[pr * HWi * HWi + (int64_t)p * HWi + pp];
+            acc += xform<T, CIN_MAP>(A, ia, ib, p, pp, k, (T)0, h, sa, sb);
+          }
+      }
+    A.out[e] = acc / (T)16;
+  }
+}
+
+// Forward readout: the pair's mean of map(src) (before sw2 and sb2).
+template <typename T>
+__global__ void k_map_mean(const FArgs<T> A, T* __restrict__ mean) {
   __shared__ double red[32];
   const int64_t pr = blockIdx.x;
+  const int HW = A.H * A.W;
+  const int64_t HW2 = (int64_t)HW * HW;
+  int64_t i, j;
+  pair_of(A.pair0 + pr, A.na, A.nb, A.sym, &i, &j);
+  const int64_t ia = A.a0 + i, ib = A.b0 + j;
   double acc = 0.0;
-  for (int64_t e = threadIdx.x; e < HW2; e += blockDim.x) acc += (double)in[pr * HW2 + e];
+  T run = 0, h = 0, sa = 0, sb = 0;
+  int n = 0;
+  for (int64_t e = threadIdx.x; e < HW2; e += blockDim.x) {
+    const int p = (int)(e / HW), pp = (int)(e - (int64_t)p * HW);
+    run += xform<T, CIN_MAP>(A, ia, ib, p, pp, A.src[pr * HW2 + e], (T)0, h, sa, sb);
+    if (++n == 64) {
+      acc += (double)run;
+      run = 0;
+      n = 0;
+    }
+  }
+  acc += (double)run;
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x < 32) {
     acc = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (threadIdx.x == 0) out[pr] = (T)(acc / (double)HW2);
+    if (threadIdx.x == 0) mean[pr] = (T)(acc / (double)HW2);
   }
 }
 
+// The q-terms per pixel: dq_a[i][p] += sum_k prow(p's plane row, k) / (2 q_a(p)),
+// dq_b[j][p'] += sum_i pcol(i, p's plane) / (2 q_b(p')).
 template <typename T>
-__global__ void k_fill_pairs(T* __restrict__ buf, int64_t np, int64_t HW2, const T* __restrict__ val) {
-  const int64_t total = np * HW2;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x)
-    buf[e] = val[e / HW2];
-}
-
-// ReLU-map adjoint, in place on d (dKt in, dK out); h = dKt (Kt - K J'/(2 pi)).
-// The FP32 form reads the FP32 (1/sqrt q, sqrt q) tables, as the forward map
-// does: no FP64 load, conversion or division per entry (FP64 runs at a small
-// fraction of the FP32 rate here and bounded this kernel when it did).
-template <typename T>
-__global__ void k_map_adj(const T* __restrict__ Kpre, T* __restrict__ d, T* __restrict__ hbuf,
-                          int64_t np, int HW, int64_t na, int64_t nb, int sym, int64_t pair0,
-                          int64_t a0, int64_t b0, const double* __restrict__ qda,
-                          const double* __restrict__ qdb, const float* __restrict__ qsa,
-                          const float* __restrict__ qsb, int64_t nq, int qoff, double sb2, double inv_sw2,
-                          double* __restrict__ dsw2, double* __restrict__ dsb2) {
-  // the conv's sigma terms ride along: dsw2 += dK (K - sb2) / sw2, dsb2 += dK
-  // (sums in T over runs of at most 64 entries, added in FP64)
-  __shared__ double r1[32], r2[32];
-  double sa = 0.0, sbb = 0.0;
-  T ta = 0, tb = 0;
-  int run = 0;
-  const T tsb2 = (T)sb2;
-  // one pair per blockIdx.y step: its images are found once, not per entry
-  const int HW2 = HW * HW;
-  for (int64_t pr = blockIdx.y; pr < np; pr += gridDim.y) {
-   int64_t i, j;
-   pair_of(pair0 + pr, na, nb, sym, &i, &j);
-   for (int rem = blockIdx.x * blockDim.x + threadIdx.x; rem < HW2; rem += gridDim.x * blockDim.x) {
-    const int64_t e = pr * (int64_t)HW2 + rem;
-    const int p = rem / HW, pp = rem - p * HW;
-    T s, rs;  // sqrt(q q'), 1 / sqrt(q q')
-    if constexpr (sizeof(T) == 8) {
-      s = sqrt(qda[(a0 + i) * nq + qoff + p] * qdb[(b0 + j) * nq + qoff + pp]);
-      rs = s > 0.0 ? 1.0 / s : 0.0;
-    } else {
-      const float2 s1 = reinterpret_cast<const float2*>(qsa)[(a0 + i) * nq + qoff + p];
-      const float2 s2 = reinterpret_cast<const float2*>(qsb)[(b0 + j) * nq + qoff + pp];
-      s = s1.y * s2.y;
-      rs = s1.x * s2.x;
-    }
-    T dk = 0, h = 0;
-    if (s > (T)0) {
-      const T K = Kpre[e];
-      T c = K * rs;
-      c = c < (T)-1 ? (T)-1 : (c > (T)1 ? (T)1 : c);
-      const T th = acos(c);
-      const T J = sqrt(((T)1 - c * c) > (T)0 ? (T)1 - c * c : (T)0) + c * ((T)NK_PI_D - th);
-      const T dJ = (T)NK_PI_D - th;
-      const T inv2pi = (T)NK_INV_2PI_D;
-      const T Kt = s * inv2pi * J;
-      const T g = d[e];
-      dk = g * dJ * inv2pi;
-      h = g * (Kt - K * dJ * inv2pi);
-    }
-    d[e] = dk;
-    hbuf[e] = h;
-    ta += dk * (Kpre[e] - tsb2);
-    tb += dk;
-    if (++run == 64) {
-      sa += (double)ta;
-      sbb += (double)tb;
-      ta = tb = 0;
-      run = 0;
-    }
-   }
-  }
-  sa += (double)ta;
-  sbb += (double)tb;
-  for (int o = 16; o > 0; o >>= 1) {
-    sa += __shfl_xor_sync(0xffffffffu, sa, o);
-    sbb += __shfl_xor_sync(0xffffffffu, sbb, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    r1[threadIdx.x >> 5] = sa;
-    r2[threadIdx.x >> 5] = sbb;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    sa = (threadIdx.x < (blockDim.x >> 5)) ? r1[threadIdx.x] : 0.0;
-    sbb = (threadIdx.x < (blockDim.x >> 5)) ? r2[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) {
-      sa += __shfl_xor_sync(0xffffffffu, sa, o);
-      sbb += __shfl_xor_sync(0xffffffffu, sbb, o);
-    }
-    if (threadIdx.x == 0) {
-      atomicAdd(dsw2, sa * inv_sw2);
-      atomicAdd(dsb2, sbb);
-    }
-  }
-}
-
-// dq_a[i][p] += sum_p' h(p,p') / (2 q_a(p)): one warp per (pair, p)
-template <typename T>
-__global__ void k_rowsum_q(const T* __restrict__ hbuf, int64_t np, int HW, int64_t na, int64_t nb,
-                           int sym, int64_t pair0, int64_t a0, const double* __restrict__ qda,
-                           int64_t nq, int qoff, T* __restrict__ dqa) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t w = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); w < np * HW; w += nw) {
-    const int64_t pr = w / HW;
-    const int p = (int)(w - pr * HW);
-    const T* row = hbuf + (pr * HW + p) * (int64_t)HW;
-    T acc = 0;
-    for (int k = lane; k < HW; k += 32) acc += row[k];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      int64_t i, j;
-      pair_of(pair0 + pr, na, nb, sym, &i, &j);
-      const double q = qda[(a0 + i) * nq + qoff + p];
-      if (q > 0.0) atomicAdd(dqa + i * nq + qoff + p, (T)((double)acc / (2.0 * q)));
-    }
-  }
-}
-
-// dq_b[j][p'] += sum_p h(p,p') / (2 q_b(p')): one thread per (pair, p')
-template <typename T>
-__global__ void k_colsum_q(const T* __restrict__ hbuf, int64_t np, int HW, int64_t na, int64_t nb,
-                           int sym, int64_t pair0, int64_t b0, const double* __restrict__ qdb,
-                           int64_t nq, int qoff, T* __restrict__ dqb) {
-  const int64_t total = np * HW;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+__global__ void k_qsum(const FArgs<T> A, T* __restrict__ dqa, T* __restrict__ dqb) {
+  const int H = A.H, W = A.W, HW = H * W;
+  const int64_t total = A.np * HW;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 2 * total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t pr = e / HW;
-    const int pp = (int)(e - pr * HW);
-    const T* col = hbuf + pr * (int64_t)HW * HW + pp;
-    T acc = 0;
-    for (int p = 0; p < HW; ++p) acc += col[(int64_t)p * HW];
+    const bool col = e >= total;
+    const int64_t f = col ? e - total : e;
+    const int64_t pr = f / HW;
+    const int p = (int)(f - pr * HW);
+    const int r = p / W, c = p - r * W;
     int64_t i, j;
-    pair_of(pair0 + pr, na, nb, sym, &i, &j);
-    const double q = qdb[(b0 + j) * nq + qoff + pp];
-    if (q > 0.0) atomicAdd(dqb + j * nq + qoff + pp, (T)((double)acc / (2.0 * q)));
-  }
-}
-
-// dsw2 += sum d (Kpre - sb2) / sw2 ; dsb2 += sum d
-template <typename T>
-__global__ void k_sigma_terms(const T* __restrict__ d, const T* __restrict__ Kpre, int64_t total,
-                              double sb2, double inv_sw2, double* __restrict__ dsw2,
-                              double* __restrict__ dsb2) {
-  __shared__ double r1[32], r2[32];
-  // sums in T over runs of at most 64 elements, added in FP64 (FP64
-  // arithmetic runs at 1/64 of the FP32 rate on this part)
-  double a = 0.0, b = 0.0;
-  T ta = 0, tb = 0;
-  const T tsb2 = (T)sb2;
-  int run = 0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const T g = d[e];
-    ta += g * (Kpre[e] - tsb2);
-    tb += g;
-    if (++run == 64) {
-      a += (double)ta;
-      b += (double)tb;
-      ta = tb = 0;
-      run = 0;
-    }
-  }
-  a += (double)ta;
-  b += (double)tb;
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    r1[threadIdx.x >> 5] = a;
-    r2[threadIdx.x >> 5] = b;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    a = (threadIdx.x < (blockDim.x >> 5)) ? r1[threadIdx.x] : 0.0;
-    b = (threadIdx.x < (blockDim.x >> 5)) ? r2[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_xor_sync(0xffffffffu, a, o);
-      b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    if (threadIdx.x == 0) {
-      atomicAdd(dsw2, a * inv_sw2);
-      atomicAdd(dsb2, b);
+    pair_of(A.pair0 + pr, A.na, A.nb, A.sym, &i, &j);
+    T acc = 0;
+    if (!col) {
+      const T* base = A.prow + ((pr * H + r) * (int64_t)H) * W + c;  // (i = r, k, j = c)
+      for (int k = 0; k < H; ++k) acc += base[(int64_t)k * W];
+      const double q = A.qda[(A.a0 + i) * A.nq + A.qoff + p];
+      if (q > 0.0 && acc != (T)0) atomicAdd(dqa + i * A.nq + A.qoff + p, (T)((double)acc / (2.0 * q)));
+    } else {
+      const T* base = A.pcol + ((pr * H) * (int64_t)H + r) * W + c;  // (i, k = r, l = c)
+      for (int ii = 0; ii < H; ++ii) acc += base[(int64_t)ii * H * W];
+      const double q = A.qdb[(A.b0 + j) * A.nq + A.qoff + p];
+      if (q > 0.0 && acc != (T)0) atomicAdd(dqb + j * A.nq + A.qoff + p, (T)((double)acc / (2.0 * q)));
     }
   }
 }
@@ -589,8 +814,9 @@ k_self_adj(SelfAdjGeom G, double sw2, double sb2, const float* __restrict__ X, i
 template <typename T>
 struct BwdPlan {
   int64_t chunk;
-  size_t stored_per_pair;  // elements of T
-  size_t hw0sq;
+  size_t stored_per_pair;  // elements of T: every layer's pre-activation
+  size_t hw0sq;            // elements of the largest (stage-0) pair tensor
+  size_t part_per_pair;    // elements of one partial-sum buffer (largest stage)
   size_t bytes;            // total workspace
   size_t self_bytes;
   SelfAdjGeom sg;
@@ -601,13 +827,14 @@ template <typename T>
 BwdPlan<T> plan_backward(const NkGeom& g, int64_t npairs, int64_t na, int64_t nb, int sym, int sm) {
   BwdPlan<T> P = {};
   P.hw0sq = (size_t)g.Hs[0] * g.Ws[0] * g.Hs[0] * g.Ws[0];
+  P.part_per_pair = (size_t)g.Hs[0] * g.Hs[0] * g.Ws[0];
   int layer = 0;
   for (int s = 0; s < g.n_stages; ++s)
     for (int k = 0; k < g.convs[s]; ++k, ++layer) {
       const size_t hw = (size_t)g.Hs[s] * g.Ws[s];
       P.stored_per_pair += hw * hw;
     }
-  const size_t per_pair = (P.stored_per_pair + 3 * P.hw0sq + 2) * sizeof(T);
+  const size_t per_pair = (P.stored_per_pair + 2 * P.hw0sq + 2 * P.part_per_pair + 2) * sizeof(T);
   const size_t budget = (size_t)3 << 30;
   P.chunk = (int64_t)std::max<size_t>(1, budget / per_pair);
   if (P.chunk > npairs) P.chunk = npairs;
@@ -634,12 +861,43 @@ BwdPlan<T> plan_backward(const NkGeom& g, int64_t npairs, int64_t na, int64_t nb
   return P;
 }
 
+// One streamed stencil pass (k_conv_fused) over the chunk's pair tensors at
+// stage resolution A.H x A.W: two pairs per block at the 32 x 32 stage (four
+// at the smaller ones, one at 64 x 64).
+template <typename T, int MODE, int W, int NPB>
+cudaError_t conv_launch(const FArgs<T>& A, cudaStream_t st) {
+  const size_t smem = (size_t)(MODE == CIN_ADJ ? 5 : 4) * NPB * W * W * sizeof(T);
+  const dim3 grid((unsigned)(2 * A.H - 1), (unsigned)std::min<int64_t>((A.np + NPB - 1) / NPB, 65535));
+  cudaError_t e = cudaFuncSetAttribute(k_conv_fused<T, MODE, W, NPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_conv_fused<T, MODE, W, NPB><<<grid, 256, smem, st>>>(A);
+  return cudaGetLastError();
+}
+
+// Stage widths 1 .. 64 (powers of two: the 2x2 pools halve 8 .. 64 pixel
+// images); nk_block_backward refuses the others.
+template <typename T, int MODE>
+cudaError_t conv_pass(const FArgs<T>& A, cudaStream_t st) {
+  switch (A.W) {
+    case 1: return conv_launch<T, MODE, 1, 4>(A, st);
+    case 2: return conv_launch<T, MODE, 2, 4>(A, st);
+    case 4: return conv_launch<T, MODE, 4, 4>(A, st);
+    case 8: return conv_launch<T, MODE, 8, 4>(A, st);
+    case 16: return conv_launch<T, MODE, 16, 4>(A, st);
+    case 32: return conv_launch<T, MODE, 32, 1>(A, st);
+    case 64: return conv_launch<T, MODE, 64, 1>(A, st);
+  }
+  return cudaErrorNotSupported;
+}
+
 template <typename T>
 cudaError_t run_backward(const NkGeom& g, double sw2, double sb2, const float* Xa, const double* qda,
                          const float* qsa, int64_t a0, int64_t a1, const float* Xb, const double* qdb,
                          const float* qsb, int64_t b0, int64_t b1, const T* dK, int64_t lddk, int sym, T* dXa, T* dXb,
                          double* dsw2, double* dsb2, void* ws, const BwdPlan<T>& P, cudaStream_t st,
                          int64_t* launches, unsigned int* dstatus) {
+  (void)dstatus;
   const int64_t na = a1 - a0, nb = b1 - b0;
   const int64_t npairs = sym ? na * (na + 1) / 2 : na * nb;
   const int64_t chunk = P.chunk;
@@ -651,9 +909,10 @@ cudaError_t run_backward(const NkGeom& g, double sw2, double sb2, const float* X
     return p;
   };
   T* stored = reinterpret_cast<T*>(take(P.stored_per_pair * chunk * sizeof(T)));
-  T* cur0 = reinterpret_cast<T*>(take(P.hw0sq * chunk * sizeof(T)));
-  T* nxt0 = reinterpret_cast<T*>(take(P.hw0sq * chunk * sizeof(T)));
-  T* hbuf = reinterpret_cast<T*>(take(P.hw0sq * chunk * sizeof(T)));
+  T* buf0 = reinterpret_cast<T*>(take(P.hw0sq * chunk * sizeof(T)));
+  T* buf1 = reinterpret_cast<T*>(take(P.hw0sq * chunk * sizeof(T)));
+  T* prow = reinterpret_cast<T*>(take(P.part_per_pair * chunk * sizeof(T)));
+  T* pcol = reinterpret_cast<T*>(take(P.part_per_pair * chunk * sizeof(T)));
   T* useed = reinterpret_cast<T*>(take(chunk * sizeof(T)));
   T* gmean = reinterpret_cast<T*>(take(chunk * sizeof(T)));
   T* dqa = reinterpret_cast<T*>(take((size_t)na * g.nq * sizeof(T)));
@@ -671,98 +930,146 @@ cudaError_t run_backward(const NkGeom& g, double sw2, double sb2, const float* X
 
   for (int64_t pair0 = 0; pair0 < npairs; pair0 += chunk) {
     const int64_t np = std::min<int64_t>(chunk, npairs - pair0);
-    // ---- forward, storing each layer's pre-activation tensor
-    T* cur = cur0;
-    T* nxt = nxt0;
+    FArgs<T> A = {};
+    A.np = np;
+    A.pair0 = pair0;
+    A.na = na;
+    A.nb = nb;
+    A.a0 = a0;
+    A.b0 = b0;
+    A.sym = sym;
+    A.Xa = Xa;
+    A.Xb = Xb;
+    A.C = g.C;
+    A.relu = relu;
+    A.qda = qda;
+    A.qdb = qdb;
+    A.qsa = qsa;
+    A.qsb = qsb;
+    A.nq = g.nq;
+    A.prow = prow;
+    A.pcol = pcol;
+    A.sb2 = sb2;
+    A.inv_sw2 = 1.0 / sw2;
+    A.dsw2 = dsw2;
+    A.dsb2 = dsb2;
     T* Kst[NK_MAX_LAYERS];
+    int lstage[NK_MAX_LAYERS];
     {
       size_t off = 0;
       int layer = 0;
       for (int s = 0; s < g.n_stages; ++s)
         for (int k = 0; k < g.convs[s]; ++k, ++layer) {
           Kst[layer] = stored + off * np;
+          lstage[layer] = s;
           off += (size_t)g.Hs[s] * g.Ws[s] * g.Hs[s] * g.Ws[s];
         }
     }
-    ++*launches;
-    k_input_cov<T><<<pair_grid(np, (int64_t)P.hw0sq), 256, 0, st>>>(Xa, Xb, a0, b0, na, nb, sym, pair0, np,
-                                                                     g.Hs[0], g.Ws[0], g.C, cur);
+    // ---- forward: store each layer's pre-activation; the map of the
+    // previous layer is applied as the next pass loads it
+    const T* pend = nullptr;  // tensor the next pass reads (after its map, if pend_layer >= 0)
+    int pend_layer = -1;
     int layer = 0;
     for (int s = 0; s <= last_conv_stage; ++s) {
-      const int H = g.Hs[s], W = g.Ws[s];
-      const int64_t HW = (int64_t)H * W;
+      A.H = g.Hs[s];
+      A.W = g.Ws[s];
       if (s > 0) {
+        T* pooled = (pend == buf0) ? buf1 : buf0;
+        const int64_t HWo = (int64_t)A.H * A.W;
+        FArgs<T> B = A;
+        B.src = pend;
+        B.out = pooled;
+        B.relu = relu && pend_layer >= 0;
+        B.qoff = pend_layer >= 0 ? g.layer_qoff[pend_layer] : 0;
         ++*launches;
-        k_pool<T><<<grid_for(np * HW * HW), 256, 0, st>>>(cur, nxt, np, 2 * H, 2 * W);
-        T* t = cur; cur = nxt; nxt = t;
+        k_pool_map<T><<<grid_for(np * HWo * HWo), 256, 0, st>>>(B, A.H, A.W);
+        pend = pooled;
+        pend_layer = -1;
       }
       for (int k = 0; k < g.convs[s]; ++k, ++layer) {
+        A.out = Kst[layer];
+        A.a = a_conv;
+        A.b = (T)sb2;
         ++*launches;
-        conv_layer<T>(cur, Kst[layer], np, H, W, g.filter, a_conv, (T)sb2, st);
-        if (relu) {
-          // the pre-activation stays in Kst for the reverse sweep
-          ++*launches;
-          k_relu<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(Kst[layer], nxt, np, (int)HW, na, nb, sym, pair0, a0,
-                                                            b0, qda, qdb, qsa, qsb, g.nq, g.layer_qoff[layer],
-                                                            dstatus);
+        if (layer == 0) {
+          e = conv_pass<T, CIN_COV>(A, st);
+        } else if (pend_layer >= 0) {
+          A.src = pend;
+          A.qoff = g.layer_qoff[pend_layer];
+          e = conv_pass<T, CIN_MAP>(A, st);
         } else {
-          e = cudaMemcpyAsync(nxt, Kst[layer], (size_t)np * HW * HW * sizeof(T), cudaMemcpyDeviceToDevice, st);
-          if (e != cudaSuccess) return e;
+          A.src = pend;
+          e = conv_pass<T, CIN_PLAIN>(A, st);
         }
-        T* t = cur; cur = nxt; nxt = t;
+        if (e != cudaSuccess) return e;
+        pend = Kst[layer];
+        pend_layer = layer;
       }
     }
-    // cur: post-activation of the last conv layer; its mean is the readout's
-    const int64_t HWl = (int64_t)g.Hs[last_conv_stage] * g.Ws[last_conv_stage];
-    ++*launches;
-    k_pair_mean<T><<<(unsigned)np, 256, 0, st>>>(cur, HWl * HWl, gmean);
+    // readout value: the mean of the last layer's post-activation
+    {
+      FArgs<T> B = A;
+      B.H = g.Hs[last_conv_stage];
+      B.W = g.Ws[last_conv_stage];
+      B.src = pend;
+      B.qoff = g.layer_qoff[pend_layer];
+      ++*launches;
+      k_map_mean<T><<<(unsigned)np, 256, 0, st>>>(B, gmean);
+    }
     // ---- reverse
     ++*launches;
     k_pair_seed<T><<<grid_for(np), 256, 0, st>>>(dK, lddk, gmean, na, nb, sym, pair0, np, sw2, hwl * hwl, useed,
                                                  dsw2, dsb2);
-    ++*launches;
-    k_fill_pairs<T><<<grid_for(np * HWl * HWl), 256, 0, st>>>(cur, np, HWl * HWl, useed);
+    const T* gcur = useed;  // gradient of the current layer's post-activation
+    int gmode = G_CONST;
     for (int s = last_conv_stage; s >= 0; --s) {
-      const int H = g.Hs[s], W = g.Ws[s];
-      const int64_t HW = (int64_t)H * W;
+      A.H = g.Hs[s];
+      A.W = g.Ws[s];
       for (int k = g.convs[s] - 1; k >= 0; --k) {
         --layer;
-        if (relu) {
-          *launches += 3;
-          k_map_adj<T><<<pair_grid(np, HW * HW), 256, 0, st>>>(Kst[layer], cur, hbuf, np, (int)HW, na, nb, sym,
-                                                               pair0, a0, b0, qda, qdb, qsa, qsb, g.nq,
-                                                               g.layer_qoff[layer], sb2, 1.0 / sw2, dsw2, dsb2);
-          k_rowsum_q<T><<<grid_for(np * HW * 32), 256, 0, st>>>(hbuf, np, (int)HW, na, nb, sym, pair0, a0, qda,
-                                                                g.nq, g.layer_qoff[layer], dqa);
-          k_colsum_q<T><<<grid_for(np * HW), 256, 0, st>>>(hbuf, np, (int)HW, na, nb, sym, pair0, b0, qdb, g.nq,
-                                                           g.layer_qoff[layer], dqb);
-        }
+        T* out = (gcur == buf0) ? buf1 : buf0;
+        A.src = Kst[layer];
+        A.qoff = g.layer_qoff[layer];
+        A.gsrc = gcur;
+        A.gmode = gmode;
+        A.out = out;
+        A.a = a_conv;
+        A.b = (T)0;
         ++*launches;
-        if (!relu) {  // with a ReLU the map adjoint has added the sigma terms
+        e = conv_pass<T, CIN_ADJ>(A, st);
+        if (e != cudaSuccess) return e;
+        if (relu) {
           ++*launches;
-          k_sigma_terms<T><<<std::min(grid_for(np * HW * HW), 1024), 256, 0, st>>>(cur, Kst[layer], np * HW * HW,
-                                                                                 sb2, 1.0 / sw2, dsw2, dsb2);
+          k_qsum<T><<<grid_for(2 * np * (int64_t)A.H * A.W), 256, 0, st>>>(A, dqa, dqb);
         }
-        conv_layer<T>(cur, nxt, np, H, W, g.filter, a_conv, (T)0, st);
-        T* t = cur; cur = nxt; nxt = t;
+        gcur = out;
+        gmode = G_TENSOR;
       }
       if (s > 0) {
-        const int64_t HWp = 4 * HW;
-        ++*launches;
-        k_pool_adj<T><<<grid_for(np * HWp * HWp), 256, 0, st>>>(cur, nxt, np, H, W);
-        T* t = cur; cur = nxt; nxt = t;
+        if (g.convs[s - 1] > 0) {
+          gmode = G_POOLED;  // the previous stage's last layer reads it through the pool adjoint
+        } else {
+          // an empty stage: its input gradient is the pool adjoint itself
+          T* out = (gcur == buf0) ? buf1 : buf0;
+          const int64_t HWp = 4 * (int64_t)A.H * A.W;
+          ++*launches;
+          k_pool_adj<T><<<grid_for(np * HWp * HWp), 256, 0, st>>>(gcur, out, np, A.H, A.W);
+          gcur = out;
+          gmode = G_TENSOR;
+        }
       }
     }
+    // gcur: gradient of the input covariance K_0
     const int HW0 = g.Hs[0] * g.Ws[0];
     if (dXa) {
       ++*launches;
-      k_seed_adj_a<T><<<grid_for((int64_t)np * HW0 * 32), 256, 0, st>>>(cur, Xb, np, HW0, g.C, na, nb, sym, pair0,
+      k_seed_adj_a<T><<<grid_for((int64_t)np * HW0 * 32), 256, 0, st>>>(gcur, Xb, np, HW0, g.C, na, nb, sym, pair0,
                                                                         a0, b0, dXa);
     }
     T* dXb_eff = sym ? dXa : dXb;
     if (dXb_eff) {
       ++*launches;
-      k_seed_adj_b<T><<<grid_for((int64_t)np * HW0), 256, 0, st>>>(cur, Xa, np, HW0, g.C, na, nb, sym, pair0, a0,
+      k_seed_adj_b<T><<<grid_for((int64_t)np * HW0), 256, 0, st>>>(gcur, Xa, np, HW0, g.C, na, nb, sym, pair0, a0,
                                                                    b0, dXb_eff);
     }
     e = cudaGetLastError();

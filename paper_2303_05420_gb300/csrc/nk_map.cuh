@@ -123,6 +123,19 @@ __device__ __forceinline__ double nk_erf_map_f64(double K, double q1, double q2)
   return (2.0 / NK_PI_D) * asin(c);
 }
 
+// J(c) and J'(c) = pi - arccos c together, from one arcsine: J' = pi/2 +
+// asin c and J = sqrt(1 - c^2) + c J' (the adjoint needs both).  Near c = -1
+// the two terms of J cancel to (1 + c)^{3/2}; the absolute error stays at
+// FP32 rounding of sqrt(1 - c^2), which is what the adjoint's products see.
+__device__ __forceinline__ void nk_J_dJ_f32(float c, float& J, float& dJ) {
+  c = fminf(fmaxf(c, -1.f), 1.f);
+  const float sn = nk_sqrt_approx(fmaf(-c, c, 1.f));
+  const float a = fabsf(c);
+  const float as = nk_asin_small(fminf(a, sn));
+  dJ = NK_HALF_PI_F + copysignf((a > sn) ? (NK_HALF_PI_F - as) : as, c);
+  J = fmaf(c, dJ, sn);
+}
+
 // J(c) in FP64 with the CUDA double-precision arccos.
 __device__ __forceinline__ double nk_J_f64(double c) {
   c = fmin(fmax(c, -1.0), 1.0);
