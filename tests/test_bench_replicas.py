@@ -97,16 +97,25 @@ def test_reference_arm_line_on_cpu():
 
 
 def test_adjoint_traffic_model():
-    """The adjoint's traffic model counts 41 stage-0 tensor passes per pair of
-    a three-stage net (1 input covariance, 12 forward, 1 pool, 1 pool adjoint,
-    24 reverse, 2 input adjoints) and scales with the pair count and time."""
+    """The layer-fused adjoint's traffic model, counted by hand for a
+    three-stage net at 32x32 (E_s = (32 / 2^s)^4, widths 32, 16, 8):
+    stage 0: forward 5 passes (input covariance write, two read+write) and
+    the pool's read; reverse 2 + 3 + 3 (the last layer reads the pooled
+    gradient of stage 1 instead of a stage-0 tensor), q-term partials
+    3 x 4 E0 / 32, input adjoints 2 -> 16 E0 + 12 E0 / 32;
+    stage 1: pool write, 3 x 2 forward, the next pool's read, reverse
+    3 + 3 + 2 and stage 0's pooled-gradient read, partials 3 x 4 E1 / 16 ->
+    17 E1 + 12 E1 / 16;  stage 2: pool write, 3 x 2 forward, the readout's
+    read, reverse 2 (readout constant) + 3 + 3 and stage 1's pooled-gradient
+    read, partials 3 x 4 E2 / 8 -> 17 E2 + 12 E2 / 8."""
     import bench
 
     E0, E1, E2 = 32 ** 4, 16 ** 4, 8 ** 4
     b = bench.adjoint_layerwise_bytes((3, 3, 3), 32)
-    assert b == 4 * (41 * E0 + 40 * E1 + 40 * E2)
-    # a single-stage net: input cov, conv+relu, mean, fill, reverse, input adjoints
-    assert bench.adjoint_layerwise_bytes((1,), 8) == 4 * (1 + 4 + 2 + 8 + 2) * 8 ** 4
+    assert b == 4 * (16 * E0 + 12 * E0 // 32 + 17 * E1 + 12 * E1 // 16 + 17 * E2 + 12 * E2 // 8)
+    # a single-stage net: input covariance write, readout read, one reverse
+    # pass (constant gradient) with its partials, two input adjoints
+    assert bench.adjoint_layerwise_bytes((1,), 8) == 4 * ((1 + 1 + 2 + 2) * 8 ** 4 + 4 * 8 ** 4 // 8)
     r = bench.adjoint_roofline(2.0, 1000, {"hbm_gbs": 5000.0})
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert abs(r["achieved"] - b * 1000 / 2.0 / 1e9) < 1e-9 and abs(r["frac"] - r["achieved"] / 5000.0) < 1e-12
