@@ -20,7 +20,7 @@
 //    outputs are recomputed, not exchanged); the p-side tables cover the
 //    band's rows, the p'-side tables the window of rows (r + t_y) mod R and
 //    columns (c + t_x) mod R it touches.  At 64x64 with two stage-0 layers
-//    the tables take 194 KB; 64 tasks a pair.
+//    the tables take 198 KB; 64 tasks a pair.
 //  * the pooled output goes into a per-pair slot in global memory (L2
 //    resident: a ring of S slots) by vector atomic adds; rows are paired in
 //    registers, columns too when t_x is even.
@@ -53,7 +53,7 @@ namespace nkf {
 namespace tiled {
 
 // Threads per CTA: 512 with one CTA per SM wherever 64x64 blocks are present
-// (their tables take 194 KB); 256 with two CTAs per SM for 32x32-only
+// (their tables take 198 KB); 256 with two CTAs per SM for 32x32-only
 // launches (97 KB each), so that one CTA's table staging and barriers
 // overlap the other's row streams.
 constexpr int MAX_WARPS = 16;
@@ -72,6 +72,19 @@ struct G0 {
   static constexpr int WT = TX * YW;          // warp tasks per CTA task
   static constexpr int SXP = R + NQ;          // p-side row stride: one pad after each part
   static constexpr int SQ = R + TX - 1;       // p'-side window columns (odd)
+  // p'-side window layout.  At 64x64 a warp holds 16 row parts (4 columns
+  // apart) of 2 shifts t_y, so row-major tables put the parts' float2 / float4
+  // reads on 4 (or 2) bank groups.  There the window is stored column-phase
+  // major within a row, column c at (c mod 4) NPH + c / 4, so that for a fixed
+  // element k a warp's parts read consecutive entries; the row strides make
+  // the two t_y rows fall on the other half of the banks (float2 tables:
+  // 72 = 8 mod 16 entries; x', float4: 76 = 4 mod 8).  32x32 keeps the plain
+  // rows (conflict-free there).
+  static constexpr bool PH = (R == 64);
+  static constexpr int NPH = (SQ + 3) / 4;                  // column groups of a phased row
+  static constexpr int SQQ = PH ? 4 * NPH : SQ;             // row stride of the q tables
+  static constexpr int SQX = PH ? 4 * NPH + 4 : SQ;         // row stride of the x' table
+  static_assert(!PH || (SQQ % 16 == 8 && SQX % 8 == 4), "phased strides");
   static_assert(R % B == 0 && COLS % 2 == 0 && SQ % 2 == 1, "tiling");
   static_assert(NT0 == sched::tasks_per_pair(R), "task count of the item order (tiled_schedule.h)");
 };
@@ -83,10 +96,11 @@ struct L0 {
   static constexpr int NRP = G::B + HALO;  // streamed rows of a band (at most)
   static constexpr int NRQ = NRP + G::TY - 1;
   static constexpr int PL = NRP * G::SXP;  // p-side layer stride (elements)
-  static constexpr int QL = NRQ * G::SQ;
+  static constexpr int QL = NRQ * G::SQQ;  // p'-side layer stride of the q tables
+  static constexpr int QLX = NRQ * G::SQX; // p'-side x' table
   static constexpr size_t xs_off = 0;
   static constexpr size_t xq_off = xs_off + (size_t)PL * 16;
-  static constexpr size_t p_off = xq_off + (size_t)QL * 16;
+  static constexpr size_t p_off = xq_off + (size_t)QLX * 16;
   static constexpr size_t q_off = p_off + (size_t)N * PL * 8;
   static constexpr size_t bytes = q_off + (size_t)N * QL * 8;
 };
@@ -187,7 +201,8 @@ __device__ __forceinline__ void take_row(float* p, float (&v)[COLS]) {
 //   WRAP: p'-side tables hold all rows (row index (r + t_y) mod R); else a
 //         window starting at row s0 + ty0.
 // ---------------------------------------------------------------------------
-template <int R, int NQ, int N, bool SEED, bool GAP, bool BIAS, bool WRAP, int SXP, int SQ, int PL, int QL, int ACT>
+template <int R, int NQ, int N, bool SEED, bool GAP, bool BIAS, bool WRAP, int SXP, int SQ, int PL, int QL, int ACT,
+          int SQX = SQ, bool PH = false>
 struct Band {
   static constexpr int COLS = R / NQ, TYW = 32 / NQ;
   static constexpr int R1 = R / 2;
@@ -203,6 +218,7 @@ struct Band {
   const float2* ptab;
   const float2* qtab;
   int pcol, qr0, qc;
+  int qo[PH ? COLS : 1];  // phased p'-side offsets of the row part's columns
   float* slot;          // pooled output slot (stage 0 of a two-stage net)
   float b;
 
@@ -211,11 +227,20 @@ struct Band {
   __device__ __forceinline__ void input_row(int t, float (&A)[COLS]) {
     if constexpr (SEED) {
       const float4* xa = xs + (t - s0) * SXP + pcol;
-      const float4* xb = xq + qrow(t) * SQ + qc;
+      if constexpr (PH) {
+        const float4* xb = xq + qrow(t) * SQX;
 #pragma unroll
-      for (int k = 0; k < COLS; ++k) {
-        const float4 u = xa[k], w = xb[k];
-        A[k] = fmaf(u.x, w.x, fmaf(u.y, w.y, u.z * w.z));
+        for (int k = 0; k < COLS; ++k) {
+          const float4 u = xa[k], w = xb[qo[k]];
+          A[k] = fmaf(u.x, w.x, fmaf(u.y, w.y, u.z * w.z));
+        }
+      } else {
+        const float4* xb = xq + qrow(t) * SQ + qc;
+#pragma unroll
+        for (int k = 0; k < COLS; ++k) {
+          const float4 u = xa[k], w = xb[k];
+          A[k] = fmaf(u.x, w.x, fmaf(u.y, w.y, u.z * w.z));
+        }
       }
     } else {
 #pragma unroll
@@ -240,12 +265,12 @@ struct Band {
   template <int j>
   __device__ __forceinline__ void finish(int ro, float e, const float (&Hc)[COLS], float (&A)[COLS]) {
     const float2* pt = ptab + j * PL + (ro - s0) * SXP + pcol;
-    const float2* qt = qtab + j * QL + qrow(ro) * SQ + qc;
+    const float2* qt = qtab + j * QL + qrow(ro) * SQ + (PH ? 0 : qc);
 #pragma unroll
     for (int k = 0; k < COLS; ++k) {
       float K = fmaf(e, Hc[k], Pp[j][k]);
       if constexpr (BIAS) K += b;
-      const float2 pv = pt[k], qv = qt[k];
+      const float2 pv = pt[k], qv = PH ? qt[qo[k]] : qt[k];
       const float c = K * (pv.x * qv.x);
       float J;
       if constexpr (ACT == NK_ACT_ERF)
@@ -463,9 +488,10 @@ __device__ void stage0_task(const TiledParams& Q, int b, int64_t g, int sub, uns
     for (int e = threadIdx.x; e < nq; e += NT) {
       const int wr = e / G::SQ, wc = e - wr * G::SQ;
       const int r = (s0 + ty0 + wr) & (R - 1), c = (tx0 + wc) & (R - 1);
-      xq[e] = ld_x(xb + (r * R + c) * C, C, 1.f);
+      const int pc = G::PH ? (wc & 3) * G::NPH + (wc >> 2) : wc;  // column position in a window row
+      xq[wr * G::SQX + pc] = ld_x(xb + (r * R + c) * C, C, 1.f);
 #pragma unroll
-      for (int l = 0; l < N0; ++l) qt[l * L::QL + e] = qb[P.qoff[l] + r * R + c];
+      for (int l = 0; l < N0; ++l) qt[l * L::QL + wr * G::SQQ + pc] = qb[P.qoff[l] + r * R + c];
     }
   }
   __syncthreads();
@@ -474,7 +500,7 @@ __device__ void stage0_task(const TiledParams& Q, int b, int64_t g, int sub, uns
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = lane / G::TYW, tyl = lane - q * G::TYW;
   double gap = 0.0;
-  using BT = Band<R, G::NQ, N0, true, !TWO, BIAS, false, G::SXP, G::SQ, L::PL, L::QL, ACT>;
+  using BT = Band<R, G::NQ, N0, true, !TWO, BIAS, false, G::SXP, G::SQQ, L::PL, L::QL, ACT, G::SQX, G::PH>;
   static_assert(BT::COLS == G::COLS && BT::TYW == G::TYW, "split");
   for (int w = warp; w < G::WT; w += NT / 32) {
     BT T;
@@ -496,6 +522,13 @@ __device__ void stage0_task(const TiledParams& Q, int b, int64_t g, int sub, uns
     T.pcol = q * (G::COLS + 1);
     T.qr0 = tyw - s0;
     T.qc = T.c0 + txl;
+    if constexpr (G::PH) {
+#pragma unroll
+      for (int k = 0; k < G::COLS; ++k) {
+        const int c = T.qc + k;
+        T.qo[k] = (c & 3) * G::NPH + (c >> 2);
+      }
+    }
     T.slot = slot;
     T.b = P.sb2;
     T.run(gap);
