@@ -212,8 +212,8 @@ nk_status nk_fc_block(nk_handle* h, int depth, const nk_params* prm, const float
  *              tables (required unless PLAIN_FP64).
  *   symmetric  the block is the upper triangle of Xa x Xa: dK[i][j] and
  *              dK[j][i] both count for that entry; dXa must equal dXb.
- * Needs sigma_w2 > 0, C <= 4, 3x3 filters, stage widths powers of two up to
- * 64, ReLU or identity, no norm and the global-average readout (other
+ * Needs sigma_w2 > 0, C <= 4, 3x3 filters, square images whose stage sides
+ * are powers of two up to 64, ReLU or identity, no norm and the global-average readout (other
  * architectures: NK_ERR_UNSUPPORTED).  Per chunk of pairs the forward recursion is recomputed
  * and each layer's pre-activation kept in the handle's workspace; every pass
  * applies the previous map (forward) or this layer's map adjoint (reverse)

@@ -197,39 +197,68 @@ __device__ __forceinline__ T xform(const FArgs<T>& A, int64_t ia, int64_t ib, in
   }
 }
 
-// One block per (group of NPB pairs, diagonal d = k - i of the (i, k)
-// image-row planes); planes (i, i + d) of every pair of the group are
-// transformed, row-filtered along their (j, l) diagonal into a ring of
-// three, and each output plane sums three of them.  The loads of plane s + 2
-// are issued while plane s is processed (two register buffers), so about two
-// steps of work cover their latency.  W (the stage width) is a compile-time
-// constant and each thread's in-plane coordinates (jj, ll) are fixed, so the
-// per-element index arithmetic is a few adds.  Reverse: the q-terms' row sums
-// of a plane are warp shuffles when a warp covers a row (W >= 32), the column
-// sums per-thread partials reduced across warps; smaller stages reduce from
-// shared memory.
+// Shared memory of k_conv_fused, in elements of T: two buffers (by plane
+// parity) of the transformed plane and, reverse, of its q-terms and of the
+// column partials of those q-terms.
 template <typename T, int MODE, int W, int NPB>
-__global__ void __launch_bounds__(256) k_conv_fused(const __grid_constant__ FArgs<T> A) {
+__host__ __device__ constexpr size_t conv_smem_bytes() {
+  constexpr int W2 = W * W, CG = W >= 32 ? 256 / W : 1;
+  // per pair the two images' factor tables of the layer (H = W): float2 in
+  // FP32, the q values (double) in FP64
+  constexpr size_t tab = (MODE == CIN_MAP || MODE == CIN_ADJ) ? (size_t)NPB * 2 * W2 * 8 : 0;  // float2 or double
+  return (size_t)(2 * NPB * W2 + (MODE == CIN_ADJ ? 2 * NPB * W2 + 2 * NPB * CG * W : 0)) * sizeof(T) + tab;
+}
+
+// One block per (group of NPB pairs, diagonal d = k - i of the (i, k)
+// image-row planes).  Each thread owns EPT fixed in-plane elements (jj, ll)
+// of every plane of the diagonal, so all its addresses are a per-plane base
+// plus a per-thread offset.  Per plane s: transform the loaded values (the
+// loads of plane s + 2 are then issued), publish them in shared memory (two
+// buffers by plane parity, one barrier per plane), row-filter the thread's own
+// elements along the (j, l) diagonal (its value plus two neighbours), and
+// output plane s - 1 from a register ring of the last three row-filtered
+// planes.  Reverse: the q-terms' row sums of a plane are read as float4 runs
+// and reduced over the row's lanes by shuffles; column sums are per-warp
+// partials finished one plane later (stages narrower than 32 sum with plain
+// loops).  The stage is square (H = W, a compile-time constant), and each
+// pair's factor tables of the layer (both images, H x W entries each) are
+// staged in shared memory once per block.
+template <typename T, int MODE, int W, int NPB>
+__global__ void __launch_bounds__(256, 3) k_conv_fused(const __grid_constant__ FArgs<T> A) {
   extern __shared__ __align__(16) unsigned char fsm[];
   T* sh = reinterpret_cast<T*>(fsm);
   constexpr int W2 = W * W, EPT = W2 > 256 ? W2 / 256 : 1;
-  constexpr bool WIDE = W >= 32;          // a warp covers (part of) one row
-  constexpr int RPW = WIDE ? W / 32 : 1;  // warps per row
-  constexpr int CG = WIDE ? 256 / W : 1;  // row groups of the column partials
-  const int H = A.H, HW = H * W;
-  T* slot = sh;                  // [NPB][3][W2] row-filtered planes
-  T* raw = sh + 3 * NPB * W2;    // [NPB][W2] transformed plane
-  T* hs = raw + NPB * W2;        // [NPB][W2] q-terms (narrow stages) / row and column partials (wide)
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr bool WIDE = W >= 32;
+  constexpr int CG = WIDE ? 256 / W : 1;  // column groups (one per W threads)
+  constexpr int H = W, HW = W2;
+  constexpr bool TAB = (MODE == CIN_MAP || MODE == CIN_ADJ);
+  T* raw = sh;                            // [2][NPB][W2]
+  T* hs = raw + 2 * NPB * W2;             // [2][NPB][W2] (reverse only)
+  T* cpart = hs + 2 * NPB * W2;           // [2][NPB][CG][W] (reverse only)
+  // [NPB][2][HW] factor tables: (1/sqrt q, sqrt q) pairs in FP32, q in FP64;
+  // they follow the last buffer this mode has (conv_smem_bytes)
+  constexpr int TAB_OFF = MODE == CIN_ADJ ? 4 * NPB * W2 + 2 * NPB * CG * W : 2 * NPB * W2;
+  float2* tab2 = reinterpret_cast<float2*>(sh + TAB_OFF);
+  double* tabd = reinterpret_cast<double*>(tab2);
+  const int tid = threadIdx.x, lane = tid & 31;
   const int d = (int)blockIdx.x - (H - 1);
   const int i0 = d < 0 ? -d : 0;
   const int i1 = (d > 0 ? H - d : H) - 1;
-  int jj_[EPT], ll_[EPT];
+  // the thread's elements: in-plane coordinates, offsets and stencil masks
+  int jj_[EPT], ll_[EPT], off_[EPT], offg_[EPT];
+  bool in_[EPT];
+  T mlo_[EPT], mhi_[EPT];
+  constexpr int HWn = (H >> 1) * (W >> 1);
 #pragma unroll
   for (int u = 0; u < EPT; ++u) {
     const int e = tid + u * 256;
+    in_[u] = e < W2;
     jj_[u] = e / W;
     ll_[u] = e % W;
+    off_[u] = jj_[u] * HW + ll_[u];
+    offg_[u] = (jj_[u] >> 1) * HWn + (ll_[u] >> 1);
+    mlo_[u] = (jj_[u] > 0 && ll_[u] > 0) ? (T)1 : (T)0;
+    mhi_[u] = (jj_[u] + 1 < W && ll_[u] + 1 < W) ? (T)1 : (T)0;
   }
   double dsa = 0.0, dsb = 0.0;
   for (int64_t pg = (int64_t)blockIdx.y * NPB; pg < A.np; pg += (int64_t)gridDim.y * NPB) {
@@ -243,112 +272,229 @@ __global__ void __launch_bounds__(256) k_conv_fused(const __grid_constant__ FArg
       ia[b] = A.a0 + i;
       ib[b] = A.b0 + j;
     }
+    // loads of plane ii into (rk, rg)
     T k0[NPB][EPT], g0[NPB][EPT], k1[NPB][EPT], g1[NPB][EPT];
     auto fetch = [&](int ii, T (&rk)[NPB][EPT], T (&rg)[NPB][EPT]) {
       const int kk = ii + d;
 #pragma unroll
-      for (int b = 0; b < NPB; ++b)
+      for (int b = 0; b < NPB; ++b) {
+        const int64_t pbase = (pg + b) * (int64_t)HW * HW + (int64_t)(ii * W) * HW + kk * W;
 #pragma unroll
         for (int u = 0; u < EPT; ++u) {
           rk[b][u] = 0;
           rg[b][u] = 0;
-          if (ok[b] && tid + u * 256 < W2)
-            fetch_el<T, MODE, W>(A, pg + b, ia[b], ib[b], ii, jj_[u], kk, ll_[u], rk[b][u], rg[b][u]);
+          if (!ok[b] || !in_[u]) continue;
+          if constexpr (MODE == CIN_COV) {
+            const float* xa = A.Xa + ((ia[b] * HW + ii * W + jj_[u]) * (int64_t)A.C);
+            const float* xb = A.Xb + ((ib[b] * HW + kk * W + ll_[u]) * (int64_t)A.C);
+            T acc = 0;
+            for (int c = 0; c < A.C; ++c) acc += (T)xa[c] * (T)xb[c];
+            rk[b][u] = acc / (T)A.C;
+          } else {
+            rk[b][u] = A.src[pbase + off_[u]];
+          }
+          if constexpr (MODE == CIN_ADJ) {
+            if (A.gmode == G_TENSOR)
+              rg[b][u] = A.gsrc[pbase + off_[u]];
+            else if (A.gmode == G_POOLED)
+              rg[b][u] = A.gsrc[(pg + b) * (int64_t)HWn * HWn + (int64_t)((ii >> 1) * (W >> 1)) * HWn +
+                                (kk >> 1) * (W >> 1) + offg_[u]] *
+                         (T)(1.0 / 16.0);
+            else
+              rg[b][u] = A.gsrc[pg + b];
+          }
         }
+      }
     };
-    // one step: transform plane s from (rk, rg), refill them with plane s + 2,
-    // row-filter plane s, reduce its q-terms, output plane s - 1
+    T rA[NPB][EPT], rB[NPB][EPT], rC[NPB][EPT];  // row-filtered planes s - 2, s - 1, s
+#pragma unroll
+    for (int b = 0; b < NPB; ++b)
+#pragma unroll
+      for (int u = 0; u < EPT; ++u) rA[b][u] = rB[b][u] = rC[b][u] = 0;
     auto step = [&](int s, T (&rk)[NPB][EPT], T (&rg)[NPB][EPT]) {
+      const int par = s & 1;
+      T own[NPB][EPT];
       if (s <= i1) {
+        // ---- transform plane s, publish it
         const int kk = s + d;
         T sa = 0, sb = 0;
 #pragma unroll
         for (int b = 0; b < NPB; ++b) {
-          T colp = 0;
+          T* rw = raw + (par * NPB + b) * W2;
+          T* hw = hs + (par * NPB + b) * W2;
 #pragma unroll
           for (int u = 0; u < EPT; ++u) {
-            const int e = tid + u * 256;
-            if (e < W2) {
-              T h = 0;
-              raw[b * W2 + e] = xform<T, MODE>(A, ia[b], ib[b], s * W + jj_[u], kk * W + ll_[u], rk[b][u], rg[b][u],
-                                               h, sa, sb);
-              if constexpr (MODE == CIN_ADJ) {
-                if constexpr (WIDE) {
-                  colp += h;
-                  T r = h;
-#pragma unroll
-                  for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-                  if (lane == 0) hs[b * W2 + jj_[u] * RPW + ll_[u] / 32] = r;  // row partial
+            own[b][u] = 0;
+            if (!in_[u]) continue;
+            T h = 0;
+            T v = rk[b][u];
+            if constexpr (MODE == CIN_MAP || MODE == CIN_ADJ) {
+              if (A.relu) {
+                T sc, rs;
+                if constexpr (sizeof(T) == 8) {
+                  const double q1 = tabd[(b * 2) * HW + s * W + jj_[u]];
+                  const double q2 = tabd[(b * 2 + 1) * HW + kk * W + ll_[u]];
+                  sc = sqrt(q1 * q2);
+                  rs = sc > 0.0 ? 1.0 / sc : 0.0;
                 } else {
-                  hs[b * W2 + e] = h;
+                  const float2 s1 = tab2[(b * 2) * HW + s * W + jj_[u]];
+                  const float2 s2 = tab2[(b * 2 + 1) * HW + kk * W + ll_[u]];
+                  sc = s1.y * s2.y;
+                  rs = s1.x * s2.x;
                 }
+                const T inv2pi = (T)NK_INV_2PI_D;
+                if constexpr (MODE == CIN_MAP) {
+                  v = sc > (T)0 ? sc * inv2pi * J_only<T>(v * rs) : (T)0;
+                } else {
+                  T dk = 0;
+                  if (sc > (T)0) {
+                    T J, dJ;
+                    J_dJ<T>(v * rs, J, dJ);
+                    dk = rg[b][u] * dJ * inv2pi;
+                    h = rg[b][u] * (sc * inv2pi * J - v * dJ * inv2pi);
+                  }
+                  sa += dk * (v - (T)A.sb2);
+                  sb += dk;
+                  v = dk;
+                }
+              } else if constexpr (MODE == CIN_ADJ) {
+                sa += rg[b][u] * (v - (T)A.sb2);
+                sb += rg[b][u];
+                v = rg[b][u];
               }
             }
+            own[b][u] = v;
+            rw[jj_[u] * W + ll_[u]] = v;
+            if constexpr (MODE == CIN_ADJ) hw[jj_[u] * W + ll_[u]] = h;
           }
-          if constexpr (MODE == CIN_ADJ && WIDE) hs[b * W2 + W * RPW + (tid / W) * W + ll_[0]] = colp;
         }
         dsa += (double)sa;
         dsb += (double)sb;
-        if (s + 2 <= i1) fetch(s + 2, rk, rg);  // in flight during the next two steps
+        if (s + 2 <= i1) fetch(s + 2, rk, rg);  // in flight during the next two planes
       }
       __syncthreads();
       if (s <= i1) {
-        for (int e = tid; e < NPB * W2; e += 256) {
-          const int b = e / W2, f = e - b * W2;
-          const int jj = f / W, ll = f - jj * W;
-          const T* r = raw + b * W2;
-          T v = r[f];
-          if (jj > 0 && ll > 0) v += r[f - W - 1];
-          if (jj + 1 < W && ll + 1 < W) v += r[f + W + 1];
-          slot[(b * 3 + s % 3) * W2 + f] = v;
+        // ---- row filter of the thread's own elements
+#pragma unroll
+        for (int b = 0; b < NPB; ++b) {
+          const T* rw = raw + (par * NPB + b) * W2;
+#pragma unroll
+          for (int u = 0; u < EPT; ++u) {
+            const int f = jj_[u] * W + ll_[u];
+            T v = own[b][u];
+            if (in_[u]) {
+              if (jj_[u] > 0 && ll_[u] > 0) v += rw[f - W - 1];
+              if (jj_[u] + 1 < W && ll_[u] + 1 < W) v += rw[f + W + 1];
+            }
+            rC[b][u] = v;
+          }
         }
         if constexpr (MODE == CIN_ADJ) {
           const int kk = s + d;
-          for (int t = tid; t < NPB * 2 * W; t += 256) {
-            const int b = t / (2 * W), r = t - b * 2 * W;
-            if (!ok[b]) continue;
-            const T* hb = hs + b * W2;
-            T v = 0;
-            if constexpr (WIDE) {
-              if (r < W) {
+          if constexpr (WIDE) {
+            // rows: float4 runs, W/4 lanes per row reduced by shuffles
+            constexpr int RT = W / 4, RPI = 256 / RT;
+            for (int b = 0; b < NPB; ++b) {
+              const float4* h4 = reinterpret_cast<const float4*>(hs + (par * NPB + b) * W2);
+              const int64_t base = (((pg + b) * H + s) * (int64_t)H + kk) * W;
+              for (int r0 = 0; r0 < W; r0 += RPI) {
+                const int r = r0 + tid / RT, g = tid % RT;
+                T v = 0;
+                if constexpr (sizeof(T) == 4) {
+                  const float4 x = h4[r * RT + g];
+                  v = (x.x + x.y) + (x.z + x.w);
+                } else {
+                  const T* hb = hs + (par * NPB + b) * W2 + r * W + 4 * g;
+                  v = (hb[0] + hb[1]) + (hb[2] + hb[3]);
+                }
 #pragma unroll
-                for (int c = 0; c < RPW; ++c) v += hb[r * RPW + c];
-              } else {
-#pragma unroll
-                for (int g = 0; g < CG; ++g) v += hb[W * RPW + g * W + (r - W)];
+                for (int o = RT / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (g == 0 && ok[b]) A.prow[base + r] = v;
               }
-            } else {
-              // skewed row reads avoid bank conflicts; column reads are consecutive
+              // columns: this thread's W / CG rows of column tid % W
+              const T* hb = hs + (par * NPB + b) * W2;
+              const int c = tid % W, cg = tid / W;
+              T v = 0;
+#pragma unroll
+              for (int i = 0; i < W / CG; ++i) v += hb[(cg * (W / CG) + i) * W + c];
+              cpart[((par * NPB + b) * CG + cg) * W + c] = v;
+            }
+          } else {
+            // narrow stages: one thread per row / column sum
+            for (int t = tid; t < NPB * 2 * W; t += 256) {
+              const int b = t / (2 * W), r = t - b * 2 * W;
+              if (!ok[b]) continue;
+              const T* hb = hs + (par * NPB + b) * W2;
+              T v = 0;
               if (r < W) {
                 for (int l = 0; l < W; ++l) v += hb[r * W + ((l + r) & (W - 1))];
               } else {
                 for (int jj = 0; jj < W; ++jj) v += hb[jj * W + (r - W)];
               }
+              const int64_t base = (((pg + b) * H + s) * (int64_t)H + kk) * W;
+              if (r < W)
+                A.prow[base + r] = v;
+              else
+                A.pcol[base + r - W] = v;
             }
-            const int64_t base = (((pg + b) * H + s) * (int64_t)H + kk) * W;
-            if (r < W)
-              A.prow[base + r] = v;
-            else
-              A.pcol[base + r - W] = v;
           }
         }
       }
-      __syncthreads();
-      if (s - 1 >= i0) {
-        const int io = s - 1, ko = io + d;
-        for (int e = tid; e < NPB * W2; e += 256) {
-          const int b = e / W2, f = e - b * W2;
-          if (!ok[b]) continue;
-          const T* sl = slot + b * 3 * W2;
-          T acc = sl[(io % 3) * W2 + f];
-          if (io > i0) acc += sl[((io + 2) % 3) * W2 + f];
-          if (io < i1) acc += sl[((io + 1) % 3) * W2 + f];
-          const int jj = f / W, ll = f - jj * W;
-          A.out[(pg + b) * (int64_t)HW * HW + (int64_t)(io * W + jj) * HW + ko * W + ll] = A.a * acc + A.b;
+      if constexpr (MODE == CIN_ADJ && WIDE) {
+        // the column sums of plane s - 1 (partials published before this
+        // plane's barrier)
+        if (s - 1 >= i0) {
+          const int io = s - 1, ko = io + d, pp = io & 1;
+          for (int t = tid; t < NPB * W; t += 256) {
+            const int b = t / W, c = t - b * W;
+            if (!ok[b]) continue;
+            T v = 0;
+#pragma unroll
+            for (int g = 0; g < CG; ++g) v += cpart[((pp * NPB + b) * CG + g) * W + c];
+            A.pcol[(((pg + b) * H + io) * (int64_t)H + ko) * W + c] = v;
+          }
         }
       }
+      // ---- output plane s - 1 from the register ring
+      if (s - 1 >= i0) {
+        const int io = s - 1, ko = io + d;
+#pragma unroll
+        for (int b = 0; b < NPB; ++b) {
+          if (!ok[b]) continue;
+          T* dst = A.out + (pg + b) * (int64_t)HW * HW + (int64_t)(io * W) * HW + ko * W;
+#pragma unroll
+          for (int u = 0; u < EPT; ++u) {
+            if (!in_[u]) continue;
+            T acc = rB[b][u];
+            if (io > i0) acc += rA[b][u];
+            if (io < i1) acc += rC[b][u];
+            dst[off_[u]] = A.a * acc + A.b;
+          }
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < NPB; ++b)
+#pragma unroll
+        for (int u = 0; u < EPT; ++u) {
+          rA[b][u] = rB[b][u];
+          rB[b][u] = rC[b][u];
+        }
     };
-    __syncthreads();  // the previous group's planes are no longer read
+    __syncthreads();  // the previous group's buffers are no longer read
+    if constexpr (TAB) {
+      if (A.relu) {
+        for (int t = tid; t < NPB * 2 * HW; t += 256) {
+          const int b = t / (2 * HW), r = t - b * 2 * HW, side = r / HW, e = r - side * HW;
+          if (!ok[b]) continue;
+          const int64_t row = (side == 0 ? ia[b] : ib[b]) * A.nq + A.qoff + e;
+          if constexpr (sizeof(T) == 8)
+            tabd[(b * 2 + side) * HW + e] = (side == 0 ? A.qda : A.qdb)[row];
+          else
+            tab2[(b * 2 + side) * HW + e] = reinterpret_cast<const float2*>(side == 0 ? A.qsa : A.qsb)[row];
+        }
+      }
+      __syncthreads();  // the tables are read by every thread's first transform
+    }
     fetch(i0, k0, g0);
     if (i0 + 1 <= i1) fetch(i0 + 1, k1, g1);
     int s = i0;
@@ -365,8 +511,8 @@ __global__ void __launch_bounds__(256) k_conv_fused(const __grid_constant__ FArg
       dsb += __shfl_xor_sync(0xffffffffu, dsb, o);
     }
     if (lane == 0) {
-      r1[warp] = dsa;
-      r2[warp] = dsb;
+      r1[tid >> 5] = dsa;
+      r2[tid >> 5] = dsb;
     }
     __syncthreads();
     if (tid == 0) {
@@ -866,7 +1012,7 @@ BwdPlan<T> plan_backward(const NkGeom& g, int64_t npairs, int64_t na, int64_t nb
 // at the smaller ones, one at 64 x 64).
 template <typename T, int MODE, int W, int NPB>
 cudaError_t conv_launch(const FArgs<T>& A, cudaStream_t st) {
-  const size_t smem = (size_t)(MODE == CIN_ADJ ? 5 : 4) * NPB * W * W * sizeof(T);
+  const size_t smem = conv_smem_bytes<T, MODE, W, NPB>();
   const dim3 grid((unsigned)(2 * A.H - 1), (unsigned)std::min<int64_t>((A.np + NPB - 1) / NPB, 65535));
   cudaError_t e = cudaFuncSetAttribute(k_conv_fused<T, MODE, W, NPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);

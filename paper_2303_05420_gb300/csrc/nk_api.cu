@@ -532,10 +532,11 @@ nk_status nk_block_backward(nk_handle* h, const nk_arch* arch, const nk_params* 
   for (int s = 0; s <= g.last_act_stage && s < g.n_stages; ++s) {
     const int w = g.Ws[s];
     if (w != 1 && w != 2 && w != 4 && w != 8 && w != 16 && w != 32 && w != 64) widths_ok = false;
+    if (g.Hs[s] != w) widths_ok = false;  // square stages
   }
   if (!widths_ok)
     return nk_fail(h, NK_ERR_UNSUPPORTED,
-                   "nk_block_backward: needs 3x3 filters and stage widths in {1, 2, 4, ..., 64}");
+                   "nk_block_backward: needs 3x3 filters and square stages of side 1, 2, 4, ..., 64");
   if (g.act == NK_ACT_ERF || g.norm != NK_NORM_NONE || g.readout != NK_READOUT_GAP)
     return nk_fail(h, NK_ERR_UNSUPPORTED,
                    "nk_block_backward: ReLU or identity, no norm, global-average readout only");
