@@ -257,7 +257,7 @@ nk_status nk_autotune_set(nk_handle* h, const nk_arch* arch, const nk_params* pr
  * 16 KB device array inside the library, shared by all calls on a device:
  *   - the first call on a device (and the first after that device's
  *     context was reset) looks up the array's device address with the
- *     device current; make that first call before any stream capture;
+ *     device current;
  *   - each call clears the slots it uses (stream-ordered) before its kernel;
  *   - calls whose kernels overlap on the GPU (unordered streams) race on the
  *     array; order them on one stream;
