@@ -5,33 +5,38 @@
 //
 // The Gram X_a X_b^T is the one dense contraction of the method (d = 3072
 // for the CIFAR-shaped inputs).  It runs as a BF16 tcgen05 GEMM with FP32
-// accumulation in TMEM on split operands: x = x_hi + x_lo (BF16 each), and
-// x . x' ~ hi.lo' + lo.hi' + hi.hi' is one GEMM over a tripled K with
-// A' = [hi | lo | hi] and B' = [lo' | hi' | hi'] (zero-padded to a multiple
-// of 64).  Persistent CTAs (one per SM) walk the 128 x 256 output tiles in a
-// grouped raster (16 tile rows at a time, so that concurrent CTAs share B
-// tiles in L2).  Operand tiles (128 x 64 and 256 x 64 BF16) arrive by TMA
-// with 128-byte swizzle through a 4-stage mbarrier ring (each CTA loads its
-// own tiles); one thread issues the MMAs; eight epilogue warps take the
-// finished accumulator out of TMEM into registers (32 rows x 128 columns a
-// warp), release TMEM at once so that the next tile's MMAs start, and then
-// apply the whole arc-cosine recursion layer by layer over 32 entries at a
-// time (column factors staged in shared memory) and store 16 bytes of a K
-// row per lane.  The self-variances q_l of each row follow the closed
-// diagonal recursion q_1 = sw2 |x|^2/d + sb2, q_{l+1} = sw2 q_l / 2 + sb2
-// (FP64).  Symmetric blocks run only tiles touching the upper triangle and
-// store each entry at (i, j) and (j, i).
+// accumulation in TMEM on split operands: x = x_hi + x_lo (BF16 each) and
+// x . x' ~ hi.lo' + lo.hi' + hi.hi'.  Each row is rewritten once with every
+// 32-column block of x as 64 BF16 columns, its high parts then its low parts
+// (zero-padded to a multiple of 64), so one 128-byte TMA row of a stage holds
+// both parts of 32 columns and feeds all three products: per stage 6 MMAs
+// (128 x 256 x 16) on 48 KB of operands.  Persistent CTAs (one per SM) walk
+// the 128 x 256 output tiles in a grouped raster (16 tile rows at a time, so
+// that concurrent CTAs share B tiles in L2).  Operand tiles (128 x 64 and
+// 256 x 64 BF16) arrive by TMA with 128-byte swizzle through a 4-stage
+// mbarrier ring (each CTA loads its own tiles); one thread issues the MMAs;
+// eight epilogue warps take the finished sums out of TMEM into registers
+// (32 rows x 128 columns a warp), release TMEM at once so that the next
+// tile's MMAs start, and then apply the whole arc-cosine recursion layer by
+// layer over 32 entries at a time (column factors staged in shared memory)
+// and store 16 bytes of a K row per lane.  The self-variances q_l of each
+// row follow the closed diagonal recursion q_1 = sw2 |x|^2/d + sb2,
+// q_{l+1} = sw2 q_l / 2 + sb2 (FP64).  Symmetric blocks run only tiles
+// touching the upper triangle and store each entry at (i, j) and (j, i).
 //
 // Accumulation accuracy.  The tensor core adds each 16-element MMA step to
 // the FP32 accumulator with a rounding that always goes toward zero, so for
-// a sum of 3d products of one sign (a row with itself or with a near copy of
-// itself) the errors add up one way: about 2e-5 relative at d = 3072 when
-// the large hi.hi' products come first.  Two measures bring that to about
-// 6e-6: the small hi.lo' and lo.hi' products come first, while the running
-// sum is still small, and each tile accumulates its even and odd 64-wide K
-// blocks into two separate TMEM accumulators (two chunk sums, each half as
-// long, added in FP32 by the epilogue).  The two 128 x 256 FP32 chunks fill
-// all 512 TMEM columns.  Self pairs take K_1 from the FP64 norm.
+// a sum of products of one sign (a row with itself or with a near copy of
+// itself) the errors add up one way, in proportion to the number of steps
+// taken at the full size of the sum: about 2e-5 relative at d = 3072 for one
+// accumulator over all 3d products.  Here the small products hi.lo' and
+// lo.hi' go to their own accumulator (TMEM columns [0, 256)), whose sum is
+// about 2^-8 of the total, and the hi.hi' products to a second one
+// ([256, 512)), which the epilogue copies into registers once half of the K
+// blocks are in, so that each half is summed from zero (about 4e-6 for near
+// copies in a model of the rounding, the level of two alternating chunks).
+// The epilogue adds the three sums in FP32.  Self pairs take K_1 from the
+// FP64 norm.
 //
 // Every mbarrier wait of the pipeline is bounded by the handle's wait limit;
 // on a timeout the kernel records NK_DEV_TIMEOUT and skips its stores, and
@@ -49,8 +54,8 @@
 namespace {
 
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int KD = BK / 2;      // columns of x per stage (high and low parts)
 constexpr int GROUP_M = 16;     // tile rows per raster group (L2 reuse of B)
-constexpr int NCHUNK = 2;       // accumulators per tile (even / odd K blocks)
 constexpr int EPI_WARPS = 8;    // two per TMEM lane quarter, 128 columns each
 constexpr int EPI_COLS = BN / 2;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
@@ -64,13 +69,14 @@ struct GemmSmem {
   float2 qa[BM * MAX_DEPTH];             // per-row (1/sqrt q, sqrt q * sw2/(2 pi))
   uint64_t full[STAGES], empty[STAGES];  // operand ring
   uint64_t tfull, tempty;                // TMEM accumulators: MMA -> epilogue, epilogue -> MMA
+  uint64_t hfull, hempty;                // the first half's hi.hi' sum: MMA -> epilogue, epilogue -> MMA
   uint64_t done;
   uint32_t tslot;
 };
 
 struct FcParams {
   int64_t M, N;          // rows of A', B'
-  int kpad;              // padded K' (multiple of 64)
+  int kpad;              // 64 ceil(d / 32): the split columns of a row
   int depth;
   float kscale;          // sw2 / d
   float sb2;
@@ -179,8 +185,9 @@ __device__ __forceinline__ void epi_entries(const FcParams& P, float (&w)[32], c
 
 // Persistent kernel, one CTA per SM; CTA c takes tile slots t = c + k * CTAs.
 // Warp 0: TMA producer; warp 1: TMEM owner and MMA issuer; warps 2..9:
-// epilogue.  TMEM columns [0, 256) hold chunk 0 (even K blocks) of the
-// current tile, [256, 512) chunk 1 (odd K blocks).  The epilogue copies a
+// epilogue.  TMEM columns [0, 256) hold the small products' sum of the
+// current tile, [256, 512) its hi.hi' sum (first half, copied out by the
+// epilogue at mid-tile, then the second half).  The epilogue copies a
 // finished tile into registers and releases TMEM before its arithmetic, so
 // the MMAs of the next tile overlap that arithmetic.
 __global__ void __launch_bounds__(THREADS, 1)
@@ -190,6 +197,8 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   GemmSmem& S = *reinterpret_cast<GemmSmem*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nk = P.kpad / BK;
+  // stages whose hi.hi' products form the first half's sum (0: one sum)
+  const int H = nk >= 2 ? nk / 2 : 0;
   const int64_t cta = blockIdx.x, ncta = gridDim.x;
   const int64_t nslots = (int64_t)P.ntm * P.ntn;
   if (warp == 0 && lane == 0) {
@@ -199,6 +208,8 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
     }
     tc::mbar_init(&S.tfull, 1);
     tc::mbar_init(&S.tempty, EPI_WARPS);
+    tc::mbar_init(&S.hfull, 1);
+    tc::mbar_init(&S.hempty, EPI_WARPS);
     tc::mbar_init(&S.done, 1);
     tc::mbar_fence_init();
     tc::prefetch_tmap(&ta);
@@ -259,13 +270,31 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
             break;
           }
           tc::tc_fence_after();
+          // a 128-byte operand row holds the high parts of 32 columns in
+          // bytes [0, 64) (K steps 0, 1) and their low parts in [64, 128)
           const uint32_t a0 = tc::smem_addr(S.A[s]), b0 = tc::smem_addr(S.B[s]);
-          const uint32_t tch = tbase + (uint32_t)((kb & 1) * BN);  // chunk of this K block
+          const uint32_t ts = tbase, tl = tbase + BN;
 #pragma unroll
-          for (int k = 0; k < BK / 16; ++k)
-            tc::mma_bf16(tch, tc::sdesc_k128(a0 + 32 * k), tc::sdesc_k128(b0 + 32 * k), idesc,
-                         (kb >= NCHUNK) || (k != 0));
+          for (int k = 0; k < 2; ++k) {
+            tc::mma_bf16(ts, tc::sdesc_k128(a0 + 32 * k), tc::sdesc_k128(b0 + 64 + 32 * k), idesc,
+                         (kb > 0) || (k != 0));                                                   // hi.lo'
+            tc::mma_bf16(ts, tc::sdesc_k128(a0 + 64 + 32 * k), tc::sdesc_k128(b0 + 32 * k), idesc, 1);  // lo.hi'
+          }
+          if (H > 0 && kb == H) {
+            // the epilogue has copied the first half's hi.hi' sum out of TMEM
+            if (!tc::mbar_wait(&S.hempty, (uint32_t)(n & 1), P.wait_limit)) {
+              atomicOr(P.dstatus, NK_DEV_TIMEOUT);
+              ok = false;
+              break;
+            }
+            tc::tc_fence_after();
+          }
+#pragma unroll
+          for (int k = 0; k < 2; ++k)
+            tc::mma_bf16(tl, tc::sdesc_k128(a0 + 32 * k), tc::sdesc_k128(b0 + 32 * k), idesc,
+                         !((kb == 0 || kb == H) && k == 0));                                      // hi.hi'
           tc::mma_commit(&S.empty[s]);  // the stage may be refilled once these MMAs have read it
+          if (kb == H - 1) tc::mma_commit(&S.hfull);
         }
         if (!ok) break;
         tc::mma_commit(&S.tfull);
@@ -282,7 +311,6 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
     const int cbeg = ((warp - 2) >> 2) * EPI_COLS;
     const int et = threadIdx.x - 64;  // 0 .. 32 * EPI_WARPS - 1
     const bool vec_ok = (P.ldk % 4 == 0) && ((reinterpret_cast<uintptr_t>(P.K) & 15) == 0);
-    const bool two = nk > 1;  // chunk 1 holds the odd K blocks (none when nk == 1)
     int n = 0;
     for (int64_t t = cta; t < nslots; t += ncta) {
       int tm, tn;
@@ -299,26 +327,45 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
         S.qa[e] = i < P.M ? P.qa[m0 * P.depth + e] : make_float2(0.f, 0.f);
       }
       named_sync(1, 32 * EPI_WARPS);
+      // this warp's 32 rows x 128 columns
+      const uint32_t taddr = tbase + (uint32_t)cbeg + ((uint32_t)(32 * q) << 16);
+      float v[EPI_COLS / 32][32];
+      if (H > 0) {
+        // mid-tile: the first half's hi.hi' sum into registers
+        const bool got = tc::mbar_wait(&S.hfull, (uint32_t)(n & 1), P.wait_limit);
+        // the epilogue warps leave together (they share named barriers)
+        if (named_any(2, 32 * EPI_WARPS, !got)) {
+          atomicOr(P.dstatus, NK_DEV_TIMEOUT);
+          break;
+        }
+        tc::tc_fence_after();
+#pragma unroll
+        for (int c = 0; c < EPI_COLS / 32; ++c) tc::tmem_ld32(taddr + (uint32_t)(BN + 32 * c), v[c]);
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&S.hempty);
+      } else {
+#pragma unroll
+        for (int c = 0; c < EPI_COLS / 32; ++c)
+#pragma unroll
+          for (int e = 0; e < 32; ++e) v[c][e] = 0.f;
+      }
       const bool got = tc::mbar_wait(&S.tfull, (uint32_t)(n & 1), P.wait_limit);
-      // the epilogue warps leave together (they share named barriers)
       if (named_any(2, 32 * EPI_WARPS, !got)) {
         atomicOr(P.dstatus, NK_DEV_TIMEOUT);
         break;
       }
       tc::tc_fence_after();
-      // this warp's 32 rows x 128 columns into registers, both chunks added
-      const uint32_t taddr = tbase + (uint32_t)cbeg + ((uint32_t)(32 * q) << 16);
-      float v[EPI_COLS / 32][32];
+      // (first half + second half of hi.hi') + small products
 #pragma unroll
-      for (int c = 0; c < EPI_COLS / 32; ++c) tc::tmem_ld32(taddr + (uint32_t)(32 * c), v[c]);
-      if (two) {
+      for (int c = 0; c < EPI_COLS / 32; ++c) {
+        float u[32];
+        tc::tmem_ld32(taddr + (uint32_t)(BN + 32 * c), u);
 #pragma unroll
-        for (int c = 0; c < EPI_COLS / 32; ++c) {
-          float u[32];
-          tc::tmem_ld32(taddr + (uint32_t)(BN + 32 * c), u);
+        for (int e = 0; e < 32; ++e) v[c][e] += u[e];
+        tc::tmem_ld32(taddr + (uint32_t)(32 * c), u);
 #pragma unroll
-          for (int e = 0; e < 32; ++e) v[c][e] += u[e];
-        }
+        for (int e = 0; e < 32; ++e) v[c][e] += u[e];
       }
       // TMEM is free for the next tile
       tc::tc_fence_before();
@@ -352,24 +399,24 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   if (warp == 1) tc::tmem_dealloc(tbase, 512);
 }
 
-// A' = [hi | lo | hi] (role a) or B' = [lo | hi | hi] (role b), zero-padded to
-// kpad: the small cross products hi.lo' and lo.hi' come first in K'.
-__global__ void k_split_bf16(const float* __restrict__ X, int64_t rows, int d, int kpad, int role_b,
+// Split rows: each 32-column block of x becomes 64 BF16 columns, the
+// round-to-nearest high parts hi = bf16(x) of its 32 columns, then their low
+// parts bf16(x - hi); columns past d are zero (kpad = 64 ceil(d / 32)).
+__global__ void k_split_bf16(const float* __restrict__ X, int64_t rows, int d, int kpad,
                              __nv_bfloat16* __restrict__ out) {
   const int64_t total = rows * (int64_t)kpad;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / kpad;
     const int k = (int)(e - r * kpad);
-    float v = 0.f;
-    if (k < 3 * d) {
-      const int seg = k / d, c = k - seg * d;
+    const int c = (k >> 6) * KD + (k & (KD - 1));
+    __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+    if (c < d) {
       const float x = X[r * d + c];
       const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-      const bool want_lo = role_b ? (seg == 0) : (seg == 1);
-      v = want_lo ? __bfloat162float(__float2bfloat16_rn(x - __bfloat162float(hi))) : __bfloat162float(hi);
+      v = (k & KD) ? __float2bfloat16_rn(x - __bfloat162float(hi)) : hi;
     }
-    out[e] = __float2bfloat16_rn(v);
+    out[e] = v;
   }
 }
 
@@ -431,8 +478,7 @@ bool make_map(CUtensorMap* m, void* ptr, int64_t rows, int kpad, int box_rows) {
 }  // namespace
 
 size_t nk_fc_ws_bytes(int64_t na, int64_t nb, int d, int depth) {
-  // A' and B' have different layouts even for a symmetric block
-  const int64_t kpad = (3 * (int64_t)d + BK - 1) / BK * BK;
+  const int64_t kpad = ((int64_t)d + KD - 1) / KD * BK;
   return ((size_t)na + nb) * kpad * 2 + ((size_t)na + nb) * depth * sizeof(float2) + (size_t)na * 4 + 5 * 1024;
 }
 
@@ -441,7 +487,7 @@ cudaError_t nk_launch_fc_block(int depth, double sw2, double sb2, const float* X
                                void* ws, int sm, unsigned int* dstatus, uint32_t wait_limit, cudaStream_t st,
                                int64_t* launches) {
   const int64_t na = a1 - a0, nb = b1 - b0;
-  const int kpad = (int)((3 * (int64_t)d + BK - 1) / BK * BK);
+  const int kpad = (int)(((int64_t)d + KD - 1) / KD * BK);
   char* w = reinterpret_cast<char*>(ws);
   auto take = [&](size_t bytes) {
     char* p = w;
@@ -456,14 +502,15 @@ cudaError_t nk_launch_fc_block(int depth, double sw2, double sb2, const float* X
   const float* xa = Xa + a0 * (int64_t)d;
   const float* xb = Xb + b0 * (int64_t)d;
   auto grid = [](int64_t total) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 32)); };
-  *launches += 4;
-  k_split_bf16<<<grid(na * kpad), 256, 0, st>>>(xa, na, d, kpad, 0, Ap);
-  k_split_bf16<<<grid(nb * kpad), 256, 0, st>>>(xb, nb, d, kpad, 1, Bp);
+  // a symmetric block has the same rows on both sides: one split serves both
+  *launches += sym ? 3 : 4;
+  k_split_bf16<<<grid(na * kpad), 256, 0, st>>>(xa, na, d, kpad, Ap);
+  if (!sym) k_split_bf16<<<grid(nb * kpad), 256, 0, st>>>(xb, nb, d, kpad, Bp);
   const double inv2pi = 0.15915494309189533577;
   k_fc_q<<<grid(na * 32), 256, 0, st>>>(xa, na, d, depth, sw2, sb2, (float)(sw2 * inv2pi), qa, q1a);
   k_fc_q<<<grid(nb * 32), 256, 0, st>>>(xb, nb, d, depth, sw2, sb2, 1.f, qb, nullptr);
   CUtensorMap ta, tb;
-  if (!make_map(&ta, Ap, na, kpad, BM) || !make_map(&tb, Bp, nb, kpad, BN)) return cudaErrorInvalidValue;
+  if (!make_map(&ta, Ap, na, kpad, BM) || !make_map(&tb, sym ? Ap : Bp, nb, kpad, BN)) return cudaErrorInvalidValue;
   FcParams P = {};
   P.M = na;
   P.N = nb;

@@ -25,8 +25,11 @@ def _maxrel(got, want):
     return float(np.max(np.abs(got - want) / np.abs(want)))
 
 
+# d = 20: one K stage (a single hi.hi' sum); d = 33: two stages, one per half;
+# d = 200: an odd number of stages (7)
 @pytest.mark.parametrize("na,nb,d,sym", [(300, 200, 3072, False), (300, 300, 3072, True), (1000, 777, 100, False),
-                                         (129, 257, 64, False), (513, 513, 200, True)])
+                                         (129, 257, 64, False), (513, 513, 200, True), (200, 150, 20, False),
+                                         (260, 260, 33, True)])
 def test_fc3_matches_oracle(h, na, nb, d, sym):
     xa = nkdata.fc_rows(na, d, seed=0).astype(np.float32)
     xb = xa if sym else nkdata.fc_rows(nb, d, seed=1).astype(np.float32)
