@@ -58,7 +58,20 @@ constexpr int KD = BK / 2;      // columns of x per stage (high and low parts)
 constexpr int GROUP_M = 16;     // tile rows per raster group (L2 reuse of B)
 constexpr int EPI_WARPS = 8;    // two per TMEM lane quarter, 128 columns each
 constexpr int EPI_COLS = BN / 2;
-constexpr int THREADS = 64 + 32 * EPI_WARPS;
+// warpgroup 0: TMA producer (warp 0), MMA issuer (warp 1), two idle warps;
+// warpgroups 1 and 2: the epilogue
+constexpr int THREADS = 128 + 32 * EPI_WARPS;
+// Register split.  Twelve warps on four SM sub-partitions cap a thread at
+// 168 registers (three warps per sub-partition), too few for the
+// epilogue's 128 drained sums plus the recursion's temporaries (it
+// spilled).  The control warpgroup gives registers back and the epilogue
+// takes them: 128 x 40 + 256 x 232 = 384 x 168, the launch allocation; per
+// sub-partition one control and two epilogue warps, 40 + 2 x 232 = 3 x 168.
+// The host refuses the launch unless the kernel was built with exactly
+// REG_LAUNCH registers per thread, since an increase beyond the launch
+// allocation would never be granted.
+constexpr int REG_LAUNCH = 168, REG_CTRL = 40, REG_EPI = 232;
+static_assert(128 * REG_CTRL + 32 * EPI_WARPS * REG_EPI <= THREADS * REG_LAUNCH, "register split");
 constexpr uint32_t DRAIN_LIMIT = 1u << 26;  // waits for own copies / MMAs before exit
 constexpr int MAX_DEPTH = 8;
 
@@ -184,7 +197,7 @@ __device__ __forceinline__ void epi_entries(const FcParams& P, float (&w)[32], c
 }
 
 // Persistent kernel, one CTA per SM; CTA c takes tile slots t = c + k * CTAs.
-// Warp 0: TMA producer; warp 1: TMEM owner and MMA issuer; warps 2..9:
+// Warp 0: TMA producer; warp 1: TMEM owner and MMA issuer; warps 4..11:
 // epilogue.  TMEM columns [0, 256) hold the small products' sum of the
 // current tile, [256, 512) its hi.hi' sum (first half, copied out by the
 // epilogue at mid-tile, then the second half).  The epilogue copies a
@@ -221,6 +234,7 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   tc::tc_fence_after();
   const uint32_t tbase = S.tslot;
   bool ok = true;
+  if (warp < 4) tc::setmaxnreg_dec<REG_CTRL>();
   if (warp == 0) {
     if (lane == 0) {
       // TMA producer: the operand ring runs on across tiles
@@ -304,12 +318,13 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
       tc::mma_commit(&S.done);
       if (!tc::mbar_wait(&S.done, 0, DRAIN_LIMIT)) atomicOr(P.dstatus, NK_DEV_TIMEOUT);
     }
-  } else {
+  } else if (warp >= 4) {
+    tc::setmaxnreg_inc<REG_EPI>();
     // epilogue: TMEM lane quarter q holds tile rows 32q .. 32q+31; the two
     // warps of a quarter take columns [0, 128) and [128, 256)
     const int q = warp & 3;
-    const int cbeg = ((warp - 2) >> 2) * EPI_COLS;
-    const int et = threadIdx.x - 64;  // 0 .. 32 * EPI_WARPS - 1
+    const int cbeg = ((warp - 4) >> 2) * EPI_COLS;
+    const int et = threadIdx.x - 128;  // 0 .. 32 * EPI_WARPS - 1
     const bool vec_ok = (P.ldk % 4 == 0) && ((reinterpret_cast<uintptr_t>(P.K) & 15) == 0);
     int n = 0;
     for (int64_t t = cta; t < nslots; t += ncta) {
@@ -531,7 +546,11 @@ cudaError_t nk_launch_fc_block(int depth, double sw2, double sb2, const float* X
   P.wait_limit = wait_limit;
   const int64_t slots = (int64_t)P.ntm * P.ntn;
   const size_t smem = sizeof(GemmSmem) + 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_fc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, k_fc_gram);
+  if (e != cudaSuccess) return e;
+  if (fa.numRegs != REG_LAUNCH) return cudaErrorInvalidConfiguration;  // the register split needs it
+  e = cudaFuncSetAttribute(k_fc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   P.dstatus = dstatus;
   ++*launches;

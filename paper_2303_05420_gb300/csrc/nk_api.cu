@@ -587,6 +587,9 @@ nk_status nk_fc_block(nk_handle* h, int depth, const nk_params* prm, const float
                                      symmetric, ws, h->sm_count, h->dstatus, fc_wait_limit(h), (cudaStream_t)stream,
                                      &h->launches);
   if (e == cudaErrorInvalidValue) return nk_fail(h, NK_ERR_CUDA, "nk_fc_block: tensor map encoding failed");
+  if (e == cudaErrorInvalidConfiguration)
+    return nk_fail(h, NK_ERR_CUDA, "nk_fc_block: the Gram kernel was built with another register count than its "
+                                   "warpgroup register split assumes");
   return nk_cuda_check(h, e, "nk_fc_block");
 }
 

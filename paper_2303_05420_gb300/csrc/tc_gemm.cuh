@@ -83,6 +83,22 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+// ---------------------------------------------------------------- registers
+// Per-thread register budget of the calling warpgroup (all four warps
+// execute it): dec gives registers back to the CTA's pool, inc waits until
+// the pool holds enough.  The budgets of all warpgroups must add up to at
+// most the CTA's launch allocation (threads x registers per thread).
+template <int N>
+__device__ __forceinline__ void setmaxnreg_dec() {
+  static_assert(N >= 24 && N <= 256 && N % 8 == 0, "register count");
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(N));
+}
+template <int N>
+__device__ __forceinline__ void setmaxnreg_inc() {
+  static_assert(N >= 24 && N <= 256 && N % 8 == 0, "register count");
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(N));
+}
+
 // ---------------------------------------------------------------- descriptors
 // Shared-memory matrix descriptor: K-major operand tile whose rows are 128
 // bytes (64 BF16), written by TMA with 128-byte swizzle; 8-row groups are
