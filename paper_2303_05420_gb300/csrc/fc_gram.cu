@@ -264,6 +264,14 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
     if (lane == 0) {
       // MMA issuer
       constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+      // Descriptors: the start-address field is the shared-memory byte
+      // address / 16 in the low bits, so a stage s and a byte offset o within
+      // a 128-byte row move a descriptor by (s * stage bytes + o) / 16 (all
+      // addresses stay below 2^18, so the field never carries).  The loop
+      // only adds constants to the stage-0 descriptors.
+      const uint64_t ad0 = tc::sdesc_k128(tc::smem_addr(S.A[0]));
+      const uint64_t bd0 = tc::sdesc_k128(tc::smem_addr(S.B[0]));
+      constexpr uint64_t A_STEP = BM * BK * 2 / 16, B_STEP = BN * BK * 2 / 16;
       int64_t kb_all = 0;
       int n = 0;  // tiles of this CTA so far
       for (int64_t t = cta; t < nslots && ok; t += ncta) {
@@ -285,15 +293,14 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
           }
           tc::tc_fence_after();
           // a 128-byte operand row holds the high parts of 32 columns in
-          // bytes [0, 64) (K steps 0, 1) and their low parts in [64, 128)
-          const uint32_t a0 = tc::smem_addr(S.A[s]), b0 = tc::smem_addr(S.B[s]);
+          // bytes [0, 64) (K steps 0, 1: descriptor + 0, + 2) and their low
+          // parts in [64, 128) (K steps 2, 3: + 4, + 6)
+          const uint64_t ad = ad0 + (uint64_t)s * A_STEP, bd = bd0 + (uint64_t)s * B_STEP;
           const uint32_t ts = tbase, tl = tbase + BN;
-#pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            tc::mma_bf16(ts, tc::sdesc_k128(a0 + 32 * k), tc::sdesc_k128(b0 + 64 + 32 * k), idesc,
-                         (kb > 0) || (k != 0));                                                   // hi.lo'
-            tc::mma_bf16(ts, tc::sdesc_k128(a0 + 64 + 32 * k), tc::sdesc_k128(b0 + 32 * k), idesc, 1);  // lo.hi'
-          }
+          tc::mma_bf16(ts, ad + 0, bd + 4, idesc, kb > 0);  // hi.lo'
+          tc::mma_bf16(ts, ad + 2, bd + 6, idesc, 1);
+          tc::mma_bf16(ts, ad + 4, bd + 0, idesc, 1);       // lo.hi'
+          tc::mma_bf16(ts, ad + 6, bd + 2, idesc, 1);
           if (H > 0 && kb == H) {
             // the epilogue has copied the first half's hi.hi' sum out of TMEM
             if (!tc::mbar_wait(&S.hempty, (uint32_t)(n & 1), P.wait_limit)) {
@@ -303,10 +310,8 @@ k_fc_gram(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
             }
             tc::tc_fence_after();
           }
-#pragma unroll
-          for (int k = 0; k < 2; ++k)
-            tc::mma_bf16(tl, tc::sdesc_k128(a0 + 32 * k), tc::sdesc_k128(b0 + 32 * k), idesc,
-                         !((kb == 0 || kb == H) && k == 0));                                      // hi.hi'
+          tc::mma_bf16(tl, ad + 0, bd + 0, idesc, kb != 0 && kb != H);  // hi.hi'
+          tc::mma_bf16(tl, ad + 2, bd + 2, idesc, 1);
           tc::mma_commit(&S.empty[s]);  // the stage may be refilled once these MMAs have read it
           if (kb == H - 1) tc::mma_commit(&S.hfull);
         }
