@@ -422,6 +422,23 @@ def run_ours(args, rank, world, dist):
         b.record(stream)
         torch.cuda.synchronize()
         extra["ntk_plain_fp32_entries_per_s"] = tile * tile / (a.elapsed_time(b) / 1e3)
+        # fused NTK (the tiled row stream carrying Theta beside K): the same
+        # tile for accuracy against the layer-wise form, a symmetric
+        # 256-image block for the rate
+        Km, Tm = h.block_ntk(X, q, X, q, CONVS, SW2, SB2, prec="mixed", a_range=(0, tile),
+                             b_range=(tile, 2 * tile))
+        nsym = min(256, n_tr)
+        h.block_ntk(X, q, X, q, CONVS, SW2, SB2, prec="mixed", a_range=(0, nsym), b_range=(0, nsym), symmetric=True)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        h.block_ntk(X, q, X, q, CONVS, SW2, SB2, prec="mixed", a_range=(0, nsym), b_range=(0, nsym), symmetric=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        h.sync_status()
+        extra["ntk_mixed_entries_per_s"] = nsym * (nsym + 1) / 2 / (a.elapsed_time(b) / 1e3)
+        extra["ntk_mixed_over_plain_fp32"] = extra["ntk_mixed_entries_per_s"] / extra["ntk_plain_fp32_entries_per_s"]
+        extra["ntk_mixed_workload"] = f"myrtle5_(2,1,0)_32x32_ntk_symmetric{nsym}_mixed_tiled"
         # the 64x64 problem of the mixed-resolution workload in the layer-wise
         # FP32 form, on a 16 x 16 sample of pairs (the fused form: queue leg)
         x64 = nkdata.standardise(nkdata.images(32, 64, 3, nkdata.SEED_TRAIN, blur=True))[0]
@@ -438,6 +455,7 @@ def run_ours(args, rank, world, dist):
         extra["plain_fp32_64x64_entries_per_s"] = r64
         extra["plain_fp32_64x64_blocks_s_extrapolated"] = (512 * 513 // 2 + 128 * 512) / r64
         extra["ntk_over_nngp_mean"] = float((Tn.double() / Kn.double()).mean())
+        extra["ntk_maxrel_mixed_vs_plain_fp32"] = float(((Tm.double() - Tn.double()).abs() / Tn.double().abs()).max())
         # PCG: mixed vs plain FP64 on the same train block, with the Jacobi
         # preconditioner of the configuration and with the paper's pivoted
         # Cholesky one (rank 100)
@@ -512,7 +530,7 @@ def run_ours(args, rank, world, dist):
     # the output keeps them)
     keys = ["mixed_over_plain_fp32", "plain_fp32_entries_per_s", "plain_fp64_entries_per_s", "pcg_iters_per_s",
             "pcg_mixed_iters_per_s", "pcg_plain_fp64_iters_per_s", "fc3_gram_ms", "grad_backward_s",
-            "queue_graph_ms", "erf_entries_per_s", "cv8_entries_per_s", "config1_entries_per_s"]
+            "queue_graph_ms", "erf_entries_per_s", "cv8_entries_per_s", "config1_entries_per_s", "ntk_mixed_entries_per_s"]
     line["summary"] = {"value": value, "e2e": e2e_val, "roofline_frac": achieved_tops / peak_tops,
                        **{k: line.get(k) for k in keys if k in line}}
     if rank == 0:

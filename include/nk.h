@@ -278,8 +278,16 @@ nk_status nk_block_fused_noalloc(const nk_arch* arch, const nk_params* prm,
  *   ReLU: Kt = relu map of K, Theta_t = Theta (pi - arccos c) / (2 pi);
  *   pools on both; readout K = sw2 mean Kt + sb2, Theta = K + sw2 mean Theta_t.
  * Arguments as nk_block; K and Theta are [a1 - a0][ldk] outputs of the
- * precision's type.  ReLU or identity, no norm.  Layer-wise forms only: prec = NK_PREC_PLAIN_FP32 or
- * NK_PREC_PLAIN_FP64 (NK_PREC_MIXED: NK_ERR_UNSUPPORTED, no fused NTK). */
+ * precision's type.  ReLU or identity, no norm, global-average readout.
+ * NK_PREC_PLAIN_FP32 / NK_PREC_PLAIN_FP64: the layer-wise forms (K and Theta
+ * as pixel-pair tensors in HBM).  NK_PREC_MIXED: the fused tiled form of
+ * nk_block with the tangent rows carried beside K on chip (FP32 recursion,
+ * FP64 global averages; qsa / qsb needed, float outputs): ReLU, filter 3,
+ * C <= 3, H == W in {32, 64} and the stage pattern (2,1,0), otherwise
+ * NK_ERR_UNSUPPORTED.  Its K is nk_block's MIXED K (the same arithmetic; the
+ * pooled sums are atomic adds, so the last bits may differ).  The tiled form's
+ * slot ring holds both pooled tensors, so the workspace is twice nk_block's;
+ * waits are bounded as there (NK_ERR_TIMEOUT through nk_sync_status). */
 nk_status nk_block_ntk(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_prec prec,
                        const float* Xa, const double* qda, const float* qsa, int64_t a0, int64_t a1,
                        const float* Xb, const double* qdb, const float* qsb, int64_t b0, int64_t b1, int H,

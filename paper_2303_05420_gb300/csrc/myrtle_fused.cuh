@@ -120,6 +120,7 @@ struct FusedParams {
   double out_bias;            // sb2
   double* gacc;               // [2 * nclusters] global-average accumulators
   int* gcnt;                  // [2 * nclusters] arrival counters
+  float* Th;                  // NTK block (tiled NTK form only), same ldk as K
 };
 
 // ---------------------------------------------------------------------------
@@ -890,13 +891,20 @@ cudaError_t dispatch_r8(const int c[3], bool bias, int variant, FusedParams& P, 
 // Tiled form (myrtle_tiled.cu): 64x64 blocks, and queues mixing 64x64 and
 // 32x32 blocks (R[b] in {64, 32}, largest first) in one persistent launch.
 bool tiled_supported(const int c[3]);
-size_t tiled_ws_bytes(const int c[3], const int* R, const int64_t* npairs, int n, int sm_count);
+// tensors: pooled tensors per pair (1; 2 for the NTK form)
+size_t tiled_ws_bytes(const int c[3], const int* R, const int64_t* npairs, int n, int sm_count, int tensors = 1);
 // wait_limit: polls of a dependency wait before it gives up (NK_DEV_TIMEOUT).
 // act: NK_ACT_RELU or NK_ACT_ERF (the map of every activation layer).
 cudaError_t launch_tiled(const int c[3], bool bias, int act, const int* R, const FusedParams* B, int n,
                          int sm_count,
                          void* ws, size_t ws_bytes, unsigned int* dstatus, long long wait_limit,
                          cudaStream_t st);
+// The NTK form (myrtle_tiled_ntk.cu): K and Theta (B[b].Th) of ReLU blocks of
+// the stage pattern (2,1,0), 64x64 and/or 32x32.
+bool tiled_ntk_supported(const int c[3]);
+cudaError_t launch_tiled_ntk(const int c[3], bool bias, const int* R, const FusedParams* B, int n, int sm_count,
+                             void* ws, size_t ws_bytes, unsigned int* dstatus, long long wait_limit,
+                             cudaStream_t st);
 
 }  // namespace nkf
 

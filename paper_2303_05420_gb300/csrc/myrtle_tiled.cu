@@ -12,10 +12,10 @@ bool tiled_supported(const int c[3]) {
          (c[0] == 1 && c[1] == 1 && c[2] == 0);
 }
 
-size_t tiled_ws_bytes(const int c[3], const int* R, const int64_t* npairs, int n, int sm_count) {
+size_t tiled_ws_bytes(const int c[3], const int* R, const int64_t* npairs, int n, int sm_count, int tensors) {
   // an upper bound of what launch_tiled asks for (it runs one 512-thread or
   // two 256-thread CTAs per SM; four are assumed here)
-  return (size_t)sched::make_plan(c[1] > 0, R, npairs, n, 4 * sm_count).bytes;
+  return (size_t)sched::make_plan(c[1] > 0, R, npairs, n, 4 * sm_count, tensors).bytes;
 }
 
 // Erf instantiations (myrtle_tiled_erf.cu).

@@ -200,31 +200,49 @@ __device__ __forceinline__ void take_row(float* p, float (&v)[COLS]) {
 //         into the slot of the next stage.
 //   WRAP: p'-side tables hold all rows (row index (r + t_y) mod R); else a
 //         window starting at row s0 + ty0.
+//   NTK:  a tangent row B (the neural tangent kernel's Theta, NTK
+//         parameterisation) streams beside the NNGP row A through the same
+//         stencil: a conv gives Theta = a S(Theta_t) + K (K with its bias; at
+//         the first conv Theta_t = 0, so Theta = K), the ReLU gives Theta_t =
+//         Theta (pi - arccos c) / (2 pi), and the layer's folded factor (a /
+//         (2 pi), / 16 before a pool) scales B as it scales A, without the
+//         sqrt(q q') that A's map carries.  Pools and the global average act
+//         on both; the slot holds K's pooled tensor, then Theta's.
 // ---------------------------------------------------------------------------
 template <int R, int NQ, int N, bool SEED, bool GAP, bool BIAS, bool WRAP, int SXP, int SQ, int PL, int QL, int ACT,
-          int SQX = SQ, bool PH = false>
+          int SQX = SQ, bool PH = false, bool NTK = false>
 struct Band {
   static constexpr int COLS = R / NQ, TYW = 32 / NQ;
   static constexpr int R1 = R / 2;
+  static constexpr int CT = NTK ? COLS : 1;  // tangent row width (1: unused)
+  static constexpr int NTL = NTK ? N : 1;
   int t_x, t_y, c0;
   int s0, s1, b0;
   bool tyodd;
   float E[COLS + 1];
   float Hp[N][COLS], Pp[N][COLS], acc[COLS];
   float nx[COLS];       // prefetched next input row (stage 1)
+  float HpT[NTL][CT], PpT[NTL][CT], accT[CT], nxT[CT];  // the tangent row's pipeline
   const float4* xs;     // p-side x, at (r - s0) * SXP + pcol
   const float4* xq;     // p'-side x'
   float* in;            // stage-1 input super-plane in its slot (row stride R)
+  float* inT;           // its tangent (NTK)
   const float2* ptab;
   const float2* qtab;
   int pcol, qr0, qc;
   int qo[PH ? COLS : 1];  // phased p'-side offsets of the row part's columns
   float* slot;          // pooled output slot (stage 0 of a two-stage net)
+  float* slotT;         // its tangent half (NTK)
+  const float* fth;     // folded factor of each layer of this stage (NTK)
   float b;
+
+  // the tangent row enters layer j (not the first conv of stage 0)
+  template <int j>
+  static constexpr bool tin() { return NTK && !(SEED && j == 0); }
 
   __device__ __forceinline__ int qrow(int r) const { return WRAP ? ((r + t_y) & (R - 1)) : (r + qr0); }
 
-  __device__ __forceinline__ void input_row(int t, float (&A)[COLS]) {
+  __device__ __forceinline__ void input_row(int t, float (&A)[COLS], float (&B)[CT]) {
     if constexpr (SEED) {
       const float4* xa = xs + (t - s0) * SXP + pcol;
       if constexpr (PH) {
@@ -245,25 +263,41 @@ struct Band {
     } else {
 #pragma unroll
       for (int k = 0; k < COLS; ++k) A[k] = nx[k];
-      if (t + 1 < R) take_row<COLS>(in + (t + 1) * R, nx);
+      if constexpr (NTK) {
+#pragma unroll
+        for (int k = 0; k < COLS; ++k) B[k] = nxT[k];
+      }
+      if (t + 1 < R) {
+        take_row<COLS>(in + (t + 1) * R, nx);
+        if constexpr (NTK) take_row<COLS>(inT + (t + 1) * R, nxT);
+      }
     }
   }
 
   template <int j, bool FIN>
-  __device__ __forceinline__ void layer(int r, float (&A)[COLS]) {
-    float Hc[COLS];
+  __device__ __forceinline__ void layer(int r, float (&A)[COLS], float (&B)[CT]) {
+    float Hc[COLS], HcT[CT];
     hsum<COLS, TYW>(A, Hc, E);
+    if constexpr (tin<j>()) hsum<COLS, TYW>(B, HcT, E);
     const float e = (r != R - t_y) ? 1.f : 0.f;
-    if (FIN) finish<j>(r - 1, e, Hc, A);
+    if (FIN) finish<j>(r - 1, e, Hc, HcT, A, B);
 #pragma unroll
     for (int k = 0; k < COLS; ++k) {
       Pp[j][k] = fmaf(e, Hp[j][k], Hc[k]);
       Hp[j][k] = Hc[k];
     }
+    if constexpr (tin<j>()) {
+#pragma unroll
+      for (int k = 0; k < COLS; ++k) {
+        PpT[j][k] = fmaf(e, HpT[j][k], HcT[k]);
+        HpT[j][k] = HcT[k];
+      }
+    }
   }
 
   template <int j>
-  __device__ __forceinline__ void finish(int ro, float e, const float (&Hc)[COLS], float (&A)[COLS]) {
+  __device__ __forceinline__ void finish(int ro, float e, const float (&Hc)[COLS], const float (&HcT)[CT],
+                                         float (&A)[COLS], float (&B)[CT]) {
     const float2* pt = ptab + j * PL + (ro - s0) * SXP + pcol;
     const float2* qt = qtab + j * QL + qrow(ro) * SQ + (PH ? 0 : qc);
 #pragma unroll
@@ -277,21 +311,33 @@ struct Band {
         J = nk_asin_f32(c);  // Erf: (2/pi) asin(c), 2/pi folded into the p side
       else
         J = (SEED && j == 0) ? nk_J_f32(c) : nk_J01_f32(c);
-      A[k] = (pv.y * qv.y) * J;
+      const float sq = pv.y * qv.y;
+      A[k] = sq * J;
+      if constexpr (NTK) {
+        float T = K;
+        if constexpr (tin<j>()) T += fmaf(e, HcT[k], PpT[j][k]);
+        // pi - arccos c; a zero self-variance on either side gives a zero
+        // derivative kernel
+        const float dJ = (sq != 0.f) ? (NK_HALF_PI_F + nk_asin_f32(c)) : 0.f;
+        B[k] = (T * dJ) * fth[j];
+      }
     }
   }
 
   template <int j>
-  __device__ __forceinline__ void finish_last(float (&A)[COLS]) {
-    float Hz[COLS];
+  __device__ __forceinline__ void finish_last(float (&A)[COLS], float (&B)[CT]) {
+    float Hz[COLS], HzT[CT];
 #pragma unroll
     for (int k = 0; k < COLS; ++k) Hz[k] = 0.f;
-    finish<j>(R - 1, 0.f, Hz, A);
+#pragma unroll
+    for (int k = 0; k < CT; ++k) HzT[k] = 0.f;
+    finish<j>(R - 1, 0.f, Hz, HzT, A, B);
   }
 
-  // pooled scatter of one row part into super-plane row (Ty, I) of the slot
-  __device__ __forceinline__ void scatter(int Ty, int I, const float (&v)[COLS]) const {
-    float* aE = slot + ((size_t)(Ty * R1 + (t_x >> 1)) * R1 + I) * R1 + (c0 >> 1);
+  // pooled scatter of one row part into super-plane row (Ty, I) of a slot
+  // tensor at `base`
+  __device__ __forceinline__ void scatter(float* base, int Ty, int I, const float (&v)[COLS]) const {
+    float* aE = base + ((size_t)(Ty * R1 + (t_x >> 1)) * R1 + I) * R1 + (c0 >> 1);
     if (!(t_x & 1)) {
       if constexpr (COLS == 8) {
         red_v4(aE, v[0] + v[1], v[2] + v[3], v[4] + v[5], v[6] + v[7]);
@@ -303,7 +349,7 @@ struct Band {
       }
     } else {
       // even pixel columns keep T_x = t_x >> 1, odd ones go to the next T_x
-      float* aO = slot + ((size_t)(Ty * R1 + (((t_x + 1) >> 1) & (R1 - 1))) * R1 + I) * R1 + (c0 >> 1);
+      float* aO = base + ((size_t)(Ty * R1 + (((t_x + 1) >> 1) & (R1 - 1))) * R1 + I) * R1 + (c0 >> 1);
       if constexpr (COLS == 8) {
         red_v4(aE, v[0], v[2], v[4], v[6]);
         red_v4(aO, v[1], v[3], v[5], v[7]);
@@ -321,30 +367,51 @@ struct Band {
   }
 
   template <int PAR>
-  __device__ __forceinline__ void output(int ro, const float (&A)[COLS], double& gap) {
+  __device__ __forceinline__ void output(int ro, const float (&A)[COLS], const float (&B)[CT], double& gap,
+                                         double& gapT) {
     if constexpr (GAP) {
       float s = 0.f;
 #pragma unroll
       for (int k = 0; k < COLS; ++k) s += A[k];
       gap += (double)s;
+      if constexpr (NTK) {
+        float u = 0.f;
+#pragma unroll
+        for (int k = 0; k < COLS; ++k) u += B[k];
+        gapT += (double)u;
+      }
     } else if constexpr (PAR == 0) {
 #pragma unroll
       for (int k = 0; k < COLS; ++k) acc[k] = A[k];
+      if constexpr (NTK) {
+#pragma unroll
+        for (int k = 0; k < COLS; ++k) accT[k] = B[k];
+      }
     } else {
       const int I = ro >> 1;
       float v[COLS];
 #pragma unroll
       for (int k = 0; k < COLS; ++k) v[k] = tyodd ? acc[k] : acc[k] + A[k];
-      scatter(t_y >> 1, I, v);
-      if (tyodd) scatter(((t_y + 1) >> 1) & (R1 - 1), I, A);
+      scatter(slot, t_y >> 1, I, v);
+      if (tyodd) scatter(slot, ((t_y + 1) >> 1) & (R1 - 1), I, A);
+      if constexpr (NTK) {
+        float w[COLS], bt[COLS];
+#pragma unroll
+        for (int k = 0; k < COLS; ++k) {
+          w[k] = tyodd ? accT[k] : accT[k] + B[k];
+          bt[k] = B[k];
+        }
+        scatter(slotT, t_y >> 1, I, w);
+        if (tyodd) scatter(slotT, ((t_y + 1) >> 1) & (R1 - 1), I, bt);
+      }
     }
   }
 
   template <int j0, int j1>
-  __device__ __forceinline__ void layers_fin(int t, float (&A)[COLS]) {
+  __device__ __forceinline__ void layers_fin(int t, float (&A)[COLS], float (&B)[CT]) {
     if constexpr (j0 < j1) {
-      layer<j0, true>(t - j0, A);
-      layers_fin<j0 + 1, j1>(t, A);
+      layer<j0, true>(t - j0, A, B);
+      layers_fin<j0 + 1, j1>(t, A, B);
     }
   }
 
@@ -353,56 +420,67 @@ struct Band {
   template <int T>
   __device__ __forceinline__ void fill() {
     if constexpr (T < N) {
-      float A[COLS];
-      input_row(s0 + T, A);
-      layers_fin<0, T>(s0 + T, A);
-      layer<T, false>(s0, A);
+      float A[COLS], B[CT];
+      input_row(s0 + T, A, B);
+      layers_fin<0, T>(s0 + T, A, B);
+      layer<T, false>(s0, A, B);
       fill<T + 1>();
     }
   }
 
   template <int PAR>
-  __device__ __forceinline__ void steady(int t, double& gap) {
-    float A[COLS];
-    input_row(t, A);
-    layers_fin<0, N>(t, A);
-    output<PAR>(t - N, A, gap);
+  __device__ __forceinline__ void steady(int t, double& gap, double& gapT) {
+    float A[COLS], B[CT];
+    input_row(t, A, B);
+    layers_fin<0, N>(t, A, B);
+    output<PAR>(t - N, A, B, gap, gapT);
   }
 
   template <int D>
-  __device__ __forceinline__ void drain(double& gap) {
+  __device__ __forceinline__ void drain(double& gap, double& gapT) {
     if constexpr (D < N) {
-      float A[COLS];
+      float A[COLS], B[CT];
 #pragma unroll
       for (int k = 0; k < COLS; ++k) A[k] = 0.f;
-      finish_last<D>(A);
-      layers_fin<D + 1, N>(R + D, A);
-      output<((R + D - N) & 1)>(R + D - N, A, gap);
-      drain<D + 1>(gap);
+#pragma unroll
+      for (int k = 0; k < CT; ++k) B[k] = 0.f;
+      finish_last<D>(A, B);
+      layers_fin<D + 1, N>(R + D, A, B);
+      output<((R + D - N) & 1)>(R + D - N, A, B, gap, gapT);
+      drain<D + 1>(gap, gapT);
     }
   }
 
-  __device__ __forceinline__ void run(double& gap) {
+  __device__ __forceinline__ void run(double& gap, double& gapT) {
 #pragma unroll
     for (int j = 0; j < N; ++j)
 #pragma unroll
       for (int k = 0; k < COLS; ++k) Hp[j][k] = Pp[j][k] = 0.f;
-    if constexpr (!SEED) take_row<COLS>(in, nx);
+    if constexpr (NTK) {
+#pragma unroll
+      for (int j = 0; j < N; ++j)
+#pragma unroll
+        for (int k = 0; k < CT; ++k) HpT[j][k] = PpT[j][k] = 0.f;
+    }
+    if constexpr (!SEED) {
+      take_row<COLS>(in, nx);
+      if constexpr (NTK) take_row<COLS>(inT, nxT);
+    }
     fill<0>();
     int t = s0 + N;
     // halo rows: computed, not output (b0 - s0 is 0 or N)
     for (; t < b0 + N; ++t) {
-      float A[COLS];
-      input_row(t, A);
-      layers_fin<0, N>(t, A);
+      float A[COLS], B[CT];
+      input_row(t, A, B);
+      layers_fin<0, N>(t, A, B);
     }
     // output rows from b0 (even) in pairs
     for (; t + 1 < s1; t += 2) {
-      steady<0>(t, gap);
-      steady<1>(t + 1, gap);
+      steady<0>(t, gap, gapT);
+      steady<1>(t + 1, gap, gapT);
     }
-    if (t < s1) steady<0>(t, gap);
-    if (s1 == R) drain<0>(gap);
+    if (t < s1) steady<0>(t, gap, gapT);
+    if (s1 == R) drain<0>(gap, gapT);
   }
 };
 
@@ -434,10 +512,18 @@ __device__ __forceinline__ float* slot_of(const TiledParams& Q, int b, int64_t g
   return Q.slots + Q.ring_off[r] + k * Q.slot_floats[r];
 }
 
+// Theta of the NTK: K + sw2 mean(Theta_t), i.e. the GAP scale applied to the
+// sum of both global-average sums (K's bias added once).
+__device__ __forceinline__ void store_theta(const FusedParams& P, int64_t i, int64_t j, double tot) {
+  const float v = (float)(P.out_scale * tot + P.out_bias);
+  P.Th[i * P.ldk + j] = v;
+  if (P.sym && i != j) P.Th[j * P.ldk + i] = v;
+}
+
 // ---------------------------------------------------------------------------
 // Stage-0 task `sub` of pair g (block b).
 // ---------------------------------------------------------------------------
-template <int R, int N0, int N1, bool BIAS, int NT, int ACT>
+template <int R, int N0, int N1, bool BIAS, int NT, int ACT, bool NTK>
 __device__ void stage0_task(const TiledParams& Q, int b, int64_t g, int sub, unsigned char* smem, double* red,
                             int* flag) {
   using G = G0<R>;
@@ -456,6 +542,8 @@ __device__ void stage0_task(const TiledParams& Q, int b, int64_t g, int sub, uns
   const int ty0 = yg * G::TY, tx0 = xg * G::TX;
   int64_t prev = -1;
   float* slot = TWO ? slot_of(Q, b, g, &prev) : nullptr;
+  constexpr int64_t R1 = R / 2;
+  float* slotT = (TWO && NTK) ? slot + R1 * R1 * R1 * R1 : nullptr;  // the tangent's pooled tensor
 
   // the slot's previous pair must have been taken by its stage-1 task
   if (threadIdx.x == 0) {
@@ -499,8 +587,8 @@ __device__ void stage0_task(const TiledParams& Q, int b, int64_t g, int sub, uns
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = lane / G::TYW, tyl = lane - q * G::TYW;
-  double gap = 0.0;
-  using BT = Band<R, G::NQ, N0, true, !TWO, BIAS, false, G::SXP, G::SQQ, L::PL, L::QL, ACT, G::SQX, G::PH>;
+  double gap = 0.0, gapT = 0.0;
+  using BT = Band<R, G::NQ, N0, true, !TWO, BIAS, false, G::SXP, G::SQQ, L::PL, L::QL, ACT, G::SQX, G::PH, NTK>;
   static_assert(BT::COLS == G::COLS && BT::TYW == G::TYW, "split");
   for (int w = warp; w < G::WT; w += NT / 32) {
     BT T;
@@ -530,8 +618,11 @@ __device__ void stage0_task(const TiledParams& Q, int b, int64_t g, int sub, uns
       }
     }
     T.slot = slot;
+    T.slotT = slotT;
+    T.inT = nullptr;
+    T.fth = P.fold;
     T.b = P.sb2;
-    T.run(gap);
+    T.run(gap, gapT);
   }
   if constexpr (TWO) {
     // publish this task's atomic adds, then count it: the barrier orders
@@ -546,16 +637,27 @@ __device__ void stage0_task(const TiledParams& Q, int b, int64_t g, int sub, uns
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) gap += __shfl_xor_sync(FULL, gap, o);
     if (lane == 0) red[warp] = gap;
+    if constexpr (NTK) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) gapT += __shfl_xor_sync(FULL, gapT, o);
+      if (lane == 0) red[MAX_WARPS + warp] = gapT;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-      double s = 0.0;
+      double s = 0.0, sT = 0.0;
       for (int w = 0; w < NT / 32; ++w) s += red[w];
       atomicAdd(Q.gacc + g, s);
+      if constexpr (NTK) {
+        for (int w = 0; w < NT / 32; ++w) sT += red[MAX_WARPS + w];
+        atomicAdd(Q.gacc + Q.G + g, sT);
+      }
       __threadfence();
       const int old = atomicAdd(Q.cnt0 + g, 1);
       if (old == Q.nt0[b] - 1) {
         __threadfence();
-        store_entry(P, i, j, atomicAdd(Q.gacc + g, 0.0));
+        const double tk = atomicAdd(Q.gacc + g, 0.0);
+        store_entry(P, i, j, tk);
+        if constexpr (NTK) store_theta(P, i, j, tk + atomicAdd(Q.gacc + Q.G + g, 0.0));
       }
     }
   }
@@ -564,7 +666,7 @@ __device__ void stage0_task(const TiledParams& Q, int b, int64_t g, int sub, uns
 // ---------------------------------------------------------------------------
 // Stage-1 task of pair g: the whole R1 stage on this CTA, then K.
 // ---------------------------------------------------------------------------
-template <int R1, int N0, int N1, bool BIAS, int NT, int ACT>
+template <int R1, int N0, int N1, bool BIAS, int NT, int ACT, bool NTK>
 __device__ void stage1_task(const TiledParams& Q, int64_t g, unsigned char* smem, double* red, int* flag) {
   using L = L1<R1, N1>;
   using SP = Split<R1>;
@@ -598,8 +700,8 @@ __device__ void stage1_task(const TiledParams& Q, int64_t g, unsigned char* smem
   if (*flag == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = lane / SP::TYW, tyl = lane - q * SP::TYW;
-  double gap = 0.0;
-  using BT = Band<R1, SP::NQ, N1, false, true, BIAS, true, R1, L::S, L::PL, L::QL, ACT>;
+  double gap = 0.0, gapT = 0.0;
+  using BT = Band<R1, SP::NQ, N1, false, true, BIAS, true, R1, L::S, L::PL, L::QL, ACT, L::S, false, NTK>;
   static_assert(BT::COLS == SP::COLS && BT::TYW == SP::TYW, "split");
   constexpr int NH = SP::WPT;
   for (int task = warp; task < R1 * NH; task += NT / 32) {
@@ -615,6 +717,9 @@ __device__ void stage1_task(const TiledParams& Q, int64_t g, unsigned char* smem
     T.xs = nullptr;
     T.xq = nullptr;
     T.in = slot + ((size_t)(T.t_y * R1 + T.t_x) * R1) * R1 + T.c0;
+    T.inT = NTK ? T.in + (size_t)R1 * R1 * R1 * R1 : nullptr;
+    T.slotT = nullptr;
+    T.fth = P.fold + N0;
     T.ptab = pt;
     T.qtab = qt;
     T.pcol = T.c0;
@@ -622,11 +727,16 @@ __device__ void stage1_task(const TiledParams& Q, int64_t g, unsigned char* smem
     T.qc = T.c0 + T.t_x;
     T.slot = nullptr;
     T.b = P.sb2;
-    T.run(gap);
+    T.run(gap, gapT);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) gap += __shfl_xor_sync(FULL, gap, o);
   if (lane == 0) red[warp] = gap;
+  if constexpr (NTK) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) gapT += __shfl_xor_sync(FULL, gapT, o);
+    if (lane == 0) red[MAX_WARPS + warp] = gapT;
+  }
   // the cleared slot is published before the flag that frees it (barrier,
   // then thread 0's fence)
   __syncthreads();
@@ -634,28 +744,36 @@ __device__ void stage1_task(const TiledParams& Q, int64_t g, unsigned char* smem
     double s = 0.0;
     for (int w = 0; w < NT / 32; ++w) s += red[w];
     store_entry(P, i, j, s);
+    if constexpr (NTK) {
+      double sT = 0.0;
+      for (int w = 0; w < NT / 32; ++w) sT += red[MAX_WARPS + w];
+      store_theta(P, i, j, s + sT);
+    }
     __threadfence();
     atomicExch(Q.done1 + g, 1);
   }
 }
 
-template <int N0, int N1, int RMAX>
+template <int N0, int N1, int RMAX, bool NTK = false>
 struct Smem {
   static constexpr size_t s0 = RMAX == 64 ? std::max(L0<64, N0>::bytes, L0<32, N0>::bytes) : L0<32, N0>::bytes;
   static constexpr size_t s1 =
       N1 > 0 ? (RMAX == 64 ? std::max(L1<32, N1>::bytes, L1<16, N1>::bytes) : L1<16, N1>::bytes) : 0;
   static constexpr size_t tables = std::max(s0, s1);
-  static constexpr size_t bytes = tables + MAX_WARPS * 8 + 16;
+  static constexpr size_t red = (NTK ? 2 : 1) * MAX_WARPS * 8;  // per-warp global-average sums
+  static constexpr size_t bytes = tables + red + 16;
 };
 
-template <int N0, int N1, bool BIAS, int NT, int RMAX, int ACT>
-__global__ void __launch_bounds__(NT, 512 / NT) k_myrtle_tiled(const __grid_constant__ TiledParams Q) {
+// NTK instantiations carry the tangent rows (twice the pipeline registers)
+// and run one CTA per SM.
+template <int N0, int N1, bool BIAS, int NT, int RMAX, int ACT, bool NTK = false>
+__global__ void __launch_bounds__(NT, NTK ? 1 : 512 / NT) k_myrtle_tiled(const __grid_constant__ TiledParams Q) {
   extern __shared__ __align__(16) unsigned char smem[];
-  using SM = Smem<N0, N1, RMAX>;
+  using SM = Smem<N0, N1, RMAX, NTK>;
   constexpr bool TWO = N1 > 0;
   double* red = reinterpret_cast<double*>(smem + SM::tables);
-  int* flag = reinterpret_cast<int*>(smem + SM::tables + MAX_WARPS * 8);
-  long long* item_s = reinterpret_cast<long long*>(smem + SM::tables + MAX_WARPS * 8 + 8);
+  int* flag = reinterpret_cast<int*>(smem + SM::tables + SM::red);
+  long long* item_s = reinterpret_cast<long long*>(smem + SM::tables + SM::red + 8);
   for (;;) {
     if (threadIdx.x == 0) {
       const long long m =
@@ -679,20 +797,20 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_myrtle_tiled(const __grid_cons
       sched::stage0_of(Q, k, &b, &g, &sub);
       if constexpr (RMAX == 64) {
         if (Q.R[b] == 64)
-          stage0_task<64, N0, N1, BIAS, NT, ACT>(Q, b, g, sub, smem, red, flag);
+          stage0_task<64, N0, N1, BIAS, NT, ACT, NTK>(Q, b, g, sub, smem, red, flag);
         else
-          stage0_task<32, N0, N1, BIAS, NT, ACT>(Q, b, g, sub, smem, red, flag);
+          stage0_task<32, N0, N1, BIAS, NT, ACT, NTK>(Q, b, g, sub, smem, red, flag);
       } else {
-        stage0_task<32, N0, N1, BIAS, NT, ACT>(Q, b, g, sub, smem, red, flag);
+        stage0_task<32, N0, N1, BIAS, NT, ACT, NTK>(Q, b, g, sub, smem, red, flag);
       }
     } else if constexpr (TWO) {
       if constexpr (RMAX == 64) {
         if (Q.R[block_of(Q, k)] == 64)
-          stage1_task<32, N0, N1, BIAS, NT, ACT>(Q, k, smem, red, flag);
+          stage1_task<32, N0, N1, BIAS, NT, ACT, NTK>(Q, k, smem, red, flag);
         else
-          stage1_task<16, N0, N1, BIAS, NT, ACT>(Q, k, smem, red, flag);
+          stage1_task<16, N0, N1, BIAS, NT, ACT, NTK>(Q, k, smem, red, flag);
       } else {
-        stage1_task<16, N0, N1, BIAS, NT, ACT>(Q, k, smem, red, flag);
+        stage1_task<16, N0, N1, BIAS, NT, ACT, NTK>(Q, k, smem, red, flag);
       }
     }
     // the next item's staging overwrites the tables
@@ -700,11 +818,12 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_myrtle_tiled(const __grid_cons
   }
 }
 
-template <int N0, int N1, bool BIAS, int NT, int RMAX, int ACT>
+template <int N0, int N1, bool BIAS, int NT, int RMAX, int ACT, bool NTK = false>
 cudaError_t launch_t(TiledParams& Q, const int64_t* npairs, int sm_count, void* ws, size_t ws_bytes,
                      cudaStream_t st) {
-  using SM = Smem<N0, N1, RMAX>;
-  auto kern = k_myrtle_tiled<N0, N1, BIAS, NT, RMAX, ACT>;
+  using SM = Smem<N0, N1, RMAX, NTK>;
+  auto kern = k_myrtle_tiled<N0, N1, BIAS, NT, RMAX, ACT, NTK>;
+  constexpr int tensors = NTK ? 2 : 1;
   static bool attr_set[64] = {false};
   static int per_sm[64] = {0};
   int dev = 0;
@@ -720,7 +839,7 @@ cudaError_t launch_t(TiledParams& Q, const int64_t* npairs, int sm_count, void* 
   }
   const int grid = std::max(1, sm_count * per_sm[dev]);
   constexpr bool TWO = N1 > 0;
-  const sched::Plan p = sched::make_plan(TWO, Q.R, npairs, Q.n, grid);
+  const sched::Plan p = sched::make_plan(TWO, Q.R, npairs, Q.n, grid, tensors);
   if (p.bytes > ws_bytes) return cudaErrorInvalidValue;
   Q.LAG = p.LAG;
   Q.nitems = Q.T0 + (TWO ? Q.G : 0);
@@ -733,9 +852,9 @@ cudaError_t launch_t(TiledParams& Q, const int64_t* npairs, int sm_count, void* 
   }
   Q.slots = reinterpret_cast<float*>(c);
   Q.gacc = reinterpret_cast<double*>(c + p.slot_bytes);
-  Q.cnt0 = reinterpret_cast<int*>(c + p.slot_bytes + G * sizeof(double));
+  Q.cnt0 = reinterpret_cast<int*>(c + p.slot_bytes + tensors * G * sizeof(double));
   Q.done1 = Q.cnt0 + G;
-  Q.next = reinterpret_cast<unsigned long long*>(c + p.slot_bytes + G * (2 * sizeof(int) + sizeof(double)));
+  Q.next = reinterpret_cast<unsigned long long*>(c + p.slot_bytes + G * (2 * sizeof(int) + tensors * sizeof(double)));
   Q.abort_flag = reinterpret_cast<int*>(Q.next + 1);
   cudaError_t e = cudaMemsetAsync(ws, 0, p.bytes, st);
   if (e != cudaSuccess) return e;

@@ -385,12 +385,18 @@ nk_status nk_block_ntk(nk_handle* h, const nk_arch* arch, const nk_params* prm, 
   if (!prm) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: params is NULL");
   if (!(prm->sigma_w2 >= 0.0) || !(prm->sigma_b2 >= 0.0))
     return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: negative variance");
-  if (prec == NK_PREC_MIXED)
-    return nk_fail(h, NK_ERR_UNSUPPORTED, "nk_block_ntk: the NTK has the layer-wise forms only (PLAIN_FP32/FP64)");
   if (g.act == NK_ACT_ERF || g.norm != NK_NORM_NONE || g.readout != NK_READOUT_GAP)
     return nk_fail(h, NK_ERR_UNSUPPORTED, "nk_block_ntk: ReLU or identity, no norm, global-average readout only");
-  if (prec != NK_PREC_PLAIN_FP64 && prec != NK_PREC_PLAIN_FP32)
+  if (prec != NK_PREC_PLAIN_FP64 && prec != NK_PREC_PLAIN_FP32 && prec != NK_PREC_MIXED)
     return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: unknown precision");
+  int pat[3];
+  stage_pattern(g, pat);
+  if (prec == NK_PREC_MIXED &&
+      (g.act != NK_ACT_RELU || g.filter != 3 || g.C > 3 || g.Hs[0] != g.Ws[0] ||
+       (g.Hs[0] != 32 && g.Hs[0] != 64) || !nkf::tiled_ntk_supported(pat)))
+    return nk_fail(h, NK_ERR_UNSUPPORTED,
+                   "nk_block_ntk MIXED: needs ReLU, filter 3, C <= 3, H == W in {32, 64} and the stage pattern "
+                   "(2,1,0)");
   if (a0 < 0 || b0 < 0 || a1 < a0 || b1 < b0)
     return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: bad index range");
   if (a1 == a0 || b1 == b0) return NK_OK;
@@ -401,8 +407,24 @@ nk_status nk_block_ntk(nk_handle* h, const nk_arch* arch, const nk_params* prm, 
   const bool needq = (g.act == NK_ACT_RELU);
   if (needq && prec == NK_PREC_PLAIN_FP64 && (!qda || !qdb))
     return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: PLAIN_FP64 needs qda and qdb");
-  if (needq && prec == NK_PREC_PLAIN_FP32 && (!qsa || !qsb))
-    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: PLAIN_FP32 needs qsa and qsb");
+  if (needq && prec != NK_PREC_PLAIN_FP64 && (!qsa || !qsb))
+    return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: FP32 paths need qsa and qsb");
+  if (prec == NK_PREC_MIXED) {
+    // the tiled row stream with the tangent rows beside K
+    nkf::FusedParams P = nk_fused_params(g, prm->sigma_w2, prm->sigma_b2, Xa, qsa, a0, a1, Xb, qsb, b0, b1,
+                                         (float*)K, ldk, symmetric);
+    P.Th = (float*)Theta;
+    const int R[1] = {g.Hs[0]};
+    const int64_t np[1] = {P.npairs};
+    void* ws = nullptr;
+    nk_status s = nk_workspace(h, nkf::tiled_ws_bytes(pat, R, np, 1, h->sm_count, 2), &ws);
+    if (s != NK_OK) return s;
+    h->launches += 1;
+    return nk_cuda_check(h,
+                         nkf::launch_tiled_ntk(pat, prm->sigma_b2 != 0.0, R, &P, 1, h->sm_count, ws, h->ws_bytes,
+                                               h->dstatus, tiled_wait_limit(h), (cudaStream_t)stream),
+                         "nk_block_ntk tiled launch");
+  }
   const int fp64 = (prec == NK_PREC_PLAIN_FP64);
   const int64_t na = a1 - a0, nb = b1 - b0;
   const int64_t npairs = symmetric ? na * (na + 1) / 2 : na * nb;

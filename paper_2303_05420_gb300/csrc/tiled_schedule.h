@@ -90,7 +90,9 @@ NK_SCHED_HD int64_t slot(const Q& q, int b, int64_t g, int* ring, int64_t* prev)
 // Lag and ring sizes of a launch of `grid` CTAs: stage-1 tasks come LAG =
 // two waves after their pair's last stage-0 task; order alone needs
 // S >= LAG / tasks + 1, and one more LAG between a slot's stage-1 task and
-// its next user lets that task finish before it is waited for.
+// its next user lets that task finish before it is waited for.  `tensors`
+// pooled tensors per slot and global-average sums per pair (2 for the NTK:
+// K and Theta).
 struct Plan {
   int64_t LAG;
   int S[2];
@@ -98,7 +100,7 @@ struct Plan {
   uint64_t slot_bytes, bytes;
 };
 
-inline Plan make_plan(bool two, const int* R, const int64_t* npairs, int n, int grid) {
+inline Plan make_plan(bool two, const int* R, const int64_t* npairs, int n, int grid, int tensors = 1) {
   Plan p = {};
   p.LAG = 2 * (int64_t)grid;
   int64_t G = 0;
@@ -113,12 +115,12 @@ inline Plan make_plan(bool two, const int* R, const int64_t* npairs, int n, int 
     const int nt = tasks_per_pair(side[r]);
     const int64_t R1 = side[r] / 2;
     p.S[r] = (two && has[r]) ? (int)((2 * p.LAG + nt - 1) / nt) + 2 : 1;
-    p.slot_floats[r] = (two && has[r]) ? R1 * R1 * R1 * R1 : 0;
+    p.slot_floats[r] = (two && has[r]) ? tensors * R1 * R1 * R1 * R1 : 0;
     p.ring_off[r] = off;
     off += p.S[r] * p.slot_floats[r];
   }
   p.slot_bytes = (uint64_t)off * sizeof(float);
-  p.bytes = p.slot_bytes + (uint64_t)G * (2 * sizeof(int) + sizeof(double)) + 64;
+  p.bytes = p.slot_bytes + (uint64_t)G * (2 * sizeof(int) + tensors * sizeof(double)) + 64;
   return p;
 }
 

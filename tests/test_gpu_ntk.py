@@ -59,6 +59,7 @@ def test_ntk_symmetric_ranges_and_unsupported(h):
     T, Tr = T.cpu().numpy(), Tr.cpu().numpy()
     assert np.array_equal(T, T.T)
     assert np.allclose(Tr, T[1:4, :], rtol=1e-13)
+    # the fused NTK (prec "mixed") takes 32x32 and 64x64 images only
     with pytest.raises(NkError) as ei:
         h.block_ntk(X, q, X, q, convs, 2.0, 0.0, prec="mixed")
     assert ei.value.status == NK_ERR_UNSUPPORTED
