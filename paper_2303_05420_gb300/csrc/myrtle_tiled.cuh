@@ -765,9 +765,9 @@ struct Smem {
 };
 
 // NTK instantiations carry the tangent rows (twice the pipeline registers)
-// and run one CTA per SM.
+// in the same launch shapes (at 128 registers they spill a few bytes).
 template <int N0, int N1, bool BIAS, int NT, int RMAX, int ACT, bool NTK = false>
-__global__ void __launch_bounds__(NT, NTK ? 1 : 512 / NT) k_myrtle_tiled(const __grid_constant__ TiledParams Q) {
+__global__ void __launch_bounds__(NT, 512 / NT) k_myrtle_tiled(const __grid_constant__ TiledParams Q) {
   extern __shared__ __align__(16) unsigned char smem[];
   using SM = Smem<N0, N1, RMAX, NTK>;
   constexpr bool TWO = N1 > 0;

@@ -40,9 +40,9 @@ def _oracle(xa, xb, sb2):
 
 @pytest.mark.parametrize("sb2", [0.0, 0.01])
 def test_fused_ntk_32x32_symmetric_block_matches_oracle(h, sb2):
-    # 16 images: 136 pairs, more than the 78 slots of the one-CTA-per-SM
-    # launch's ring (LAG = 2 x 152 stage-0 tasks), so slots are reused
-    x = _imgs(16, 32, 21)
+    # 18 images: 171 pairs, more than the 154 slots of the ring of a launch
+    # of two CTAs per SM (LAG = 2 x 304 stage-0 tasks), so slots are reused
+    x = _imgs(18, 32, 21)
     X = torch.tensor(x, device="cuda")
     q = h.self_diag(X, CONVS, 2.0, sb2)
     K, T = h.block_ntk(X, q, X, q, CONVS, 2.0, sb2, prec="mixed", symmetric=True)
