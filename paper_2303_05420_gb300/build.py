@@ -25,7 +25,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
          "--expt-relaxed-constexpr", "-diag-suppress", "177"]
 SOURCES = ["nk_api.cu", "self_diag.cu", "myrtle_fused.cu", "myrtle_fused_r32.cu", "myrtle_fused_r32b.cu", "myrtle_fused_r16.cu",
            "myrtle_fused_r8.cu", "myrtle_fused_static.cu", "myrtle_queue.cu", "myrtle_tiled.cu", "myrtle_tiled_erf.cu", "myrtle_tiled_ntk.cu", "myrtle_plain.cu",
-           "myrtle_backward.cu", "fc_gram.cu", "pcg.cu", "cv_diag.cu", "probe.cu"]
+           "myrtle_backward.cu", "fc_gram.cu", "seed_gemm.cu", "pcg.cu", "cv_diag.cu", "probe.cu"]
 
 
 def nvcc() -> str:

@@ -960,6 +960,8 @@ k_self_adj(SelfAdjGeom G, double sw2, double sb2, const float* __restrict__ X, i
 template <typename T>
 struct BwdPlan {
   int64_t chunk;
+  int sm;                  // SMs of the device
+  size_t patch_bytes;      // FP32 with the tensor-core seed: split patch rows of both image sets
   size_t stored_per_pair;  // elements of T: every layer's pre-activation
   size_t hw0sq;            // elements of the largest (stage-0) pair tensor
   size_t part_per_pair;    // elements of one partial-sum buffer (largest stage)
@@ -1003,7 +1005,11 @@ BwdPlan<T> plan_backward(const NkGeom& g, int64_t npairs, int64_t na, int64_t nb
   P.self_grid = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(na, sym ? na : nb), sm));
   P.self_bytes = (size_t)P.self_grid * (size_t)(off + 3 * mx) * sizeof(double);
   const size_t nqa = (size_t)na * g.nq, nqb = sym ? 0 : (size_t)nb * g.nq;
-  P.bytes = per_pair * P.chunk + (nqa + nqb) * sizeof(T) + P.self_bytes + 4096;
+  P.sm = sm;
+  P.patch_bytes = (sizeof(T) == 4 && nk_seed_gemm_supported(g.Hs[0], g.Ws[0], g.C, g.filter))
+                      ? nk_seed_patch_bytes(na + (sym ? 0 : nb), g.Hs[0], g.Ws[0])
+                      : 0;
+  P.bytes = per_pair * P.chunk + (nqa + nqb) * sizeof(T) + P.self_bytes + P.patch_bytes + 4096;
   return P;
 }
 
@@ -1043,7 +1049,6 @@ cudaError_t run_backward(const NkGeom& g, double sw2, double sb2, const float* X
                          const float* qsb, int64_t b0, int64_t b1, const T* dK, int64_t lddk, int sym, T* dXa, T* dXb,
                          double* dsw2, double* dsb2, void* ws, const BwdPlan<T>& P, cudaStream_t st,
                          int64_t* launches, unsigned int* dstatus) {
-  (void)dstatus;
   const int64_t na = a1 - a0, nb = b1 - b0;
   const int64_t npairs = sym ? na * (na + 1) / 2 : na * nb;
   const int64_t chunk = P.chunk;
@@ -1067,6 +1072,21 @@ cudaError_t run_backward(const NkGeom& g, double sw2, double sb2, const float* X
   cudaError_t e = cudaMemsetAsync(dqa, 0, (size_t)na * g.nq * sizeof(T), st);
   if (e == cudaSuccess && !sym) e = cudaMemsetAsync(dqb, 0, (size_t)nb * g.nq * sizeof(T), st);
   if (e != cudaSuccess) return e;
+  // FP32: the first layer's pre-activation is the patch Gram on the tensor
+  // cores (seed_gemm.cu); the patch rows of both image sets are split once
+  const bool tc_seed = P.patch_bytes > 0;
+  void* patch_a = nullptr;
+  void* patch_b = nullptr;
+  if (tc_seed) {
+    const int64_t HW0 = (int64_t)g.Hs[0] * g.Ws[0];
+    patch_a = take(nk_seed_patch_bytes(na, g.Hs[0], g.Ws[0]));
+    patch_b = sym ? patch_a : take(nk_seed_patch_bytes(nb, g.Hs[0], g.Ws[0]));
+    (void)HW0;
+    *launches += sym ? 1 : 2;
+    e = nk_seed_patches(Xa + a0 * HW0 * g.C, na, g.Hs[0], g.Ws[0], g.C, patch_a, st);
+    if (e == cudaSuccess && !sym) e = nk_seed_patches(Xb + b0 * HW0 * g.C, nb, g.Hs[0], g.Ws[0], g.C, patch_b, st);
+    if (e != cudaSuccess) return e;
+  }
   const T a_conv = (T)(sw2 / (double)(g.filter * g.filter));
   const bool relu = (g.act == NK_ACT_RELU);
   int last_conv_stage = 0;
@@ -1137,7 +1157,11 @@ cudaError_t run_backward(const NkGeom& g, double sw2, double sb2, const float* X
         A.a = a_conv;
         A.b = (T)sb2;
         ++*launches;
-        if (layer == 0) {
+        if (layer == 0 && tc_seed) {
+          if constexpr (sizeof(T) == 4)
+            e = nk_launch_seed_gemm(patch_a, na, patch_b, nb, sym, pair0, np, g.Hs[0], g.Ws[0], g.C, sw2, sb2,
+                                    Kst[0], P.sm, dstatus, st);
+        } else if (layer == 0) {
           e = conv_pass<T, CIN_COV>(A, st);
         } else if (pend_layer >= 0) {
           A.src = pend;

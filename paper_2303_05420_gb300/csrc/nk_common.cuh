@@ -112,6 +112,14 @@ cudaError_t nk_launch_fc_block(int depth, double sw2, double sb2, const float* X
                                int64_t* launches);
 
 // Adjoint of the Myrtle block (layer-wise, FP32 or FP64 pixel-pair tensors).
+// The first layer as a patch Gram on the tensor cores (seed_gemm.cu): FP32
+// pre-activation K_1[pair][p][p'] of an image-pair chunk, written row-major.
+bool nk_seed_gemm_supported(int H, int W, int C, int filter);
+size_t nk_seed_patch_bytes(int64_t n_images, int H, int W);
+cudaError_t nk_seed_patches(const float* X, int64_t n, int H, int W, int C, void* patches, cudaStream_t st);
+cudaError_t nk_launch_seed_gemm(const void* pa, int64_t na, const void* pb, int64_t nb, int sym, int64_t pair0,
+                                int64_t np, int H, int W, int C, double sw2, double sb2, float* out, int sm,
+                                unsigned int* dstatus, cudaStream_t st);
 size_t nk_backward_ws_bytes(const NkGeom& g, int fp64, int64_t npairs, int64_t na, int64_t nb, int sym,
                             int sm);
 cudaError_t nk_launch_backward(const NkGeom& g, int fp64, double sw2, double sb2, const float* Xa,

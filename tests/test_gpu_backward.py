@@ -179,3 +179,30 @@ def test_backward_myrtle10_32x32(h, symmetric):
         assert _rel(dXb.double().cpu().numpy(), want_b) <= 1e-4
     assert abs(float(dsw2) - want_s) <= 1e-4 * abs(want_s)
     assert abs(float(dsb2) - want_b2) <= 1e-4 * abs(want_b2)
+
+
+@pytest.mark.parametrize("hw,na,nb", [(32, 5, 6), (64, 1, 2)])
+def test_backward_tensor_core_seed(h, hw, na, nb):
+    """FP32 adjoints at 32x32 and 64x64 take the first layer's stored
+    pre-activation from the patch Gram on the tensor cores (seed_gemm.cu).
+    5 x 6 pairs at 32x32 are 960 GEMM tiles, more than the 4-stage operand
+    ring and the two accumulators hold per CTA; the gradients are checked
+    element by element against the oracle's autograd."""
+    convs, sb2 = (2, 1, 0), 0.01
+    xa, xb = _imgs(na, hw, 5), _imgs(nb, hw, 6)
+    rng = np.random.default_rng(9)
+    dK = rng.standard_normal((na, nb))
+    want_a, want_b, want_s, want_b2 = _oracle_grads(convs, 2.0, sb2, xa, xb, dK, False)
+    Xa, Xb = torch.tensor(xa, device="cuda"), torch.tensor(xb, device="cuda")
+    qa, qb = h.self_diag(Xa, convs, 2.0, sb2), h.self_diag(Xb, convs, 2.0, sb2)
+    dXa = torch.zeros(Xa.shape, dtype=torch.float32, device="cuda")
+    dXb = torch.zeros(Xb.shape, dtype=torch.float32, device="cuda")
+    dsw2 = torch.zeros(1, dtype=F64, device="cuda")
+    dsb2 = torch.zeros(1, dtype=F64, device="cuda")
+    dKt = torch.tensor(dK, dtype=torch.float32, device="cuda")
+    h.block_backward(Xa, qa, Xb, qb, convs, 2.0, sb2, dKt, dXa, dXb, dsw2, dsb2, prec="plain_fp32")
+    h.sync_status()
+    assert _rel(dXa.double().cpu().numpy(), want_a) <= 1e-4
+    assert _rel(dXb.double().cpu().numpy(), want_b) <= 1e-4
+    assert abs(float(dsw2) - want_s) <= 1e-4 * abs(want_s)
+    assert abs(float(dsb2) - want_b2) <= 1e-4 * abs(want_b2)
