@@ -21,10 +21,13 @@
 // so the accumulator's rounding does not drift.
 //
 // Persistent kernel, one CTA per SM: warp 0 issues the TMA loads into a
-// 4-stage mbarrier ring, warp 1 owns TMEM (two 128 x 256 FP32 accumulators)
+// 3-stage mbarrier ring, warp 1 owns TMEM (two 128 x 256 FP32 accumulators)
 // and issues the MMAs, eight epilogue warps drain one accumulator (32 rows x
-// 128 columns a warp, 32 columns at a time) while the MMAs fill the other,
-// apply the scale and bias and store 16 bytes per lane per instruction.  The
+// 128 columns a warp, 32 columns at a time) while the MMAs fill the other.
+// A tcgen05.ld gives each lane 32 columns of its own row; the warp turns the
+// 32 x 32 block around in shared memory so that each store instruction
+// writes 128 contiguous bytes of one row (a lane-per-row store wrote 16
+// bytes into 32 different rows: eight times the L2 write requests).  The
 // output (4 MB per 32 x 32 image pair) makes it an HBM-write-bound kernel.
 // Every mbarrier wait is bounded; a timeout sets NK_DEV_TIMEOUT, skips the
 // remaining work, and the kernel still waits for its own copies and MMAs and
@@ -39,14 +42,17 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 3;
 constexpr int EPI_WARPS = 8, EPI_COLS = BN / 2;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t DRAIN_LIMIT = 1u << 26;
 
+constexpr int STG = 33;  // row stride of a warp's 32 x 32 staging tile (odd: no bank conflicts)
+
 struct SeedSmem {
   alignas(1024) __nv_bfloat16 A[STAGES][BM * BK];
   alignas(1024) __nv_bfloat16 B[STAGES][BN * BK];
+  float stage[EPI_WARPS][32 * STG];  // epilogue: 32 rows x 32 columns, transposed for row-contiguous stores
   uint64_t full[STAGES], empty[STAGES];
   uint64_t tfull[2], tempty[2];  // accumulators: MMA -> epilogue, epilogue -> MMA
   uint64_t done;
@@ -202,18 +208,20 @@ k_seed_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUte
       int64_t pr;
       int tm, tn;
       item_of(P, t, pr, tm, tn);
-      const int row = tm * BM + 32 * q + lane;
-      float* orow = P.out + (pr * P.HW + row) * (int64_t)P.HW + tn * BN + cbeg;
+      const int row0 = tm * BM + 32 * q;  // this warp's first row
+      float* obase = P.out + (pr * P.HW + row0) * (int64_t)P.HW + tn * BN + cbeg + lane;
       const uint32_t taddr = tbase + (uint32_t)(acc * BN + cbeg) + ((uint32_t)(32 * q) << 16);
+      float* stg = S.stage[warp - 2];
 #pragma unroll 1
       for (int c = 0; c < EPI_COLS / 32; ++c) {
         float v[32];
         tc::tmem_ld32(taddr + (uint32_t)(32 * c), v);
 #pragma unroll
-        for (int e = 0; e < 32; e += 4)
-          *reinterpret_cast<float4*>(orow + 32 * c + e) =
-              make_float4(fmaf(P.scale, v[e], P.bias), fmaf(P.scale, v[e + 1], P.bias),
-                          fmaf(P.scale, v[e + 2], P.bias), fmaf(P.scale, v[e + 3], P.bias));
+        for (int e = 0; e < 32; ++e) stg[lane * STG + e] = fmaf(P.scale, v[e], P.bias);
+        __syncwarp();
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) obase[(int64_t)r * P.HW + 32 * c] = stg[r * STG + lane];
+        __syncwarp();
       }
       // this accumulator is free for the item after next
       tc::tc_fence_before();
