@@ -341,6 +341,17 @@ nk_status nk_block_queue(nk_handle* h, const nk_arch* arch, const nk_params* prm
  *   polls < 0: the defaults. */
 nk_status nk_set_wait_limit(nk_handle* h, int64_t polls);
 
+/* Warm start of later nk_pcg_solve calls on this handle (on != 0): A holds
+ * the initial iterate on entry instead of being overwritten with zero, so a
+ * solve can resume from a saved iterate (Section 2: the block-wise pipeline
+ * is preemption-safe; CG's iterate is usable at any point).  MIXED refines
+ * it (its first sweep forms the true residual of the given A); the plain
+ * precisions solve one correction (K + lambda I) D = Y - (K + lambda I) A to
+ * the relative tolerance that brings every column to tol, then A += D.  The
+ * Krylov space of the interrupted solve is not kept, only its iterate.
+ * Default off; NK_OK. */
+nk_status nk_pcg_set_warm_start(nk_handle* h, int on);
+
 /* Rank of the partial pivoted Cholesky preconditioner (NK_PRECOND_PIVCHOL)
  * used by later nk_pcg_solve calls on this handle (default 100; at most N is
  * used).  rank in 1..1024, else NK_ERR_INVALID_ARG. */
@@ -357,7 +368,8 @@ nk_status nk_pcg_set_rank(nk_handle* h, int rank);
  *   device reads directly (cudaHostAlloc / cudaHostRegister; on a Grace
  *   system over the chip-to-chip link): the solve is then out of core, for
  *   kernels larger than HBM), Y [N][R] float64 (device, row
- *   major), A [N][R] float64 (device, out).
+ *   major), A [N][R] float64 (device, out; in and out after
+ *   nk_pcg_set_warm_start(h, 1)).
  *   prec = NK_PREC_MIXED: iterative refinement: the true residual
  *          Y - (K + lambda I) A is formed in double-FP32 arithmetic (exact
  *          FP32 products and two-float sums, about 2^-48 relative per step),

@@ -27,7 +27,7 @@ PRECOND = {"none": 0, "jacobi": 1, "pivchol": 2}
 EXPORTS = ["nk_create", "nk_destroy", "nk_status_string", "nk_last_error", "nk_sync_status",
            "nk_q_size", "nk_launch_count", "nk_last_lambda", "nk_self_diag", "nk_block", "nk_block_backward", "nk_fc_block",
            "nk_autotune",
-           "nk_autotune_set", "nk_block_fused_noalloc", "nk_block_queue", "nk_block_ntk", "nk_set_wait_limit", "nk_pcg_set_rank",
+           "nk_autotune_set", "nk_block_fused_noalloc", "nk_block_queue", "nk_block_ntk", "nk_set_wait_limit", "nk_pcg_set_rank", "nk_pcg_set_warm_start",
            "nk_pcg_solve", "nk_probe"]
 PROBE = {"fp32_fma": 0, "fp64_fma": 1, "l2_read": 2, "hbm_read": 3}
 
@@ -120,6 +120,8 @@ def lib():
     L.nk_set_wait_limit.restype = c_int
     L.nk_pcg_set_rank.argtypes = [c_void_p, c_int]
     L.nk_pcg_set_rank.restype = c_int
+    L.nk_pcg_set_warm_start.argtypes = [c_void_p, c_int]
+    L.nk_pcg_set_warm_start.restype = c_int
     L.nk_pcg_solve.argtypes = [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_int, c_double, c_int,
                                c_int, c_double, c_int, c_int, c_void_p, POINTER(c_int),
                                c_void_p, c_void_p]

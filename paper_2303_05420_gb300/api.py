@@ -221,6 +221,10 @@ class Handle:
         """Rank of the pivoted Cholesky preconditioner (precond="pivchol")."""
         self.check(lib().nk_pcg_set_rank(self._h, int(rank)), "nk_pcg_set_rank")
 
+    def pcg_set_warm_start(self, on: bool):
+        """Later pcg_solve calls start from the A they are given (resume)."""
+        self.check(lib().nk_pcg_set_warm_start(self._h, int(bool(on))), "nk_pcg_set_warm_start")
+
     def pcg_solve(self, K: torch.Tensor, Y: torch.Tensor, lam: float, precond: str = "jacobi",
                   prec: str = "mixed", tol: float = 1e-6, maxit: int = 10000, refine_max: int = 16,
                   A: Optional[torch.Tensor] = None, allow_not_converged: bool = False):

@@ -717,6 +717,12 @@ nk_status nk_set_wait_limit(nk_handle* h, int64_t polls) {
   return NK_OK;
 }
 
+nk_status nk_pcg_set_warm_start(nk_handle* h, int on) {
+  if (!h) return NK_ERR_INVALID_ARG;
+  h->pcg_warm = on != 0;
+  return NK_OK;
+}
+
 nk_status nk_pcg_set_rank(nk_handle* h, int rank) {
   if (!h) return NK_ERR_INVALID_ARG;
   if (rank < 1 || rank > 1024) return nk_fail(h, NK_ERR_INVALID_ARG, "nk_pcg_set_rank: rank outside 1..1024");

@@ -58,6 +58,7 @@ struct nk_handle {
   void* pcg_ws;
   size_t pcg_bytes;
   int pcg_rank;            // pivoted Cholesky preconditioner rank
+  int pcg_warm;            // nk_pcg_solve starts from the caller's A (nk_pcg_set_warm_start)
   long long wait_polls;    // bound of device waits (nk_set_wait_limit); < 0: defaults
 };
 

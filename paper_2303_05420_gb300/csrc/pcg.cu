@@ -1152,17 +1152,22 @@ nk_status nk_pcg_impl(nk_handle* h, const float* K, int64_t ldk, int64_t N, cons
     if (e != cudaSuccess) return finish(nk_cuda_check(h, e, "pcg preconditioner"));
   }
   const bool f64 = prec == NK_PREC_PLAIN_FP64;
-  double* Xc = prec == NK_PREC_MIXED ? D : A;
+  const bool warm = h->pcg_warm != 0;
+  // CG iterates into the correction D when it refines the caller's or its
+  // own earlier A (the captured iteration block writes one fixed array)
+  double* Xc = (prec == NK_PREC_MIXED || warm) ? D : A;
   int64_t per_block = 0;
   graph = f64 ? capture_block<true>(c, Xc, NK_CHECK_EVERY, &per_block)
               : capture_block<false>(c, Xc, NK_CHECK_EVERY, &per_block);
   bool converged = false;
   int total_it = 0;
   if (prec == NK_PREC_MIXED) {
-    ++h->launches;
-    k_zero<<<(unsigned)std::min<int64_t>((NR + 255) / 256, 4 * c.sm), 256, 0, st>>>(A, NR);
+    if (!warm) {
+      ++h->launches;
+      k_zero<<<(unsigned)std::min<int64_t>((NR + 255) / 256, 4 * c.sm), 256, 0, st>>>(A, NR);
+    }
     for (int outer = 0;; ++outer) {
-      if (outer == 0) {
+      if (outer == 0 && !warm) {
         // A = 0: the residual is Y itself
         h->launches += 3;
         k_zero<<<1, 256, 0, st>>>(c.sc, (int64_t)SC_N * R);
@@ -1188,6 +1193,25 @@ nk_status nk_pcg_impl(nk_handle* h, const float* K, int64_t ldk, int64_t N, cons
       ++h->launches;
       k_add<<<(unsigned)std::min<int64_t>((NR + 255) / 256, 4 * c.sm), 256, 0, st>>>(NR, A, D);
     }
+  } else if (warm) {
+    // from the caller's A: one correction solve (K + lam I) D = Y - (K + lam I) A
+    // to the relative tolerance that brings every column's residual to tol
+    e = true_residual(c, Y, A, c.B2, f64);
+    if (e == cudaSuccess) e = read_sc();
+    const double worst = e == cudaSuccess ? worst_rel() : 0.0;
+    if (e == cudaSuccess && worst > tol) {
+      const double eta = tol / worst;
+      e = f64 ? cg_run<true>(c, c.B2, D, eta, maxit, graph, per_block, hflag, &total_it)
+              : cg_run<false>(c, c.B2, D, eta, maxit, graph, per_block, hflag, &total_it);
+      if (e == cudaSuccess) {
+        ++h->launches;
+        k_add<<<(unsigned)std::min<int64_t>((NR + 255) / 256, 4 * c.sm), 256, 0, st>>>(NR, A, D);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = true_residual(c, Y, A, c.B2, f64);
+      if (e == cudaSuccess) e = read_sc();
+    }
+    if (e == cudaSuccess) converged = worst_rel() <= tol;
   } else {
     e = f64 ? cg_run<true>(c, Y, A, tol, maxit, graph, per_block, hflag, &total_it)
             : cg_run<false>(c, Y, A, tol, maxit, graph, per_block, hflag, &total_it);

@@ -27,7 +27,7 @@ int main(void) {
       (const void*)&nk_launch_count,   (const void*)&nk_last_lambda,      (const void*)&nk_self_diag,
       (const void*)&nk_block,          (const void*)&nk_block_backward,   (const void*)&nk_fc_block,
       (const void*)&nk_autotune,       (const void*)&nk_autotune_set,     (const void*)&nk_block_fused_noalloc,
-      (const void*)&nk_block_ntk,      (const void*)&nk_block_queue,      (const void*)&nk_pcg_set_rank,
+      (const void*)&nk_block_ntk,      (const void*)&nk_block_queue,      (const void*)&nk_pcg_set_rank, (const void*)&nk_pcg_set_warm_start,
       (const void*)&nk_set_wait_limit, (const void*)&nk_probe,
       (const void*)&nk_pcg_solve,
   };
