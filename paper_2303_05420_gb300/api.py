@@ -298,14 +298,20 @@ class NNGPBlock(torch.autograd.Function):
         fp64 = ctx.bprec == "plain_fp64"
         dt = torch.float64 if fp64 else torch.float32
         dK = dK.to(dt).contiguous()
-        dXa = torch.zeros(Xa.shape, dtype=dt, device=Xa.device)
-        dXb = dXa if ctx.sym else torch.zeros(Xb.shape, dtype=dt, device=Xb.device)
+        # image gradients only where autograd wants them (nk_block_backward
+        # skips the input contraction for a NULL dX; the self-variance adjoint
+        # still runs for both sets, since q depends on sigma_w^2 and sigma_b^2)
+        need_a, need_b = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if ctx.sym:
+            need_a = need_b = need_a or need_b
+        dXa = torch.zeros(Xa.shape, dtype=dt, device=Xa.device) if need_a else None
+        dXb = dXa if ctx.sym else (torch.zeros(Xb.shape, dtype=dt, device=Xb.device) if need_b else None)
         dsw2 = torch.zeros(1, dtype=torch.float64, device=Xa.device)
         dsb2 = torch.zeros(1, dtype=torch.float64, device=Xa.device)
         ctx.h.block_backward(Xa, (qda, qsa), Xb, (qdb, qsb), ctx.convs, ctx.sw2, ctx.sb2, dK, dXa, dXb,
                              dsw2, dsb2, prec=ctx.bprec, symmetric=ctx.sym)
-        gXa = dXa.to(Xa.dtype)
-        gXb = None if ctx.sym else dXb.to(Xb.dtype)
+        gXa = dXa.to(Xa.dtype) if need_a else None
+        gXb = None if (ctx.sym or not need_b) else dXb.to(Xb.dtype)
         return gXa, gXb, dsw2.reshape(()), dsb2.reshape(()), None, None, None, None, None
 
 

@@ -688,6 +688,96 @@ __global__ void k_seed_adj_b(const T* __restrict__ d0, const float* __restrict__
   }
 }
 
+// FP32 input adjoints for C <= 3 with the pair's other image staged in shared
+// memory as float4 (one broadcast or consecutive LDS.128 per element instead
+// of C scalar loads).  Image b, one thread per column p' of a 256-column
+// slab, eight rows' loads in flight:
+//   dXb[j][p'][c] += (1/C) sum_p dK0(p,p') xa[p][c];
+// image a, one warp per row p of an 8-row group:
+//   dXa[i][p][c] += (1/C) sum_p' dK0(p,p') xb[p'][c].
+__device__ __forceinline__ void stage_image4(const float* __restrict__ x, int HW, int C, float4* s) {
+  for (int p = threadIdx.x; p < HW; p += blockDim.x) {
+    const float* v = x + (int64_t)p * C;
+    s[p] = make_float4(v[0], C > 1 ? v[1] : 0.f, C > 2 ? v[2] : 0.f, 0.f);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_seed_adj_b4(const float* __restrict__ d0, const float* __restrict__ Xa,
+                                                     int64_t np, int HW, int C, int64_t na, int64_t nb, int sym,
+                                                     int64_t pair0, int64_t a0, int64_t b0, float* __restrict__ dXb) {
+  extern __shared__ float4 xs4[];
+  const int pp = blockIdx.x * 256 + threadIdx.x;
+  for (int64_t pr = blockIdx.y; pr < np; pr += gridDim.y) {
+    int64_t i, j;
+    pair_of(pair0 + pr, na, nb, sym, &i, &j);
+    __syncthreads();  // the previous pair's image is no longer read
+    stage_image4(Xa + (a0 + i) * (int64_t)HW * C, HW, C, xs4);
+    __syncthreads();
+    const float* col = d0 + pr * (int64_t)HW * HW + pp;
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    for (int p = 0; p < HW; p += 8) {
+      float g[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) g[u] = __ldcs(col + (int64_t)(p + u) * HW);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float4 x = xs4[p + u];
+        ax = fmaf(g[u], x.x, ax);
+        ay = fmaf(g[u], x.y, ay);
+        az = fmaf(g[u], x.z, az);
+      }
+    }
+    float* o = dXb + ((b0 + j) * (int64_t)HW + pp) * C;
+    const float ic = 1.f / (float)C;
+    atomicAdd(o, ax * ic);
+    if (C > 1) atomicAdd(o + 1, ay * ic);
+    if (C > 2) atomicAdd(o + 2, az * ic);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_seed_adj_a4(const float* __restrict__ d0, const float* __restrict__ Xb,
+                                                     int64_t np, int HW, int C, int64_t na, int64_t nb, int sym,
+                                                     int64_t pair0, int64_t a0, int64_t b0, float* __restrict__ dXa) {
+  extern __shared__ float4 xs4[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t pr = blockIdx.y; pr < np; pr += gridDim.y) {
+    int64_t i, j;
+    pair_of(pair0 + pr, na, nb, sym, &i, &j);
+    __syncthreads();
+    stage_image4(Xb + (b0 + j) * (int64_t)HW * C, HW, C, xs4);
+    __syncthreads();
+    for (int p = blockIdx.x * 8 + warp; p < HW; p += gridDim.x * 8) {
+      const float* row = d0 + (pr * (int64_t)HW + p) * HW;
+      float ax = 0.f, ay = 0.f, az = 0.f;
+      for (int k = lane; k < HW; k += 128) {
+        float g[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) g[u] = __ldcs(row + k + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float4 x = xs4[k + 32 * u];
+          ax = fmaf(g[u], x.x, ax);
+          ay = fmaf(g[u], x.y, ay);
+          az = fmaf(g[u], x.z, az);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        az += __shfl_xor_sync(0xffffffffu, az, o);
+      }
+      if (lane == 0) {
+        float* out = dXa + ((a0 + i) * (int64_t)HW + p) * C;
+        const float ic = 1.f / (float)C;
+        atomicAdd(out, ax * ic);
+        if (C > 1) atomicAdd(out + 1, ay * ic);
+        if (C > 2) atomicAdd(out + 2, az * ic);
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Adjoint of the banded self recursion that produces q_l(p) (FP64).
 // One CTA per image.  Forward: the offset planes of every layer (as in
@@ -1231,16 +1321,38 @@ cudaError_t run_backward(const NkGeom& g, double sw2, double sb2, const float* X
     }
     // gcur: gradient of the input covariance K_0
     const int HW0 = g.Hs[0] * g.Ws[0];
+    T* dXb_eff = sym ? dXa : dXb;
+    // FP32, C <= 3, whole 256-column slabs: the staged float4 forms
+    const bool staged = sizeof(T) == 4 && g.C <= 3 && HW0 % 256 == 0;
+    const size_t xs_bytes = (size_t)HW0 * sizeof(float4);
+    const unsigned pair_grid_y = (unsigned)std::min<int64_t>(np, 65535);
     if (dXa) {
       ++*launches;
-      k_seed_adj_a<T><<<grid_for((int64_t)np * HW0 * 32), 256, 0, st>>>(gcur, Xb, np, HW0, g.C, na, nb, sym, pair0,
-                                                                        a0, b0, dXa);
+      if constexpr (sizeof(T) == 4) {
+        if (staged) {
+          if (xs_bytes > 48 * 1024)
+            cudaFuncSetAttribute(k_seed_adj_a4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs_bytes);
+          k_seed_adj_a4<<<dim3((unsigned)(HW0 / 8 < 32 ? HW0 / 8 : 32), pair_grid_y), 256, xs_bytes, st>>>(
+              gcur, Xb, np, HW0, g.C, na, nb, sym, pair0, a0, b0, dXa);
+        }
+      }
+      if (!staged)
+        k_seed_adj_a<T><<<grid_for((int64_t)np * HW0 * 32), 256, 0, st>>>(gcur, Xb, np, HW0, g.C, na, nb, sym,
+                                                                          pair0, a0, b0, dXa);
     }
-    T* dXb_eff = sym ? dXa : dXb;
     if (dXb_eff) {
       ++*launches;
-      k_seed_adj_b<T><<<grid_for((int64_t)np * HW0), 256, 0, st>>>(gcur, Xa, np, HW0, g.C, na, nb, sym, pair0, a0,
-                                                                   b0, dXb_eff);
+      if constexpr (sizeof(T) == 4) {
+        if (staged) {
+          if (xs_bytes > 48 * 1024)
+            cudaFuncSetAttribute(k_seed_adj_b4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs_bytes);
+          k_seed_adj_b4<<<dim3((unsigned)(HW0 / 256), pair_grid_y), 256, xs_bytes, st>>>(
+              gcur, Xa, np, HW0, g.C, na, nb, sym, pair0, a0, b0, dXb_eff);
+        }
+      }
+      if (!staged)
+        k_seed_adj_b<T><<<grid_for((int64_t)np * HW0), 256, 0, st>>>(gcur, Xa, np, HW0, g.C, na, nb, sym, pair0,
+                                                                     a0, b0, dXb_eff);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
