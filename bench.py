@@ -548,7 +548,7 @@ def pcg_l2_roofline(n: int, iters: float, seconds: float) -> dict:
                     "iteration is latency-bound at this size (four dependent launches)"}
 
 
-def adjoint_layerwise_bytes(convs, hw: int, esize: int = 4) -> int:
+def adjoint_layerwise_bytes(convs, hw: int, esize: int = 4, input_sides: int = 2) -> int:
     """Bytes the layer-fused adjoint (nk_block_backward, FP32) moves through
     HBM per image pair (E_s = (hw / 2^s)^4 elements at stage s).  Forward:
     the first layer writes its pre-activation (the input covariance is formed
@@ -559,7 +559,8 @@ def adjoint_layerwise_bytes(convs, hw: int, esize: int = 4) -> int:
     constant, the next stage's tensor through the pool adjoint, else this
     stage's) and the outgoing gradient, plus the q-term partial sums (two
     H^2 W buffers written and read); the input adjoints read the last
-    gradient twice.  Stage patterns without empty middle stages."""
+    gradient once per image set that needs a gradient (input_sides, 2 or 1).
+    Stage patterns without empty middle stages."""
     last = max(s for s, n in enumerate(convs) if n > 0)
     E = [(hw >> s) ** 4 for s in range(last + 1)]
     Wd = [hw >> s for s in range(last + 1)]
@@ -582,15 +583,18 @@ def adjoint_layerwise_bytes(convs, hw: int, esize: int = 4) -> int:
                 tot += E[s + 1]
             else:
                 tot += E[s]
-    tot += 2 * E[0]
+    tot += input_sides * E[0]
     return esize * tot
 
 
-def adjoint_roofline(seconds: float, n_pairs: int, peaks: dict, convs=(3, 3, 3), hw: int = 32) -> dict:
+def adjoint_roofline(seconds: float, pairs_two: int, pairs_one: int, peaks: dict, convs=(3, 3, 3),
+                     hw: int = 32) -> dict:
     """Achieved HBM bandwidth of the layer-wise adjoint under the traffic
-    model above, against the measured copy bandwidth."""
+    model above (pairs_two pairs with both input gradients, pairs_one with
+    one), against the measured copy bandwidth."""
     per_pair = adjoint_layerwise_bytes(convs, hw)
-    gbs = per_pair * n_pairs / seconds / 1e9
+    tot = per_pair * pairs_two + adjoint_layerwise_bytes(convs, hw, input_sides=1) * pairs_one
+    gbs = tot / seconds / 1e9
     peak = float(peaks.get("hbm_gbs", 6800.0))
     return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
             "bytes_per_pair": per_pair, "traffic": None,
@@ -654,7 +658,8 @@ def grad_leg(h, dev, n_sup=100, n_tgt=2048):
             f"grad_myrtle10_{n_sup}x{n_tgt}_s": dt, "grad_entries_per_s": entries / dt,
             "grad_forward_s": t_fwd, "grad_backward_s": t_bwd,
             "grad_backward_entries_per_s": entries / t_bwd,
-            "grad_adjoint_hbm": adjoint_roofline(t_bwd, entries, load_peaks()),
+            # K_ss: both input gradients (one image set); K_ts: the support side only
+            "grad_adjoint_hbm": adjoint_roofline(t_bwd, n_sup * (n_sup + 1) // 2, n_tgt * n_sup, load_peaks()),
             "grad_loss": L, "grad_dsw2": gs, "grad_dsb2": gb}
 
 

@@ -116,9 +116,14 @@ def test_adjoint_traffic_model():
     # a single-stage net: input covariance write, readout read, one reverse
     # pass (constant gradient) with its partials, two input adjoints
     assert bench.adjoint_layerwise_bytes((1,), 8) == 4 * ((1 + 1 + 2 + 2) * 8 ** 4 + 4 * 8 ** 4 // 8)
-    r = bench.adjoint_roofline(2.0, 1000, {"hbm_gbs": 5000.0})
+    # one image set without a gradient: one read of the input-covariance
+    # gradient instead of two
+    b1 = bench.adjoint_layerwise_bytes((3, 3, 3), 32, input_sides=1)
+    assert b - b1 == 4 * E0
+    r = bench.adjoint_roofline(2.0, 1000, 300, {"hbm_gbs": 5000.0})
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
-    assert abs(r["achieved"] - b * 1000 / 2.0 / 1e9) < 1e-9 and abs(r["frac"] - r["achieved"] / 5000.0) < 1e-12
+    assert abs(r["achieved"] - (b * 1000 + b1 * 300) / 2.0 / 1e9) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 5000.0) < 1e-12
 
 
 def test_cpu_baseline_line():
