@@ -1171,7 +1171,6 @@ cudaError_t run_backward(const NkGeom& g, double sw2, double sb2, const float* X
     const int64_t HW0 = (int64_t)g.Hs[0] * g.Ws[0];
     patch_a = take(nk_seed_patch_bytes(na, g.Hs[0], g.Ws[0]));
     patch_b = sym ? patch_a : take(nk_seed_patch_bytes(nb, g.Hs[0], g.Ws[0]));
-    (void)HW0;
     *launches += sym ? 1 : 2;
     e = nk_seed_patches(Xa + a0 * HW0 * g.C, na, g.Hs[0], g.Ws[0], g.C, patch_a, st);
     if (e == cudaSuccess && !sym) e = nk_seed_patches(Xb + b0 * HW0 * g.C, nb, g.Hs[0], g.Ws[0], g.C, patch_b, st);
