@@ -108,3 +108,31 @@ def test_fused_ntk_refusals(h):
         with pytest.raises(NkError) as ei:
             h.block_ntk(X, q, X, q, convs, 2.0, 0.0, prec="mixed")
         assert ei.value.status == NK_ERR_UNSUPPORTED
+
+
+def test_fused_ntk_bench_block_sampled(h):
+    """The bench's fused-NTK workload at full size (a symmetric block of 256
+    32x32 images, 32,896 pairs: the slot ring turns over about 200 times):
+    entries from the start, the middle and the end of the item order and a
+    random sample, each against the oracle's NTK pair; K and Theta of the
+    whole block exactly symmetric."""
+    x = nkdata.standardise(nkdata.images(256, 32, 3, nkdata.SEED_TRAIN, blur=True))[0].astype(np.float32)
+    X = torch.tensor(x, device="cuda")
+    q = h.self_diag(X, CONVS, 2.0, 0.0)
+    K, T = h.block_ntk(X, q, X, q, CONVS, 2.0, 0.0, prec="mixed", symmetric=True)
+    h.sync_status()
+    K, T = K.double().cpu().numpy(), T.double().cpu().numpy()
+    assert np.array_equal(K, K.T) and np.array_equal(T, T.T)
+    rng = np.random.default_rng(12)
+    pairs = [(0, 0), (0, 1), (0, 255), (1, 1), (127, 128), (128, 200), (254, 255), (255, 255)]
+    pairs += [tuple(sorted(p)) for p in rng.integers(0, 256, size=(8, 2))]
+    arch = oracle.Arch(CONVS)
+    x64 = torch.tensor(x.astype(np.float64))
+    qx = {}
+    for i, j in pairs:
+        for k in (i, j):
+            if k not in qx:
+                qx[k] = oracle.myrtle_self_q(arch, 2.0, 0.0, x64[k])
+        kw, tw = oracle.myrtle_ntk_pair(arch, 2.0, 0.0, x64[i], x64[j], qx[i], qx[j])
+        assert abs(K[i, j] - float(kw)) <= 1e-5 * abs(float(kw)), (i, j)
+        assert abs(T[i, j] - float(tw)) <= 1e-5 * abs(float(tw)), (i, j)
