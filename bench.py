@@ -176,6 +176,34 @@ def load_peaks() -> dict:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
+TRAFFIC_HEADLINE = os.path.join(ROOT, "profiles", "k_myrtle_tiled_traffic_headline.json")
+
+
+def headline_traffic(config_name: str, variant: int):
+    """DRAM bytes of the tiled kernel's two launches of a headline step, from
+    the ncu capture recorded in profiles/ (dram__bytes_read + write), while
+    the kernel's source files hash as they did at the capture; None
+    otherwise (another kernel, another workload, or changed sources)."""
+    import hashlib
+
+    if variant != 3 or config_name != "headline":
+        return None, "no capture of this kernel and workload"
+    try:
+        with open(TRAFFIC_HEADLINE) as f:
+            rec = json.load(f)
+        h = hashlib.sha256()
+        for rel in rec["sources"]:
+            with open(os.path.join(ROOT, rel), "rb") as g:
+                h.update(g.read())
+        if h.hexdigest() != rec["sources_sha256"]:
+            return None, "the kernel's sources changed since the capture"
+        return float(rec["bytes_per_step"]), ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the step's two "
+                                              "launches (profiles/k_myrtle_tiled_traffic_headline.json); the kernel "
+                                              "is ALU-bound, this is about 9 GB/s of DRAM traffic")
+    except Exception as e:
+        return None, f"no traffic record ({type(e).__name__})"
+
+
 def load_probe() -> dict:
     """Rates measured by `bench.py --probe-peaks` on this GPU type (nk_probe),
     stored per SM and cycle so that they scale with the clock a run saw."""
@@ -382,6 +410,7 @@ def run_ours(args, rank, world, dist):
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     run_clock = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
     peak_tops, peak_source = fp32_peak(sm_count, run_clock)
+    traffic, traffic_src = headline_traffic(args.config, variant)
 
     # ---- plain layer-wise forms on sample tiles, at equal accuracy
     extra = {}
@@ -514,7 +543,7 @@ def run_ours(args, rank, world, dist):
         "kernel_only_entries_per_s": entries / blk_s,
         "fused_variant": variant,
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "TFLOP/s",
-                     "frac": achieved_tops / peak_tops, "traffic": None,
+                     "frac": achieved_tops / peak_tops, "traffic": traffic, "traffic_source": traffic_src,
                      "kernel": "k_myrtle_tiled" if variant == 3 else "k_myrtle_fused",
                      "peak_source": peak_source, "ops_per_entry": ops_entry},
         "e2e": {"value": e2e_val, "unit": "entries/s",
@@ -834,8 +863,20 @@ def cv8_leg(h, dev):
     t = ev[0].elapsed_time(ev[1]) / 1e3
     tp = ev[2].elapsed_time(ev[3]) / 1e3
     entries = 2048 * 2049 // 2 + 512 * 2048
+    # FP32 operations of the diagonal recursion per entry: per pixel and layer
+    # the vertical and horizontal 3-tap sums (4 adds), the scale and bias (1),
+    # the factor products and the scaled map output (2 + 3) and the map
+    # (J01: a degree-5 polynomial, a square root and the combine, about 10),
+    # plus C = 3 contraction FMAs per pixel; the same count as DESIGN's
+    # H W (8 + 9 + 12) per layer, rounded to 29 + 3 C / L
+    ops = 32 * 32 * (8 * 29 + 3)
+    props = torch.cuda.get_device_properties(dev)
+    peak, src = fp32_peak(props.multi_processor_count, 2070.0)
+    achieved = ops * entries / t / 1e12
     return {"cv8_workload": "cv8_relu_32x32_train2048_test512_flatten_mixed_diagonal",
             "cv8_entries_per_s": entries / t, "cv8_blocks_ms": 1e3 * t,
+            "cv8_roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak, "ops_per_entry": ops, "peak_source": src},
             "cv8_plain_fp32_entries_per_s": 256 / tp,
             "cv8_maxrel_mixed_vs_plain_fp32": float(((Ktr[:16, 16:32] - Kp).abs() / Kp.abs()).max())}
 

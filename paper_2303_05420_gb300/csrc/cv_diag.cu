@@ -14,12 +14,17 @@
 // (nk_self_diag's tables) of both images at the same pixel.  That is H W
 // values per pair and layer instead of (H W)^2.
 //
-// One warp per pair: lane = image column, the rows of the column in
-// registers.  The vertical taps of the 3x3 box are register neighbours, the
-// horizontal taps two shuffles; the per-pixel tables are read row by row
-// (each row a coalesced 256-byte load per image).  FP32 recursion, the final
-// mean summed in FP64.  Consecutive warps take consecutive pairs, so the warps
-// of a CTA mostly share the image of side a in L1.
+// One warp per pair: lane = image column.  The warp's H x 32 diagonal tile
+// lives in shared memory (4 KB at H = 32) and every layer sweeps it row by
+// row in a rolled loop: the vertical taps are the previous row (carried in a
+// register, the value the row had before this layer) and the next row (read
+// from the tile), the horizontal taps two shuffles, then the map with the
+// per-pixel factors of both images (a coalesced 256-byte load per image and
+// row) overwrites the row.  Few registers and a small loop body keep many
+// warps resident to hide the factor loads (holding the column in unrolled
+// register arrays took 255 registers and one CTA per SM).  FP32 recursion,
+// the final mean summed in FP64.  Consecutive warps take consecutive pairs,
+// so the warps of a CTA mostly share the image of side a in L1.
 #include "myrtle_plain.cuh"
 
 namespace {
@@ -47,33 +52,20 @@ struct CvParams {
 };
 
 template <int H>
-__device__ __forceinline__ void box3(const float (&v)[H], float (&k)[H], int lane, int W, float a, float b) {
-  float s[H];
-#pragma unroll
-  for (int r = 0; r < H; ++r) s[r] = v[r] + (r > 0 ? v[r - 1] : 0.f) + (r + 1 < H ? v[r + 1] : 0.f);
-#pragma unroll
-  for (int r = 0; r < H; ++r) {
-    const float up = __shfl_up_sync(0xffffffffu, s[r], 1);
-    const float dn = __shfl_down_sync(0xffffffffu, s[r], 1);
-    const float h = s[r] + (lane > 0 ? up : 0.f) + (lane + 1 < W ? dn : 0.f);
-    k[r] = fmaf(a, h, b);
-  }
-}
-
-template <int H>
 __global__ void __launch_bounds__(32 * CV_WARPS) k_cv_diag(const __grid_constant__ CvParams P) {
-  const int lane = threadIdx.x & 31;
+  __shared__ float tile[CV_WARPS][H][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool col = lane < P.W;
+  float (&v)[H][32] = tile[warp];
   const int64_t nw = (int64_t)gridDim.x * CV_WARPS;
-  for (int64_t pr = (int64_t)blockIdx.x * CV_WARPS + (threadIdx.x >> 5); pr < P.npairs; pr += nw) {
+  for (int64_t pr = (int64_t)blockIdx.x * CV_WARPS + warp; pr < P.npairs; pr += nw) {
     int64_t i, j;
     nkp::pair_of(pr, P.na, P.nb, P.sym, &i, &j);
     const int64_t ia = P.a0 + i, ib = P.b0 + j;
     const float* xa = P.Xa + ia * (int64_t)H * P.W * P.C;
     const float* xb = P.Xb + ib * (int64_t)H * P.W * P.C;
     // channel contraction at every pixel of the column
-    float v[H], k[H];
-#pragma unroll
+#pragma unroll 4
     for (int r = 0; r < H; ++r) {
       float u = 0.f;
       if (col) {
@@ -81,20 +73,33 @@ __global__ void __launch_bounds__(32 * CV_WARPS) k_cv_diag(const __grid_constant
         const float* pb = xb + ((int64_t)r * P.W + lane) * P.C;
         for (int c = 0; c < P.C; ++c) u = fmaf(pa[c], pb[c], u);
       }
-      v[r] = u;
+      v[r][lane] = u;
     }
+    __syncwarp();
     const float2* ta = P.qa + ia * (int64_t)P.nq;
     const float2* tb = P.qb + ib * (int64_t)P.nq;
     for (int l = 0; l < P.L; ++l) {
-      box3<H>(v, k, lane, P.W, l == 0 ? P.xscale : P.cscale, P.sb2);
-      const float2* la = ta + (int64_t)l * H * P.W;
-      const float2* lb = tb + (int64_t)l * H * P.W;
-#pragma unroll
+      const float a = l == 0 ? P.xscale : P.cscale;
+      const float2* la = ta + (int64_t)l * H * P.W + lane;
+      const float2* lb = tb + (int64_t)l * H * P.W + lane;
+      float prev = 0.f, cur = v[0][lane];
+      float2 fa = col ? la[0] : make_float2(0.f, 0.f), fb = col ? lb[0] : make_float2(0.f, 0.f);
+#pragma unroll 2
       for (int r = 0; r < H; ++r) {
+        const float next = r + 1 < H ? v[r + 1][lane] : 0.f;
+        // the factors of the next row are in flight while this row is mapped
+        float2 fa1 = fa, fb1 = fb;
+        if (col && r + 1 < H) {
+          fa1 = la[(r + 1) * P.W];
+          fb1 = lb[(r + 1) * P.W];
+        }
+        const float s = prev + cur + next;
+        const float up = __shfl_up_sync(0xffffffffu, s, 1);
+        const float dn = __shfl_down_sync(0xffffffffu, s, 1);
+        const float k = fmaf(a, s + (lane > 0 ? up : 0.f) + (lane + 1 < P.W ? dn : 0.f), P.sb2);
         float o = 0.f;
         if (col) {
-          const float2 fa = la[r * P.W + lane], fb = lb[r * P.W + lane];
-          const float c = k[r] * (fa.x * fb.x);
+          const float c = k * (fa.x * fb.x);
           float m;
           if (P.act == NK_ACT_ERF)
             m = nk_asin_f32(c);
@@ -102,12 +107,16 @@ __global__ void __launch_bounds__(32 * CV_WARPS) k_cv_diag(const __grid_constant
             m = (l == 0) ? nk_J_f32(c) : nk_J01_f32(c);  // after a ReLU layer every K_l >= 0
           o = (fa.y * fb.y) * P.fold * m;
         }
-        v[r] = o;
+        v[r][lane] = o;
+        prev = cur;
+        cur = next;
+        fa = fa1;
+        fb = fb1;
       }
+      __syncwarp();
     }
     double s = 0.0;
-#pragma unroll
-    for (int r = 0; r < H; ++r) s += (double)v[r];
+    for (int r = 0; r < H; ++r) s += (double)v[r][lane];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
@@ -115,6 +124,7 @@ __global__ void __launch_bounds__(32 * CV_WARPS) k_cv_diag(const __grid_constant
       P.K[i * P.ldk + j] = out;
       if (P.sym && i != j) P.K[j * P.ldk + i] = out;
     }
+    __syncwarp();
   }
 }
 
@@ -156,7 +166,7 @@ cudaError_t nk_launch_cv_diag(const NkGeom& g, double sw2, double sb2, const flo
   P.K = K;
   P.ldk = ldk;
   const int64_t want = (P.npairs + CV_WARPS - 1) / CV_WARPS;
-  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count * 16));
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count * 32));
   switch (g.Hs[0]) {
     case 8: k_cv_diag<8><<<grid, 32 * CV_WARPS, 0, st>>>(P); break;
     case 16: k_cv_diag<16><<<grid, 32 * CV_WARPS, 0, st>>>(P); break;

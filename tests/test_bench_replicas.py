@@ -133,3 +133,15 @@ def test_cpu_baseline_line():
     assert d["value"] == 160.0 and d["unit"] == "entries/s" and d["cores"] == 16 and d["kind"] == "oracle"
     assert d["per_core"] == 10.0 and abs(d["workload_extrapolated_s"] - 3146752 / 160.0) < 1e-9
     assert "320 Myrtle-5 32x32" in d["sample"] and "2.0 s" in d["sample"]
+
+
+def test_headline_traffic_record():
+    """The recorded DRAM traffic of the headline's tiled launches is reported
+    only for that kernel and workload, and only while the kernel's sources
+    hash as they did at the capture."""
+    import bench
+
+    v, note = bench.headline_traffic("headline", 3)
+    assert (v is None and "changed" in note) or (v > 0 and "ncu" in note)
+    assert bench.headline_traffic("small", 3)[0] is None
+    assert bench.headline_traffic("headline", 0)[0] is None
