@@ -416,7 +416,9 @@ def run_ours(args, rank, world, dist):
     extra = {}
     if not args.skip_plain:
         q = h.self_diag(X, CONVS, SW2, SB2)
-        tile = min(64, n_tr)
+        # rows [0, tile) against columns [tile, 2 tile): both inside the
+        # n_tr + n_te images (the small profiling configs have 80)
+        tile = min(64, n_tr, (n_tr + n_te) // 2)
         res = {}
         for prec, t in [("mixed", tile), ("plain_fp32", tile), ("plain_fp64", min(16, n_tr))]:
             out = torch.empty((t, t), dtype=torch.float64 if prec == "plain_fp64" else torch.float32,

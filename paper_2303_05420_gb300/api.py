@@ -25,6 +25,16 @@ def _stream() -> int:
     return torch.cuda.current_stream().cuda_stream
 
 
+def _ranges(Xa: torch.Tensor, Xb: torch.Tensor, a_range, b_range) -> Tuple[int, int, int, int]:
+    """Index ranges of a block, checked against the image tensors (the C ABI
+    takes plain pointers and cannot check them)."""
+    a0, a1 = a_range if a_range is not None else (0, Xa.shape[0])
+    b0, b1 = b_range if b_range is not None else (0, Xb.shape[0])
+    if not (0 <= a0 <= a1 <= Xa.shape[0] and 0 <= b0 <= b1 <= Xb.shape[0]):
+        raise ValueError(f"block ranges [{a0}, {a1}) x [{b0}, {b1}) outside {Xa.shape[0]} x {Xb.shape[0]} images")
+    return int(a0), int(a1), int(b0), int(b1)
+
+
 class Handle:
     """Owns an nk_handle (workspace, device status word)."""
 
@@ -108,8 +118,7 @@ class Handle:
         """K[i - a0, j - b0] = NNGP(Xa[i], Xb[j]) over the given index ranges."""
         assert Xa.is_cuda and Xb.is_cuda and Xa.dtype == torch.float32 and Xb.dtype == torch.float32
         _, H, W, C = Xa.shape
-        a0, a1 = a_range if a_range is not None else (0, Xa.shape[0])
-        b0, b1 = b_range if b_range is not None else (0, Xb.shape[0])
+        a0, a1, b0, b1 = _ranges(Xa, Xb, a_range, b_range)
         dt = torch.float64 if prec == "plain_fp64" else torch.float32
         if out is None:
             out = torch.empty((a1 - a0, b1 - b0), dtype=dt, device=Xa.device)
@@ -129,8 +138,7 @@ class Handle:
                   filt: int = 3, act: str = "relu"):
         """(K, Theta): NNGP and NTK blocks by the layer-wise forms (nk_block_ntk)."""
         _, H, W, C = Xa.shape
-        a0, a1 = a_range if a_range is not None else (0, Xa.shape[0])
-        b0, b1 = b_range if b_range is not None else (0, Xb.shape[0])
+        a0, a1, b0, b1 = _ranges(Xa, Xb, a_range, b_range)
         dt = torch.float64 if prec == "plain_fp64" else torch.float32
         K = torch.empty((a1 - a0, b1 - b0), dtype=dt, device=Xa.device)
         T = torch.empty_like(K)
@@ -160,8 +168,7 @@ class Handle:
             assert Xa.is_cuda and Xa.dtype == torch.float32 and Xb.dtype == torch.float32
             _, H, W, Ck = Xa.shape
             C = Ck if C is None else C
-            a0, a1 = t.get("a_range") or (0, Xa.shape[0])
-            b0, b1 = t.get("b_range") or (0, Xb.shape[0])
+            a0, a1, b0, b1 = _ranges(Xa, Xb, t.get("a_range"), t.get("b_range"))
             out = t.get("out")
             if out is None:
                 out = torch.empty((a1 - a0, b1 - b0), dtype=torch.float32, device=Xa.device)
@@ -182,8 +189,7 @@ class Handle:
         """FC NNGP block (tensor-core Gram + fused arc-cosine recursion)."""
         assert Xa.dtype == torch.float32 and Xa.is_contiguous() and Xb.is_contiguous()
         d = Xa.shape[1]
-        a0, a1 = a_range if a_range is not None else (0, Xa.shape[0])
-        b0, b1 = b_range if b_range is not None else (0, Xb.shape[0])
+        a0, a1, b0, b1 = _ranges(Xa, Xb, a_range, b_range)
         if out is None:
             out = torch.empty((a1 - a0, b1 - b0), dtype=torch.float32, device=Xa.device)
         p = make_params(sw2, sb2)
@@ -200,8 +206,7 @@ class Handle:
         into dXa, dXb (image-shaped, may be None), dsw2, dsb2 (1-element
         float64 CUDA tensors)."""
         _, H, W, C = Xa.shape
-        a0, a1 = a_range if a_range is not None else (0, Xa.shape[0])
-        b0, b1 = b_range if b_range is not None else (0, Xb.shape[0])
+        a0, a1, b0, b1 = _ranges(Xa, Xb, a_range, b_range)
         a = make_arch(convs, filt, act)
         p = make_params(sw2, sb2)
         assert dK.stride(1) == 1
