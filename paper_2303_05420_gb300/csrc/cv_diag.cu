@@ -51,11 +51,49 @@ struct CvParams {
   int64_t ldk;
 };
 
-template <int H>
-__global__ void __launch_bounds__(32 * CV_WARPS) k_cv_diag(const __grid_constant__ CvParams P) {
+// One layer's sweep over the warp's tile: v <- map(a box3(v) + b) row by row.
+// FIRST: the first layer (its correlations may be negative; the later ones,
+// after a ReLU, are not).  FULL: all 32 lanes are image columns.
+template <int H, int ACT, bool FIRST, bool FULL>
+__device__ __forceinline__ void cv_layer(const CvParams& P, float (&v)[H][32], const float2* la, const float2* lb,
+                                         int lane, float a) {
+  const bool col = FULL || lane < P.W;
+  const bool hasr = FULL ? lane < 31 : lane + 1 < P.W;
+  float prev = 0.f, cur = v[0][lane];
+  float2 fa = col ? la[0] : make_float2(0.f, 0.f), fb = col ? lb[0] : make_float2(0.f, 0.f);
+#pragma unroll 2
+  for (int r = 0; r < H; ++r) {
+    const float next = r + 1 < H ? v[r + 1][lane] : 0.f;
+    // the factors of the next row are in flight while this row is mapped
+    float2 fa1 = fa, fb1 = fb;
+    if (col && r + 1 < H) {
+      fa1 = la[(r + 1) * P.W];
+      fb1 = lb[(r + 1) * P.W];
+    }
+    const float s = prev + cur + next;
+    const float up = __shfl_up_sync(0xffffffffu, s, 1);
+    const float dn = __shfl_down_sync(0xffffffffu, s, 1);
+    const float k = fmaf(a, s + (lane > 0 ? up : 0.f) + (hasr ? dn : 0.f), P.sb2);
+    const float c = k * (fa.x * fb.x);
+    float m;
+    if constexpr (ACT == NK_ACT_ERF)
+      m = nk_asin_f32(c);
+    else
+      m = FIRST ? nk_J_f32(c) : nk_J01_f32(c);
+    v[r][lane] = col ? (fa.y * fb.y) * P.fold * m : 0.f;
+    prev = cur;
+    cur = next;
+    fa = fa1;
+    fb = fb1;
+  }
+  __syncwarp();
+}
+
+template <int H, int ACT, bool FULL>
+__global__ void __launch_bounds__(32 * CV_WARPS, 6) k_cv_diag(const __grid_constant__ CvParams P) {
   __shared__ float tile[CV_WARPS][H][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool col = lane < P.W;
+  const bool col = FULL || lane < P.W;
   float (&v)[H][32] = tile[warp];
   const int64_t nw = (int64_t)gridDim.x * CV_WARPS;
   for (int64_t pr = (int64_t)blockIdx.x * CV_WARPS + warp; pr < P.npairs; pr += nw) {
@@ -76,45 +114,11 @@ __global__ void __launch_bounds__(32 * CV_WARPS) k_cv_diag(const __grid_constant
       v[r][lane] = u;
     }
     __syncwarp();
-    const float2* ta = P.qa + ia * (int64_t)P.nq;
-    const float2* tb = P.qb + ib * (int64_t)P.nq;
-    for (int l = 0; l < P.L; ++l) {
-      const float a = l == 0 ? P.xscale : P.cscale;
-      const float2* la = ta + (int64_t)l * H * P.W + lane;
-      const float2* lb = tb + (int64_t)l * H * P.W + lane;
-      float prev = 0.f, cur = v[0][lane];
-      float2 fa = col ? la[0] : make_float2(0.f, 0.f), fb = col ? lb[0] : make_float2(0.f, 0.f);
-#pragma unroll 2
-      for (int r = 0; r < H; ++r) {
-        const float next = r + 1 < H ? v[r + 1][lane] : 0.f;
-        // the factors of the next row are in flight while this row is mapped
-        float2 fa1 = fa, fb1 = fb;
-        if (col && r + 1 < H) {
-          fa1 = la[(r + 1) * P.W];
-          fb1 = lb[(r + 1) * P.W];
-        }
-        const float s = prev + cur + next;
-        const float up = __shfl_up_sync(0xffffffffu, s, 1);
-        const float dn = __shfl_down_sync(0xffffffffu, s, 1);
-        const float k = fmaf(a, s + (lane > 0 ? up : 0.f) + (lane + 1 < P.W ? dn : 0.f), P.sb2);
-        float o = 0.f;
-        if (col) {
-          const float c = k * (fa.x * fb.x);
-          float m;
-          if (P.act == NK_ACT_ERF)
-            m = nk_asin_f32(c);
-          else
-            m = (l == 0) ? nk_J_f32(c) : nk_J01_f32(c);  // after a ReLU layer every K_l >= 0
-          o = (fa.y * fb.y) * P.fold * m;
-        }
-        v[r][lane] = o;
-        prev = cur;
-        cur = next;
-        fa = fa1;
-        fb = fb1;
-      }
-      __syncwarp();
-    }
+    const float2* ta = P.qa + ia * (int64_t)P.nq + lane;
+    const float2* tb = P.qb + ib * (int64_t)P.nq + lane;
+    cv_layer<H, ACT, true, FULL>(P, v, ta, tb, lane, P.xscale);
+    for (int l = 1; l < P.L; ++l)
+      cv_layer<H, ACT, false, FULL>(P, v, ta + (int64_t)l * H * P.W, tb + (int64_t)l * H * P.W, lane, P.cscale);
     double s = 0.0;
     for (int r = 0; r < H; ++r) s += (double)v[r][lane];
 #pragma unroll
@@ -126,6 +130,23 @@ __global__ void __launch_bounds__(32 * CV_WARPS) k_cv_diag(const __grid_constant
     }
     __syncwarp();
   }
+}
+
+template <int H>
+cudaError_t cv_launch(const CvParams& P, unsigned grid, cudaStream_t st) {
+  const bool full = P.W == 32;
+  if (P.act == NK_ACT_ERF) {
+    if (full)
+      k_cv_diag<H, NK_ACT_ERF, true><<<grid, 32 * CV_WARPS, 0, st>>>(P);
+    else
+      k_cv_diag<H, NK_ACT_ERF, false><<<grid, 32 * CV_WARPS, 0, st>>>(P);
+  } else {
+    if (full)
+      k_cv_diag<H, NK_ACT_RELU, true><<<grid, 32 * CV_WARPS, 0, st>>>(P);
+    else
+      k_cv_diag<H, NK_ACT_RELU, false><<<grid, 32 * CV_WARPS, 0, st>>>(P);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -168,9 +189,8 @@ cudaError_t nk_launch_cv_diag(const NkGeom& g, double sw2, double sb2, const flo
   const int64_t want = (P.npairs + CV_WARPS - 1) / CV_WARPS;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count * 32));
   switch (g.Hs[0]) {
-    case 8: k_cv_diag<8><<<grid, 32 * CV_WARPS, 0, st>>>(P); break;
-    case 16: k_cv_diag<16><<<grid, 32 * CV_WARPS, 0, st>>>(P); break;
-    default: k_cv_diag<32><<<grid, 32 * CV_WARPS, 0, st>>>(P); break;
+    case 8: return cv_launch<8>(P, grid, st);
+    case 16: return cv_launch<16>(P, grid, st);
+    default: return cv_launch<32>(P, grid, st);
   }
-  return cudaGetLastError();
 }
