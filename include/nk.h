@@ -171,8 +171,13 @@ nk_status nk_self_diag(nk_handle* h, const nk_arch* arch, const nk_params* prm,
  * 64x64 pairs, 250 MB when 32x32 blocks share the queue, 80 MB with 32x32
  * pairs only) plus 16 bytes per pair of the block, and is allocated on first
  * use.  The same form is the default at
- * 32x32 for these stage patterns (see nk_autotune).  Device-side waits are
- * bounded and report NK_ERR_TIMEOUT through nk_sync_status. */
+ * 32x32 for these stage patterns (see nk_autotune).  At 32x32 the tiled form
+ * also takes the three-stage ReLU patterns (3,3,3) and (2,1,1): its stage-1
+ * task pools into an 8x8 stage-2 tile in shared memory and runs stage 2 on
+ * the same CTA (one CTA of 512 threads per SM; 1.5x the cluster kernel on
+ * Myrtle-10 blocks).
+ * Device-side waits are bounded and report NK_ERR_TIMEOUT through
+ * nk_sync_status. */
 nk_status nk_block(nk_handle* h, const nk_arch* arch, const nk_params* prm, nk_prec prec,
                    const float* Xa, const double* qda, const float* qsa, int64_t a0, int64_t a1,
                    const float* Xb, const double* qdb, const float* qsb, int64_t b0, int64_t b1,
@@ -232,9 +237,10 @@ nk_status nk_block_backward(nk_handle* h, const nk_arch* arch, const nk_params* 
  * caches the fastest in the handle; later nk_block calls with the same key
  * use it.  Variants at 32x32: 0 = super-plane cluster kernel, 768 threads x
  * 8 row parts, 1 = 512 x 8, 2 = 512 x 4, 3 = the tiled form of the 64x64
- * blocks (stage patterns (2,1,0) and (1) at 32x32; it needs the handle's
- * workspace, which grows on first use); other sizes have one.  Without a
- * tuned entry nk_block uses variant 3 where it exists, else 0.  *variant
+ * blocks (stage patterns (2,1,0), (1), (1,1), and with ReLU (3,3,3), (2,1,1)
+ * at 32x32; it needs the handle's workspace, which grows on first use);
+ * other sizes have one.  Without a tuned entry nk_block uses variant 3
+ * where it exists, else 0.  *variant
  * (may be NULL) receives the choice.  Synchronises `stream`. */
 nk_status nk_autotune(nk_handle* h, const nk_arch* arch, const nk_params* prm, int H, int W, int C,
                       int* variant, void* stream);
@@ -283,8 +289,8 @@ nk_status nk_block_fused_noalloc(const nk_arch* arch, const nk_params* prm,
  * as pixel-pair tensors in HBM).  NK_PREC_MIXED: the fused tiled form of
  * nk_block with the tangent rows carried beside K on chip (FP32 recursion,
  * FP64 global averages; qsa / qsb needed, float outputs): ReLU, filter 3,
- * C <= 3, H == W in {32, 64} and the stage pattern (2,1,0), otherwise
- * NK_ERR_UNSUPPORTED.  Its K is nk_block's MIXED K (the same arithmetic; the
+ * C <= 3, H == W in {32, 64} with the stage pattern (2,1,0), or H == W == 32
+ * with (3,3,3) (Myrtle-10) or (2,1,1), otherwise NK_ERR_UNSUPPORTED.  Its K is nk_block's MIXED K (the same arithmetic; the
  * pooled sums are atomic adds, so the last bits may differ).  The tiled form's
  * slot ring holds both pooled tensors, so the workspace is twice nk_block's;
  * waits are bounded as there (NK_ERR_TIMEOUT through nk_sync_status). */

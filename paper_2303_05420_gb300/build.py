@@ -24,7 +24,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
          "--expt-relaxed-constexpr", "-diag-suppress", "177"]
 SOURCES = ["nk_api.cu", "self_diag.cu", "myrtle_fused.cu", "myrtle_fused_r32.cu", "myrtle_fused_r32b.cu", "myrtle_fused_r16.cu",
-           "myrtle_fused_r8.cu", "myrtle_fused_static.cu", "myrtle_queue.cu", "myrtle_tiled.cu", "myrtle_tiled_erf.cu", "myrtle_tiled_ntk.cu", "myrtle_plain.cu",
+           "myrtle_fused_r8.cu", "myrtle_fused_static.cu", "myrtle_queue.cu", "myrtle_tiled.cu", "myrtle_tiled_erf.cu", "myrtle_tiled_ntk.cu", "myrtle_tiled3.cu", "myrtle_plain.cu",
            "myrtle_backward.cu", "fc_gram.cu", "seed_gemm.cu", "pcg.cu", "cv_diag.cu", "probe.cu"]
 
 

@@ -899,6 +899,12 @@ cudaError_t launch_tiled(const int c[3], bool bias, int act, const int* R, const
                          int sm_count,
                          void* ws, size_t ws_bytes, unsigned int* dstatus, long long wait_limit,
                          cudaStream_t st);
+// Three-stage nets at 32x32 (myrtle_tiled3.cu): (3,3,3) and (2,1,1), ReLU,
+// NNGP (ntk false) or NTK (ntk true: K and Theta, B[b].Th).
+bool tiled3_supported(const int c[3]);
+cudaError_t launch_tiled3(const int c[3], bool bias, bool ntk, const int* R, const FusedParams* B, int n,
+                          int sm_count, void* ws, size_t ws_bytes, unsigned int* dstatus, long long wait_limit,
+                          cudaStream_t st);
 // The NTK form (myrtle_tiled_ntk.cu): K and Theta (B[b].Th) of ReLU blocks of
 // the stage pattern (2,1,0), 64x64 and/or 32x32.
 bool tiled_ntk_supported(const int c[3]);

@@ -169,9 +169,14 @@ __device__ inline bool wait_geq(const TiledParams& Q, const int* p, int v) {
 }
 
 // Loads COLS consecutive floats of a slot row (L2 only) and clears them.
-template <int COLS>
+// SH: the row is in this CTA's shared memory (the stage-2 tile of a
+// three-stage net, cleared before each stage-1 task): plain loads.
+template <int COLS, bool SH = false>
 __device__ __forceinline__ void take_row(float* p, float (&v)[COLS]) {
-  if constexpr (COLS == 4) {
+  if constexpr (SH) {
+#pragma unroll
+    for (int k = 0; k < COLS; ++k) v[k] = p[k];
+  } else if constexpr (COLS == 4) {
     const float4 u = __ldcg(reinterpret_cast<const float4*>(p));
     v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w;
     __stcg(reinterpret_cast<float4*>(p), make_float4(0.f, 0.f, 0.f, 0.f));
@@ -209,8 +214,9 @@ __device__ __forceinline__ void take_row(float* p, float (&v)[COLS]) {
 //         sqrt(q q') that A's map carries.  Pools and the global average act
 //         on both; the slot holds K's pooled tensor, then Theta's.
 // ---------------------------------------------------------------------------
+//   SHIN: input rows come from shared memory (the stage-2 tile), not a slot.
 template <int R, int NQ, int N, bool SEED, bool GAP, bool BIAS, bool WRAP, int SXP, int SQ, int PL, int QL, int ACT,
-          int SQX = SQ, bool PH = false, bool NTK = false>
+          int SQX = SQ, bool PH = false, bool NTK = false, bool SHIN = false>
 struct Band {
   static constexpr int COLS = R / NQ, TYW = 32 / NQ;
   static constexpr int R1 = R / 2;
@@ -234,6 +240,7 @@ struct Band {
   float* slot;          // pooled output slot (stage 0 of a two-stage net)
   float* slotT;         // its tangent half (NTK)
   const float* fth;     // folded factor of each layer of this stage (NTK)
+  bool dg;              // NTK: the diagonal super-plane t = (0, 0) of an image with itself
   float b;
 
   // the tangent row enters layer j (not the first conv of stage 0)
@@ -268,8 +275,8 @@ struct Band {
         for (int k = 0; k < COLS; ++k) B[k] = nxT[k];
       }
       if (t + 1 < R) {
-        take_row<COLS>(in + (t + 1) * R, nx);
-        if constexpr (NTK) take_row<COLS>(inT + (t + 1) * R, nxT);
+        take_row<COLS, SHIN>(in + (t + 1) * R, nx);
+        if constexpr (NTK) take_row<COLS, SHIN>(inT + (t + 1) * R, nxT);
       }
     }
   }
@@ -317,8 +324,10 @@ struct Band {
         float T = K;
         if constexpr (tin<j>()) T += fmaf(e, HcT[k], PpT[j][k]);
         // pi - arccos c; a zero self-variance on either side gives a zero
-        // derivative kernel
-        const float dJ = (sq != 0.f) ? (NK_HALF_PI_F + nk_asin_f32(c)) : 0.f;
+        // derivative kernel.  Its slope is infinite at c = 1, where an FP32
+        // c short of 1 by d moves it by sqrt(2 d); the pixel pairs (p, p) of
+        // an image with itself have c = 1 exactly and take pi.
+        const float dJ = (sq != 0.f) ? (dg ? NK_PI_F : NK_HALF_PI_F + nk_asin_f32(c)) : 0.f;
         B[k] = (T * dJ) * fth[j];
       }
     }
@@ -463,8 +472,8 @@ struct Band {
         for (int k = 0; k < CT; ++k) HpT[j][k] = PpT[j][k] = 0.f;
     }
     if constexpr (!SEED) {
-      take_row<COLS>(in, nx);
-      if constexpr (NTK) take_row<COLS>(inT, nxT);
+      take_row<COLS, SHIN>(in, nx);
+      if constexpr (NTK) take_row<COLS, SHIN>(inT, nxT);
     }
     fill<0>();
     int t = s0 + N;
@@ -621,6 +630,7 @@ __device__ void stage0_task(const TiledParams& Q, int b, int64_t g, int sub, uns
     T.slotT = slotT;
     T.inT = nullptr;
     T.fth = P.fold;
+    T.dg = NTK && P.Xa == P.Xb && ia == ib && T.t_x == 0 && T.t_y == 0;
     T.b = P.sb2;
     T.run(gap, gapT);
   }
@@ -666,10 +676,22 @@ __device__ void stage0_task(const TiledParams& Q, int b, int64_t g, int sub, uns
 // ---------------------------------------------------------------------------
 // Stage-1 task of pair g: the whole R1 stage on this CTA, then K.
 // ---------------------------------------------------------------------------
-template <int R1, int N0, int N1, bool BIAS, int NT, int ACT, bool NTK>
+// Shared memory of a stage-1 task: its tables, then (three-stage nets) the
+// pooled stage-2 tile of K (and of Theta) and the stage-2 tables.
+template <int R1, int N1, int N2, bool NTK>
+struct L1x {
+  static constexpr int R2 = R1 / 2;
+  static constexpr size_t tile_off = (L1<R1, N1>::bytes + 15) / 16 * 16;
+  static constexpr size_t tile_floats = N2 > 0 ? (size_t)R2 * R2 * R2 * R2 : 0;
+  static constexpr size_t tab2_off = tile_off + (NTK ? 2 : 1) * tile_floats * 4;
+  static constexpr size_t bytes = N2 > 0 ? tab2_off + L1<(R2 > 0 ? R2 : 1), N2>::bytes : L1<R1, N1>::bytes;
+};
+
+template <int R1, int N0, int N1, bool BIAS, int NT, int ACT, bool NTK, int N2 = 0>
 __device__ void stage1_task(const TiledParams& Q, int64_t g, unsigned char* smem, double* red, int* flag) {
   using L = L1<R1, N1>;
   using SP = Split<R1>;
+  using X1 = L1x<R1, N1, N2, NTK>;
   const int b = block_of(Q, g);
   const FusedParams& P = Q.B[b];
   int64_t i, j;
@@ -695,14 +717,40 @@ __device__ void stage1_task(const TiledParams& Q, int64_t g, unsigned char* smem
         qt[l * L::QL + row * L::S + col] = qb[P.qoff[Lr] + row * R1 + (col & (R1 - 1))];
       }
     }
+    if constexpr (N2 > 0) {
+      // stage-2 tables, and the stage-2 tile(s) cleared for this pair's pooled adds
+      using L2 = L1<X1::R2, N2>;
+      constexpr int R2 = X1::R2;
+      float2* pt2 = reinterpret_cast<float2*>(smem + X1::tab2_off + L2::p_off);
+      float2* qt2 = reinterpret_cast<float2*>(smem + X1::tab2_off + L2::q_off);
+      for (int l = 0; l < N2; ++l) {
+        const int Lr = N0 + N1 + l;
+        const float f = P.fold[Lr];
+        for (int e = threadIdx.x; e < R2 * R2; e += NT) {
+          const float2 v = qa[P.qoff[Lr] + e];
+          pt2[l * L2::PL + e] = make_float2(v.x, v.y * f);
+        }
+        for (int e = threadIdx.x; e < R2 * 2 * R2; e += NT) {
+          const int row = e / (2 * R2), col = e - row * 2 * R2;
+          qt2[l * L2::QL + row * L2::S + col] = qb[P.qoff[Lr] + row * R2 + (col & (R2 - 1))];
+        }
+      }
+      float* tile = reinterpret_cast<float*>(smem + X1::tile_off);
+      for (size_t e = threadIdx.x; e < (NTK ? 2 : 1) * X1::tile_floats; e += NT) tile[e] = 0.f;
+    }
   }
   __syncthreads();
   if (*flag == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = lane / SP::TYW, tyl = lane - q * SP::TYW;
   double gap = 0.0, gapT = 0.0;
-  using BT = Band<R1, SP::NQ, N1, false, true, BIAS, true, R1, L::S, L::PL, L::QL, ACT, L::S, false, NTK>;
+  // stage 1 feeds the global average (two-stage nets) or pools into the
+  // stage-2 tile in shared memory (three-stage nets)
+  constexpr bool GAP1 = N2 == 0;
+  float* tile = N2 > 0 ? reinterpret_cast<float*>(smem + X1::tile_off) : nullptr;
+  using BT = Band<R1, SP::NQ, N1, false, GAP1, BIAS, true, R1, L::S, L::PL, L::QL, ACT, L::S, false, NTK>;
   static_assert(BT::COLS == SP::COLS && BT::TYW == SP::TYW, "split");
+  static_assert(GAP1 || BT::COLS == 2, "the pooled adds into the shared tile use generic atomics (COLS == 2)");
   constexpr int NH = SP::WPT;
   for (int task = warp; task < R1 * NH; task += NT / 32) {
     BT T;
@@ -718,16 +766,55 @@ __device__ void stage1_task(const TiledParams& Q, int64_t g, unsigned char* smem
     T.xq = nullptr;
     T.in = slot + ((size_t)(T.t_y * R1 + T.t_x) * R1) * R1 + T.c0;
     T.inT = NTK ? T.in + (size_t)R1 * R1 * R1 * R1 : nullptr;
-    T.slotT = nullptr;
+    T.slotT = (N2 > 0 && NTK) ? tile + X1::tile_floats : nullptr;
     T.fth = P.fold + N0;
+    T.dg = NTK && P.Xa == P.Xb && ia == ib && T.t_x == 0 && T.t_y == 0;
     T.ptab = pt;
     T.qtab = qt;
     T.pcol = T.c0;
     T.qr0 = 0;
     T.qc = T.c0 + T.t_x;
-    T.slot = nullptr;
+    T.slot = tile;
     T.b = P.sb2;
     T.run(gap, gapT);
+  }
+  if constexpr (N2 > 0) {
+    // stage 2 from the pooled tile, on the same CTA
+    __syncthreads();
+    constexpr int R2 = X1::R2;
+    using L2 = L1<R2, N2>;
+    using SP2 = Split<R2>;
+    using BT2 = Band<R2, SP2::NQ, N2, false, true, BIAS, true, R2, L2::S, L2::PL, L2::QL, ACT, L2::S, false, NTK,
+                     true>;
+    static_assert(BT2::COLS == SP2::COLS && BT2::TYW == SP2::TYW, "split");
+    const int q2 = lane / SP2::TYW, tyl2 = lane - q2 * SP2::TYW;
+    constexpr int NH2 = SP2::WPT;
+    for (int task = warp; task < R2 * NH2; task += NT / 32) {
+      BT2 T;
+      T.t_x = task / NH2;
+      T.t_y = (task % NH2) * SP2::TYW + tyl2;
+      T.c0 = q2 * SP2::COLS;
+      T.s0 = 0;
+      T.s1 = R2;
+      T.b0 = 0;
+      T.tyodd = (T.t_y & 1) != 0;
+      edges<SP2::COLS>(T.E, R2, T.t_x, q2);
+      T.xs = nullptr;
+      T.xq = nullptr;
+      T.in = tile + ((size_t)(T.t_y * R2 + T.t_x) * R2) * R2 + T.c0;
+      T.inT = NTK ? T.in + X1::tile_floats : nullptr;
+      T.slotT = nullptr;
+      T.fth = P.fold + N0 + N1;
+      T.dg = NTK && P.Xa == P.Xb && ia == ib && T.t_x == 0 && T.t_y == 0;
+      T.ptab = reinterpret_cast<const float2*>(smem + X1::tab2_off + L2::p_off);
+      T.qtab = reinterpret_cast<const float2*>(smem + X1::tab2_off + L2::q_off);
+      T.pcol = T.c0;
+      T.qr0 = 0;
+      T.qc = T.c0 + T.t_x;
+      T.slot = nullptr;
+      T.b = P.sb2;
+      T.run(gap, gapT);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) gap += __shfl_xor_sync(FULL, gap, o);
@@ -754,11 +841,12 @@ __device__ void stage1_task(const TiledParams& Q, int64_t g, unsigned char* smem
   }
 }
 
-template <int N0, int N1, int RMAX, bool NTK = false>
+template <int N0, int N1, int RMAX, bool NTK = false, int N2 = 0>
 struct Smem {
+  static_assert(N2 == 0 || RMAX == 32, "three-stage nets: 32x32 images only");
   static constexpr size_t s0 = RMAX == 64 ? std::max(L0<64, N0>::bytes, L0<32, N0>::bytes) : L0<32, N0>::bytes;
   static constexpr size_t s1 =
-      N1 > 0 ? (RMAX == 64 ? std::max(L1<32, N1>::bytes, L1<16, N1>::bytes) : L1<16, N1>::bytes) : 0;
+      N1 > 0 ? (RMAX == 64 ? std::max(L1<32, N1>::bytes, L1<16, N1>::bytes) : L1x<16, N1, N2, NTK>::bytes) : 0;
   static constexpr size_t tables = std::max(s0, s1);
   static constexpr size_t red = (NTK ? 2 : 1) * MAX_WARPS * 8;  // per-warp global-average sums
   static constexpr size_t bytes = tables + red + 16;
@@ -766,10 +854,10 @@ struct Smem {
 
 // NTK instantiations carry the tangent rows (twice the pipeline registers)
 // in the same launch shapes (at 128 registers they spill a few bytes).
-template <int N0, int N1, bool BIAS, int NT, int RMAX, int ACT, bool NTK = false>
+template <int N0, int N1, bool BIAS, int NT, int RMAX, int ACT, bool NTK = false, int N2 = 0>
 __global__ void __launch_bounds__(NT, 512 / NT) k_myrtle_tiled(const __grid_constant__ TiledParams Q) {
   extern __shared__ __align__(16) unsigned char smem[];
-  using SM = Smem<N0, N1, RMAX, NTK>;
+  using SM = Smem<N0, N1, RMAX, NTK, N2>;
   constexpr bool TWO = N1 > 0;
   double* red = reinterpret_cast<double*>(smem + SM::tables);
   int* flag = reinterpret_cast<int*>(smem + SM::tables + SM::red);
@@ -810,7 +898,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_myrtle_tiled(const __grid_cons
         else
           stage1_task<16, N0, N1, BIAS, NT, ACT, NTK>(Q, k, smem, red, flag);
       } else {
-        stage1_task<16, N0, N1, BIAS, NT, ACT, NTK>(Q, k, smem, red, flag);
+        stage1_task<16, N0, N1, BIAS, NT, ACT, NTK, N2>(Q, k, smem, red, flag);
       }
     }
     // the next item's staging overwrites the tables
@@ -818,11 +906,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_myrtle_tiled(const __grid_cons
   }
 }
 
-template <int N0, int N1, bool BIAS, int NT, int RMAX, int ACT, bool NTK = false>
+template <int N0, int N1, bool BIAS, int NT, int RMAX, int ACT, bool NTK = false, int N2 = 0>
 cudaError_t launch_t(TiledParams& Q, const int64_t* npairs, int sm_count, void* ws, size_t ws_bytes,
                      cudaStream_t st) {
-  using SM = Smem<N0, N1, RMAX, NTK>;
-  auto kern = k_myrtle_tiled<N0, N1, BIAS, NT, RMAX, ACT, NTK>;
+  using SM = Smem<N0, N1, RMAX, NTK, N2>;
+  auto kern = k_myrtle_tiled<N0, N1, BIAS, NT, RMAX, ACT, NTK, N2>;
   constexpr int tensors = NTK ? 2 : 1;
   static bool attr_set[64] = {false};
   static int per_sm[64] = {0};

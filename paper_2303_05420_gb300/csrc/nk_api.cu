@@ -138,12 +138,14 @@ bool fused_variant_valid(const NkGeom& g, int v) {
   if (v < 0 || v >= NK_FUSED_VARIANTS) return false;
   int c[3];
   stage_pattern(g, c);
-  if (v == NK_TILED_VARIANT) return nkf::tiled_supported(c);
+  if (v == NK_TILED_VARIANT)
+    return nkf::tiled_supported(c) || (g.act == NK_ACT_RELU && nkf::tiled3_supported(c));
   return g.act == NK_ACT_RELU && nk_cluster_pattern(c);  // the cluster launches
 }
 
 // Default variant without a tuned entry: the tiled form where it exists
-// (measured faster than the cluster launches at 32x32), else variant 0.
+// (measured faster than the cluster launches at 32x32: 1.15x for (2,1,0),
+// 1.5x for Myrtle-10 (3,3,3)), else variant 0.
 int fused_default_variant(const NkGeom& g) {
   return fused_variant_valid(g, NK_TILED_VARIANT) ? NK_TILED_VARIANT : 0;
 }
@@ -173,6 +175,9 @@ nk_status fused_block(nk_handle* h, const NkGeom& g, const nk_params* prm, const
     nk_status s = nk_workspace(h, nkf::tiled_ws_bytes(c, R, np, 1, h->sm_count), &ws);
     if (s != NK_OK) return s;
     h->launches += 1;
+    if (!nkf::tiled_supported(c))  // three-stage nets at 32x32
+      return nk_cuda_check(h, nkf::launch_tiled3(c, prm->sigma_b2 != 0.0, false, R, &P, 1, h->sm_count, ws,
+                                                 h->ws_bytes, h->dstatus, tiled_wait_limit(h), st), what);
     return nk_cuda_check(h, nkf::launch_tiled(c, prm->sigma_b2 != 0.0, g.act, R, &P, 1, h->sm_count, ws,
                                               h->ws_bytes, h->dstatus, tiled_wait_limit(h), st), what);
   }
@@ -391,12 +396,13 @@ nk_status nk_block_ntk(nk_handle* h, const nk_arch* arch, const nk_params* prm, 
     return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: unknown precision");
   int pat[3];
   stage_pattern(g, pat);
+  const bool ntk3 = nkf::tiled3_supported(pat) && g.Hs[0] == 32;
   if (prec == NK_PREC_MIXED &&
       (g.act != NK_ACT_RELU || g.filter != 3 || g.C > 3 || g.Hs[0] != g.Ws[0] ||
-       (g.Hs[0] != 32 && g.Hs[0] != 64) || !nkf::tiled_ntk_supported(pat)))
+       !(((g.Hs[0] == 32 || g.Hs[0] == 64) && nkf::tiled_ntk_supported(pat)) || ntk3)))
     return nk_fail(h, NK_ERR_UNSUPPORTED,
-                   "nk_block_ntk MIXED: needs ReLU, filter 3, C <= 3, H == W in {32, 64} and the stage pattern "
-                   "(2,1,0)");
+                   "nk_block_ntk MIXED: needs ReLU, filter 3, C <= 3 and H == W in {32, 64} with the stage "
+                   "pattern (2,1,0), or H == W == 32 with (3,3,3) or (2,1,1)");
   if (a0 < 0 || b0 < 0 || a1 < a0 || b1 < b0)
     return nk_fail(h, NK_ERR_INVALID_ARG, "nk_block_ntk: bad index range");
   if (a1 == a0 || b1 == b0) return NK_OK;
@@ -420,6 +426,11 @@ nk_status nk_block_ntk(nk_handle* h, const nk_arch* arch, const nk_params* prm, 
     nk_status s = nk_workspace(h, nkf::tiled_ws_bytes(pat, R, np, 1, h->sm_count, 2), &ws);
     if (s != NK_OK) return s;
     h->launches += 1;
+    if (ntk3)
+      return nk_cuda_check(h,
+                           nkf::launch_tiled3(pat, prm->sigma_b2 != 0.0, true, R, &P, 1, h->sm_count, ws,
+                                              h->ws_bytes, h->dstatus, tiled_wait_limit(h), (cudaStream_t)stream),
+                           "nk_block_ntk tiled launch");
     return nk_cuda_check(h,
                          nkf::launch_tiled_ntk(pat, prm->sigma_b2 != 0.0, R, &P, 1, h->sm_count, ws, h->ws_bytes,
                                                h->dstatus, tiled_wait_limit(h), (cudaStream_t)stream),

@@ -103,7 +103,8 @@ def test_fused_ntk_refusals(h):
     x16 = torch.tensor(_imgs(2, 16, 27), device="cuda")
     q16 = h.self_diag(x16, CONVS, 2.0, 0.0)
     x32 = torch.tensor(_imgs(2, 32, 28), device="cuda")
-    for X, convs in ((x16, CONVS), (x32, (3, 3, 3)), (x32, (1,))):
+    # (3,3,3) and (2,1,1) at 32x32 have the fused NTK (test_gpu_tiled3.py)
+    for X, convs in ((x16, CONVS), (x32, (1,)), (x32, (1, 1))):
         q = q16 if X is x16 else h.self_diag(X, convs, 2.0, 0.0)
         with pytest.raises(NkError) as ei:
             h.block_ntk(X, q, X, q, convs, 2.0, 0.0, prec="mixed")
