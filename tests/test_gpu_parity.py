@@ -256,9 +256,9 @@ def test_autotune_variants_agree(h):
 
     x = _imgs(6, 32, 4)
     X = _dev(x)
-    # (2,1,0) has the three cluster launches and the tiled form (3); (3,3,3)
-    # the cluster launches only
-    for convs, sb2, nvar in [((2, 1, 0), 0.0, 4), ((3, 3, 3), 0.01, 3)]:
+    # (2,1,0) and (3,3,3) have the three cluster launches and the tiled form
+    # (3); (1,1,1) the cluster launches only
+    for convs, sb2, nvar in [((2, 1, 0), 0.0, 4), ((3, 3, 3), 0.01, 4), ((1, 1, 1), 0.0, 3)]:
         q = h.self_diag(X, convs, 2.0, sb2)
         chosen = h.autotune(convs, 2.0, sb2, 32, 32, 3)
         assert 0 <= chosen < nvar
@@ -272,7 +272,7 @@ def test_autotune_variants_agree(h):
     with pytest.raises(NkError):
         h.autotune_set((2, 1, 0), 2.0, 0.0, 32, 32, 4)
     with pytest.raises(NkError):
-        h.autotune_set((3, 3, 3), 2.0, 0.0, 32, 32, 3)
+        h.autotune_set((1, 1, 1), 2.0, 0.0, 32, 32, 3)
 
 
 @pytest.mark.parametrize("precond", ["none", "jacobi", "pivchol"])
