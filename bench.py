@@ -470,6 +470,25 @@ def run_ours(args, rank, world, dist):
         extra["ntk_mixed_entries_per_s"] = nsym * (nsym + 1) / 2 / (a.elapsed_time(b) / 1e3)
         extra["ntk_mixed_over_plain_fp32"] = extra["ntk_mixed_entries_per_s"] / extra["ntk_plain_fp32_entries_per_s"]
         extra["ntk_mixed_workload"] = f"myrtle5_(2,1,0)_32x32_ntk_symmetric{nsym}_mixed_tiled"
+        # Myrtle-10 (3,3,3) on the same images: NNGP and NTK in the three-stage tiled form
+        c10, sb10 = (3, 3, 3), 0.01
+        q10 = h.self_diag(X, c10, SW2, sb10)
+        for key, fn in (("myrtle10_mixed_entries_per_s",
+                         lambda: h.block(X, q10, X, q10, c10, SW2, sb10, prec="mixed", a_range=(0, nsym),
+                                         b_range=(0, nsym), symmetric=True)),
+                        ("ntk10_mixed_entries_per_s",
+                         lambda: h.block_ntk(X, q10, X, q10, c10, SW2, sb10, prec="mixed", a_range=(0, nsym),
+                                             b_range=(0, nsym), symmetric=True))):
+            fn()
+            torch.cuda.synchronize()
+            a, b = ev(), ev()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            extra[key] = nsym * (nsym + 1) / 2 / (a.elapsed_time(b) / 1e3)
+        h.sync_status()
+        extra["myrtle10_workload"] = f"myrtle10_(3,3,3)_32x32_symmetric{nsym}_sb2_0.01_mixed_tiled"
         # the 64x64 problem of the mixed-resolution workload in the layer-wise
         # FP32 form, on a 16 x 16 sample of pairs (the fused form: queue leg)
         x64 = nkdata.standardise(nkdata.images(32, 64, 3, nkdata.SEED_TRAIN, blur=True))[0]
@@ -561,7 +580,7 @@ def run_ours(args, rank, world, dist):
     # the output keeps them)
     keys = ["mixed_over_plain_fp32", "plain_fp32_entries_per_s", "plain_fp64_entries_per_s", "pcg_iters_per_s",
             "pcg_mixed_iters_per_s", "pcg_plain_fp64_iters_per_s", "fc3_gram_ms", "grad_backward_s",
-            "queue_graph_ms", "erf_entries_per_s", "cv8_entries_per_s", "config1_entries_per_s", "ntk_mixed_entries_per_s"]
+            "queue_graph_ms", "erf_entries_per_s", "cv8_entries_per_s", "config1_entries_per_s", "ntk_mixed_entries_per_s", "ntk10_mixed_entries_per_s"]
     line["summary"] = {"value": value, "e2e": e2e_val, "roofline_frac": achieved_tops / peak_tops,
                        **{k: line.get(k) for k in keys if k in line}}
     if rank == 0:
