@@ -689,7 +689,7 @@ def grad_leg(h, dev, n_sup=100, n_tgt=2048):
         L.backward()
         ev[2].record()
         torch.cuda.synchronize()
-        return (float(L), float(s.grad), float(b.grad), ev[0].elapsed_time(ev[1]) / 1e3,
+        return (float(L.detach()), float(s.grad), float(b.grad), ev[0].elapsed_time(ev[1]) / 1e3,
                 ev[1].elapsed_time(ev[2]) / 1e3)
 
     once(4, 8)  # loads every kernel; untimed

@@ -56,4 +56,4 @@ def krr_loss_and_grads(arch: Arch, sw2: float, sb2: float, Xs, Ys, Xt, Yt, lam: 
     Xs_t = torch.as_tensor(Xs, dtype=F64).clone().requires_grad_(True)
     L = krr_loss(arch, sw2_t, sb2_t, Xs_t, Ys, Xt, Yt, lam)
     L.backward()
-    return float(L), float(sw2_t.grad), float(sb2_t.grad), Xs_t.grad.detach().clone()
+    return float(L.detach()), float(sw2_t.grad), float(sb2_t.grad), Xs_t.grad.detach().clone()

@@ -162,6 +162,15 @@ __device__ __forceinline__ T J_only(T c) {
   }
 }
 
+// s += x with Kahan compensation c (s - c is the compensated sum).
+template <typename T>
+__device__ __forceinline__ void kahan_add(T& s, T& c, T x) {
+  const T y = x - c;
+  const T t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
 template <typename T, int MODE>
 __device__ __forceinline__ T xform(const FArgs<T>& A, int64_t ia, int64_t ib, int p, int pp, T k, T g, T& h, T& sa,
                                    T& sb) {
@@ -260,8 +269,15 @@ __global__ void __launch_bounds__(256, 3) k_conv_fused(const __grid_constant__ F
     mlo_[u] = (jj_[u] > 0 && ll_[u] > 0) ? (T)1 : (T)0;
     mhi_[u] = (jj_[u] + 1 < W && ll_[u] + 1 < W) ? (T)1 : (T)0;
   }
+  // sigma sums (reverse): per plane in T, then in FP64.  FP32 at W = 32 sums
+  // a pair group's planes in FP32 with Kahan compensation first, which keeps
+  // FP64 instructions (about 1/64 of the FP32 rate) out of the plane loop;
+  // the other forms, short of registers or in FP64, add each plane in FP64.
+  constexpr bool KAHAN = MODE == CIN_ADJ && W == 32 && sizeof(T) == 4;
+  const T sb2 = (T)A.sb2;
   double dsa = 0.0, dsb = 0.0;
   for (int64_t pg = (int64_t)blockIdx.y * NPB; pg < A.np; pg += (int64_t)gridDim.y * NPB) {
+    T csa = 0, csb = 0, ksa = 0, ksb = 0;
     int64_t ia[NPB], ib[NPB];
     bool ok[NPB];
 #pragma unroll
@@ -353,12 +369,12 @@ __global__ void __launch_bounds__(256, 3) k_conv_fused(const __grid_constant__ F
                     dk = rg[b][u] * dJ * inv2pi;
                     h = rg[b][u] * (sc * inv2pi * J - v * dJ * inv2pi);
                   }
-                  sa += dk * (v - (T)A.sb2);
+                  sa += dk * (v - sb2);
                   sb += dk;
                   v = dk;
                 }
               } else if constexpr (MODE == CIN_ADJ) {
-                sa += rg[b][u] * (v - (T)A.sb2);
+                sa += rg[b][u] * (v - sb2);
                 sb += rg[b][u];
                 v = rg[b][u];
               }
@@ -368,8 +384,13 @@ __global__ void __launch_bounds__(256, 3) k_conv_fused(const __grid_constant__ F
             if constexpr (MODE == CIN_ADJ) hw[jj_[u] * W + ll_[u]] = h;
           }
         }
-        dsa += (double)sa;
-        dsb += (double)sb;
+        if constexpr (KAHAN) {
+          kahan_add(csa, ksa, sa);
+          kahan_add(csb, ksb, sb);
+        } else if constexpr (MODE == CIN_ADJ) {
+          dsa += (double)sa;
+          dsb += (double)sb;
+        }
         if (s + 2 <= i1) fetch(s + 2, rk, rg);  // in flight during the next two planes
       }
       __syncthreads();
@@ -503,6 +524,10 @@ __global__ void __launch_bounds__(256, 3) k_conv_fused(const __grid_constant__ F
       step(s + 1, k1, g1);
     }
     if (s <= i1 + 1) step(s, k0, g0);
+    if constexpr (KAHAN) {
+      dsa += (double)csa - (double)ksa;
+      dsb += (double)csb - (double)ksb;
+    }
   }
   if constexpr (MODE == CIN_ADJ) {
     __shared__ double r1[8], r2[8];
