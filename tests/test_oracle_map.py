@@ -93,7 +93,7 @@ def test_map_derivatives_by_central_differences():
             out.backward()
             f = lambda k, x, y: float(relu_map(torch.tensor(k, dtype=F64), torch.tensor(x, dtype=F64),
                                                torch.tensor(y, dtype=F64)))
-            k0 = float(K)
+            k0 = float(K.detach())
             dK = (f(k0 + h, q1, q2) - f(k0 - h, q1, q2)) / (2 * h)
             dq1 = (f(k0, q1 + h, q2) - f(k0, q1 - h, q2)) / (2 * h)
             dq2 = (f(k0, q1, q2 + h) - f(k0, q1, q2 - h)) / (2 * h)
