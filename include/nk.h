@@ -212,7 +212,12 @@ nk_status nk_fc_block(nk_handle* h, int depth, const nk_params* prm, const float
  * q on the images and on sigma_w2, sigma_b2.
  *   prec   NK_PREC_PLAIN_FP32 or NK_PREC_MIXED: float dK, dXa, dXb; FP32
  *          pixel-pair tensors; NK_PREC_PLAIN_FP64: double dK, dXa, dXb.
- *          The self-variance adjoint is FP64 in all cases.
+ *          The self-variance adjoint is FP64 in all cases.  Every pair's
+ *          contribution carries FP32 rounding of about 1e-7 in the FP32
+ *          forms, so an upstream gradient whose contributions cancel
+ *          strongly (a kernel-ridge loss at a near-singular ridge, where
+ *          the sum is about 1e-3 of its terms) loses accuracy in
+ *          proportion; PLAIN_FP64 is the form for such gradients.
  *   qda, qdb   nk_self_diag FP64 outputs (required); qsa, qsb its FP32 scale
  *              tables (required unless PLAIN_FP64).
  *   symmetric  the block is the upper triangle of Xa x Xa: dK[i][j] and
