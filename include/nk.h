@@ -343,7 +343,8 @@ nk_status nk_block_queue(nk_handle* h, const nk_arch* arch, const nk_params* prm
  * block that cannot finish must end with an error, never hang).  The tiled
  * MIXED kernel waits for earlier items of its queue (each poll about
  * 0.25-1 us; default 2^22 polls, seconds); the FC kernel's pipeline waits on
- * its mbarriers (each poll a bounded try_wait; default 2^26 polls).  A wait
+ * its mbarriers (each poll a bounded try_wait; default 2^26 polls), and so
+ * does the tensor-core first layer of nk_block_backward (FP32, same bound).  A wait
  * that runs out sets NK_ERR_TIMEOUT (read by nk_sync_status), the kernel
  * stops taking work, and the results of that call are undefined; the handle
  * stays usable.  The waits a kernel makes before it exits, for its own copies

@@ -1162,8 +1162,8 @@ template <typename T>
 cudaError_t run_backward(const NkGeom& g, double sw2, double sb2, const float* Xa, const double* qda,
                          const float* qsa, int64_t a0, int64_t a1, const float* Xb, const double* qdb,
                          const float* qsb, int64_t b0, int64_t b1, const T* dK, int64_t lddk, int sym, T* dXa, T* dXb,
-                         double* dsw2, double* dsb2, void* ws, const BwdPlan<T>& P, cudaStream_t st,
-                         int64_t* launches, unsigned int* dstatus) {
+                         double* dsw2, double* dsb2, void* ws, const BwdPlan<T>& P, uint32_t wait_limit,
+                         cudaStream_t st, int64_t* launches, unsigned int* dstatus) {
   const int64_t na = a1 - a0, nb = b1 - b0;
   const int64_t npairs = sym ? na * (na + 1) / 2 : na * nb;
   const int64_t chunk = P.chunk;
@@ -1274,7 +1274,7 @@ cudaError_t run_backward(const NkGeom& g, double sw2, double sb2, const float* X
         if (layer == 0 && tc_seed) {
           if constexpr (sizeof(T) == 4)
             e = nk_launch_seed_gemm(patch_a, na, patch_b, nb, sym, pair0, np, g.Hs[0], g.Ws[0], g.C, sw2, sb2,
-                                    Kst[0], P.sm, dstatus, st);
+                                    Kst[0], P.sm, dstatus, wait_limit, st);
         } else if (layer == 0) {
           e = conv_pass<T, CIN_COV>(A, st);
         } else if (pend_layer >= 0) {
@@ -1409,16 +1409,18 @@ cudaError_t nk_launch_backward(const NkGeom& g, int fp64, double sw2, double sb2
                                const double* qda, const float* qsa, int64_t a0, int64_t a1, const float* Xb,
                                const double* qdb, const float* qsb, int64_t b0, int64_t b1, const void* dK,
                                int64_t lddk, int sym, void* dXa, void* dXb, double* dsw2, double* dsb2,
-                               void* ws, int sm, cudaStream_t st, int64_t* launches,
+                               void* ws, int sm, uint32_t wait_limit, cudaStream_t st, int64_t* launches,
                                unsigned int* dstatus) {
   const int64_t na = a1 - a0, nb = b1 - b0;
   const int64_t npairs = sym ? na * (na + 1) / 2 : na * nb;
   if (fp64) {
     auto P = plan_backward<double>(g, npairs, na, nb, sym, sm);
     return run_backward<double>(g, sw2, sb2, Xa, qda, qsa, a0, a1, Xb, qdb, qsb, b0, b1, (const double*)dK, lddk,
-                                sym, (double*)dXa, (double*)dXb, dsw2, dsb2, ws, P, st, launches, dstatus);
+                                sym, (double*)dXa, (double*)dXb, dsw2, dsb2, ws, P, wait_limit, st, launches,
+                                dstatus);
   }
   auto P = plan_backward<float>(g, npairs, na, nb, sym, sm);
   return run_backward<float>(g, sw2, sb2, Xa, qda, qsa, a0, a1, Xb, qdb, qsb, b0, b1, (const float*)dK, lddk,
-                             sym, (float*)dXa, (float*)dXb, dsw2, dsb2, ws, P, st, launches, dstatus);
+                             sym, (float*)dXa, (float*)dXb, dsw2, dsb2, ws, P, wait_limit, st, launches,
+                             dstatus);
 }

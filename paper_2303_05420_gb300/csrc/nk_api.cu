@@ -150,7 +150,9 @@ int fused_default_variant(const NkGeom& g) {
   return fused_variant_valid(g, NK_TILED_VARIANT) ? NK_TILED_VARIANT : 0;
 }
 
-// Bounds of the device waits of the two kernels that wait (nk_set_wait_limit).
+// Bounds of the device waits (nk_set_wait_limit): the tiled queue's item waits,
+// and the mbarrier waits of the FC Gram and of the adjoint's tensor-core first
+// layer.
 long long tiled_wait_limit(const nk_handle* h) {
   return h->wait_polls < 0 ? NK_TILED_WAIT_DEFAULT : h->wait_polls;
 }
@@ -592,7 +594,7 @@ nk_status nk_block_backward(nk_handle* h, const nk_arch* arch, const nk_params* 
   if (s != NK_OK) return s;
   cudaError_t e = nk_launch_backward(g, fp64, prm->sigma_w2, prm->sigma_b2, Xa, qda, qsa, a0, a1, Xb, qdb, qsb,
                                      b0, b1, dK, lddk, symmetric, dXa, dXb, dsw2, dsb2, ws, h->sm_count,
-                                     (cudaStream_t)stream, &h->launches, h->dstatus);
+                                     fc_wait_limit(h), (cudaStream_t)stream, &h->launches, h->dstatus);
   return nk_cuda_check(h, e, "nk_block_backward");
 }
 

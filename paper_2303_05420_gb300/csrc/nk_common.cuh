@@ -120,14 +120,14 @@ size_t nk_seed_patch_bytes(int64_t n_images, int H, int W);
 cudaError_t nk_seed_patches(const float* X, int64_t n, int H, int W, int C, void* patches, cudaStream_t st);
 cudaError_t nk_launch_seed_gemm(const void* pa, int64_t na, const void* pb, int64_t nb, int sym, int64_t pair0,
                                 int64_t np, int H, int W, int C, double sw2, double sb2, float* out, int sm,
-                                unsigned int* dstatus, cudaStream_t st);
+                                unsigned int* dstatus, uint32_t wait_limit, cudaStream_t st);
 size_t nk_backward_ws_bytes(const NkGeom& g, int fp64, int64_t npairs, int64_t na, int64_t nb, int sym,
                             int sm);
 cudaError_t nk_launch_backward(const NkGeom& g, int fp64, double sw2, double sb2, const float* Xa,
                                const double* qda, const float* qsa, int64_t a0, int64_t a1, const float* Xb,
                                const double* qdb, const float* qsb, int64_t b0, int64_t b1, const void* dK,
                                int64_t lddk, int sym, void* dXa, void* dXb, double* dsw2, double* dsb2,
-                               void* ws, int sm, cudaStream_t st, int64_t* launches,
+                               void* ws, int sm, uint32_t wait_limit, cudaStream_t st, int64_t* launches,
                                unsigned int* dstatus);
 
 // Plain layer-wise Myrtle block (FP32 or FP64).

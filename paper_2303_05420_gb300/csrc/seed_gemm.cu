@@ -285,7 +285,7 @@ cudaError_t nk_seed_patches(const float* X, int64_t n, int H, int W, int C, void
 
 cudaError_t nk_launch_seed_gemm(const void* pa, int64_t na, const void* pb, int64_t nb, int sym, int64_t pair0,
                                 int64_t np, int H, int W, int C, double sw2, double sb2, float* out, int sm,
-                                unsigned int* dstatus, cudaStream_t st) {
+                                unsigned int* dstatus, uint32_t wait_limit, cudaStream_t st) {
   const int HW = H * W;
   if (np <= 0) return cudaSuccess;
   CUtensorMap ta, tb;
@@ -304,7 +304,7 @@ cudaError_t nk_launch_seed_gemm(const void* pa, int64_t na, const void* pb, int6
   P.bias = (float)sb2;
   P.out = out;
   P.dstatus = dstatus;
-  P.wait_limit = NK_FC_WAIT_DEFAULT;
+  P.wait_limit = wait_limit;
   const size_t smem = sizeof(SeedSmem) + 1024;
   cudaError_t e = cudaFuncSetAttribute(k_seed_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

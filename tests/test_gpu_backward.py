@@ -206,3 +206,45 @@ def test_backward_tensor_core_seed(h, hw, na, nb):
     assert _rel(dXb.double().cpu().numpy(), want_b) <= 1e-4
     assert abs(float(dsw2) - want_s) <= 1e-4 * abs(want_s)
     assert abs(float(dsb2) - want_b2) <= 1e-4 * abs(want_b2)
+
+
+def test_backward_wait_limit_runs_out_and_the_handle_recovers(h):
+    """A wait limit of 0 polls makes the mbarrier waits of the adjoint's
+    tensor-core first layer (seed_gemm.cu) give up: the call returns,
+    nk_sync_status reports NK_ERR_TIMEOUT, and with the default limit
+    restored the next call on the same handle matches the oracle.  Each CTA
+    still waits, with a fixed bound, for the loads it issued before it exits,
+    so no wait is left unbounded."""
+    from paper_2303_05420_gb300._lib import NK_ERR_TIMEOUT, NkError
+
+    convs, sb2 = (2, 1, 0), 0.01
+    xa, xb = _imgs(2, 32, 11), _imgs(2, 32, 12)
+    dK = np.random.default_rng(13).standard_normal((2, 2))
+    Xa, Xb = torch.tensor(xa, device="cuda"), torch.tensor(xb, device="cuda")
+    qa, qb = h.self_diag(Xa, convs, 2.0, sb2), h.self_diag(Xb, convs, 2.0, sb2)
+    dKt = torch.tensor(dK, dtype=torch.float32, device="cuda")
+    h.sync_status()
+
+    def run():
+        dXa = torch.zeros(Xa.shape, dtype=torch.float32, device="cuda")
+        dXb = torch.zeros(Xb.shape, dtype=torch.float32, device="cuda")
+        dsw2 = torch.zeros(1, dtype=F64, device="cuda")
+        dsb2 = torch.zeros(1, dtype=F64, device="cuda")
+        h.block_backward(Xa, qa, Xb, qb, convs, 2.0, sb2, dKt, dXa, dXb, dsw2, dsb2, prec="plain_fp32")
+        return dXa, dXb, dsw2, dsb2
+
+    h.set_wait_limit(0)
+    try:
+        run()
+        with pytest.raises(NkError) as ei:
+            h.sync_status()
+        assert ei.value.status == NK_ERR_TIMEOUT
+    finally:
+        h.set_wait_limit(-1)
+    dXa, dXb, dsw2, dsb2 = run()
+    h.sync_status()
+    want_a, want_b, want_s, want_b2 = _oracle_grads(convs, 2.0, sb2, xa, xb, dK, False)
+    assert _rel(dXa.double().cpu().numpy(), want_a) <= 1e-4
+    assert _rel(dXb.double().cpu().numpy(), want_b) <= 1e-4
+    assert abs(float(dsw2) - want_s) <= 1e-4 * abs(want_s)
+    assert abs(float(dsb2) - want_b2) <= 1e-4 * abs(want_b2)
