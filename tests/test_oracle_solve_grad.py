@@ -122,10 +122,10 @@ def test_euler_identities():
     K, _, _ = myrtle_layers_pair(arch, sw2, 0.0, x, xp, qx, qxp)
     K.backward()
     # degree 1 in x (q(x) scales as x^2 and the map is 1-homogeneous)
-    assert abs(float((x * x.grad).sum()) - float(K.detach())) <= 1e-12 * abs(float(K.detach()))
+    assert abs(float((x.detach() * x.grad).sum()) - float(K.detach())) <= 1e-12 * abs(float(K.detach()))
     # degree L = #weight layers in sigma_w^2
     L = arch.n_weight_layers
-    assert abs(float(sw2.grad) - L * float(K) / 1.6) <= 1e-12 * abs(float(K))
+    assert abs(float(sw2.grad) - L * float(K.detach()) / 1.6) <= 1e-12 * abs(float(K.detach()))
 
 
 # --------------------------------------------------------------------------
