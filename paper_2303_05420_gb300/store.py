@@ -151,6 +151,8 @@ def solve_resumable(handle, K, Y, lam: float, path: str, piece_iters: int = 200,
     Returns (A, pieces run by this call, converged)."""
     import torch
 
+    if "maxit" in solve_kw:
+        raise ValueError("solve_resumable bounds each piece by piece_iters; pass no maxit")
     A = torch.zeros_like(Y)
     if os.path.exists(path):
         A.copy_(torch.from_numpy(np.load(path)).to(Y.device))

@@ -102,3 +102,59 @@ def test_store_refuses_another_shape(tmp_path):
         BlockStore(path, 10, 12, 4)
     with pytest.raises(RuntimeError):
         BlockStore(path, 10, 10, 4, symmetric=True).assemble()
+
+
+class _RichardsonHandle:
+    """Stands in for Handle's PCG calls: maxit Richardson steps on
+    (K + lam I) A = Y from the A it is given when warm start is on (from zero
+    otherwise), relres per column."""
+
+    def __init__(self):
+        self.warm, self.starts = False, []
+
+    def pcg_set_warm_start(self, on):
+        self.warm = bool(on)
+
+    def pcg_solve(self, K, Y, lam, A=None, maxit=100, allow_not_converged=False, tol=1e-6):
+        import torch
+
+        M = K + lam * torch.eye(K.shape[0], dtype=K.dtype)
+        w = 1.0 / float(torch.linalg.matrix_norm(M, 2))
+        X = A.clone() if self.warm else torch.zeros_like(Y)
+        self.starts.append(X.clone())
+        its = 0
+        for its in range(1, maxit + 1):
+            X = X + w * (Y - M @ X)
+            rel = ((Y - M @ X).norm(dim=0) / Y.norm(dim=0)).tolist()
+            if max(rel) <= tol:
+                break
+        A.copy_(X)
+        return A, its, rel
+
+
+def test_solve_resumable_saves_each_piece_and_resumes(tmp_path):
+    import torch
+
+    from paper_2303_05420_gb300.store import solve_resumable
+
+    rng = np.random.default_rng(3)
+    G = rng.standard_normal((6, 6))
+    K = torch.tensor(G @ G.T / 6 + 0.5 * np.eye(6))
+    Y = torch.tensor(rng.standard_normal((6, 2)))
+    lam, path = 0.1, str(tmp_path / "A.npy")
+    h = _RichardsonHandle()
+    A1, pieces, ok = solve_resumable(h, K, Y, lam, path, piece_iters=5, max_pieces=2, tol=1e-10)
+    assert (pieces, ok) == (2, False) and not h.warm
+    saved = np.load(path)
+    assert np.array_equal(saved, A1.numpy())
+    # each piece starts from the previous one's iterate
+    assert torch.equal(h.starts[0], torch.zeros_like(Y)) and not torch.equal(h.starts[1], h.starts[0])
+    h2 = _RichardsonHandle()
+    A2, pieces2, ok2 = solve_resumable(h2, K, Y, lam, path, piece_iters=50, max_pieces=1000, tol=1e-10)
+    assert ok2 and not h2.warm
+    assert np.array_equal(h2.starts[0].numpy(), saved)  # a restart resumes from the saved iterate
+    want = torch.linalg.solve(K + lam * torch.eye(6, dtype=K.dtype), Y)
+    assert float((A2 - want).abs().max() / want.abs().max()) <= 1e-8
+    assert np.array_equal(np.load(path), A2.numpy())
+    with pytest.raises(ValueError):
+        solve_resumable(h2, K, Y, lam, path, maxit=10)
