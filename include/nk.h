@@ -43,7 +43,7 @@ typedef enum {
   NK_ERR_NOT_CONVERGED = 4, /* PCG hit maxit; A holds the best iterate */
   NK_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
   NK_ERR_NO_MEMORY = 6,
-  NK_ERR_UNSUPPORTED = 7    /* valid request that this build does not implement */
+  NK_ERR_UNSUPPORTED = 7    /* valid request that the library does not implement */
 } nk_status;
 
 /* Arithmetic of nk_block:

@@ -227,7 +227,7 @@ const char* nk_status_string(nk_status s) {
     case NK_ERR_NOT_CONVERGED: return "not converged";
     case NK_ERR_TIMEOUT: return "device wait timed out";
     case NK_ERR_NO_MEMORY: return "out of device memory";
-    case NK_ERR_UNSUPPORTED: return "unsupported by this build";
+    case NK_ERR_UNSUPPORTED: return "unsupported by the library";
   }
   return "unknown status";
 }
